@@ -1,0 +1,179 @@
+"""Seeded synthetic inputs for the oct-grid Poisson solve.
+
+This module holds no arithmetic of the method (no Morton keys, no hashing, no
+Poisson operator): it produces integer oct coordinates and densities in
+oct-major layout, which both the CUDA library and the CPU oracle consume.
+
+Stand-ins for the paper's Cosmo256/512/1024 MUSIC initial conditions (Sec. 7.1),
+which are not available: Gaussian random fields with P(k) ~ k^-2, lognormal
+densities, overdensity-flagged refinement (threshold 8 rho_bar, one-cell
+dilation) and mass-conserving child densities.
+
+Layout conventions (shared by both sides of every parity test):
+  * level l has 2^l cells and 2^(l-1) octs per axis (n_x = 1, box [0,1)^3);
+  * a dense cell array is indexed field[x, y, z];
+  * an oct-major array is [n_octs, 8] with child c = bx + 2 by + 4 bz;
+  * uniform levels list their octs in lexicographic order, x fastest.
+"""
+import numpy as np
+
+
+# ----------------------------------------------------------------- layouts
+
+def uniform_oct_coords(level):
+    """All oct coordinates of a full level, x fastest: uint32 [n^3, 3]."""
+    n = 1 << (level - 1)
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    return np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1).astype(np.uint32)
+
+
+def child_offsets():
+    """(bx, by, bz) of child c = bx + 2 by + 4 bz, as int [8, 3]."""
+    c = np.arange(8)
+    return np.stack([c & 1, (c >> 1) & 1, (c >> 2) & 1], axis=1)
+
+
+def dense_to_octs(field, coords):
+    """Gather a dense cell array field[x, y, z] into oct-major [n, 8]."""
+    off = child_offsets()
+    X = 2 * coords[:, None, :].astype(np.int64) + off[None, :, :]
+    return np.ascontiguousarray(field[X[..., 0], X[..., 1], X[..., 2]])
+
+
+def octs_to_dense(values, coords, n_cells):
+    """Scatter oct-major [n, 8] back into a dense array (unset cells = NaN)."""
+    out = np.full((n_cells,) * 3, np.nan, dtype=values.dtype)
+    off = child_offsets()
+    X = 2 * coords[:, None, :].astype(np.int64) + off[None, :, :]
+    out[X[..., 0], X[..., 1], X[..., 2]] = values
+    return out
+
+
+# --------------------------------------------------------------- densities
+
+def grf(n, rms, seed, slope=-2.0):
+    """Periodic Gaussian random field on n^3 cells, P(k) ~ |k|^slope for integer
+    0 < |k| <= n/2 (DC and modes beyond Nyquist zeroed), rescaled to rms."""
+    rng = np.random.default_rng(seed)
+    white = rng.standard_normal((n, n, n))
+    wk = np.fft.rfftn(white)
+    kx = np.fft.fftfreq(n) * n
+    kz = np.fft.rfftfreq(n) * n
+    k = np.sqrt(kx[:, None, None] ** 2 + kx[None, :, None] ** 2 + kz[None, None, :] ** 2)
+    amp = np.zeros_like(k)
+    sel = (k > 0) & (k <= n / 2)
+    amp[sel] = k[sel] ** (slope / 2.0)
+    g = np.fft.irfftn(wk * amp, s=(n, n, n), axes=(0, 1, 2))
+    g -= g.mean()
+    return g * (rms / np.sqrt(np.mean(g * g)))
+
+
+def lognormal(n, sigma, seed):
+    """rho = exp(sigma g) / mean(exp(sigma g)), g a unit-rms k^-2 GRF: mean 1,
+    sigma_ln(rho) = sigma exactly."""
+    g = grf(n, 1.0, seed)
+    e = np.exp(sigma * g)
+    return e / e.mean()
+
+
+# -------------------------------------------------------------- refinement
+
+def dilate_periodic(flags):
+    """One-cell dilation over the 6 face neighbours on a periodic dense grid.
+    (A 26-neighbour dilation of the k^-2 lognormal flags refines ~23 % of the
+    volume at sigma = 1.5; the face dilation gives ~9 %, inside the 5-10 %
+    band the two-level workload is specified with.)"""
+    out = flags.copy()
+    for axis in range(3):
+        for s in (-1, 1):
+            out |= np.roll(flags, s, axis=axis)
+    return out
+
+
+def refine_cells(level, coords, rho_octs, threshold):
+    """Cells of a level to refine: rho > threshold, dilated by one cell (face
+    neighbours) among existing cells, keeping only cells whose 26 neighbours
+    all exist (so that the new octs' coarse-fine ghost stencils exist).
+
+    coords: oct coords [n, 3] of the level, rho_octs [n, 8].  Returns the global
+    cell coordinates [m, 3] (uint32) in oct-major order of the level, i.e. the
+    oct coordinates of the new octs one level down."""
+    off = child_offsets()
+    cells = (2 * coords[:, None, :].astype(np.int64) + off[None, :, :]).reshape(-1, 3)
+    flag = (rho_octs.reshape(-1) > threshold)
+    size = 1 << level  # dense bookkeeping on the whole periodic level
+    exist = np.zeros((size,) * 3, dtype=bool)
+    exist[cells[:, 0], cells[:, 1], cells[:, 2]] = True
+    fl = np.zeros_like(exist)
+    fl[cells[flag, 0], cells[flag, 1], cells[flag, 2]] = True
+    fl = dilate_periodic(fl) & exist
+    # keep cells whose full 26-neighbourhood exists
+    ok = exist.copy()
+    for dx in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dz in (-1, 0, 1):
+                if dx or dy or dz:
+                    ok &= np.roll(exist, (-dx, -dy, -dz), axis=(0, 1, 2))
+    fl &= ok
+    keep = fl[cells[:, 0], cells[:, 1], cells[:, 2]]
+    return cells[keep].astype(np.uint32)
+
+
+def child_density(rho_parent_cells, seed, level, sigma_inc=0.5):
+    """Mass-conserving child densities: rho_child = rho_parent * e^{s xi} /
+    mean_8(e^{s xi}), xi ~ N(0, 1) drawn per child.  Returns [m, 8]."""
+    rng = np.random.default_rng([seed, level])
+    xi = rng.standard_normal((len(rho_parent_cells), 8))
+    e = np.exp(sigma_inc * xi)
+    return rho_parent_cells[:, None] * e / e.mean(axis=1, keepdims=True)
+
+
+# ------------------------------------------------------------------ configs
+
+def periodic_grf_level(level, rms=0.5, seed=1):
+    """Uniform periodic level with rho = 1 + delta, delta a k^-2 GRF of the
+    given rms (the 32^3 plain-FP64 workload at level 5)."""
+    n = 1 << level
+    rho = 1.0 + grf(n, rms, seed)
+    coords = uniform_oct_coords(level)
+    return {"levels": [level], "coords": [coords], "rho": [dense_to_octs(rho, coords)], "rho_bar": 1.0}
+
+
+def amr_lognormal(base_level, n_refine, sigma, seed, threshold=8.0, sigma_inc=0.5):
+    """Periodic lognormal base level plus n_refine refined levels, each refining
+    the cells above threshold * rho_bar (dilated, properly nested)."""
+    n = 1 << base_level
+    rho = lognormal(n, sigma, seed)
+    coords = uniform_oct_coords(base_level)
+    levels = [base_level]
+    all_coords = [coords]
+    all_rho = [dense_to_octs(rho, coords)]
+    rho_bar = 1.0
+    for r in range(n_refine):
+        lev = base_level + r
+        cells = refine_cells(lev, all_coords[-1], all_rho[-1], threshold * rho_bar)
+        if len(cells) == 0:
+            break
+        # density of each refined (parent) cell, in the order of `cells`
+        off = child_offsets()
+        pc = all_coords[-1]
+        X = (2 * pc[:, None, :].astype(np.int64) + off[None, :, :]).reshape(-1, 3)
+        dense = np.zeros((1 << lev,) * 3)
+        dense[X[:, 0], X[:, 1], X[:, 2]] = all_rho[-1].reshape(-1)
+        parent_rho = dense[cells[:, 0], cells[:, 1], cells[:, 2]]
+        levels.append(lev + 1)
+        all_coords.append(cells)
+        all_rho.append(child_density(parent_rho, seed, lev + 1, sigma_inc))
+    return {"levels": levels, "coords": all_coords, "rho": all_rho, "rho_bar": rho_bar}
+
+
+def two_level_amr(base_level=7, sigma=1.5, seed=2):
+    """Periodic lognormal base (sigma_ln rho = 1.5, k^-2) plus one level refined
+    where rho > 8 rho_bar (the 128^3 two-level AMR workload at base level 7)."""
+    return amr_lognormal(base_level, 1, sigma, seed)
+
+
+def mixed_amr(base_level=8, n_refine=3, sigma=2.0, seed=3):
+    """Periodic lognormal base (sigma_ln rho = 2) plus three refined levels at
+    threshold 8 rho_bar each (the 256^3 mixed-precision workload)."""
+    return amr_lognormal(base_level, n_refine, sigma, seed)
