@@ -1,0 +1,167 @@
+/*
+ * cmg.h -- C ABI of libcmg.so: a GB300 (sm_103a) level-by-level multigrid
+ * Poisson solver on RAMSES oct grids, after cuRAMSES (arXiv 2604.06035).
+ *
+ * Problem (Sec. 5, Sec. 5.1.1): on one AMR level l, solve the 7-point
+ * cell-centred discretisation of  lap(phi) = f,  f = 4 pi G (rho - rho_bar),
+ * with cell size h = 2^-l / n_x in a unit box.  A level without a parent must
+ * be complete and periodic (the base level); a level with a parent takes
+ * Dirichlet values at its coarse-fine faces, interpolated from the parent's phi.
+ *
+ * Conventions shared by every call:
+ *  - Return value: CMG_OK (0) or a negative cmg_status.  cmg_last_error()
+ *    gives a message for the calling thread.  No C++ exception crosses the ABI.
+ *  - Octs are numbered by their position in the key array given to
+ *    cmg_level_build.  Oct-major arrays are [n_octs][8] with child index
+ *    c = bx + 2 by + 4 bz (bit b of the cell offset inside its oct).
+ *  - A pointer argument is host or device memory as its cmg_mem tag says.  The
+ *    caller owns every buffer it passes; the library reads or writes it on the
+ *    context's stream and keeps no reference after the call returns.  Calls
+ *    that return data to host memory synchronise the stream first.
+ *  - All computation runs in the library's CUDA kernels on the context's GPU;
+ *    there is no CPU fallback.  A missing or failing GPU gives CMG_ERR_CUDA.
+ *  - Objects are not thread-safe; use one context per host thread.
+ */
+#ifndef CMG_H
+#define CMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CMG_OK = 0,
+  CMG_ERR_INVALID_ARG = -1,      /* bad pointer, size, level, parameter */
+  CMG_ERR_DUPLICATE_KEY = -2,    /* the same Morton key given twice */
+  CMG_ERR_KEY_OUT_OF_RANGE = -3, /* coordinate >= 2^(l-1) n_x or key >= 2^63 */
+  CMG_ERR_MISSING_PARENT = -4,   /* a coarse-fine ghost value has no parent cells */
+  CMG_ERR_OOM = -5,              /* device allocation failed */
+  CMG_ERR_CUDA = -6,             /* any other CUDA error */
+  CMG_ERR_NOT_CONVERGED = -7,    /* max_cycles reached above tol */
+  CMG_ERR_DIVERGED = -8,         /* residual NaN or grew 1000-fold */
+  CMG_ERR_TIMEOUT = -9           /* a bounded device-side wait gave up */
+} cmg_status;
+
+typedef enum { CMG_MEM_HOST = 0, CMG_MEM_DEVICE = 1 } cmg_mem;
+
+typedef enum {
+  CMG_PREC_FP64 = 0,  /* every step in FP64 */
+  CMG_PREC_MIXED = 1  /* FP32 V-cycle inside FP64 iterative refinement */
+} cmg_precision;
+
+typedef struct cmg_ctx cmg_ctx;
+typedef struct cmg_level cmg_level;
+
+typedef struct {
+  double tol;        /* stop when ||f - L phi|| <= tol ||f - L 0|| (2-norms) */
+  int max_cycles;    /* <= 256 */
+  int n_pre, n_post; /* red-black Gauss-Seidel sweeps before / after the coarse correction */
+  int coarse_sweeps; /* sweeps on a non-periodic coarsest level */
+  int fixed_cycles;  /* > 0: run exactly this many cycles and ignore tol */
+  int precision;     /* cmg_precision */
+  int inner_cycles;  /* MIXED: FP32 V-cycles per FP64 refinement step (>= 1) */
+} cmg_solve_params;
+
+typedef struct {
+  int cycles;            /* V-cycles (FP64) or refinement steps (MIXED) run */
+  int status;            /* same value as the call's return */
+  double rel_initial;    /* relative residual of the initial guess */
+  double rel_final;      /* relative residual at return */
+  double norm0;          /* ||f - L 0||_2 */
+  double ms;             /* device time of the call (CUDA events) */
+  int64_t cell_updates;  /* cells visited by full red-black sweeps, all MG levels */
+  double rel_history[256];
+} cmg_solve_stats;
+
+/* Library version string, e.g. "cmg 0.1.0 sm_103a". */
+const char *cmg_version(void);
+/* Message of the last failing call on this host thread ("" if none). */
+const char *cmg_last_error(void);
+
+/* Context: a device and a stream.  stream is a cudaStream_t (NULL = the
+ * legacy default stream); the caller keeps it alive while the context lives. */
+int cmg_ctx_create(int device, void *stream, cmg_ctx **out);
+int cmg_ctx_destroy(cmg_ctx *ctx);
+int cmg_ctx_synchronize(cmg_ctx *ctx);
+
+/* Morton keys (Sec. 4.2 Eq. (morton_encode), App. A Alg. 1; B = 21 bits per
+ * coordinate): ijk is [n][3] uint32 (i, j, k), keys is [n] uint64.  Both in
+ * the same memory space.  Coordinates >= 2^21 give CMG_ERR_KEY_OUT_OF_RANGE. */
+int cmg_morton_encode(cmg_ctx *ctx, const uint32_t *ijk, int64_t n, uint64_t *keys, cmg_mem mem);
+int cmg_morton_decode(cmg_ctx *ctx, const uint64_t *keys, int64_t n, uint32_t *ijk, cmg_mem mem);
+
+/* Build level `level` (>= 1) from n_octs Morton keys (Sec. 4.2; App. B):
+ * per-level open-addressing hash table (hash of App. B Eq. (hash_func),
+ * linear probing, power-of-two capacity with fill <= 0.7), the neighbour
+ * cache of App. D.1 Eq. (nbor_precompute) (directions -x,+x,-y,+y,-z,+z, with
+ * periodic wrap on the axes set in periodic_mask), the coarse-fine ghost
+ * stencils (morton_nbor_cell, App. B) and the multigrid hierarchy.
+ * parent: NULL for a base level (which must then hold all (2^(l-1) n_x)^3
+ * octs with periodic_mask = 7 to be solvable), else the level l-1 whose phi
+ * gives the Dirichlet values; it must outlive this level.
+ * Errors: DUPLICATE_KEY, KEY_OUT_OF_RANGE, MISSING_PARENT, INVALID_ARG, OOM. */
+int cmg_level_build(cmg_ctx *ctx, int level, int nx, int periodic_mask, const uint64_t *keys,
+                    int64_t n_octs, cmg_mem mem, cmg_level *parent, cmg_level **out);
+int cmg_level_destroy(cmg_level *lvl);
+int cmg_level_n_octs(const cmg_level *lvl, int64_t *n_octs);
+/* Hash capacity (power of two) of the level's table. */
+int cmg_level_hash_capacity(const cmg_level *lvl, int64_t *capacity);
+
+/* Hash lookup (App. B): idx[t] = oct index of key q[t], or -1. */
+int cmg_level_lookup(cmg_level *lvl, const uint64_t *q, int64_t n, int32_t *idx, cmg_mem mem);
+/* Neighbour cache, [n][7] int32: column 0 = the oct itself, 1..6 = the
+ * same-level neighbour in -x,+x,-y,+y,-z,+z or -1 (App. D.1). */
+int cmg_level_get_neighbors(cmg_level *lvl, int32_t *out, cmg_mem mem);
+/* morton_nbor_cell (App. B): for each missing neighbour, the father cell in
+ * the parent level as (parent oct, octant); (-1,-1) elsewhere.  [n][6][2]. */
+int cmg_level_get_father_cells(cmg_level *lvl, int32_t *out, cmg_mem mem);
+
+/* f = four_pi_g * (rho - rho_bar) (Sec. 5.1.1 item (iii)); rho [n][8] FP64. */
+int cmg_level_set_density(cmg_level *lvl, const double *rho, cmg_mem mem, double rho_bar, double four_pi_g);
+/* phi [n][8] FP64: the initial guess (warm start) of the next solve. */
+int cmg_level_set_phi(cmg_level *lvl, const double *phi, cmg_mem mem);
+int cmg_level_get_phi(cmg_level *lvl, double *out, cmg_mem mem);
+/* r = f - lap_h(phi) of the current phi, [n][8] FP64. */
+int cmg_level_get_residual(cmg_level *lvl, double *out, cmg_mem mem);
+/* Dirichlet ghost values last interpolated from the parent (by a solve or by
+ * CMG_OP_GHOSTS): [n][6][4], face cells of direction d in increasing child
+ * index; NaN where the neighbour oct exists. */
+int cmg_level_get_ghosts(cmg_level *lvl, double *out, cmg_mem mem);
+
+/* Solve the level (App. G Alg. (vcycle) run as a stationary iteration, red
+ * black Gauss-Seidel smoothing of App. D.2 Eq. (gs_update)).  Periodic base
+ * levels return zero-mean phi.  stats may be NULL. */
+int cmg_level_solve(cmg_level *lvl, const cmg_solve_params *params, cmg_solve_stats *stats);
+
+/* ---- multigrid hierarchy introspection and single steps (for tests) ----
+ * m = 0 is the level itself; m + 1 is the coarsening of m (octs = the parents
+ * of m's fully active octs, in order of first appearance; a cell is active iff
+ * a fully active oct of m refines it). */
+int cmg_level_mg_depth(const cmg_level *lvl, int *depth);
+int cmg_level_mg_info(const cmg_level *lvl, int m, int64_t *n_octs, int *amr_level);
+int cmg_level_mg_keys(cmg_level *lvl, int m, uint64_t *out, cmg_mem mem);
+int cmg_level_mg_active(cmg_level *lvl, int m, uint8_t *out /* [n][8] 0/1 */, cmg_mem mem);
+
+typedef enum { CMG_FIELD_PHI = 0, CMG_FIELD_F = 1 } cmg_field;
+/* Read / write a field of MG level m as [n][8] FP64 (precision FP64) or FP32
+ * (precision MIXED selects the FP32 copy). */
+int cmg_level_mg_get(cmg_level *lvl, int m, int field, int precision, void *out, cmg_mem mem);
+int cmg_level_mg_set(cmg_level *lvl, int m, int field, int precision, const void *in, cmg_mem mem);
+
+typedef enum {
+  CMG_OP_SWEEP = 0,    /* n red-black sweeps on MG level m (ghosts at m = 0) */
+  CMG_OP_RESIDUAL = 1, /* *norm2 = sum of r^2 on MG level m */
+  CMG_OP_RESTRICT = 2, /* f[m+1] = mean of the children's residual; phi[m+1] = 0 */
+  CMG_OP_PROLONG = 3,  /* phi[m] += trilinear interpolation of phi[m+1] */
+  CMG_OP_COARSE = 4,   /* the coarsest-level solve (m must be depth - 1) */
+  CMG_OP_GHOSTS = 5    /* interpolate the Dirichlet ghosts from the parent's phi */
+} cmg_op;
+int cmg_level_mg_step(cmg_level *lvl, int m, int op, int precision, int n, double *norm2);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CMG_H */

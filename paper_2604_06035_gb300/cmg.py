@@ -1,0 +1,367 @@
+"""Thin ctypes binding of libcmg.so (include/cmg.h): the same function names,
+argument marshalling only.  Every computation runs in the library's CUDA
+kernels; if the library or a GPU is missing the calls raise, there is no CPU
+path.
+
+Array arguments may be NumPy arrays (passed as CMG_MEM_HOST) or CUDA torch
+tensors (passed as CMG_MEM_DEVICE, read/written on the context's stream).
+Outputs are NumPy arrays unless ``device=True`` (CUDA torch tensors) or an
+``out`` array is given.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcmg.so")
+
+CMG_OK = 0
+CMG_ERR_INVALID_ARG = -1
+CMG_ERR_DUPLICATE_KEY = -2
+CMG_ERR_KEY_OUT_OF_RANGE = -3
+CMG_ERR_MISSING_PARENT = -4
+CMG_ERR_OOM = -5
+CMG_ERR_CUDA = -6
+CMG_ERR_NOT_CONVERGED = -7
+CMG_ERR_DIVERGED = -8
+CMG_ERR_TIMEOUT = -9
+
+CMG_MEM_HOST = 0
+CMG_MEM_DEVICE = 1
+CMG_PREC_FP64 = 0
+CMG_PREC_MIXED = 1
+CMG_FIELD_PHI = 0
+CMG_FIELD_F = 1
+CMG_OP_SWEEP, CMG_OP_RESIDUAL, CMG_OP_RESTRICT, CMG_OP_PROLONG, CMG_OP_COARSE, CMG_OP_GHOSTS = range(6)
+
+
+class cmg_solve_params(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_cycles", C.c_int), ("n_pre", C.c_int), ("n_post", C.c_int),
+                ("coarse_sweeps", C.c_int), ("fixed_cycles", C.c_int), ("precision", C.c_int),
+                ("inner_cycles", C.c_int)]
+
+
+class cmg_solve_stats(C.Structure):
+    _fields_ = [("cycles", C.c_int), ("status", C.c_int), ("rel_initial", C.c_double), ("rel_final", C.c_double),
+                ("norm0", C.c_double), ("ms", C.c_double), ("cell_updates", C.c_int64),
+                ("rel_history", C.c_double * 256)]
+
+
+class CmgError(RuntimeError):
+    def __init__(self, code, fn, msg):
+        super().__init__("%s failed (status %d): %s" % (fn, code, msg))
+        self.code = code
+
+
+_P = C.c_void_p
+_I64 = C.c_int64
+_I = C.c_int
+_SIGS = {
+    "cmg_version": (C.c_char_p, []),
+    "cmg_last_error": (C.c_char_p, []),
+    "cmg_ctx_create": (_I, [_I, _P, C.POINTER(_P)]),
+    "cmg_ctx_destroy": (_I, [_P]),
+    "cmg_ctx_synchronize": (_I, [_P]),
+    "cmg_morton_encode": (_I, [_P, _P, _I64, _P, _I]),
+    "cmg_morton_decode": (_I, [_P, _P, _I64, _P, _I]),
+    "cmg_level_build": (_I, [_P, _I, _I, _I, _P, _I64, _I, _P, C.POINTER(_P)]),
+    "cmg_level_destroy": (_I, [_P]),
+    "cmg_level_n_octs": (_I, [_P, C.POINTER(_I64)]),
+    "cmg_level_hash_capacity": (_I, [_P, C.POINTER(_I64)]),
+    "cmg_level_lookup": (_I, [_P, _P, _I64, _P, _I]),
+    "cmg_level_get_neighbors": (_I, [_P, _P, _I]),
+    "cmg_level_get_father_cells": (_I, [_P, _P, _I]),
+    "cmg_level_set_density": (_I, [_P, _P, _I, C.c_double, C.c_double]),
+    "cmg_level_set_phi": (_I, [_P, _P, _I]),
+    "cmg_level_get_phi": (_I, [_P, _P, _I]),
+    "cmg_level_get_residual": (_I, [_P, _P, _I]),
+    "cmg_level_get_ghosts": (_I, [_P, _P, _I]),
+    "cmg_level_solve": (_I, [_P, C.POINTER(cmg_solve_params), C.POINTER(cmg_solve_stats)]),
+    "cmg_level_mg_depth": (_I, [_P, C.POINTER(_I)]),
+    "cmg_level_mg_info": (_I, [_P, _I, C.POINTER(_I64), C.POINTER(_I)]),
+    "cmg_level_mg_keys": (_I, [_P, _I, _P, _I]),
+    "cmg_level_mg_active": (_I, [_P, _I, _P, _I]),
+    "cmg_level_mg_get": (_I, [_P, _I, _I, _I, _P, _I]),
+    "cmg_level_mg_set": (_I, [_P, _I, _I, _I, _P, _I]),
+    "cmg_level_mg_step": (_I, [_P, _I, _I, _I, _I, C.POINTER(C.c_double)]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libcmg.so (built by build.py / __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libcmg.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def _check(rc, fn):
+    if rc != CMG_OK:
+        raise CmgError(rc, fn, lib().cmg_last_error().decode())
+    return rc
+
+
+# ------------------------------------------------------------ marshalling
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _in(x, dtype):
+    """(pointer, mem, keepalive) for an input array."""
+    if _is_torch(x):
+        import torch
+        if x.is_cuda:
+            want = {np.float64: torch.float64, np.float32: torch.float32, np.uint64: torch.uint64,
+                    np.uint32: torch.uint32, np.int32: torch.int32, np.uint8: torch.uint8}[dtype]
+            if x.dtype != want or not x.is_contiguous():
+                raise TypeError("device tensor must be contiguous %s" % want)
+            return C.c_void_p(x.data_ptr()), CMG_MEM_DEVICE, x
+        x = x.numpy()
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data_as(C.c_void_p), CMG_MEM_HOST, a
+
+
+def _out(shape, dtype, device=False, out=None):
+    if out is not None:
+        p, mem, keep = _in(out, dtype)
+        if mem == CMG_MEM_HOST and keep is not out:
+            raise TypeError("out must be a contiguous array of dtype %s" % np.dtype(dtype))
+        return p, mem, out
+    if device:
+        import torch
+        want = {np.float64: torch.float64, np.float32: torch.float32, np.uint64: torch.uint64,
+                np.uint32: torch.uint32, np.int32: torch.int32, np.uint8: torch.uint8}[dtype]
+        t = torch.empty(shape, dtype=want, device="cuda")
+        return C.c_void_p(t.data_ptr()), CMG_MEM_DEVICE, t
+    a = np.empty(shape, dtype=dtype)
+    return a.ctypes.data_as(C.c_void_p), CMG_MEM_HOST, a
+
+
+def _same_mem(m1, m2, fn):
+    if m1 != m2:
+        raise TypeError("%s: input and output must both be host or both be device arrays" % fn)
+
+
+# ------------------------------------------------------------------ calls
+
+def cmg_version():
+    return lib().cmg_version().decode()
+
+
+def cmg_last_error():
+    return lib().cmg_last_error().decode()
+
+
+def cmg_ctx_create(device=0, stream=None):
+    """stream: a raw cudaStream_t (int), a torch.cuda.Stream, or None for the
+    current torch stream (if torch is importable) else the legacy default."""
+    if stream is None:
+        try:
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream if torch.cuda.is_available() else 0
+        except ImportError:
+            stream = 0
+    elif not isinstance(stream, int):
+        stream = stream.cuda_stream
+    h = C.c_void_p()
+    _check(lib().cmg_ctx_create(device, C.c_void_p(stream), C.byref(h)), "cmg_ctx_create")
+    return h
+
+
+def cmg_ctx_destroy(ctx):
+    _check(lib().cmg_ctx_destroy(ctx), "cmg_ctx_destroy")
+
+
+def cmg_ctx_synchronize(ctx):
+    _check(lib().cmg_ctx_synchronize(ctx), "cmg_ctx_synchronize")
+
+
+def cmg_morton_encode(ctx, ijk, out=None):
+    p, mem, keep = _in(ijk, np.uint32)
+    n = keep.numel() // 3 if _is_torch(keep) else keep.size // 3
+    q, mem2, res = _out((n,), np.uint64, device=(mem == CMG_MEM_DEVICE), out=out)
+    _same_mem(mem, mem2, "cmg_morton_encode")
+    _check(lib().cmg_morton_encode(ctx, p, n, q, mem), "cmg_morton_encode")
+    return res
+
+
+def cmg_morton_decode(ctx, keys, out=None):
+    p, mem, keep = _in(keys, np.uint64)
+    n = keep.numel() if _is_torch(keep) else keep.size
+    q, mem2, res = _out((n, 3), np.uint32, device=(mem == CMG_MEM_DEVICE), out=out)
+    _same_mem(mem, mem2, "cmg_morton_decode")
+    _check(lib().cmg_morton_decode(ctx, p, n, q, mem), "cmg_morton_decode")
+    return res
+
+
+class LevelHandle:
+    """Owns a cmg_level* (destroyed with the object) and keeps its parent alive."""
+
+    def __init__(self, h, parent, ctx):
+        self.h = h
+        self.parent = parent
+        self.ctx = ctx
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.cmg_level_destroy(self.h)
+            self.h = None
+
+    @property
+    def _as_parameter_(self):
+        return self.h
+
+
+def cmg_level_build(ctx, level, keys, parent=None, nx=1, periodic_mask=7):
+    p, mem, keep = _in(keys, np.uint64)
+    n = keep.numel() if _is_torch(keep) else keep.size
+    h = C.c_void_p()
+    _check(lib().cmg_level_build(ctx, level, nx, periodic_mask, p, n, mem,
+                                 parent.h if parent is not None else None, C.byref(h)), "cmg_level_build")
+    return LevelHandle(h, parent, ctx)
+
+
+def cmg_level_destroy(lvl):
+    if lvl.h:
+        _check(lib().cmg_level_destroy(lvl.h), "cmg_level_destroy")
+        lvl.h = None
+
+
+def cmg_level_n_octs(lvl):
+    v = C.c_int64()
+    _check(lib().cmg_level_n_octs(lvl.h, C.byref(v)), "cmg_level_n_octs")
+    return v.value
+
+
+def cmg_level_hash_capacity(lvl):
+    v = C.c_int64()
+    _check(lib().cmg_level_hash_capacity(lvl.h, C.byref(v)), "cmg_level_hash_capacity")
+    return v.value
+
+
+def cmg_level_lookup(lvl, q, out=None):
+    p, mem, keep = _in(q, np.uint64)
+    n = keep.numel() if _is_torch(keep) else keep.size
+    o, mem2, res = _out((n,), np.int32, device=(mem == CMG_MEM_DEVICE), out=out)
+    _same_mem(mem, mem2, "cmg_level_lookup")
+    _check(lib().cmg_level_lookup(lvl.h, p, n, o, mem), "cmg_level_lookup")
+    return res
+
+
+def _get(fn, lvl, shape, dtype, device, out):
+    o, mem, res = _out(shape, dtype, device=device, out=out)
+    _check(getattr(lib(), fn)(lvl.h, o, mem), fn)
+    return res
+
+
+def cmg_level_get_neighbors(lvl, device=False, out=None):
+    return _get("cmg_level_get_neighbors", lvl, (cmg_level_n_octs(lvl), 7), np.int32, device, out)
+
+
+def cmg_level_get_father_cells(lvl, device=False, out=None):
+    return _get("cmg_level_get_father_cells", lvl, (cmg_level_n_octs(lvl), 6, 2), np.int32, device, out)
+
+
+def cmg_level_get_phi(lvl, device=False, out=None):
+    return _get("cmg_level_get_phi", lvl, (cmg_level_n_octs(lvl), 8), np.float64, device, out)
+
+
+def cmg_level_get_residual(lvl, device=False, out=None):
+    return _get("cmg_level_get_residual", lvl, (cmg_level_n_octs(lvl), 8), np.float64, device, out)
+
+
+def cmg_level_get_ghosts(lvl, device=False, out=None):
+    return _get("cmg_level_get_ghosts", lvl, (cmg_level_n_octs(lvl), 6, 4), np.float64, device, out)
+
+
+def cmg_level_set_density(lvl, rho, rho_bar, four_pi_g=1.0):
+    p, mem, keep = _in(rho, np.float64)
+    _check(lib().cmg_level_set_density(lvl.h, p, mem, float(rho_bar), float(four_pi_g)), "cmg_level_set_density")
+
+
+def cmg_level_set_phi(lvl, phi):
+    p, mem, keep = _in(phi, np.float64)
+    _check(lib().cmg_level_set_phi(lvl.h, p, mem), "cmg_level_set_phi")
+
+
+def solve_params(tol=1e-10, max_cycles=100, n_pre=2, n_post=2, coarse_sweeps=32, fixed_cycles=0,
+                 precision=CMG_PREC_FP64, inner_cycles=1):
+    return cmg_solve_params(tol, max_cycles, n_pre, n_post, coarse_sweeps, fixed_cycles, precision, inner_cycles)
+
+
+def _stats(st):
+    return {"cycles": st.cycles, "status": st.status, "rel_initial": st.rel_initial, "rel_final": st.rel_final,
+            "norm0": st.norm0, "ms": st.ms, "cell_updates": st.cell_updates,
+            "rel_history": list(st.rel_history[:st.cycles])}
+
+
+def cmg_level_solve(lvl, params=None, raise_on_error=True, **kw):
+    """Returns (status, stats dict)."""
+    prm = params if params is not None else solve_params(**kw)
+    st = cmg_solve_stats()
+    rc = lib().cmg_level_solve(lvl.h, C.byref(prm), C.byref(st))
+    if raise_on_error:
+        _check(rc, "cmg_level_solve")
+    return rc, _stats(st)
+
+
+def cmg_level_mg_depth(lvl):
+    v = C.c_int()
+    _check(lib().cmg_level_mg_depth(lvl.h, C.byref(v)), "cmg_level_mg_depth")
+    return v.value
+
+
+def cmg_level_mg_info(lvl, m):
+    n = C.c_int64()
+    lev = C.c_int()
+    _check(lib().cmg_level_mg_info(lvl.h, m, C.byref(n), C.byref(lev)), "cmg_level_mg_info")
+    return n.value, lev.value
+
+
+def cmg_level_mg_keys(lvl, m, device=False):
+    n, _ = cmg_level_mg_info(lvl, m)
+    o, mem, res = _out((n,), np.uint64, device=device)
+    _check(lib().cmg_level_mg_keys(lvl.h, m, o, mem), "cmg_level_mg_keys")
+    return res
+
+
+def cmg_level_mg_active(lvl, m, device=False):
+    n, _ = cmg_level_mg_info(lvl, m)
+    o, mem, res = _out((n, 8), np.uint8, device=device)
+    _check(lib().cmg_level_mg_active(lvl.h, m, o, mem), "cmg_level_mg_active")
+    return res
+
+
+def cmg_level_mg_get(lvl, m, field, precision=CMG_PREC_FP64, device=False):
+    n, _ = cmg_level_mg_info(lvl, m)
+    dt = np.float64 if precision == CMG_PREC_FP64 else np.float32
+    o, mem, res = _out((n, 8), dt, device=device)
+    _check(lib().cmg_level_mg_get(lvl.h, m, field, precision, o, mem), "cmg_level_mg_get")
+    return res
+
+
+def cmg_level_mg_set(lvl, m, field, arr, precision=CMG_PREC_FP64):
+    dt = np.float64 if precision == CMG_PREC_FP64 else np.float32
+    p, mem, keep = _in(arr, dt)
+    _check(lib().cmg_level_mg_set(lvl.h, m, field, precision, p, mem), "cmg_level_mg_set")
+
+
+def cmg_level_mg_step(lvl, m, op, precision=CMG_PREC_FP64, n=1):
+    v = C.c_double(0.0)
+    _check(lib().cmg_level_mg_step(lvl.h, m, op, precision, n, C.byref(v)), "cmg_level_mg_step")
+    return v.value

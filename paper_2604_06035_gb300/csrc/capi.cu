@@ -1,0 +1,492 @@
+// capi.cu -- the extern "C" boundary of libcmg.so (declared in include/cmg.h).
+// Every entry point converts C++ exceptions into a status code and a
+// thread-local message; nothing here computes on the host.
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "cmg_internal.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg) {
+  g_last_error = msg;
+  return code;
+}
+
+template <class F>
+int guard(F &&f) {
+  try {
+    g_last_error.clear();
+    return f();
+  } catch (const cmg::Error &e) {
+    return fail(e.code, e.what());
+  } catch (const std::bad_alloc &) {
+    return fail(CMG_ERR_OOM, "host allocation failed");
+  } catch (const std::exception &e) {
+    return fail(CMG_ERR_CUDA, e.what());
+  } catch (...) {
+    return fail(CMG_ERR_CUDA, "unknown error");
+  }
+}
+
+struct DeviceScope {
+  int prev = -1;
+  explicit DeviceScope(int d) {
+    cudaGetDevice(&prev);
+    CMG_CUDA(cudaSetDevice(d));
+  }
+  ~DeviceScope() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// Temporary device buffer for host-memory arguments (freed on scope exit).
+struct Temp {
+  void *p = nullptr;
+  explicit Temp(size_t bytes) {
+    if (bytes == 0) bytes = 1;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      throw cmg::Error(CMG_ERR_OOM, "temporary device buffer");
+    }
+  }
+  ~Temp() {
+    if (p) cudaFree(p);
+  }
+  template <class T>
+  T *as() {
+    return static_cast<T *>(p);
+  }
+};
+
+void check_mem(int mem) {
+  if (mem != CMG_MEM_HOST && mem != CMG_MEM_DEVICE) throw cmg::Error(CMG_ERR_INVALID_ARG, "bad cmg_mem tag");
+}
+
+void need(bool ok, const char *what) {
+  if (!ok) throw cmg::Error(CMG_ERR_INVALID_ARG, what);
+}
+
+// Run `produce(device_out)` and deliver `bytes` to `out` in memory space mem.
+template <class F>
+void deliver(cmg_ctx *ctx, void *out, size_t bytes, int mem, F &&produce) {
+  if (mem == CMG_MEM_DEVICE) {
+    produce(out);
+    CMG_CUDA(cudaGetLastError());
+    return;
+  }
+  Temp t(bytes);
+  produce(t.p);
+  if (bytes) CMG_CUDA(cudaMemcpyAsync(out, t.p, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  CMG_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+
+// Make `in` device-resident for the duration of `use(device_in)`.
+template <class F>
+void accept(cmg_ctx *ctx, const void *in, size_t bytes, int mem, F &&use) {
+  if (mem == CMG_MEM_DEVICE) {
+    use(in);
+    return;
+  }
+  Temp t(bytes);
+  if (bytes) CMG_CUDA(cudaMemcpyAsync(t.p, in, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  use(static_cast<const void *>(t.p));
+  CMG_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cmg_version(void) { return "cmg 0.1.0 sm_103a"; }
+
+const char *cmg_last_error(void) { return g_last_error.c_str(); }
+
+int cmg_ctx_create(int device, void *stream, cmg_ctx **out) {
+  return guard([&] {
+    need(out != nullptr, "out is NULL");
+    *out = nullptr;
+    int count = 0;
+    CMG_CUDA(cudaGetDeviceCount(&count));
+    need(device >= 0 && device < count, "no such CUDA device");
+    DeviceScope ds(device);
+    cmg_ctx *c = new cmg_ctx();
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(stream);
+    try {
+      CMG_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
+      CMG_CUDA(cudaMalloc(&c->d_err, 64));
+      CMG_CUDA(cudaMemsetAsync(c->d_err, 0, 64, c->stream));
+      CMG_CUDA(cudaMallocHost(&c->h_pinned, 64));
+      CMG_CUDA(cudaMallocHost(&c->h_dpinned, 64));
+      CMG_CUDA(cudaEventCreate(&c->ev0));
+      CMG_CUDA(cudaEventCreate(&c->ev1));
+      CMG_CUDA(cudaStreamSynchronize(c->stream));
+    } catch (...) {
+      cmg_ctx_destroy(c);
+      throw;
+    }
+    *out = c;
+    return CMG_OK;
+  });
+}
+
+int cmg_ctx_destroy(cmg_ctx *ctx) {
+  if (!ctx) return CMG_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(ctx->device);
+  if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
+  if (ctx->d_err) cudaFree(ctx->d_err);
+  if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  if (ctx->h_dpinned) cudaFreeHost(ctx->h_dpinned);
+  if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+  if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  delete ctx;
+  if (prev >= 0) cudaSetDevice(prev);
+  return CMG_OK;
+}
+
+int cmg_ctx_synchronize(cmg_ctx *ctx) {
+  return guard([&] {
+    need(ctx != nullptr, "ctx is NULL");
+    DeviceScope ds(ctx->device);
+    CMG_CUDA(cudaStreamSynchronize(ctx->stream));
+    return CMG_OK;
+  });
+}
+
+int cmg_morton_encode(cmg_ctx *ctx, const uint32_t *ijk, int64_t n, uint64_t *keys, cmg_mem mem) {
+  return guard([&] {
+    need(ctx && n >= 0 && (n == 0 || (ijk && keys)), "bad arguments");
+    check_mem(mem);
+    DeviceScope ds(ctx->device);
+    CMG_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    accept(ctx, ijk, sizeof(uint32_t) * 3 * n, mem, [&](const void *din) {
+      deliver(ctx, keys, sizeof(uint64_t) * n, mem, [&](void *dout) {
+        cmg::encode_keys(static_cast<const uint32_t *>(din), n, static_cast<uint64_t *>(dout), ctx->d_err,
+                         ctx->stream);
+      });
+    });
+    CMG_CUDA(cudaMemcpyAsync(ctx->h_pinned, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CMG_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (ctx->h_pinned[0]) {
+      CMG_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+      throw cmg::Error(ctx->h_pinned[0], "coordinate outside [0, 2^21)");
+    }
+    return CMG_OK;
+  });
+}
+
+int cmg_morton_decode(cmg_ctx *ctx, const uint64_t *keys, int64_t n, uint32_t *ijk, cmg_mem mem) {
+  return guard([&] {
+    need(ctx && n >= 0 && (n == 0 || (ijk && keys)), "bad arguments");
+    check_mem(mem);
+    DeviceScope ds(ctx->device);
+    accept(ctx, keys, sizeof(uint64_t) * n, mem, [&](const void *din) {
+      deliver(ctx, ijk, sizeof(uint32_t) * 3 * n, mem, [&](void *dout) {
+        cmg::decode_keys(static_cast<const uint64_t *>(din), n, static_cast<uint32_t *>(dout), ctx->stream);
+      });
+    });
+    return CMG_OK;
+  });
+}
+
+int cmg_level_build(cmg_ctx *ctx, int level, int nx, int periodic_mask, const uint64_t *keys, int64_t n_octs,
+                    cmg_mem mem, cmg_level *parent, cmg_level **out) {
+  return guard([&] {
+    need(out != nullptr, "out is NULL");
+    *out = nullptr;
+    need(ctx != nullptr, "ctx is NULL");
+    need(level >= 1 && level <= 22 && nx >= 1, "level must be in [1, 22] and nx >= 1");
+    need(((uint64_t)nx << (level - 1)) <= (1ull << cmg::kMortonBits), "2^(level-1) nx exceeds 2^21");
+    need(periodic_mask >= 0 && periodic_mask <= 7, "periodic_mask must be in [0, 7]");
+    need(n_octs >= 0 && n_octs < (1ll << 31) - 1 && (n_octs == 0 || keys), "bad keys / n_octs");
+    check_mem(mem);
+    if (parent)
+      need(parent->ctx == ctx && parent->lev == level - 1 && parent->nx == nx && parent->pmask == periodic_mask,
+           "parent must be level-1 of the same context, nx and periodic_mask");
+    DeviceScope ds(ctx->device);
+    cmg_level *L = new cmg_level();
+    L->ctx = ctx;
+    L->lev = level;
+    L->nx = nx;
+    L->pmask = periodic_mask;
+    L->n = n_octs;
+    L->parent = parent;
+    const uint64_t npd = (uint64_t)nx << (level - 1);
+    L->periodic_full = parent == nullptr && periodic_mask == 7 && (uint64_t)n_octs == npd * npd * npd;
+    try {
+      cmg::build_level(L, keys, mem);
+      L->partials = L->mem.alloc<double>(cmg::blocks_for(n_octs > 0 ? n_octs : 1));
+      L->scal = L->mem.alloc<double>(16, true, ctx->stream);
+      CMG_CUDA(cudaStreamSynchronize(ctx->stream));
+    } catch (...) {
+      cudaStreamSynchronize(ctx->stream);
+      L->mem.release();
+      delete L;
+      throw;
+    }
+    *out = L;
+    return CMG_OK;
+  });
+}
+
+int cmg_level_destroy(cmg_level *lvl) {
+  if (!lvl) return CMG_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(lvl->ctx->device);
+  cudaStreamSynchronize(lvl->ctx->stream);
+  lvl->mem.release();
+  delete lvl;
+  if (prev >= 0) cudaSetDevice(prev);
+  return CMG_OK;
+}
+
+int cmg_level_n_octs(const cmg_level *lvl, int64_t *n) {
+  return guard([&] {
+    need(lvl && n, "NULL argument");
+    *n = lvl->n;
+    return CMG_OK;
+  });
+}
+
+int cmg_level_hash_capacity(const cmg_level *lvl, int64_t *cap) {
+  return guard([&] {
+    need(lvl && cap, "NULL argument");
+    *cap = lvl->mg[0].cap;
+    return CMG_OK;
+  });
+}
+
+int cmg_level_lookup(cmg_level *lvl, const uint64_t *q, int64_t n, int32_t *idx, cmg_mem mem) {
+  return guard([&] {
+    need(lvl && n >= 0 && (n == 0 || (q && idx)), "bad arguments");
+    check_mem(mem);
+    cmg_ctx *ctx = lvl->ctx;
+    DeviceScope ds(ctx->device);
+    accept(ctx, q, sizeof(uint64_t) * n, mem, [&](const void *din) {
+      deliver(ctx, idx, sizeof(int32_t) * n, mem, [&](void *dout) {
+        cmg::hash_lookup(lvl->mg[0], static_cast<const uint64_t *>(din), n, static_cast<int32_t *>(dout),
+                         ctx->stream);
+      });
+    });
+    return CMG_OK;
+  });
+}
+
+int cmg_level_get_neighbors(cmg_level *lvl, int32_t *out, cmg_mem mem) {
+  return guard([&] {
+    need(lvl && (lvl->n == 0 || out), "bad arguments");
+    check_mem(mem);
+    DeviceScope ds(lvl->ctx->device);
+    deliver(lvl->ctx, out, sizeof(int32_t) * 7 * lvl->n, mem,
+            [&](void *d) { cmg::ext_neighbors(lvl, static_cast<int32_t *>(d), lvl->ctx->stream); });
+    return CMG_OK;
+  });
+}
+
+int cmg_level_get_father_cells(cmg_level *lvl, int32_t *out, cmg_mem mem) {
+  return guard([&] {
+    need(lvl && (lvl->n == 0 || out), "bad arguments");
+    check_mem(mem);
+    DeviceScope ds(lvl->ctx->device);
+    deliver(lvl->ctx, out, sizeof(int32_t) * 12 * lvl->n, mem,
+            [&](void *d) { cmg::father_cells(lvl, static_cast<int32_t *>(d), lvl->ctx->stream); });
+    return CMG_OK;
+  });
+}
+
+int cmg_level_set_density(cmg_level *lvl, const double *rho, cmg_mem mem, double rho_bar, double four_pi_g) {
+  return guard([&] {
+    need(lvl && (lvl->n == 0 || rho), "bad arguments");
+    check_mem(mem);
+    DeviceScope ds(lvl->ctx->device);
+    accept(lvl->ctx, rho, sizeof(double) * 8 * lvl->n, mem,
+           [&](const void *d) { cmg::set_density(lvl, static_cast<const double *>(d), rho_bar, four_pi_g); });
+    return CMG_OK;
+  });
+}
+
+int cmg_level_set_phi(cmg_level *lvl, const double *phi, cmg_mem mem) {
+  return guard([&] {
+    need(lvl && (lvl->n == 0 || phi), "bad arguments");
+    check_mem(mem);
+    DeviceScope ds(lvl->ctx->device);
+    accept(lvl->ctx, phi, sizeof(double) * 8 * lvl->n, mem,
+           [&](const void *d) { cmg::pack_field(lvl, 0, CMG_FIELD_PHI, CMG_PREC_FP64, d); });
+    return CMG_OK;
+  });
+}
+
+int cmg_level_get_phi(cmg_level *lvl, double *out, cmg_mem mem) {
+  return guard([&] {
+    need(lvl && (lvl->n == 0 || out), "bad arguments");
+    check_mem(mem);
+    DeviceScope ds(lvl->ctx->device);
+    deliver(lvl->ctx, out, sizeof(double) * 8 * lvl->n, mem,
+            [&](void *d) { cmg::unpack_field(lvl, 0, CMG_FIELD_PHI, CMG_PREC_FP64, d); });
+    return CMG_OK;
+  });
+}
+
+int cmg_level_get_residual(cmg_level *lvl, double *out, cmg_mem mem) {
+  return guard([&] {
+    need(lvl && (lvl->n == 0 || out), "bad arguments");
+    check_mem(mem);
+    DeviceScope ds(lvl->ctx->device);
+    deliver(lvl->ctx, out, sizeof(double) * 8 * lvl->n, mem,
+            [&](void *d) { cmg::residual_out(lvl, 0, CMG_PREC_FP64, static_cast<double *>(d)); });
+    return CMG_OK;
+  });
+}
+
+int cmg_level_get_ghosts(cmg_level *lvl, double *out, cmg_mem mem) {
+  return guard([&] {
+    need(lvl && (lvl->n == 0 || out), "bad arguments");
+    check_mem(mem);
+    DeviceScope ds(lvl->ctx->device);
+    deliver(lvl->ctx, out, sizeof(double) * 24 * lvl->n, mem,
+            [&](void *d) { cmg::get_ghosts(lvl, static_cast<double *>(d)); });
+    return CMG_OK;
+  });
+}
+
+int cmg_level_solve(cmg_level *lvl, const cmg_solve_params *params, cmg_solve_stats *stats) {
+  return guard([&] {
+    need(lvl && params, "NULL argument");
+    DeviceScope ds(lvl->ctx->device);
+    const int st = cmg::solve(lvl, params, stats);
+    if (st == CMG_ERR_NOT_CONVERGED) g_last_error = "max_cycles reached above tol";
+    if (st == CMG_ERR_DIVERGED) g_last_error = "residual diverged";
+    return st;
+  });
+}
+
+int cmg_level_mg_depth(const cmg_level *lvl, int *depth) {
+  return guard([&] {
+    need(lvl && depth, "NULL argument");
+    *depth = (int)lvl->mg.size();
+    return CMG_OK;
+  });
+}
+
+int cmg_level_mg_info(const cmg_level *lvl, int m, int64_t *n_octs, int *amr_level) {
+  return guard([&] {
+    need(lvl && m >= 0 && m < (int)lvl->mg.size(), "bad MG level");
+    if (n_octs) *n_octs = lvl->mg[m].n;
+    if (amr_level) *amr_level = lvl->mg[m].lev;
+    return CMG_OK;
+  });
+}
+
+int cmg_level_mg_keys(cmg_level *lvl, int m, uint64_t *out, cmg_mem mem) {
+  return guard([&] {
+    need(lvl && m >= 0 && m < (int)lvl->mg.size(), "bad MG level");
+    check_mem(mem);
+    const cmg::MgLev &g = lvl->mg[m];
+    need(g.n == 0 || out, "out is NULL");
+    DeviceScope ds(lvl->ctx->device);
+    deliver(lvl->ctx, out, sizeof(uint64_t) * g.n, mem, [&](void *d) {
+      if (g.n) CMG_CUDA(cudaMemcpyAsync(d, g.keys, sizeof(uint64_t) * g.n, cudaMemcpyDeviceToDevice, lvl->ctx->stream));
+    });
+    return CMG_OK;
+  });
+}
+
+int cmg_level_mg_active(cmg_level *lvl, int m, uint8_t *out, cmg_mem mem) {
+  return guard([&] {
+    need(lvl && m >= 0 && m < (int)lvl->mg.size(), "bad MG level");
+    check_mem(mem);
+    const cmg::MgLev &g = lvl->mg[m];
+    need(g.n == 0 || out, "out is NULL");
+    DeviceScope ds(lvl->ctx->device);
+    deliver(lvl->ctx, out, 8 * g.n, mem,
+            [&](void *d) { cmg::mg_active_bytes(g, static_cast<uint8_t *>(d), lvl->ctx->stream); });
+    return CMG_OK;
+  });
+}
+
+int cmg_level_mg_get(cmg_level *lvl, int m, int field, int precision, void *out, cmg_mem mem) {
+  return guard([&] {
+    need(lvl && m >= 0 && m < (int)lvl->mg.size(), "bad MG level");
+    need(field == CMG_FIELD_PHI || field == CMG_FIELD_F, "bad field");
+    need(precision == CMG_PREC_FP64 || precision == CMG_PREC_MIXED, "bad precision");
+    check_mem(mem);
+    DeviceScope ds(lvl->ctx->device);
+    if (precision == CMG_PREC_MIXED) cmg::ensure_fp32(lvl);
+    const size_t es = precision == CMG_PREC_FP64 ? 8 : 4;
+    need(lvl->mg[m].n == 0 || out, "out is NULL");
+    deliver(lvl->ctx, out, es * 8 * lvl->mg[m].n, mem,
+            [&](void *d) { cmg::unpack_field(lvl, m, field, precision, d); });
+    return CMG_OK;
+  });
+}
+
+int cmg_level_mg_set(cmg_level *lvl, int m, int field, int precision, const void *in, cmg_mem mem) {
+  return guard([&] {
+    need(lvl && m >= 0 && m < (int)lvl->mg.size(), "bad MG level");
+    need(field == CMG_FIELD_PHI || field == CMG_FIELD_F, "bad field");
+    need(precision == CMG_PREC_FP64 || precision == CMG_PREC_MIXED, "bad precision");
+    check_mem(mem);
+    DeviceScope ds(lvl->ctx->device);
+    if (precision == CMG_PREC_MIXED) cmg::ensure_fp32(lvl);
+    const size_t es = precision == CMG_PREC_FP64 ? 8 : 4;
+    need(lvl->mg[m].n == 0 || in, "in is NULL");
+    accept(lvl->ctx, in, es * 8 * lvl->mg[m].n, mem,
+           [&](const void *d) { cmg::pack_field(lvl, m, field, precision, d); });
+    return CMG_OK;
+  });
+}
+
+int cmg_level_mg_step(cmg_level *lvl, int m, int op, int precision, int n, double *norm2) {
+  return guard([&] {
+    need(lvl && m >= 0 && m < (int)lvl->mg.size(), "bad MG level");
+    need(precision == CMG_PREC_FP64 || precision == CMG_PREC_MIXED, "bad precision");
+    const int depth = (int)lvl->mg.size();
+    DeviceScope ds(lvl->ctx->device);
+    const bool f64 = precision == CMG_PREC_FP64;
+    if (!f64) cmg::ensure_fp32(lvl);
+    switch (op) {
+      case CMG_OP_SWEEP:
+        need(n >= 0, "n < 0");
+        for (int k = 0; k < n; ++k) f64 ? cmg::sweep<double>(lvl, m, false) : cmg::sweep<float>(lvl, m, false);
+        break;
+      case CMG_OP_RESIDUAL:
+        need(norm2 != nullptr, "norm2 is NULL");
+        f64 ? cmg::resid_restrict<double>(lvl, m, false, true, false, lvl->scal + 2)
+            : cmg::resid_restrict<float>(lvl, m, false, true, false, lvl->scal + 2);
+        CMG_CUDA(cudaMemcpyAsync(lvl->ctx->h_dpinned, lvl->scal + 2, sizeof(double), cudaMemcpyDeviceToHost,
+                                 lvl->ctx->stream));
+        CMG_CUDA(cudaStreamSynchronize(lvl->ctx->stream));
+        *norm2 = lvl->ctx->h_dpinned[0];
+        break;
+      case CMG_OP_RESTRICT:
+        need(m + 1 < depth, "no coarser MG level");
+        f64 ? cmg::resid_restrict<double>(lvl, m, true, false, true, nullptr)
+            : cmg::resid_restrict<float>(lvl, m, true, false, true, nullptr);
+        break;
+      case CMG_OP_PROLONG:
+        need(m + 1 < depth, "no coarser MG level");
+        f64 ? cmg::prolong<double>(lvl, m) : cmg::prolong<float>(lvl, m);
+        break;
+      case CMG_OP_COARSE:
+        need(m == depth - 1 && n >= 0, "CMG_OP_COARSE needs m = depth - 1");
+        cmg::coarse_solve(lvl, precision, n);
+        break;
+      case CMG_OP_GHOSTS:
+        cmg::fill_ghosts(lvl);
+        break;
+      default:
+        throw cmg::Error(CMG_ERR_INVALID_ARG, "unknown op");
+    }
+    CMG_CUDA(cudaStreamSynchronize(lvl->ctx->stream));
+    return CMG_OK;
+  });
+}
+
+}  // extern "C"

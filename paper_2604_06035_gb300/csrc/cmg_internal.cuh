@@ -1,0 +1,272 @@
+// cmg_internal.cuh -- internal types and device helpers of libcmg.so.
+//
+// Data layout (GB300-first):
+//  * every MG level keeps its cell fields in a colour-planar oct layout:
+//      field[plane][oct][slot],  plane = parity(c) (0 = red, 1 = black),
+//      slot = c >> 1,  c = bx + 2 by + 4 bz.
+//    A red (black) sweep then reads the whole black (red) plane and writes the
+//    red (black) plane: 12 B/cell per colour pass in FP64, the algorithmic
+//    minimum, with 32-byte (FP64) / 16-byte (FP32) vector loads per oct.
+//  * the source is stored pre-scaled, g = -h^2 f / 6, so the Gauss-Seidel
+//    update of App. D.2 Eq. (gs_update) is one FMA after the neighbour sum.
+//  * oct arrays hold n real octs, then the Dirichlet ghost octs of a refined
+//    level (missing neighbours whose cells are interpolated from the parent),
+//    then one oct of zeros that stands for "no neighbour" on coarse MG levels.
+//    Kernels therefore never branch on missing neighbours.
+//  * neighbour and interpolation-block tables are structure-of-arrays
+//    ([6][n], [8][n]) so that a warp's index loads are coalesced.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "cmg.h"
+
+namespace cmg {
+
+constexpr uint64_t kEmptyKey = ~0ull;
+constexpr int kMortonBits = 21;
+
+// ------------------------------------------------------------------ errors
+
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+
+void cuda_check(cudaError_t e, const char *what);
+#define CMG_CUDA(x) ::cmg::cuda_check((x), #x)
+
+// ------------------------------------------------------- Morton keys (A1)
+// Sec. 4.2 Eq. (morton_encode): bit b of i, j, k goes to key bits 3b, 3b+1,
+// 3b+2.  Written with the usual bit-spreading masks (21 bits per axis).
+
+__host__ __device__ inline uint64_t spread3(uint32_t v) {
+  uint64_t x = v & 0x1fffffu;
+  x = (x | (x << 32)) & 0x001f00000000ffffull;
+  x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+  x = (x | (x << 8)) & 0x100f00f00f00f00full;
+  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+
+__host__ __device__ inline uint32_t compact3(uint64_t x) {
+  x &= 0x1249249249249249ull;
+  x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+  x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+  x = (x ^ (x >> 8)) & 0x001f0000ff0000ffull;
+  x = (x ^ (x >> 16)) & 0x001f00000000ffffull;
+  x = (x ^ (x >> 32)) & 0x00000000001fffffull;
+  return (uint32_t)x;
+}
+
+__host__ __device__ inline uint64_t morton_encode(uint32_t i, uint32_t j, uint32_t k) {
+  return spread3(i) | (spread3(j) << 1) | (spread3(k) << 2);
+}
+
+__host__ __device__ inline void morton_decode(uint64_t m, uint32_t &i, uint32_t &j, uint32_t &k) {
+  i = compact3(m);
+  j = compact3(m >> 1);
+  k = compact3(m >> 2);
+}
+
+// App. A Alg. 2: neighbour key in direction d (0..5 = -x,+x,-y,+y,-z,+z) on a
+// grid of npd octs per axis; periodic wrap on the axes of pmask, else the
+// all-ones key meaning "outside the box".
+__host__ __device__ inline uint64_t neighbor_key(uint64_t m, int d, uint32_t npd, int pmask) {
+  uint32_t c[3];
+  morton_decode(m, c[0], c[1], c[2]);
+  const int a = d >> 1;
+  int64_t v = (int64_t)c[a] + ((d & 1) ? 1 : -1);
+  if ((pmask >> a) & 1) {
+    if (v < 0) v += npd;
+    if (v >= (int64_t)npd) v -= npd;
+  } else if (v < 0 || v >= (int64_t)npd) {
+    return kEmptyKey;
+  }
+  c[a] = (uint32_t)v;
+  return morton_encode(c[0], c[1], c[2]);
+}
+
+// ------------------------------------------------------------ hash (A5/A6)
+// App. B Eq. (hash_func): multiplicative hash with a mixing step, modulo 2^64.
+
+__host__ __device__ inline uint64_t hash_mix(uint64_t h) {
+  uint64_t t = ((h * 2654435761ull) ^ (h >> 16)) * 0x9E3779B97F4A7C15ull;
+  return t ^ (t >> 13);
+}
+
+inline int64_t hash_capacity(int64_t n) {
+  int64_t cap = 1;
+  while (10 * n > 7 * cap) cap <<= 1;
+  return cap;
+}
+
+// Linear probing (App. B), at most cap probes.
+__device__ inline int32_t ht_find(const uint64_t *__restrict__ keys, const int32_t *__restrict__ vals,
+                                  uint64_t mask, uint64_t k) {
+  uint64_t s = hash_mix(k) & mask;
+  for (uint64_t p = 0; p <= mask; ++p) {
+    const uint64_t kk = keys[s];
+    if (kk == k) return vals[s];
+    if (kk == kEmptyKey) return -1;
+    s = (s + 1) & mask;
+  }
+  return -1;
+}
+
+// Returns the slot of k, inserting it if absent; *inserted tells which.
+// -1 if the table is full (cannot happen at fill <= 0.7).
+__device__ inline int64_t ht_insert_slot(uint64_t *keys, uint64_t mask, uint64_t k, bool *inserted) {
+  uint64_t s = hash_mix(k) & mask;
+  for (uint64_t p = 0; p <= mask; ++p) {
+    const unsigned long long prev =
+        atomicCAS(reinterpret_cast<unsigned long long *>(keys + s), (unsigned long long)kEmptyKey,
+                  (unsigned long long)k);
+    if (prev == kEmptyKey) {
+      *inserted = true;
+      return (int64_t)s;
+    }
+    if (prev == k) {
+      *inserted = false;
+      return (int64_t)s;
+    }
+    s = (s + 1) & mask;
+  }
+  return -1;
+}
+
+__device__ inline int64_t ht_slot(const uint64_t *__restrict__ keys, uint64_t mask, uint64_t k) {
+  uint64_t s = hash_mix(k) & mask;
+  for (uint64_t p = 0; p <= mask; ++p) {
+    const uint64_t kk = keys[s];
+    if (kk == k) return (int64_t)s;
+    if (kk == kEmptyKey) return -1;
+    s = (s + 1) & mask;
+  }
+  return -1;
+}
+
+__device__ inline void set_error(int *err, int code) { atomicCAS(err, 0, code); }
+
+// -------------------------------------------------------------- cell maps
+
+__host__ __device__ constexpr int cell_parity(int c) { return ((c & 1) + ((c >> 1) & 1) + ((c >> 2) & 1)) & 1; }
+// child index of (plane, slot)
+__host__ __device__ constexpr int plane_cell(int p, int q) {
+  return p == 0 ? (q == 0 ? 0 : q == 1 ? 3 : q == 2 ? 5 : 6) : (q == 0 ? 1 : q == 1 ? 2 : q == 2 ? 4 : 7);
+}
+
+// ------------------------------------------------------------------ types
+
+struct MgLev {
+  int lev = 0;
+  int64_t n = 0;        // real octs
+  int64_t n_ghost = 0;  // Dirichlet ghost octs (level 0 of a refined AMR level)
+  int64_t n_alloc = 0;  // n + n_ghost + 1 (zero oct last)
+  double h = 0.0;
+  bool all_active = true;
+  uint64_t *keys = nullptr;      // [n]
+  uint64_t *ht_keys = nullptr;   // [cap]
+  int32_t *ht_vals = nullptr;    // [cap]
+  int64_t cap = 0;
+  int32_t *nbr = nullptr;        // [6][n] internal neighbour index (>= n: ghost / zero oct)
+  uint8_t *active = nullptr;     // [n] 8-bit cell mask
+  int32_t *father = nullptr;     // [n] coarse cell (p*8 + cc) of fully active octs, else -1
+  int32_t *blk = nullptr;        // [8][n] 2x2x2 coarse octs around the father cell
+  double *phi = nullptr;         // [2][n_alloc][4]
+  double *g = nullptr;           // [2][n][4], g = -h^2 f / 6
+  float *phi32 = nullptr;        // [2][n_alloc][4]
+  float *g32 = nullptr;          // [2][n][4]
+};
+
+struct DeviceBuffers {
+  std::vector<void *> ptrs;
+  template <class T>
+  T *alloc(int64_t count, bool zero = false, cudaStream_t s = nullptr);
+  void release();
+};
+
+}  // namespace cmg
+
+struct cmg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  int *d_err = nullptr;       // device error flag
+  int *h_pinned = nullptr;    // pinned staging (ints)
+  double *h_dpinned = nullptr;  // pinned staging (doubles)
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+struct cmg_level {
+  cmg_ctx *ctx = nullptr;
+  int lev = 0, nx = 1, pmask = 7;
+  int64_t n = 0;
+  cmg_level *parent = nullptr;
+  bool periodic_full = false;
+  bool exact_coarse = false;
+  std::vector<cmg::MgLev> mg;
+  // ghosts of level 0
+  uint64_t *ghost_keys = nullptr;  // [n_ghost]
+  int32_t *ghost_blk = nullptr;    // [8][n_ghost] parent octs around the ghost's father cell
+  uint32_t *ghost_mask = nullptr;  // [n_ghost] cells some real oct reads
+  // reductions
+  double *partials = nullptr;  // [blocks of the largest MG level]
+  double *scal = nullptr;      // device scalars (norms, scales)
+  double *rbuf = nullptr;      // [n][8] residual for the API (lazy)
+  bool has32 = false;
+  cmg::DeviceBuffers mem;
+};
+
+namespace cmg {
+
+constexpr int kThreads = 256;
+
+inline unsigned blocks_for(int64_t n, int t = kThreads) { return (unsigned)((n + t - 1) / t); }
+
+// scan.cu
+void scan_exclusive(const int32_t *in, int32_t *out, int64_t n, int32_t *d_total, int32_t *scratch,
+                    int64_t scratch_n, cudaStream_t s);
+int64_t scan_scratch_size(int64_t n);
+
+// build.cu
+void build_level(cmg_level *L, const uint64_t *keys, cmg_mem mem);
+void hash_lookup(const MgLev &g, const uint64_t *q, int64_t n, int32_t *out, cudaStream_t s);
+void encode_keys(const uint32_t *ijk, int64_t n, uint64_t *keys, int *err, cudaStream_t s);
+void decode_keys(const uint64_t *keys, int64_t n, uint32_t *ijk, cudaStream_t s);
+void ext_neighbors(const cmg_level *L, int32_t *out, cudaStream_t s);
+void father_cells(const cmg_level *L, int32_t *out, cudaStream_t s);
+void mg_active_bytes(const MgLev &g, uint8_t *out, cudaStream_t s);
+
+// ops.cu
+void set_density(cmg_level *L, const double *rho, double rho_bar, double four_pi_g);
+void pack_field(cmg_level *L, int m, int field, int prec, const void *in);
+void unpack_field(cmg_level *L, int m, int field, int prec, void *out);
+void fill_ghosts(cmg_level *L);
+void get_ghosts(cmg_level *L, double *out);
+void ensure_fp32(cmg_level *L);
+template <typename T>
+void sweep(cmg_level *L, int m, bool zero_init);
+template <typename T>
+void resid_restrict(cmg_level *L, int m, bool restrict_to_coarse, bool norm, bool zero_coarse_phi,
+                    double *norm_out, const double *emit_scale = nullptr);
+void residual_out(cmg_level *L, int m, int prec, double *out);
+double residual_norm2_host(cmg_level *L, int m, int prec);
+template <typename T>
+void prolong(cmg_level *L, int m);
+void coarse_solve(cmg_level *L, int prec, int coarse_sweeps);
+void zero_phi_norm(cmg_level *L, double *out);
+void subtract_mean(cmg_level *L);
+void accumulate(cmg_level *L, const double *scale);
+void finalize_norm(cmg_level *L, int n_partials, double scale, double *out);
+
+// solve.cu
+int solve(cmg_level *L, const cmg_solve_params *p, cmg_solve_stats *st);
+
+}  // namespace cmg

@@ -1,0 +1,360 @@
+"""GPU parity: libcmg.so (through the C ABI) against the CPU oracle on the same
+seeded inputs.  Keys, hash lookups, neighbours, father cells and the MG
+hierarchy are compared bit-exactly; FP64 fields to 1e-12 relative (the
+tolerance fixed for the FP64 path); mixed precision to 1e-10 relative after
+refinement against an FP64 oracle converged to 1e-13.
+
+Sizes span several thread blocks with ragged tails; the full-size two-level
+workload (128^3 base + refined level) is checked at a fixed cycle count and by
+properties that hold at any size."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2604_06035_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+RTOL64 = 1e-12
+RTOL_MIXED = 1e-10
+
+
+@pytest.fixture(scope="module")
+def cmg():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2604_06035_gb300 import cmg as _c
+    return _c
+
+
+@pytest.fixture(scope="module")
+def ctx(cmg):
+    c = cmg.cmg_ctx_create(0)
+    yield c
+    import gc
+    gc.collect()
+    cmg.cmg_ctx_destroy(c)
+
+
+def relerr(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+# ------------------------------------------------------------------ keys
+
+def test_morton_bitexact(cmg, ctx):
+    rng = np.random.default_rng(11)
+    ijk = rng.integers(0, 1 << 21, size=(100003, 3), dtype=np.uint32)
+    k = cmg.cmg_morton_encode(ctx, ijk)
+    assert np.array_equal(k, O.morton_encode(ijk))
+    assert np.array_equal(cmg.cmg_morton_decode(ctx, k), ijk)
+    bad = ijk.copy()
+    bad[5, 1] = 1 << 21
+    with pytest.raises(cmg.CmgError) as e:
+        cmg.cmg_morton_encode(ctx, bad)
+    assert e.value.code == cmg.CMG_ERR_KEY_OUT_OF_RANGE
+
+
+def test_morton_device_memory_path(cmg, ctx):
+    import torch
+    rng = np.random.default_rng(12)
+    ijk = rng.integers(0, 1 << 21, size=(5000, 3), dtype=np.uint32)
+    t = torch.from_numpy(ijk).cuda()
+    k = cmg.cmg_morton_encode(ctx, t)
+    assert k.is_cuda
+    assert np.array_equal(k.cpu().numpy(), O.morton_encode(ijk))
+
+
+@pytest.mark.parametrize("npd,count,level", [(16, 3000, 5), (1 << 20, 70001, 21), (4, 64, 3)])
+def test_hash_lookup_bitexact(cmg, ctx, npd, count, level):
+    rng = np.random.default_rng(count)
+    coords = np.unique(rng.integers(0, npd, size=(count, 3), dtype=np.uint32), axis=0)
+    rng.shuffle(coords)
+    keys = O.morton_encode(coords)
+    G = cmg.cmg_level_build(ctx, level, keys, periodic_mask=7)
+    R = O.Level(level, keys, periodic_mask=7)
+    assert cmg.cmg_level_hash_capacity(G) == R.hash_capacity
+    q = np.concatenate([keys, O.morton_encode(rng.integers(0, npd, size=(count, 3), dtype=np.uint32))])
+    assert np.array_equal(cmg.cmg_level_lookup(G, q), R.lookup(q))
+
+
+def test_build_errors(cmg, ctx):
+    k = O.morton_encode(np.array([[0, 0, 0], [1, 0, 0], [0, 0, 0]], dtype=np.uint32))
+    with pytest.raises(cmg.CmgError) as e:
+        cmg.cmg_level_build(ctx, 3, k)
+    assert e.value.code == cmg.CMG_ERR_DUPLICATE_KEY
+    with pytest.raises(cmg.CmgError) as e:
+        cmg.cmg_level_build(ctx, 2, O.morton_encode(np.array([[2, 0, 0]], dtype=np.uint32)))
+    assert e.value.code == cmg.CMG_ERR_KEY_OUT_OF_RANGE
+    with pytest.raises(cmg.CmgError) as e:
+        cmg.cmg_level_build(ctx, 3, np.array([1 << 63], dtype=np.uint64))
+    assert e.value.code == cmg.CMG_ERR_KEY_OUT_OF_RANGE
+    with pytest.raises(cmg.CmgError) as e:
+        cmg.cmg_level_build(ctx, 0, k[:1])
+    assert e.value.code == cmg.CMG_ERR_INVALID_ARG
+    # a patch whose coarse-fine stencil leaves its parent patch
+    pc = _cube(4, 0.25, 0.75)
+    P = cmg.cmg_level_build(ctx, 4, O.morton_encode(pc))
+    with pytest.raises(cmg.CmgError) as e:
+        cmg.cmg_level_build(ctx, 5, O.morton_encode(_cube(5, 0.25, 0.75)), parent=P)
+    assert e.value.code == cmg.CMG_ERR_MISSING_PARENT
+
+
+def test_empty_level(cmg, ctx):
+    G = cmg.cmg_level_build(ctx, 4, np.zeros(0, dtype=np.uint64))
+    assert cmg.cmg_level_n_octs(G) == 0
+    assert cmg.cmg_level_get_neighbors(G).shape == (0, 7)
+    rc, st = cmg.cmg_level_solve(G, tol=1e-10)
+    assert rc == cmg.CMG_OK and st["cycles"] == 0
+
+
+@pytest.mark.parametrize("pmask", [7, 0, 3])
+def test_neighbors_bitexact(cmg, ctx, pmask):
+    rng = np.random.default_rng(20 + pmask)
+    coords = np.unique(rng.integers(0, 32, size=(20000, 3), dtype=np.uint32), axis=0)
+    rng.shuffle(coords)
+    keys = O.morton_encode(coords)
+    G = cmg.cmg_level_build(ctx, 6, keys, periodic_mask=pmask)
+    R = O.Level(6, keys, periodic_mask=pmask)
+    assert np.array_equal(cmg.cmg_level_get_neighbors(G), R.neighbors())
+
+
+def _two_level(cmg, ctx, base, seed=2):
+    cfg = inputs.two_level_amr(base_level=base, seed=seed)
+    kb = cmg.cmg_morton_encode(ctx, cfg["coords"][0])
+    kf = cmg.cmg_morton_encode(ctx, cfg["coords"][1])
+    GB = cmg.cmg_level_build(ctx, base, kb)
+    GF = cmg.cmg_level_build(ctx, base + 1, kf, parent=GB)
+    RB = O.Level(base, O.morton_encode(cfg["coords"][0]))
+    RF = O.Level(base + 1, O.morton_encode(cfg["coords"][1]), parent=RB)
+    return cfg, GB, GF, RB, RF
+
+
+def test_father_cells_and_hierarchy_bitexact(cmg, ctx):
+    cfg, GB, GF, RB, RF = _two_level(cmg, ctx, 5)
+    assert np.array_equal(cmg.cmg_level_get_neighbors(GF), RF.neighbors())
+    assert np.array_equal(cmg.cmg_level_get_father_cells(GF), RF.father_cells())
+    for G, R in ((GB, RB), (GF, RF)):
+        assert cmg.cmg_level_mg_depth(G) == R.mg_depth
+        for m in range(R.mg_depth):
+            n, lev = cmg.cmg_level_mg_info(G, m)
+            assert n == R.mg_n_octs(m) and lev == R.mg_lev(m)
+            assert np.array_equal(cmg.cmg_level_mg_keys(G, m), R.mg_keys(m))
+            assert np.array_equal(cmg.cmg_level_mg_active(G, m), R.mg_active(m))
+
+
+# ---------------------------------------------------------- single steps
+
+def _random_fields(n, rng):
+    return rng.standard_normal((n, 8)), rng.standard_normal((n, 8))
+
+
+def _set_both(cmg, G, R, m, phi, f):
+    cmg.cmg_level_mg_set(G, m, cmg.CMG_FIELD_PHI, phi)
+    cmg.cmg_level_mg_set(G, m, cmg.CMG_FIELD_F, f)
+    R.mg_set(m, "phi", phi)
+    R.mg_set(m, "f", f)
+
+
+@pytest.fixture(scope="module")
+def two5(cmg, ctx):
+    cfg, GB, GF, RB, RF = _two_level(cmg, ctx, 5)
+    rng = np.random.default_rng(5)
+    phi_b = rng.standard_normal((RB.n, 8))
+    cmg.cmg_level_set_phi(GB, phi_b)
+    RB.set_phi(phi_b)
+    cmg.cmg_level_mg_step(GF, 0, cmg.CMG_OP_GHOSTS)
+    return cfg, GB, GF, RB, RF
+
+
+def test_ghosts_parity(cmg, two5):
+    cfg, GB, GF, RB, RF = two5
+    g = cmg.cmg_level_get_ghosts(GF)
+    r = RF.ghosts()
+    assert np.array_equal(np.isnan(g), np.isnan(r))
+    ok = ~np.isnan(r)
+    assert ok.sum() > 1000
+    assert relerr(g[ok], r[ok]) <= 1e-14
+
+
+@pytest.mark.parametrize("which", ["base", "fine"])
+def test_sweep_residual_parity_all_mg_levels(cmg, two5, which):
+    cfg, GB, GF, RB, RF = two5
+    G, R = (GB, RB) if which == "base" else (GF, RF)
+    rng = np.random.default_rng(7)
+    for m in range(R.mg_depth):
+        n = R.mg_n_octs(m)
+        act = R.mg_active(m).astype(bool)
+        phi, f = _random_fields(n, rng)
+        phi[~act] = 0.0
+        _set_both(cmg, G, R, m, phi, f)
+        cmg.cmg_level_mg_step(G, m, cmg.CMG_OP_SWEEP, n=2)
+        R.rb_sweeps(m, 2, use_ghost=(m == 0))
+        got = cmg.cmg_level_mg_get(G, m, cmg.CMG_FIELD_PHI)
+        assert relerr(got, R.mg_get(m, "phi")) <= RTOL64, m
+        n2 = cmg.cmg_level_mg_step(G, m, cmg.CMG_OP_RESIDUAL)
+        r2 = R.residual(m, use_ghost=(m == 0))
+        assert abs(n2 - r2) <= 1e-11 * r2, m
+
+
+def test_residual_field_parity(cmg, two5):
+    cfg, GB, GF, RB, RF = two5
+    rng = np.random.default_rng(8)
+    phi, f = _random_fields(RF.n, rng)
+    _set_both(cmg, GF, RF, 0, phi, f)
+    r_gpu = cmg.cmg_level_get_residual(GF)
+    RF.residual(0, use_ghost=True)
+    r_or = RF.mg_get(0, "r")
+    assert relerr(r_gpu, r_or) <= RTOL64
+
+
+@pytest.mark.parametrize("which", ["base", "fine"])
+def test_restrict_prolong_coarse_parity(cmg, two5, which):
+    cfg, GB, GF, RB, RF = two5
+    G, R = (GB, RB) if which == "base" else (GF, RF)
+    rng = np.random.default_rng(9)
+    for m in range(R.mg_depth - 1):
+        n = R.mg_n_octs(m)
+        act = R.mg_active(m).astype(bool)
+        phi, f = _random_fields(n, rng)
+        phi[~act] = 0.0
+        _set_both(cmg, G, R, m, phi, f)
+        cmg.cmg_level_mg_step(G, m, cmg.CMG_OP_RESTRICT)
+        R.residual(m, use_ghost=(m == 0))
+        R.restrict(m)
+        cf = cmg.cmg_level_mg_get(G, m + 1, cmg.CMG_FIELD_F)
+        assert relerr(cf, R.mg_get(m + 1, "f")) <= 1e-11, m
+        assert np.all(cmg.cmg_level_mg_get(G, m + 1, cmg.CMG_FIELD_PHI) == 0.0)
+        cact = R.mg_active(m + 1).astype(bool)
+        e = rng.standard_normal((R.mg_n_octs(m + 1), 8))
+        e[~cact] = 0.0
+        cmg.cmg_level_mg_set(G, m + 1, cmg.CMG_FIELD_PHI, e)
+        R.mg_set(m + 1, "phi", e)
+        cmg.cmg_level_mg_step(G, m, cmg.CMG_OP_PROLONG)
+        R.prolong(m)
+        assert relerr(cmg.cmg_level_mg_get(G, m, cmg.CMG_FIELD_PHI), R.mg_get(m, "phi")) <= RTOL64, m
+    last = R.mg_depth - 1
+    f = rng.standard_normal((R.mg_n_octs(last), 8))
+    f[~R.mg_active(last).astype(bool)] = 0.0
+    if which == "base":
+        f -= f.mean()
+    _set_both(cmg, G, R, last, np.zeros_like(f), f)
+    cmg.cmg_level_mg_step(G, last, cmg.CMG_OP_COARSE, n=32)
+    R.coarse_solve(32)
+    assert relerr(cmg.cmg_level_mg_get(G, last, cmg.CMG_FIELD_PHI), R.mg_get(last, "phi")) <= RTOL64
+
+
+# ------------------------------------------------------------ V-cycles
+
+def _solve_pair(cmg, G, R, fixed=0, tol=1e-10, **kw):
+    rc, st = cmg.cmg_level_solve(G, tol=tol, fixed_cycles=fixed, **kw)
+    R.solve(tol=tol, fixed_cycles=fixed)
+    return st
+
+
+def test_config1_periodic_32cube_solve(cmg, ctx):
+    cfg = inputs.periodic_grf_level(5, seed=1)
+    keys = cmg.cmg_morton_encode(ctx, cfg["coords"][0])
+    G = cmg.cmg_level_build(ctx, 5, keys)
+    R = O.Level(5, O.morton_encode(cfg["coords"][0]))
+    cmg.cmg_level_set_density(G, cfg["rho"][0], 1.0)
+    R.set_density(cfg["rho"][0], 1.0)
+    rc, st = cmg.cmg_level_solve(G, tol=1e-10)
+    ro, so = R.solve(tol=1e-10)
+    assert st["cycles"] == so["cycles"]
+    np.testing.assert_allclose(st["rel_history"], so["rel_history"], rtol=1e-4)
+    phi = cmg.cmg_level_get_phi(G)
+    assert relerr(phi, R.get_phi()) <= RTOL64
+    assert st["rel_final"] <= 1e-10
+    assert abs(phi.mean()) <= 1e-14 * np.abs(phi).max()
+
+
+@pytest.mark.parametrize("base", [5, 6])
+def test_two_level_fixed_cycles_and_converged(cmg, ctx, base):
+    cfg, GB, GF, RB, RF = _two_level(cmg, ctx, base)
+    for G, R, rho in ((GB, RB, cfg["rho"][0]), (GF, RF, cfg["rho"][1])):
+        cmg.cmg_level_set_density(G, rho, 1.0)
+        R.set_density(rho, 1.0)
+    _solve_pair(cmg, GB, RB, fixed=3)
+    assert relerr(cmg.cmg_level_get_phi(GB), RB.get_phi()) <= RTOL64
+    _solve_pair(cmg, GF, RF, fixed=3)
+    assert relerr(cmg.cmg_level_get_phi(GF), RF.get_phi()) <= RTOL64
+    # converged to 1e-10 from zero on both sides
+    for G, R in ((GB, RB), (GF, RF)):
+        z = np.zeros((R.n, 8))
+        cmg.cmg_level_set_phi(G, z)
+        R.set_phi(z)
+        st = _solve_pair(cmg, G, R, tol=1e-10)
+        assert relerr(cmg.cmg_level_get_phi(G), R.get_phi()) <= RTOL64
+        assert st["rel_final"] <= 1e-10
+
+
+def test_two_level_full_size_128(cmg, ctx):
+    """The 128^3 two-level workload: two cycles against the oracle, then the
+    converged GPU solution checked by an independent residual evaluation."""
+    cfg, GB, GF, RB, RF = _two_level(cmg, ctx, 7)
+    for G, R, rho in ((GB, RB, cfg["rho"][0]), (GF, RF, cfg["rho"][1])):
+        cmg.cmg_level_set_density(G, rho, 1.0)
+        R.set_density(rho, 1.0)
+    _solve_pair(cmg, GB, RB, fixed=2)
+    assert relerr(cmg.cmg_level_get_phi(GB), RB.get_phi()) <= RTOL64
+    _solve_pair(cmg, GF, RF, fixed=2)
+    assert relerr(cmg.cmg_level_get_phi(GF), RF.get_phi()) <= RTOL64
+    # converged GPU solve; residual recomputed by the oracle
+    for G, R in ((GB, RB), (GF, RF)):
+        rc, st = cmg.cmg_level_solve(G, tol=1e-10)
+        assert st["rel_final"] <= 1e-10
+        R.set_phi(cmg.cmg_level_get_phi(G))
+        n2 = R.residual(0, use_ghost=True)
+        assert np.sqrt(n2) <= 1.0001e-10 * st["norm0"]
+
+
+def test_mixed_precision_matches_fp64(cmg, ctx):
+    cfg, GB, GF, RB, RF = _two_level(cmg, ctx, 6)
+    for G, R, rho in ((GB, RB, cfg["rho"][0]), (GF, RF, cfg["rho"][1])):
+        cmg.cmg_level_set_density(G, rho, 1.0)
+        R.set_density(rho, 1.0)
+        R.solve(tol=1e-13)
+        rc, st = cmg.cmg_level_solve(G, tol=1e-10, precision=cmg.CMG_PREC_MIXED)
+        assert st["rel_final"] <= 1e-10
+        assert relerr(cmg.cmg_level_get_phi(G), R.get_phi()) <= RTOL_MIXED
+        # the parent phi the fine level sees is the GPU's own mixed solution
+        if G is GB:
+            RB.set_phi(cmg.cmg_level_get_phi(GB))
+
+
+def test_status_codes(cmg, ctx):
+    cfg = inputs.periodic_grf_level(4, seed=1)
+    G = cmg.cmg_level_build(ctx, 4, cmg.cmg_morton_encode(ctx, cfg["coords"][0]))
+    cmg.cmg_level_set_density(G, cfg["rho"][0], 1.0)
+    rc, st = cmg.cmg_level_solve(G, tol=1e-10, max_cycles=2, raise_on_error=False)
+    assert rc == cmg.CMG_ERR_NOT_CONVERGED and st["cycles"] == 2
+    rho = cfg["rho"][0].copy()
+    rho[3, 2] = np.nan
+    cmg.cmg_level_set_density(G, rho, 1.0)
+    rc, st = cmg.cmg_level_solve(G, tol=1e-10, raise_on_error=False)
+    assert rc == cmg.CMG_ERR_DIVERGED
+    with pytest.raises(cmg.CmgError) as e:
+        cmg.cmg_level_solve(G, tol=1e-10, n_pre=-1)
+    assert e.value.code == cmg.CMG_ERR_INVALID_ARG
+
+
+def test_device_arrays_match_host_arrays(cmg, ctx):
+    import torch
+    cfg = inputs.periodic_grf_level(5, seed=1)
+    keys = torch.from_numpy(O.morton_encode(cfg["coords"][0])).cuda()
+    G = cmg.cmg_level_build(ctx, 5, keys)
+    cmg.cmg_level_set_density(G, torch.from_numpy(cfg["rho"][0]).cuda(), 1.0)
+    cmg.cmg_level_solve(G, tol=1e-10)
+    phi_d = cmg.cmg_level_get_phi(G, device=True)
+    H = cmg.cmg_level_build(ctx, 5, O.morton_encode(cfg["coords"][0]))
+    cmg.cmg_level_set_density(H, cfg["rho"][0], 1.0)
+    cmg.cmg_level_solve(H, tol=1e-10)
+    assert np.array_equal(phi_d.cpu().numpy(), cmg.cmg_level_get_phi(H))
+
+
+def _cube(level, lo, hi):
+    npd = 1 << (level - 1)
+    r = np.arange(int(round(lo * npd)), int(round(hi * npd)))
+    z, y, x = np.meshgrid(r, r, r, indexing="ij")
+    return np.stack([x.ravel(), y.ravel(), z.ravel()], 1).astype(np.uint32)
