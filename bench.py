@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark of the level-by-level multigrid Poisson solve (cuRAMSES,
+arXiv 2604.06035) on one GB300 per rank.
+
+Workload (default "two_level_128"): periodic 128^3 base level (lognormal
+density, sigma_ln rho = 1.5, P(k) ~ k^-2, seed 2) plus one refined level on
+the cells above 8 rho_bar (face-dilated, ~1.4 M fine cells).  A step solves
+both levels, base then fine (Dirichlet ghosts from the base phi), each from
+phi = 0 to relative residual 1e-10, through libcmg.so.  Inputs (keys,
+densities) are resident in HBM when the timed region starts; L2 is flushed
+(512 MiB write) before every timed step, outside its CUDA-event interval.
+
+metric: cell-updates per second (a cell visited by one full red-black sweep,
+summed over all multigrid levels), whole job over all ranks.  With --gpus N
+each rank solves its own replica (the level solve is not sharded): "weak".
+
+--impl reference times the CPU FP64 oracle (test infrastructure, single
+thread) on a bounded sample of the same workload: one V-cycle of each level.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 (profiling recipe); FMA = 2 flops
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="two_level_128", choices=["two_level_128"])
+    ap.add_argument("--quick", action="store_true", help="timed steps only (profiling runs)")
+    ap.add_argument("--tol", type=float, default=1e-10)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), int(
+        os.environ.get("WORLD_SIZE", "1"))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_for(kernel):
+    """ncu DRAM bytes per launch recorded in profiles/traffic.json for the
+    current kernel source (null when the source changed since the capture)."""
+    try:
+        rec = json.load(open(PROFILE_TRAFFIC))
+    except (OSError, ValueError):
+        return None
+    e = rec.get(kernel)
+    if not e:
+        return None
+    from paper_2604_06035_gb300 import build as _b
+    if e.get("source_sha") != _b.source_digest():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def cycle_updates(n_octs_per_mg, n_pre=2, n_post=2, coarse_sweeps=32, exact_coarse=True):
+    u = sum((n_pre + n_post) * 8 * n for n in n_octs_per_mg[:-1])
+    if not exact_coarse:
+        u += coarse_sweeps * 8 * n_octs_per_mg[-1]
+    return u
+
+
+# ------------------------------------------------------------- reference
+
+def run_reference(args, rank, world):
+    import numpy as np  # noqa: F401
+    import oracle as O
+    from paper_2604_06035_gb300 import inputs
+    if rank != 0:
+        return
+    cfg = inputs.two_level_amr(base_level=7, seed=2)
+    B = O.Level(7, O.morton_encode(cfg["coords"][0]))
+    F = O.Level(8, O.morton_encode(cfg["coords"][1]), parent=B)
+    B.set_density(cfg["rho"][0], 1.0)
+    F.set_density(cfg["rho"][1], 1.0)
+    ub = cycle_updates([B.mg_n_octs(m) for m in range(B.mg_depth)], exact_coarse=True)
+    uf = cycle_updates([F.mg_n_octs(m) for m in range(F.mg_depth)], exact_coarse=False)
+
+    def step():
+        B.solve(fixed_cycles=1)
+        F.solve(fixed_cycles=1)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = (ub + uf) / dt / 1e6
+    sample = "one FP64 V(2,2) cycle on the 128^3 base and one on the refined level per step"
+    print(json.dumps({
+        "metric": "poisson_cell_updates_per_s", "value": value, "unit": "Mcell-updates/s", "impl": "reference",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "two_level_128: 128^3 periodic lognormal base + 1 refined level (rho > 8 rho_bar)"},
+        "cpu_baseline": {"value": value, "unit": "Mcell-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "Mcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def cpu_baseline_sample():
+    """The oracle as it stands on a bounded sample: two V-cycles of each level
+    of the same workload, single thread."""
+    import oracle as O
+    from paper_2604_06035_gb300 import inputs
+    cfg = inputs.two_level_amr(base_level=7, seed=2)
+    B = O.Level(7, O.morton_encode(cfg["coords"][0]))
+    F = O.Level(8, O.morton_encode(cfg["coords"][1]), parent=B)
+    B.set_density(cfg["rho"][0], 1.0)
+    F.set_density(cfg["rho"][1], 1.0)
+    ub = cycle_updates([B.mg_n_octs(m) for m in range(B.mg_depth)], exact_coarse=True)
+    uf = cycle_updates([F.mg_n_octs(m) for m in range(F.mg_depth)], exact_coarse=False)
+    t0 = time.perf_counter()
+    B.solve(fixed_cycles=2)
+    F.solve(fixed_cycles=2)
+    dt = time.perf_counter() - t0
+    return {"value": 2 * (ub + uf) / dt / 1e6, "unit": "Mcell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": "two FP64 V(2,2) cycles on the 128^3 base and two on the refined level (%.1f s)" % dt}
+
+
+# ------------------------------------------------------------------- ours
+
+def run_ours(args, rank, local, world):
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if local == 0:
+        ge.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2604_06035_gb300 import cmg, inputs
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ctx = cmg.cmg_ctx_create(local, stream=stream.cuda_stream)
+    cfg = inputs.two_level_amr(base_level=7, seed=2)
+    coords = [torch.from_numpy(c).to(dev) for c in cfg["coords"]]
+    rho = [torch.from_numpy(r).to(dev) for r in cfg["rho"]]
+    zeros = [torch.zeros_like(r) for r in rho]
+
+    # setup: keys (a1), hash + neighbour cache + hierarchy (a2, a3), ghost stencils
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    keys = [cmg.cmg_morton_encode(ctx, c) for c in coords]
+    B = cmg.cmg_level_build(ctx, 7, keys[0])
+    F = cmg.cmg_level_build(ctx, 8, keys[1], parent=B)
+    torch.cuda.synchronize()
+    build_ms = (time.perf_counter() - t0) * 1e3
+
+    def step(precision=cmg.CMG_PREC_FP64):
+        stats = []
+        for L, r, z in ((B, rho[0], zeros[0]), (F, rho[1], zeros[1])):
+            cmg.cmg_level_set_phi(L, z)
+            cmg.cmg_level_set_density(L, r, 1.0)
+            rc, st = cmg.cmg_level_solve(L, tol=args.tol, precision=precision)
+            stats.append(st)
+        return stats
+
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        step()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    cmg.cmg_ctx_reset_profile(ctx)
+    cmg.cmg_ctx_set_profiling(ctx, True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    all_stats = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        all_stats.append(step())
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    cmg.cmg_ctx_set_profiling(ctx, False)
+    launches = cmg.cmg_ctx_launch_count(ctx)
+    prof = cmg.cmg_ctx_get_profile(ctx)
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    updates = sum(s["cell_updates"] for st in all_stats for s in st)
+    t_max = dev_ms
+    upd_total = updates
+    if world > 1:
+        t = torch.tensor([dev_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        u = torch.tensor([float(updates)], device=dev)
+        dist.all_reduce(u)
+        upd_total = float(u.item())
+    value = upd_total / (t_max / 1e3) / 1e6
+    st_b, st_f = all_stats[-1]
+
+    # dominant kernel family of the timed region and its roofline
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    dname, d = dom
+    achieved_tflops = d["flops"] / (d["ms"] / 1e3) / 1e12
+    achieved_gbs = d["bytes"] / (d["ms"] / 1e3) / 1e9
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm = float(peaks["hbm_gbs"])
+        hbm_src = "measured"
+    except (OSError, ValueError, KeyError):
+        hbm, hbm_src = 6800.0, "fallback"
+    fp64 = dname.endswith("fp64")
+    if fp64:
+        roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved_tflops / FP64_PEAK_TFLOPS, "kernel": dname,
+                    "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (FMA = 2)",
+                    "hbm_equivalent_gbs": achieved_gbs, "hbm_frac_of_%s" % hbm_src: achieved_gbs / hbm}
+    else:
+        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved_gbs / hbm, "kernel": dname, "peak_source": hbm_src}
+    roofline["traffic"] = traffic_for(dname)
+    roofline["launches"] = d["launches"]
+    roofline["share_of_timed_kernel_ms"] = d["ms"] / sum(v["ms"] for v in prof.values())
+
+    out = {
+        "metric": "poisson_cell_updates_per_s", "value": value, "unit": "Mcell-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "two_level_128: 128^3 periodic lognormal base (sigma 1.5, k^-2) + 1 refined level "
+                               "(rho > 8 rho_bar, %d fine octs); FP64 V(2,2) to rel. residual %g per level"
+                               % (cmg.cmg_level_n_octs(F), args.tol),
+                   "l2": "flushed before each timed step (512 MiB write)", "parallelism": "replicas" if world > 1
+                   else "single"},
+        "time_to_tol_ms": {"base": st_b["ms"], "fine": st_f["ms"]},
+        "cycles": {"base": st_b["cycles"], "fine": st_f["cycles"]},
+        "rel_residual": {"base": st_b["rel_final"], "fine": st_f["rel_final"]},
+        "setup_ms": build_ms,
+        "roofline": roofline,
+        "kernels": {k: {"launches": v["launches"], "ms": v["ms"], "GB/s": v["bytes"] / v["ms"] / 1e6,
+                        "TFLOP/s": v["flops"] / v["ms"] / 1e9} for k, v in prof.items()},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+
+    if not args.quick:
+        # mixed precision on the same workload (FP32 V-cycles, FP64 refinement)
+        for _ in range(2):
+            step(cmg.CMG_PREC_MIXED)
+        mixed_ms, mixed_upd = 0.0, 0
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sm = step(cmg.CMG_PREC_MIXED)
+            b.record(stream)
+            torch.cuda.synchronize()
+            mixed_ms += a.elapsed_time(b)
+            mixed_upd += sum(s["cell_updates"] for s in sm)
+        phi_mixed_f = cmg.cmg_level_get_phi(F)
+        step()
+        phi_fp64_f = cmg.cmg_level_get_phi(F)
+        out["mixed"] = {"ms_per_step": mixed_ms / args.steps,
+                        "Mcell_updates_per_s": mixed_upd / (mixed_ms / 1e3) / 1e6,
+                        "time_to_tol_ms": {"base": sm[0]["ms"], "fine": sm[1]["ms"]},
+                        "refinement_steps": {"base": sm[0]["cycles"], "fine": sm[1]["cycles"]},
+                        "phi_rel_diff_vs_fp64_gpu": float(np.max(np.abs(phi_mixed_f - phi_fp64_f)) /
+                                                          np.max(np.abs(phi_fp64_f)))}
+
+        # end to end through the C ABI with host buffers (pinned): H2D densities,
+        # both solves, D2H of both phi arrays
+        pin_rho = [torch.from_numpy(r).pin_memory().numpy() for r in cfg["rho"]]
+        pin_phi = [torch.empty((cmg.cmg_level_n_octs(L), 8), dtype=torch.float64).pin_memory().numpy()
+                   for L in (B, F)]
+        e2e_ms, e2e_upd = 0.0, 0
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for L, r, z, o in zip((B, F), pin_rho, zeros, pin_phi):
+                cmg.cmg_level_set_phi(L, z)  # zero initial guess, already on the device
+                cmg.cmg_level_set_density(L, r, 1.0)
+                rc, st = cmg.cmg_level_solve(L, tol=args.tol)
+                cmg.cmg_level_get_phi(L, out=o)
+                e2e_upd += st["cell_updates"]
+            e2e_ms += (time.perf_counter() - t0) * 1e3
+        h2d = sum(r.nbytes for r in pin_rho)
+        d2h = sum(o.nbytes for o in pin_phi)
+        out["e2e"] = {"value": e2e_upd * world / (e2e_ms / 1e3) / 1e6, "unit": "Mcell-updates/s",
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps}
+        if rank == 0 and world == 1:
+            out["cpu_baseline"] = cpu_baseline_sample()
+    else:
+        out["e2e"] = None
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    del B, F
+    import gc
+    gc.collect()
+    cmg.cmg_ctx_destroy(ctx)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, local, world = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, local, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -87,6 +87,25 @@ int cmg_ctx_create(int device, void *stream, cmg_ctx **out);
 int cmg_ctx_destroy(cmg_ctx *ctx);
 int cmg_ctx_synchronize(cmg_ctx *ctx);
 
+/* ---- instrumentation (no counterpart in the paper; used by the benchmark) ----
+ * With profiling on, every solver kernel launch on the context's stream is
+ * bracketed by CUDA events; cmg_ctx_get_profile synchronises the stream and
+ * returns, per kernel family, the launches, the summed event time and the
+ * algorithmic bytes / flops of those launches (the minimum traffic and
+ * arithmetic of the operation, not hardware counters). */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double ms;
+  double bytes;
+  double flops;
+} cmg_kernel_profile;
+int cmg_ctx_set_profiling(cmg_ctx *ctx, int enable);
+int cmg_ctx_get_profile(cmg_ctx *ctx, cmg_kernel_profile *out, int max_entries, int *n_entries);
+int cmg_ctx_reset_profile(cmg_ctx *ctx);
+/* Kernels this context has launched since creation or the last reset. */
+int cmg_ctx_launch_count(cmg_ctx *ctx, int64_t *launches);
+
 /* Morton keys (Sec. 4.2 Eq. (morton_encode), App. A Alg. 1; B = 21 bits per
  * coordinate): ijk is [n][3] uint32 (i, j, k), keys is [n] uint64.  Both in
  * the same memory space.  Coordinates >= 2^21 give CMG_ERR_KEY_OUT_OF_RANGE. */

@@ -40,6 +40,18 @@ def _deps():
     return files
 
 
+def source_digest():
+    """sha256 of the CUDA sources and headers (keys recorded profiler data to
+    the kernel version it was taken on)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(_deps()):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(os.path.basename(f).encode())
+            h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def up_to_date():
     if not os.path.exists(LIB):
         return False

@@ -48,6 +48,11 @@ class cmg_solve_stats(C.Structure):
                 ("rel_history", C.c_double * 256)]
 
 
+class cmg_kernel_profile(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("ms", C.c_double), ("bytes", C.c_double),
+                ("flops", C.c_double)]
+
+
 class CmgError(RuntimeError):
     def __init__(self, code, fn, msg):
         super().__init__("%s failed (status %d): %s" % (fn, code, msg))
@@ -63,6 +68,10 @@ _SIGS = {
     "cmg_ctx_create": (_I, [_I, _P, C.POINTER(_P)]),
     "cmg_ctx_destroy": (_I, [_P]),
     "cmg_ctx_synchronize": (_I, [_P]),
+    "cmg_ctx_set_profiling": (_I, [_P, _I]),
+    "cmg_ctx_get_profile": (_I, [_P, C.POINTER(cmg_kernel_profile), _I, C.POINTER(_I)]),
+    "cmg_ctx_reset_profile": (_I, [_P]),
+    "cmg_ctx_launch_count": (_I, [_P, C.POINTER(_I64)]),
     "cmg_morton_encode": (_I, [_P, _P, _I64, _P, _I]),
     "cmg_morton_decode": (_I, [_P, _P, _I64, _P, _I]),
     "cmg_level_build": (_I, [_P, _I, _I, _I, _P, _I64, _I, _P, C.POINTER(_P)]),
@@ -189,6 +198,29 @@ def cmg_ctx_destroy(ctx):
 
 def cmg_ctx_synchronize(ctx):
     _check(lib().cmg_ctx_synchronize(ctx), "cmg_ctx_synchronize")
+
+
+def cmg_ctx_set_profiling(ctx, enable):
+    _check(lib().cmg_ctx_set_profiling(ctx, int(bool(enable))), "cmg_ctx_set_profiling")
+
+
+def cmg_ctx_get_profile(ctx):
+    """{family: {"launches", "ms", "bytes", "flops"}} since the last reset."""
+    buf = (cmg_kernel_profile * 32)()
+    n = C.c_int()
+    _check(lib().cmg_ctx_get_profile(ctx, buf, 32, C.byref(n)), "cmg_ctx_get_profile")
+    return {buf[i].name.decode(): {"launches": buf[i].launches, "ms": buf[i].ms, "bytes": buf[i].bytes,
+                                   "flops": buf[i].flops} for i in range(n.value)}
+
+
+def cmg_ctx_reset_profile(ctx):
+    _check(lib().cmg_ctx_reset_profile(ctx), "cmg_ctx_reset_profile")
+
+
+def cmg_ctx_launch_count(ctx):
+    v = C.c_int64()
+    _check(lib().cmg_ctx_launch_count(ctx, C.byref(v)), "cmg_ctx_launch_count")
+    return v.value
 
 
 def cmg_morton_encode(ctx, ijk, out=None):

@@ -139,12 +139,13 @@ int cmg_ctx_destroy(cmg_ctx *ctx) {
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(ctx->device);
-  if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
   if (ctx->d_err) cudaFree(ctx->d_err);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
   if (ctx->h_dpinned) cudaFreeHost(ctx->h_dpinned);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   delete ctx;
   if (prev >= 0) cudaSetDevice(prev);
   return CMG_OK;

@@ -194,6 +194,21 @@ struct DeviceBuffers {
 
 }  // namespace cmg
 
+namespace cmg {
+enum KernelClass {
+  K_SWEEP64 = 0, K_SWEEP32, K_RESID64, K_RESID32, K_PROLONG64, K_PROLONG32, K_GHOST, K_COARSE, K_REDUCE,
+  K_CONVERT, K_NCLASS
+};
+struct ProfClass {
+  int64_t launches = 0;
+  double ms = 0.0, bytes = 0.0, flops = 0.0;
+};
+struct PendingEvent {
+  int cls;
+  int slot;
+};
+}  // namespace cmg
+
 struct cmg_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -202,7 +217,25 @@ struct cmg_ctx {
   int *h_pinned = nullptr;    // pinned staging (ints)
   double *h_dpinned = nullptr;  // pinned staging (doubles)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // instrumentation
+  int64_t launches = 0;
+  bool profiling = false;
+  cmg::ProfClass prof[cmg::K_NCLASS];
+  std::vector<cudaEvent_t> ev_pool;  // pairs (2k, 2k+1)
+  std::vector<cmg::PendingEvent> pending;
 };
+
+namespace cmg {
+// Counts a launch of family cls and, when profiling, brackets it with events.
+struct LaunchScope {
+  cmg_ctx *ctx;
+  int slot = -1;
+  LaunchScope(cmg_ctx *c, int cls, double bytes, double flops);
+  ~LaunchScope();
+};
+void harvest_profile(cmg_ctx *ctx);
+const char *kernel_class_name(int cls);
+}  // namespace cmg
 
 struct cmg_level {
   cmg_ctx *ctx = nullptr;

@@ -451,6 +451,8 @@ float *g_of<float>(MgLev &g) { return g.g32; }
 }  // namespace
 
 // ------------------------------------------------------------ launchers
+// Algorithmic work per launch (for the profile): bytes are the minimum
+// traffic of the operation, flops its floating-point operations (FMA = 2).
 
 template <typename T>
 void sweep(cmg_level *L, int m, bool zero_init) {
@@ -462,8 +464,15 @@ void sweep(cmg_level *L, int m, bool zero_init) {
   const int64_t st = g.n_alloc * 4;
   const unsigned nb = blocks_for(g.n);
   const bool mask = !g.all_active;
-#define CMG_SWEEP(P, Z, M) \
-  k_sweep<T, P, Z, M><<<nb, kThreads, 0, s>>>(g.nbr, phi + (1 - P) * st, phi + P * st, gg + P * g.n * 4, g.active, g.n)
+  const int cls = sizeof(T) == 8 ? K_SWEEP64 : K_SWEEP32;
+  const double u = 4.0 * (double)g.n;  // cells updated per colour pass
+  const double full_bytes = 3.0 * u * sizeof(T), full_flops = 7.0 * u;
+#define CMG_SWEEP(P, Z, M)                                                                                  \
+  do {                                                                                                      \
+    LaunchScope ls(L->ctx, cls, (Z) ? 2.0 * u * sizeof(T) : full_bytes, (Z) ? 0.0 : full_flops);            \
+    k_sweep<T, P, Z, M><<<nb, kThreads, 0, s>>>(g.nbr, phi + (1 - P) * st, phi + P * st, gg + P * g.n * 4, \
+                                                g.active, g.n);                                             \
+  } while (0)
   if (mask) {
     if (zero_init) CMG_SWEEP(0, true, true); else CMG_SWEEP(0, false, true);
     CMG_SWEEP(1, false, true);
@@ -488,7 +497,13 @@ void resid_restrict(cmg_level *L, int m, bool restrict_to_coarse, bool norm, boo
   T *cphi = c ? phi_of<T>(*c) : nullptr;
   const int64_t cn = c ? c->n : 0, cna = c ? c->n_alloc : 0;
   const uint8_t *act = g.all_active ? nullptr : g.active;
+  const double cells = 8.0 * (double)g.n;
+  const double bytes = cells * 2.0 * sizeof(T) + (restrict_to_coarse ? g.n * sizeof(T) : 0.0) +
+                       (emit_scale ? cells * 4.0 : 0.0);
+  const double flops = cells * (8.0 + (norm ? 2.0 : 0.0) + (restrict_to_coarse ? 1.0 : 0.0));
+  const int cls = sizeof(T) == 8 ? K_RESID64 : K_RESID32;
   if (g.n > 0) {
+    LaunchScope ls(L->ctx, cls, bytes, flops);
     if (restrict_to_coarse && !norm && !emit_scale)
       k_resid<T, false, true, false, false, false><<<nb, kThreads, 0, s>>>(
           g.nbr, phi_of<T>(g), g_of<T>(g), act, g.n, g.n_alloc, g.father, cg, cphi, cn, cna, zero_coarse_phi,
@@ -514,6 +529,7 @@ void resid_restrict(cmg_level *L, int m, bool restrict_to_coarse, bool norm, boo
     if (g.n == 0) {
       CMG_CUDA(cudaMemsetAsync(norm_out, 0, 2 * sizeof(double), s));
     } else {
+      LaunchScope ls(L->ctx, K_REDUCE, nb * 8.0, nb);
       k_finalize<<<1, 1024, 0, s>>>(L->partials, (int)nb, scale, norm_out, 1);
       CMG_CUDA(cudaGetLastError());
     }
@@ -528,6 +544,7 @@ void residual_out(cmg_level *L, int m, int prec, double *out) {
   cudaStream_t s = L->ctx->stream;
   const uint8_t *act = g.all_active ? nullptr : g.active;
   const double rscale = -6.0 / (g.h * g.h);
+  LaunchScope ls(L->ctx, prec == CMG_PREC_FP64 ? K_RESID64 : K_RESID32, 8.0 * g.n * 24.0, 8.0 * g.n * 9.0);
   if (prec == CMG_PREC_FP64)
     k_resid<double, false, false, false, true, false><<<blocks_for(g.n), kThreads, 0, s>>>(
         g.nbr, g.phi, g.g, act, g.n, g.n_alloc, nullptr, nullptr, nullptr, 0, 0, 0, nullptr, nullptr, nullptr, out,
@@ -548,10 +565,16 @@ void zero_phi_norm(cmg_level *L, double *out) {
     CMG_CUDA(cudaMemsetAsync(out, 0, 2 * sizeof(double), s));
     return;
   }
-  k_resid<double, true, false, false, false, true><<<nb, kThreads, 0, s>>>(
-      g.nbr, g.phi, g.g, nullptr, g.n, g.n_alloc, nullptr, nullptr, nullptr, 0, 0, 0, L->partials, nullptr, nullptr,
-      nullptr, 0.0);
-  k_finalize<<<1, 1024, 0, s>>>(L->partials, (int)nb, 36.0 / (g.h * g.h * g.h * g.h), out, 1);
+  {
+    LaunchScope ls(L->ctx, K_RESID64, 8.0 * g.n * 8.0, 8.0 * g.n * 9.0);
+    k_resid<double, true, false, false, false, true><<<nb, kThreads, 0, s>>>(
+        g.nbr, g.phi, g.g, nullptr, g.n, g.n_alloc, nullptr, nullptr, nullptr, 0, 0, 0, L->partials, nullptr,
+        nullptr, nullptr, 0.0);
+  }
+  {
+    LaunchScope ls(L->ctx, K_REDUCE, nb * 8.0, nb);
+    k_finalize<<<1, 1024, 0, s>>>(L->partials, (int)nb, 36.0 / (g.h * g.h * g.h * g.h), out, 1);
+  }
   CMG_CUDA(cudaGetLastError());
 }
 
@@ -561,6 +584,8 @@ void prolong(cmg_level *L, int m) {
   MgLev &c = L->mg[m + 1];
   if (g.n == 0) return;
   cudaStream_t s = L->ctx->stream;
+  LaunchScope ls(L->ctx, sizeof(T) == 8 ? K_PROLONG64 : K_PROLONG32,
+                 g.n * 17.0 * sizeof(T), g.n * 128.0);
   if (g.all_active)
     k_prolong<T, false><<<blocks_for(g.n), kThreads, 0, s>>>(g.keys, g.blk, g.n, g.n_alloc, phi_of<T>(g), g.active,
                                                              phi_of<T>(c), c.n_alloc);
@@ -576,6 +601,7 @@ void fill_ghosts(cmg_level *L) {
   MgLev &g = L->mg[0];
   if (!L->parent || g.n_ghost == 0) return;
   MgLev &pg = L->parent->mg[0];
+  LaunchScope ls(L->ctx, K_GHOST, g.n_ghost * (64.0 + 8.0 + 32.0 + 4.0), g.n_ghost * 120.0);
   k_ghost_fill<<<blocks_for(g.n_ghost), kThreads, 0, L->ctx->stream>>>(
       L->ghost_keys, L->ghost_blk, L->ghost_mask, g.n_ghost, g.n, g.n_alloc, g.phi, pg.phi, pg.n_alloc);
   CMG_CUDA(cudaGetLastError());
@@ -584,6 +610,7 @@ void fill_ghosts(cmg_level *L) {
 void get_ghosts(cmg_level *L, double *out) {
   MgLev &g = L->mg[0];
   if (g.n == 0) return;
+  LaunchScope ls(L->ctx, K_CONVERT, g.n * 24.0 * 8.0, 0.0);
   k_get_ghosts<<<blocks_for(g.n), kThreads, 0, L->ctx->stream>>>(g.nbr, g.n, g.n_ghost, g.n_alloc, g.phi, out);
   CMG_CUDA(cudaGetLastError());
 }
@@ -593,6 +620,7 @@ void coarse_solve(cmg_level *L, int prec, int coarse_sweeps) {
   MgLev &g = L->mg[m];
   cudaStream_t s = L->ctx->stream;
   if (L->exact_coarse) {
+    LaunchScope ls(L->ctx, K_COARSE, 128.0, 256.0);
     if (prec == CMG_PREC_FP64)
       k_wht<double><<<1, 32, 0, s>>>(g.g, g.phi, g.n_alloc, g.h);
     else
@@ -606,11 +634,20 @@ void coarse_solve(cmg_level *L, int prec, int coarse_sweeps) {
   }
   // mixed: the coarsest level is solved in FP64 on FP64 copies
   const int64_t mg = 8 * g.n, ma = 8 * g.n_alloc;
-  k_copy_convert_f2d<<<blocks_for(mg), kThreads, 0, s>>>(g.g32, g.g, mg);
-  k_copy_convert_f2d<<<blocks_for(ma), kThreads, 0, s>>>(g.phi32, g.phi, ma);
+  {
+    LaunchScope ls(L->ctx, K_CONVERT, 12.0 * (mg + ma), 0.0);
+    k_copy_convert_f2d<<<blocks_for(mg), kThreads, 0, s>>>(g.g32, g.g, mg);
+  }
+  {
+    LaunchScope ls(L->ctx, K_CONVERT, 12.0 * ma, 0.0);
+    k_copy_convert_f2d<<<blocks_for(ma), kThreads, 0, s>>>(g.phi32, g.phi, ma);
+  }
   CMG_CUDA(cudaGetLastError());
   for (int k = 0; k < coarse_sweeps; ++k) sweep<double>(L, m, k == 0 && m > 0);
-  k_copy_convert_d2f<<<blocks_for(ma), kThreads, 0, s>>>(g.phi, g.phi32, ma);
+  {
+    LaunchScope ls(L->ctx, K_CONVERT, 12.0 * ma, 0.0);
+    k_copy_convert_d2f<<<blocks_for(ma), kThreads, 0, s>>>(g.phi, g.phi32, ma);
+  }
   CMG_CUDA(cudaGetLastError());
 }
 
@@ -619,15 +656,25 @@ void subtract_mean(cmg_level *L) {
   if (g.n == 0) return;
   cudaStream_t s = L->ctx->stream;
   const unsigned nb = blocks_for(g.n);
-  k_sum_phi<<<nb, kThreads, 0, s>>>(g.phi, g.n, g.n_alloc, L->partials);
-  k_finalize<<<1, 1024, 0, s>>>(L->partials, (int)nb, 1.0 / (8.0 * (double)g.n), L->scal + 6, 0);
-  k_sub_scalar<<<blocks_for(8 * g.n), kThreads, 0, s>>>(g.phi, g.n, g.n_alloc, L->scal + 6);
+  {
+    LaunchScope ls(L->ctx, K_REDUCE, 64.0 * g.n, 8.0 * g.n);
+    k_sum_phi<<<nb, kThreads, 0, s>>>(g.phi, g.n, g.n_alloc, L->partials);
+  }
+  {
+    LaunchScope ls(L->ctx, K_REDUCE, nb * 8.0, nb);
+    k_finalize<<<1, 1024, 0, s>>>(L->partials, (int)nb, 1.0 / (8.0 * (double)g.n), L->scal + 6, 0);
+  }
+  {
+    LaunchScope ls(L->ctx, K_CONVERT, 128.0 * g.n, 8.0 * g.n);
+    k_sub_scalar<<<blocks_for(8 * g.n), kThreads, 0, s>>>(g.phi, g.n, g.n_alloc, L->scal + 6);
+  }
   CMG_CUDA(cudaGetLastError());
 }
 
 void accumulate(cmg_level *L, const double *scale) {
   MgLev &g = L->mg[0];
   if (g.n == 0) return;
+  LaunchScope ls(L->ctx, K_CONVERT, g.n * 8.0 * (16.0 + 4.0), g.n * 16.0);
   k_accumulate<<<blocks_for(2 * g.n), kThreads, 0, L->ctx->stream>>>(g.phi, g.phi32, g.n, g.n_alloc, scale);
   CMG_CUDA(cudaGetLastError());
 }
@@ -636,6 +683,7 @@ void set_density(cmg_level *L, const double *rho, double rho_bar, double four_pi
   MgLev &g = L->mg[0];
   if (g.n == 0) return;
   const double scale = -g.h * g.h / 6.0 * four_pi_g;
+  LaunchScope ls(L->ctx, K_CONVERT, g.n * 8.0 * 16.0, g.n * 16.0);
   k_set_density<<<blocks_for(8 * g.n), kThreads, 0, L->ctx->stream>>>(rho, g.n, rho_bar, scale, g.g);
   CMG_CUDA(cudaGetLastError());
 }
@@ -657,6 +705,7 @@ void pack_field(cmg_level *L, int m, int field, int prec, const void *in) {
   const double scale = field == 0 ? 1.0 : -g.h * g.h / 6.0;
   const int64_t stride = field == 0 ? g.n_alloc : g.n;
   const unsigned nb = blocks_for(8 * g.n);
+  LaunchScope ls(L->ctx, K_CONVERT, g.n * 8.0 * 2.0 * (prec == CMG_PREC_FP64 ? 8.0 : 4.0), 0.0);
   if (prec == CMG_PREC_FP64)
     k_pack<double, double><<<nb, kThreads, 0, s>>>((const double *)in, g.n, stride, scale, field == 0 ? g.phi : g.g);
   else
@@ -671,6 +720,7 @@ void unpack_field(cmg_level *L, int m, int field, int prec, void *out) {
   const double scale = field == 0 ? 1.0 : -6.0 / (g.h * g.h);
   const int64_t stride = field == 0 ? g.n_alloc : g.n;
   const unsigned nb = blocks_for(8 * g.n);
+  LaunchScope ls(L->ctx, K_CONVERT, g.n * 8.0 * 2.0 * (prec == CMG_PREC_FP64 ? 8.0 : 4.0), 0.0);
   if (prec == CMG_PREC_FP64)
     k_unpack<double, double><<<nb, kThreads, 0, s>>>(field == 0 ? g.phi : g.g, g.n, stride, scale, (double *)out);
   else
