@@ -146,6 +146,8 @@ int cmg_ctx_destroy(cmg_ctx *ctx) {
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->cap_stream2) cudaStreamDestroy(ctx->cap_stream2);
   delete ctx;
   if (prev >= 0) cudaSetDevice(prev);
   return CMG_OK;
@@ -242,6 +244,8 @@ int cmg_level_destroy(cmg_level *lvl) {
   cudaGetDevice(&prev);
   cudaSetDevice(lvl->ctx->device);
   cudaStreamSynchronize(lvl->ctx->stream);
+  cmg::destroy_graphs(lvl);
+  if (lvl->h_ctrl) cudaFreeHost(lvl->h_ctrl);
   lvl->mem.release();
   delete lvl;
   if (prev >= 0) cudaSetDevice(prev);

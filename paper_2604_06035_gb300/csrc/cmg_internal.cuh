@@ -217,6 +217,10 @@ struct cmg_ctx {
   int *h_pinned = nullptr;    // pinned staging (ints)
   double *h_dpinned = nullptr;  // pinned staging (doubles)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // graph capture (private streams; the caller's stream may be the legacy one)
+  cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
+  bool capturing = false;
+  int64_t captured = 0;  // kernels recorded into the graph being built
   // instrumentation
   int64_t launches = 0;
   bool profiling = false;
@@ -253,6 +257,9 @@ struct cmg_level {
   double *partials = nullptr;  // [blocks of the largest MG level]
   double *scal = nullptr;      // device scalars (norms, scales)
   double *rbuf = nullptr;      // [n][8] residual for the API (lazy)
+  uint8_t *ctrl = nullptr;     // device solve control block (cycles, status, history)
+  void *h_ctrl = nullptr;      // pinned host copy
+  std::vector<void *> graphs;  // instantiated solve graphs, keyed by parameters
   bool has32 = false;
   cmg::DeviceBuffers mem;
 };
@@ -301,5 +308,6 @@ void finalize_norm(cmg_level *L, int n_partials, double scale, double *out);
 
 // solve.cu
 int solve(cmg_level *L, const cmg_solve_params *p, cmg_solve_stats *st);
+void destroy_graphs(cmg_level *L);
 
 }  // namespace cmg

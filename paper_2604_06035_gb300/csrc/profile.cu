@@ -27,6 +27,10 @@ void harvest_profile(cmg_ctx *ctx) {
 }
 
 LaunchScope::LaunchScope(cmg_ctx *c, int cls, double bytes, double flops) : ctx(c) {
+  if (ctx->capturing) {  // counted per replay by the solver
+    ctx->captured += 1;
+    return;
+  }
   ctx->launches += 1;
   if (!ctx->profiling) return;
   if (ctx->ev_pool.empty()) {

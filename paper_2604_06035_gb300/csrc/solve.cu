@@ -1,12 +1,105 @@
 // solve.cu -- the level solve: V-cycles (App. G Alg. (vcycle), one GPU, no
 // halo exchanges) iterated to a relative residual, in FP64 or as FP32
 // V-cycles inside FP64 iterative refinement.
+//
+// The whole solve is one CUDA graph: set-up kernels, then a conditional
+// WHILE node whose body is one V-cycle plus the residual norm and a check
+// kernel that decides on the device whether to run another cycle, then the
+// periodic mean removal and a copy of the statistics to pinned host memory.
+// The host waits once per solve.  With profiling on, the same kernels are
+// launched one by one from a host loop instead (conditional bodies cannot
+// hold event nodes), so that every launch can be bracketed by CUDA events.
 #include <cmath>
 
 #include "cmg_internal.cuh"
 
 namespace cmg {
+
+struct SolveCtrl {
+  double n0sq, rel_initial, rel_final, blowup;
+  int cycles, status, zero, go;
+  double hist[256];
+};
+
+struct CachedGraph {
+  cmg_solve_params p;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches_pre = 0, launches_body = 0, launches_post = 0;
+  int64_t updates_per_cycle = 0;
+};
+
 namespace {
+
+__global__ void k_copy_scalar(double *dst, const double *src) { *dst = *src; }
+
+__device__ void decide(SolveCtrl *c, double tol, int fixed, int maxc, cudaGraphConditionalHandle h,
+                       int use_handle) {
+  int go;
+  const double rel = c->rel_final;
+  if (!(rel == rel) || rel > c->blowup || isinf(rel)) {
+    c->status = CMG_ERR_DIVERGED;
+    go = 0;
+  } else if (fixed > 0) {
+    c->status = CMG_OK;
+    go = c->cycles < fixed;
+  } else if (rel <= tol) {
+    c->status = CMG_OK;
+    go = 0;
+  } else {
+    c->status = CMG_ERR_NOT_CONVERGED;
+    go = c->cycles < maxc;
+  }
+  c->go = go;
+  if (use_handle) cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// scal: [0] ||f - L0||^2, [2] ||r||^2 of the initial guess
+__global__ void k_ctrl_init(SolveCtrl *c, const double *scal, double tol, int fixed, int maxc,
+                            cudaGraphConditionalHandle h, int use_handle) {
+  const double n0sq = scal[0];
+  c->n0sq = n0sq;
+  c->cycles = 0;
+  if (n0sq == 0.0) {
+    c->zero = 1;
+    c->status = CMG_OK;
+    c->rel_initial = c->rel_final = 0.0;
+    c->blowup = 0.0;
+    c->go = 0;
+    if (use_handle) cudaGraphSetConditional(h, 0u);
+    return;
+  }
+  c->zero = 0;
+  const double rel = sqrt(scal[2] / n0sq);
+  c->rel_initial = rel;
+  c->rel_final = rel;
+  c->blowup = 1e3 * (rel > 1.0 ? rel : 1.0);
+  if (fixed > 0) {
+    c->status = CMG_OK;
+    c->go = 1;
+    if (use_handle) cudaGraphSetConditional(h, 1u);
+    return;
+  }
+  decide(c, tol, 0, maxc, h, use_handle);
+}
+
+__global__ void k_ctrl_check(SolveCtrl *c, const double *scal, double tol, int fixed, int maxc,
+                             cudaGraphConditionalHandle h, int use_handle) {
+  const double rel = sqrt(scal[2] / c->n0sq);
+  const int k = c->cycles;
+  if (k < 256) c->hist[k] = rel;
+  c->cycles = k + 1;
+  c->rel_final = rel;
+  decide(c, tol, fixed, maxc, h, use_handle);
+}
+
+__global__ void k_zero_if(const SolveCtrl *c, double *phi, int64_t n, int64_t n_alloc) {
+  if (!c->zero) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= 8 * n) return;
+  const int p = (int)((t >> 2) & 1);
+  phi[(p * n_alloc + (t >> 3)) * 4 + (t & 3)] = 0.0;
+}
 
 // Coarse phi must start at zero unless the next operation on it overwrites
 // it without reading it (first sweep in zero-init mode, or the exact solve).
@@ -33,13 +126,174 @@ void vcycle(cmg_level *L, int m, const cmg_solve_params *p, bool zero_top, int64
   *updates += (int64_t)(p->n_pre + p->n_post) * 8 * L->mg[m].n;
 }
 
-double read_scalar(cmg_level *L, const double *d) {
-  CMG_CUDA(cudaMemcpyAsync(L->ctx->h_dpinned, d, sizeof(double), cudaMemcpyDeviceToHost, L->ctx->stream));
-  CMG_CUDA(cudaStreamSynchronize(L->ctx->stream));
-  return L->ctx->h_dpinned[0];
+SolveCtrl *ctrl_dev(cmg_level *L) { return reinterpret_cast<SolveCtrl *>(L->ctrl); }
+
+// Set-up: ghosts, ||f - L0||, initial residual (and, in mixed mode, the
+// first FP32 right-hand side), control block.
+void segment_pre(cmg_level *L, const cmg_solve_params *p, cudaGraphConditionalHandle h, int use_handle) {
+  cudaStream_t s = L->ctx->stream;
+  double *scal = L->scal;
+  fill_ghosts(L);
+  zero_phi_norm(L, scal + 0);
+  if (p->precision == CMG_PREC_MIXED) {
+    LaunchScope ls(L->ctx, K_REDUCE, 16.0, 0.0);
+    k_copy_scalar<<<1, 1, 0, s>>>(scal + 4, scal + 1);
+    CMG_CUDA(cudaGetLastError());
+    resid_restrict<double>(L, 0, false, true, false, scal + 2, scal + 4);
+  } else {
+    resid_restrict<double>(L, 0, false, true, false, scal + 2);
+  }
+  LaunchScope ls(L->ctx, K_REDUCE, 64.0, 0.0);
+  k_ctrl_init<<<1, 1, 0, s>>>(ctrl_dev(L), scal, p->tol, p->fixed_cycles, p->max_cycles, h, use_handle);
+  CMG_CUDA(cudaGetLastError());
+}
+
+// One iteration: a V-cycle (FP64) or an FP32 V-cycle + FP64 accumulation
+// (mixed), then the FP64 residual norm and the check.
+void segment_body(cmg_level *L, const cmg_solve_params *p, cudaGraphConditionalHandle h, int use_handle,
+                  int64_t *updates) {
+  cudaStream_t s = L->ctx->stream;
+  double *scal = L->scal;
+  if (p->precision == CMG_PREC_FP64) {
+    vcycle<double>(L, 0, p, false, updates);
+    resid_restrict<double>(L, 0, false, true, false, scal + 2);
+  } else {
+    MgLev &g = L->mg[0];
+    if (p->n_pre == 0) {
+      CMG_CUDA(cudaMemsetAsync(g.phi32, 0, sizeof(float) * 4 * g.n, s));
+      CMG_CUDA(cudaMemsetAsync(g.phi32 + 4 * g.n_alloc, 0, sizeof(float) * 4 * g.n, s));
+    }
+    for (int k = 0; k < p->inner_cycles; ++k) vcycle<float>(L, 0, p, k == 0, updates);
+    accumulate(L, scal + 4);
+    {
+      LaunchScope ls(L->ctx, K_REDUCE, 16.0, 0.0);
+      k_copy_scalar<<<1, 1, 0, s>>>(scal + 4, scal + 3);
+    }
+    resid_restrict<double>(L, 0, false, true, false, scal + 2, scal + 4);
+  }
+  LaunchScope ls(L->ctx, K_REDUCE, 64.0, 0.0);
+  k_ctrl_check<<<1, 1, 0, s>>>(ctrl_dev(L), scal, p->tol, p->fixed_cycles, p->max_cycles, h, use_handle);
+  CMG_CUDA(cudaGetLastError());
+}
+
+void segment_post(cmg_level *L) {
+  MgLev &g = L->mg[0];
+  {
+    LaunchScope ls(L->ctx, K_CONVERT, 0.0, 0.0);
+    k_zero_if<<<blocks_for(8 * g.n), kThreads, 0, L->ctx->stream>>>(ctrl_dev(L), g.phi, g.n, g.n_alloc);
+    CMG_CUDA(cudaGetLastError());
+  }
+  if (L->periodic_full) subtract_mean(L);
+}
+
+void copy_ctrl_to_host(cmg_level *L) {
+  CMG_CUDA(cudaMemcpyAsync(L->h_ctrl, L->ctrl, sizeof(SolveCtrl), cudaMemcpyDeviceToHost, L->ctx->stream));
+}
+
+void fill_stats(cmg_level *L, cmg_solve_stats &S, int64_t updates_per_cycle) {
+  const SolveCtrl &c = *reinterpret_cast<const SolveCtrl *>(L->h_ctrl);
+  S.cycles = c.cycles;
+  S.status = c.status;
+  S.rel_initial = c.rel_initial;
+  S.rel_final = c.rel_final;
+  S.norm0 = std::sqrt(c.n0sq);
+  for (int k = 0; k < c.cycles && k < 256; ++k) S.rel_history[k] = c.hist[k];
+  S.cell_updates = updates_per_cycle * c.cycles;
+}
+
+bool same_params(const cmg_solve_params &a, const cmg_solve_params &b) {
+  return a.tol == b.tol && a.max_cycles == b.max_cycles && a.n_pre == b.n_pre && a.n_post == b.n_post &&
+         a.coarse_sweeps == b.coarse_sweeps && a.fixed_cycles == b.fixed_cycles && a.precision == b.precision &&
+         a.inner_cycles == b.inner_cycles;
+}
+
+// Records the solve into a graph on a private stream (capture on the
+// caller's stream is impossible when it is the legacy default stream).
+CachedGraph *build_graph(cmg_level *L, const cmg_solve_params *p) {
+  cmg_ctx *ctx = L->ctx;
+  if (!ctx->cap_stream) {
+    CMG_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    CMG_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream2, cudaStreamNonBlocking));
+  }
+  auto *cg = new CachedGraph();
+  cg->p = *p;
+  cudaStream_t user = ctx->stream;
+  CMG_CUDA(cudaGraphCreate(&cg->graph, 0));
+  cudaGraphConditionalHandle h;
+  CMG_CUDA(cudaGraphConditionalHandleCreate(&h, cg->graph, 0, cudaGraphCondAssignDefault));
+  ctx->capturing = true;
+  try {
+    ctx->stream = ctx->cap_stream;
+    CMG_CUDA(cudaStreamBeginCaptureToGraph(ctx->stream, cg->graph, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeRelaxed));
+    ctx->captured = 0;
+    segment_pre(L, p, h, 1);
+    cg->launches_pre = ctx->captured;
+    // conditional WHILE node after everything captured so far
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    cudaGraph_t capg = nullptr;
+    CMG_CUDA(cudaStreamGetCaptureInfo(ctx->stream, &st, nullptr, &capg, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t cond;
+    CMG_CUDA(cudaGraphAddNode(&cond, capg, deps, nullptr, ndeps, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    CMG_CUDA(cudaStreamUpdateCaptureDependencies(ctx->stream, &cond, nullptr, 1, cudaStreamSetCaptureDependencies));
+    // body, captured on the second private stream
+    cudaStream_t main_cap = ctx->stream;
+    ctx->stream = ctx->cap_stream2;
+    CMG_CUDA(cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    ctx->captured = 0;
+    segment_body(L, p, h, 1, &cg->updates_per_cycle);
+    cg->launches_body = ctx->captured;
+    cudaGraph_t body_out = nullptr;
+    CMG_CUDA(cudaStreamEndCapture(ctx->stream, &body_out));
+    ctx->stream = main_cap;
+    ctx->captured = 0;
+    segment_post(L);
+    copy_ctrl_to_host(L);
+    cg->launches_post = ctx->captured;
+    cudaGraph_t out = nullptr;
+    CMG_CUDA(cudaStreamEndCapture(ctx->stream, &out));
+    CMG_CUDA(cudaGraphInstantiate(&cg->exec, cg->graph, 0));
+  } catch (...) {
+    cudaStreamCaptureStatus st;
+    if (cudaStreamIsCapturing(ctx->cap_stream2, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+      cudaGraph_t g;
+      cudaStreamEndCapture(ctx->cap_stream2, &g);
+    }
+    if (cudaStreamIsCapturing(ctx->cap_stream, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+      cudaGraph_t g;
+      cudaStreamEndCapture(ctx->cap_stream, &g);
+    }
+    cudaGetLastError();
+    ctx->stream = user;
+    ctx->capturing = false;
+    if (cg->graph) cudaGraphDestroy(cg->graph);
+    delete cg;
+    throw;
+  }
+  ctx->stream = user;
+  ctx->capturing = false;
+  return cg;
 }
 
 }  // namespace
+
+void destroy_graphs(cmg_level *L) {
+  for (void *v : L->graphs) {
+    auto *cg = static_cast<CachedGraph *>(v);
+    if (cg->exec) cudaGraphExecDestroy(cg->exec);
+    if (cg->graph) cudaGraphDestroy(cg->graph);
+    delete cg;
+  }
+  L->graphs.clear();
+}
 
 int solve(cmg_level *L, const cmg_solve_params *p, cmg_solve_stats *st) {
   if (!p || p->n_pre < 0 || p->n_post < 0 || p->coarse_sweeps < 0 || p->max_cycles < 0 || p->max_cycles > 256 ||
@@ -55,74 +309,56 @@ int solve(cmg_level *L, const cmg_solve_params *p, cmg_solve_stats *st) {
   cmg_solve_stats &S = st ? *st : local;
   S = cmg_solve_stats{};
   cmg_ctx *ctx = L->ctx;
-  cudaStream_t s = ctx->stream;
-  double *scal = L->scal;  // [0,1] norm0^2, norm0; [2,3] norm^2, norm; [4] emit scale; [6] mean
-  CMG_CUDA(cudaEventRecord(ctx->ev0, s));
-
-  fill_ghosts(L);
-  zero_phi_norm(L, scal + 0);
-  const double n0sq = read_scalar(L, scal + 0);
-  S.norm0 = std::sqrt(n0sq);
-  int status = CMG_OK;
-  if (n0sq == 0.0) {
-    MgLev &g = L->mg[0];
-    CMG_CUDA(cudaMemsetAsync(g.phi, 0, sizeof(double) * 4 * g.n, s));
-    CMG_CUDA(cudaMemsetAsync(g.phi + 4 * g.n_alloc, 0, sizeof(double) * 4 * g.n, s));
-  } else {
-    const bool mixed = p->precision == CMG_PREC_MIXED;
-    if (mixed) {
-      ensure_fp32(L);
-      CMG_CUDA(cudaMemcpyAsync(scal + 4, scal + 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
-      resid_restrict<double>(L, 0, false, true, false, scal + 2, scal + 4);
-    } else {
-      resid_restrict<double>(L, 0, false, true, false, scal + 2);
-    }
-    double rel = std::sqrt(read_scalar(L, scal + 2) / n0sq);
-    S.rel_initial = rel;
-    S.rel_final = rel;
-    const int target = p->fixed_cycles > 0 ? p->fixed_cycles : p->max_cycles;
-    const double blowup = 1e3 * (S.rel_initial > 1.0 ? S.rel_initial : 1.0);
-    bool done = p->fixed_cycles == 0 && rel <= p->tol;
-    status = done ? CMG_OK : CMG_ERR_NOT_CONVERGED;
-    for (int cyc = 1; cyc <= target && !done; ++cyc) {
-      if (!mixed) {
-        vcycle<double>(L, 0, p, false, &S.cell_updates);
-        resid_restrict<double>(L, 0, false, true, false, scal + 2);
-      } else {
-        MgLev &g = L->mg[0];
-        if (p->n_pre == 0) {
-          CMG_CUDA(cudaMemsetAsync(g.phi32, 0, sizeof(float) * 4 * g.n, s));
-          CMG_CUDA(cudaMemsetAsync(g.phi32 + 4 * g.n_alloc, 0, sizeof(float) * 4 * g.n, s));
-        }
-        for (int k = 0; k < p->inner_cycles; ++k) vcycle<float>(L, 0, p, k == 0, &S.cell_updates);
-        accumulate(L, scal + 4);
-        CMG_CUDA(cudaMemcpyAsync(scal + 4, scal + 3, sizeof(double), cudaMemcpyDeviceToDevice, s));
-        resid_restrict<double>(L, 0, false, true, false, scal + 2, scal + 4);
-      }
-      rel = std::sqrt(read_scalar(L, scal + 2) / n0sq);
-      S.cycles = cyc;
-      S.rel_history[cyc - 1] = rel;
-      S.rel_final = rel;
-      if (!std::isfinite(rel) || rel > blowup) {
-        status = CMG_ERR_DIVERGED;
-        break;
-      }
-      if (p->fixed_cycles > 0) {
-        status = CMG_OK;
-      } else if (rel <= p->tol) {
-        status = CMG_OK;
-        done = true;
-      }
-    }
-    if (L->periodic_full) subtract_mean(L);
+  if (p->precision == CMG_PREC_MIXED) ensure_fp32(L);
+  if (!L->ctrl) {
+    L->ctrl = L->mem.alloc<uint8_t>(sizeof(SolveCtrl), true, ctx->stream);
+    CMG_CUDA(cudaMallocHost(&L->h_ctrl, sizeof(SolveCtrl)));
   }
-  CMG_CUDA(cudaEventRecord(ctx->ev1, s));
-  CMG_CUDA(cudaEventSynchronize(ctx->ev1));
+  if (L->n == 0) {
+    S.status = CMG_OK;
+    return CMG_OK;
+  }
+  CMG_CUDA(cudaEventRecord(ctx->ev0, ctx->stream));
+  int64_t updates_per_cycle = 0;
+  if (!ctx->profiling) {
+    CachedGraph *cg = nullptr;
+    for (void *v : L->graphs)
+      if (same_params(static_cast<CachedGraph *>(v)->p, *p)) cg = static_cast<CachedGraph *>(v);
+    if (!cg) {
+      if (L->graphs.size() >= 4) destroy_graphs(L);
+      cg = build_graph(L, p);
+      L->graphs.push_back(cg);
+    }
+    CMG_CUDA(cudaGraphLaunch(cg->exec, ctx->stream));
+    CMG_CUDA(cudaEventRecord(ctx->ev1, ctx->stream));
+    CMG_CUDA(cudaEventSynchronize(ctx->ev1));
+    const SolveCtrl &c = *reinterpret_cast<const SolveCtrl *>(L->h_ctrl);
+    ctx->launches += cg->launches_pre + cg->launches_post + (int64_t)c.cycles * cg->launches_body;
+    updates_per_cycle = cg->updates_per_cycle;
+  } else {
+    // host-driven loop, every launch visible to the profiler
+    cudaGraphConditionalHandle none{};
+    segment_pre(L, p, none, 0);
+    copy_ctrl_to_host(L);
+    CMG_CUDA(cudaStreamSynchronize(ctx->stream));
+    const SolveCtrl &c = *reinterpret_cast<const SolveCtrl *>(L->h_ctrl);
+    while (c.go) {
+      int64_t u = 0;
+      segment_body(L, p, none, 0, &u);
+      updates_per_cycle = u;
+      copy_ctrl_to_host(L);
+      CMG_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    segment_post(L);
+    copy_ctrl_to_host(L);
+    CMG_CUDA(cudaEventRecord(ctx->ev1, ctx->stream));
+    CMG_CUDA(cudaEventSynchronize(ctx->ev1));
+  }
+  fill_stats(L, S, updates_per_cycle);
   float ms = 0.f;
   CMG_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
   S.ms = ms;
-  S.status = status;
-  return status;
+  return S.status;
 }
 
 }  // namespace cmg

@@ -224,8 +224,11 @@ def test_restrict_prolong_coarse_parity(cmg, two5, which):
         cmg.cmg_level_mg_step(G, m, cmg.CMG_OP_RESTRICT)
         R.residual(m, use_ghost=(m == 0))
         R.restrict(m)
+        # only active coarse cells carry a restricted residual (inactive ones
+        # are never read)
+        cact = R.mg_active(m + 1).astype(bool)
         cf = cmg.cmg_level_mg_get(G, m + 1, cmg.CMG_FIELD_F)
-        assert relerr(cf, R.mg_get(m + 1, "f")) <= 1e-11, m
+        assert relerr(cf[cact], R.mg_get(m + 1, "f")[cact]) <= 1e-11, m
         assert np.all(cmg.cmg_level_mg_get(G, m + 1, cmg.CMG_FIELD_PHI) == 0.0)
         cact = R.mg_active(m + 1).astype(bool)
         e = rng.standard_normal((R.mg_n_octs(m + 1), 8))
