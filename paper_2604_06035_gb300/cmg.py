@@ -189,11 +189,39 @@ def cmg_ctx_create(device=0, stream=None):
         stream = stream.cuda_stream
     h = C.c_void_p()
     _check(lib().cmg_ctx_create(device, C.c_void_p(stream), C.byref(h)), "cmg_ctx_create")
-    return h
+    return CtxHandle(h)
+
+
+class CtxHandle:
+    """Owns a cmg_ctx* and tracks the levels built on it, so that destroying
+    the context first destroys whatever levels are still alive (finest first)."""
+
+    def __init__(self, h):
+        self.h = h
+        self.levels = []  # weak references, in build order
+
+    @property
+    def _as_parameter_(self):
+        if not self.h:
+            raise CmgError(CMG_ERR_INVALID_ARG, "cmg", "context already destroyed")
+        return self.h
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            cmg_ctx_destroy(self)
 
 
 def cmg_ctx_destroy(ctx):
-    _check(lib().cmg_ctx_destroy(ctx), "cmg_ctx_destroy")
+    import weakref  # noqa: F401
+    if not ctx.h:
+        return
+    for ref in reversed(ctx.levels):
+        lv = ref()
+        if lv is not None and lv.h:
+            cmg_level_destroy(lv)
+    ctx.levels = []
+    h, ctx.h = ctx.h, None
+    _check(lib().cmg_ctx_destroy(h), "cmg_ctx_destroy")
 
 
 def cmg_ctx_synchronize(ctx):
@@ -245,14 +273,16 @@ class LevelHandle:
     """Owns a cmg_level* (destroyed with the object) and keeps its parent alive."""
 
     def __init__(self, h, parent, ctx):
+        import weakref
         self.h = h
         self.parent = parent
         self.ctx = ctx
+        ctx.levels.append(weakref.ref(self))
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:
-            _lib.cmg_level_destroy(self.h)
-            self.h = None
+            h, self.h = self.h, None
+            _lib.cmg_level_destroy(h)
 
     @property
     def _as_parameter_(self):
@@ -397,3 +427,4 @@ def cmg_level_mg_step(lvl, m, op, precision=CMG_PREC_FP64, n=1):
     v = C.c_double(0.0)
     _check(lib().cmg_level_mg_step(lvl.h, m, op, precision, n, C.byref(v)), "cmg_level_mg_step")
     return v.value
+

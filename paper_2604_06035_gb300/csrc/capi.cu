@@ -215,6 +215,8 @@ int cmg_level_build(cmg_ctx *ctx, int level, int nx, int periodic_mask, const ui
     DeviceScope ds(ctx->device);
     cmg_level *L = new cmg_level();
     L->ctx = ctx;
+    L->device = ctx->device;
+    L->stream = ctx->stream;
     L->lev = level;
     L->nx = nx;
     L->pmask = periodic_mask;
@@ -242,8 +244,8 @@ int cmg_level_destroy(cmg_level *lvl) {
   if (!lvl) return CMG_OK;
   int prev = -1;
   cudaGetDevice(&prev);
-  cudaSetDevice(lvl->ctx->device);
-  cudaStreamSynchronize(lvl->ctx->stream);
+  cudaSetDevice(lvl->device);  // the level's own copies: no use of its context
+  cudaStreamSynchronize(lvl->stream);
   cmg::destroy_graphs(lvl);
   if (lvl->h_ctrl) cudaFreeHost(lvl->h_ctrl);
   lvl->mem.release();

@@ -243,6 +243,8 @@ const char *kernel_class_name(int cls);
 
 struct cmg_level {
   cmg_ctx *ctx = nullptr;
+  int device = 0;                // copies of the context's device and stream, so
+  cudaStream_t stream = nullptr; // that destroying a level never reads its context
   int lev = 0, nx = 1, pmask = 7;
   int64_t n = 0;
   cmg_level *parent = nullptr;
