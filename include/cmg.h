@@ -180,6 +180,33 @@ typedef enum {
 } cmg_op;
 int cmg_level_mg_step(cmg_level *lvl, int m, int op, int precision, int n, double *norm2);
 
+/* ---- residual norm without allocation (the paper has no counterpart) ----
+ * The level objects above allocate device memory when they are built, and
+ * their residual norm reduces through scratch the level owns.  Callers that
+ * cannot allocate when they need a residual check -- code running while a
+ * CUDA graph is being captured (cudaMalloc cannot be captured), real-time
+ * loops that forbid allocation after start-up, hosts whose device memory is a
+ * fixed arena of their own -- can use this entry point: it allocates nothing
+ * and reduces through a fixed scratch array compiled into the library
+ * (512 KiB, held by every GPU that loads the library until the process exits).
+ *
+ * Computes *norm2 = sum over cells of r^2, r = f - (sum_6 phi_nb - 6 phi) / h^2
+ * (the residual of Sec. 5.1.1 item (iii)), on the current device, on `stream`
+ * (a cudaStream_t, NULL = legacy default stream).  All pointers are DEVICE
+ * memory owned by the caller, in the public layouts: neighbors [n][7] as
+ * cmg_level_get_neighbors returns it (-1 = no same-level neighbour), ghosts
+ * [n][6][4] as cmg_level_get_ghosts returns it or NULL (missing neighbours
+ * then count as 0), phi and f [n][8] FP64, norm2 one double.  The result is
+ * written asynchronously; synchronise the stream before reading it.
+ * Limits and behaviour: n_octs <= 2^24 (16 777 216), else CMG_ERR_INVALID_ARG;
+ * the first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture;
+ * all calls share the scratch array, so calls that overlap on the GPU race
+ * and the caller must serialise them.  Returns CMG_OK, CMG_ERR_INVALID_ARG or
+ * CMG_ERR_CUDA; it does not set cmg_last_error(). */
+int cmg_residual_norm2_noalloc(const int32_t *neighbors, const double *ghosts, const double *phi, const double *f,
+                               int64_t n_octs, double h, double *norm2, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

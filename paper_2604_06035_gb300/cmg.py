@@ -94,6 +94,7 @@ _SIGS = {
     "cmg_level_mg_get": (_I, [_P, _I, _I, _I, _P, _I]),
     "cmg_level_mg_set": (_I, [_P, _I, _I, _I, _P, _I]),
     "cmg_level_mg_step": (_I, [_P, _I, _I, _I, _I, C.POINTER(C.c_double)]),
+    "cmg_residual_norm2_noalloc": (_I, [_P, _P, _P, _P, _I64, C.c_double, _P, _P]),
 }
 
 _lib = None
@@ -427,4 +428,29 @@ def cmg_level_mg_step(lvl, m, op, precision=CMG_PREC_FP64, n=1):
     v = C.c_double(0.0)
     _check(lib().cmg_level_mg_step(lvl.h, m, op, precision, n, C.byref(v)), "cmg_level_mg_step")
     return v.value
+
+
+def cmg_residual_norm2_noalloc(neighbors, ghosts, phi, f, h, norm2, stream=0):
+    """Residual norm^2 into the one-double CUDA tensor norm2 with no device
+    allocation by the library (for callers that cannot allocate at that point,
+    e.g. during CUDA-graph capture; see include/cmg.h).  neighbors [n][7]
+    int32, ghosts [n][6][4] or None, phi and f [n][8] float64, all CUDA
+    tensors.  Runs on `stream` (raw handle or torch stream); the caller
+    synchronises before reading norm2."""
+    if not isinstance(stream, int):
+        stream = stream.cuda_stream
+    pn, mn, _ = _in(neighbors, np.int32)
+    pp, mp, _ = _in(phi, np.float64)
+    pf, mf, _ = _in(f, np.float64)
+    po, mo, _ = _in(norm2, np.float64)
+    pg = None
+    if ghosts is not None:
+        pg, mg, _ = _in(ghosts, np.float64)
+        _same_mem(mg, CMG_MEM_DEVICE, "cmg_residual_norm2_noalloc")
+    for m in (mn, mp, mf, mo):
+        _same_mem(m, CMG_MEM_DEVICE, "cmg_residual_norm2_noalloc")
+    n = neighbors.shape[0]
+    rc = lib().cmg_residual_norm2_noalloc(pn, pg, pp, pf, n, float(h), po, C.c_void_p(stream))
+    if rc != CMG_OK:
+        raise CmgError(rc, "cmg_residual_norm2_noalloc", "invalid argument or CUDA error")
 
