@@ -374,6 +374,18 @@ int cmg_level_solve(cmg_level *lvl, const cmg_solve_params *params, cmg_solve_st
   });
 }
 
+int cmg_level_set_schedule(cmg_level *lvl, int64_t tail_octs_fp64, int64_t tail_octs_fp32) {
+  return guard([&] {
+    need(lvl != nullptr, "NULL level");
+    DeviceScope ds(lvl->device);
+    CMG_CUDA(cudaStreamSynchronize(lvl->stream));
+    if (tail_octs_fp64 >= 0) lvl->tail_octs_fp64 = tail_octs_fp64;
+    if (tail_octs_fp32 >= 0) lvl->tail_octs_fp32 = tail_octs_fp32;
+    cmg::destroy_graphs(lvl);  // recorded graphs follow the old schedule
+    return CMG_OK;
+  });
+}
+
 int cmg_level_mg_depth(const cmg_level *lvl, int *depth) {
   return guard([&] {
     need(lvl && depth, "NULL argument");

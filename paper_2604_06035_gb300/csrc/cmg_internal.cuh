@@ -263,6 +263,10 @@ struct cmg_level {
   void *h_ctrl = nullptr;      // pinned host copy
   std::vector<void *> graphs;  // instantiated solve graphs, keyed by parameters
   bool has32 = false;
+  // schedule: MG levels with at most this many octs (and all coarser ones) run
+  // in one cluster "tail" launch; 0 = one launch per operation everywhere
+  int64_t tail_octs_fp64 = 2048;
+  int64_t tail_octs_fp32 = 16384;
   cmg::DeviceBuffers mem;
 };
 
@@ -307,6 +311,10 @@ void zero_phi_norm(cmg_level *L, double *out);
 void subtract_mean(cmg_level *L);
 void accumulate(cmg_level *L, const double *scale);
 void finalize_norm(cmg_level *L, int n_partials, double scale, double *out);
+
+// tail.cu
+template <typename T>
+void tail_vcycle(cmg_level *L, int m0, const cmg_solve_params *p, const bool *zero_coarse);
 
 // solve.cu
 int solve(cmg_level *L, const cmg_solve_params *p, cmg_solve_stats *st);

@@ -1,0 +1,263 @@
+// oct_ops.cuh -- per-oct bodies of the multigrid operators, shared by the
+// one-kernel-per-operation path (ops.cu) and the cluster tail kernel
+// (tail.cu).  Layout: see cmg_internal.cuh.  CG = true routes every load of
+// data that another thread block of the same launch may have written through
+// L2 (ld.global.cg), as the tail kernel's blocks exchange data via global
+// memory between cluster barriers.
+#pragma once
+
+#include "cmg_internal.cuh"
+
+namespace cmg {
+namespace dev {
+
+template <bool CG>
+__device__ __forceinline__ double2 ldv(const double2 *p) {
+  if constexpr (CG) return __ldcg(p); else return *p;
+}
+template <bool CG>
+__device__ __forceinline__ float4 ldv(const float4 *p) {
+  if constexpr (CG) return __ldcg(p); else return *p;
+}
+template <bool CG, typename T>
+__device__ __forceinline__ T ld1(const T *p) {
+  if constexpr (CG) return __ldcg(p); else return *p;
+}
+
+template <bool CG>
+__device__ __forceinline__ void load4(const double *p, double v[4]) {
+  const double2 a = ldv<CG>(reinterpret_cast<const double2 *>(p));
+  const double2 b = ldv<CG>(reinterpret_cast<const double2 *>(p + 2));
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
+}
+template <bool CG>
+__device__ __forceinline__ void load4(const float *p, float v[4]) {
+  const float4 a = ldv<CG>(reinterpret_cast<const float4 *>(p));
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = a.z;
+  v[3] = a.w;
+}
+__device__ __forceinline__ void store4(double *p, const double v[4]) {
+  *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+  *reinterpret_cast<double2 *>(p + 2) = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void store4(float *p, const float v[4]) {
+  *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+template <typename T>
+__device__ __forceinline__ T fma_t(T a, T b, T c);
+template <>
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+template <>
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+
+// One colour pass of red-black Gauss-Seidel (App. D.2 Eq. (gs_update)) on
+// oct i: plane P from the other plane of the oct and of its six face
+// neighbours.  ZERO: the other plane is known to be zero, so phi = g.
+template <typename T, int P, bool ZERO, bool MASK, bool CG>
+__device__ __forceinline__ void sweep_oct(int64_t i, const int32_t *__restrict__ nbr, const T *src, T *dst,
+                                          const T *g, const uint8_t *__restrict__ active, int64_t n) {
+  T gv[4], out[4];
+  load4<CG>(g + i * 4, gv);
+  if (ZERO) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[q] = gv[q];
+  } else {
+    T own[4];
+    load4<CG>(src + i * 4, own);
+    int32_t nb[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) nb[d] = __ldg(nbr + d * n + i);
+    const T inv6 = T(1) / T(6);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = plane_cell(P, q);
+      T s = T(0);
+#pragma unroll
+      for (int d = 0; d < 6; ++d) {
+        const int a = d >> 1, side = d & 1, c2 = c ^ (1 << a);
+        const T v = (((c >> a) & 1) != side) ? own[c2 >> 1] : ld1<CG>(src + (int64_t)nb[d] * 4 + (c2 >> 1));
+        s = d == 0 ? v : s + v;
+      }
+      out[q] = fma_t(s, inv6, gv[q]);
+    }
+  }
+  if (MASK) {
+    const unsigned m = __ldg(active + i);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (!((m >> plane_cell(P, q)) & 1)) out[q] = T(0);
+  }
+  store4(dst + i * 4, out);
+}
+
+// Residual of oct i: d = fma(s, 1/6, g) - phi per cell, r = (-6 / h^2) d.
+// Returns the sum of d^2 over the oct (NORM).  RESTRICT: a fully active oct
+// writes its father cell g_c = 0.5 * sum_8 d (= -h_c^2/6 * mean_8 r) and, if
+// zero_cphi, zeroes the father's phi.  EMIT: g32 = (float)(d * inv_s).
+// ROUT: r oct-major.  ZPHI: phi taken as zero on real octs.
+template <typename T, bool NORM, bool RESTRICT, bool EMIT, bool ROUT, bool ZPHI, bool CG>
+__device__ __forceinline__ double resid_oct(int64_t i, const int32_t *__restrict__ nbr, const T *phi, const T *g,
+                                            const uint8_t *__restrict__ active, int64_t n, int64_t n_alloc,
+                                            const int32_t *__restrict__ father, T *cg, T *cphi, int64_t cn,
+                                            int64_t cn_alloc, int zero_cphi, float *g32, double inv_s,
+                                            double *rout, double rscale) {
+  T pl[2][4], gv[2][4];
+  if (ZPHI) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) pl[0][q] = pl[1][q] = T(0);
+  } else {
+    load4<CG>(phi + i * 4, pl[0]);
+    load4<CG>(phi + (n_alloc + i) * 4, pl[1]);
+  }
+  load4<CG>(g + i * 4, gv[0]);
+  load4<CG>(g + (n + i) * 4, gv[1]);
+  int32_t nb[6];
+#pragma unroll
+  for (int d = 0; d < 6; ++d) nb[d] = __ldg(nbr + d * n + i);
+  const T inv6 = T(1) / T(6);
+  const unsigned m = active ? __ldg(active + i) : 0xFFu;
+  T rsum = T(0);
+  double acc = 0.0;
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = plane_cell(p, q);
+      T s = T(0);
+#pragma unroll
+      for (int d = 0; d < 6; ++d) {
+        const int a = d >> 1, side = d & 1, c2 = c ^ (1 << a);
+        T v;
+        if (((c >> a) & 1) != side) {
+          v = pl[1 - p][c2 >> 1];
+        } else {
+          const int64_t o = nb[d];
+          v = (ZPHI && o < n) ? T(0) : ld1<CG>(phi + ((1 - p) * n_alloc + o) * 4 + (c2 >> 1));
+        }
+        s = d == 0 ? v : s + v;
+      }
+      T dv = fma_t(s, inv6, gv[p][q]) - pl[p][q];
+      if (!((m >> c) & 1)) dv = T(0);
+      if (NORM) acc = fma((double)dv, (double)dv, acc);
+      if (RESTRICT) rsum += dv;
+      if (EMIT) g32[(p * n + i) * 4 + q] = (float)((double)dv * inv_s);
+      if (ROUT) rout[i * 8 + c] = rscale * (double)dv;
+    }
+  }
+  if (RESTRICT) {
+    const int32_t fa = __ldg(father + i);
+    if (fa >= 0) {
+      const int64_t pc = fa >> 3;
+      const int cc = fa & 7;
+      cg[((int64_t)cell_parity(cc) * cn + pc) * 4 + (cc >> 1)] = T(0.5) * rsum;
+      if (zero_cphi) cphi[((int64_t)cell_parity(cc) * cn_alloc + pc) * 4 + (cc >> 1)] = T(0);
+    }
+  }
+  return acc;
+}
+
+// Block index and child bit of the coarse cell at offset e - 1 (e = 0, 1, 2)
+// along one axis from a father cell whose octant bit is cx; the block of 8
+// coarse octs is displaced toward the father's octant.
+__device__ __forceinline__ void axis_cell(int cx, int e, int &a, int &bit) {
+  if (cx == 0) {
+    a = (e == 0);
+    bit = (e != 1);
+  } else {
+    a = (e == 2);
+    bit = (e == 1);
+  }
+}
+
+// Trilinear cell-centred interpolation of a coarse field onto the 8 children
+// of the coarse cell (block octs b, octant cc): per axis weight 3/4 for the
+// father, 1/4 for its neighbour toward the child (Sec. 5.1.1).
+template <typename T, bool CG>
+__device__ __forceinline__ void interp8(const T *cphi, int64_t cn_alloc, const int32_t b[8], int cc, T out[8]) {
+  T v[27];
+#pragma unroll
+  for (int ez = 0; ez < 3; ++ez)
+#pragma unroll
+    for (int ey = 0; ey < 3; ++ey)
+#pragma unroll
+      for (int ex = 0; ex < 3; ++ex) {
+        int ax, bx, ay, by, az, bz;
+        axis_cell(cc & 1, ex, ax, bx);
+        axis_cell((cc >> 1) & 1, ey, ay, by);
+        axis_cell((cc >> 2) & 1, ez, az, bz);
+        const int ch = bx | (by << 1) | (bz << 2);
+        const int64_t oct = b[ax | (ay << 1) | (az << 2)];
+        v[ex + 3 * ey + 9 * ez] = ld1<CG>(cphi + ((int64_t)cell_parity(ch) * cn_alloc + oct) * 4 + (ch >> 1));
+      }
+  const T w0 = T(0.75), w1 = T(0.25);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int fx = c & 1, fy = (c >> 1) & 1, fz = (c >> 2) & 1;
+    const int ex1 = fx ? 2 : 0, ey1 = fy ? 2 : 0, ez1 = fz ? 2 : 0;
+    T acc = w0 * w0 * w0 * v[1 + 3 * 1 + 9 * 1];
+    acc = fma_t(w1 * w0 * w0, v[ex1 + 3 * 1 + 9 * 1], acc);
+    acc = fma_t(w0 * w1 * w0, v[1 + 3 * ey1 + 9 * 1], acc);
+    acc = fma_t(w1 * w1 * w0, v[ex1 + 3 * ey1 + 9 * 1], acc);
+    acc = fma_t(w0 * w0 * w1, v[1 + 3 * 1 + 9 * ez1], acc);
+    acc = fma_t(w1 * w0 * w1, v[ex1 + 3 * 1 + 9 * ez1], acc);
+    acc = fma_t(w0 * w1 * w1, v[1 + 3 * ey1 + 9 * ez1], acc);
+    acc = fma_t(w1 * w1 * w1, v[ex1 + 3 * ey1 + 9 * ez1], acc);
+    out[c] = acc;
+  }
+}
+
+// phi[i] += trilinear interpolation of the coarse correction (active cells).
+template <typename T, bool MASK, bool CG>
+__device__ __forceinline__ void prolong_oct(int64_t i, const uint64_t *__restrict__ keys,
+                                            const int32_t *__restrict__ blk, int64_t n, int64_t n_alloc, T *phi,
+                                            const uint8_t *__restrict__ active, const T *cphi, int64_t cn_alloc) {
+  const int cc = (int)(__ldg(keys + i) & 7);
+  int32_t b[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) b[t] = __ldg(blk + t * n + i);
+  T corr[8];
+  interp8<T, CG>(cphi, cn_alloc, b, cc, corr);
+  const unsigned m = MASK ? __ldg(active + i) : 0xFFu;
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    T v[4];
+    load4<CG>(phi + (p * n_alloc + i) * 4, v);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = plane_cell(p, q);
+      if ((m >> c) & 1) v[q] += corr[c];
+    }
+    store4(phi + (p * n_alloc + i) * 4, v);
+  }
+}
+
+// Exact solve of the periodic 2^3 oct (one thread): eigenvectors
+// (-1)^{k.b}, eigenvalues -4 |k|_1 / h^2, mean mode dropped; FP64 inside.
+template <typename S, typename T, bool CG>
+__device__ void wht_solve(const S *g, T *phi, int64_t n_alloc, double h) {
+  double f[8], fh[8];
+  for (int c = 0; c < 8; ++c) f[c] = (double)ld1<CG>(g + cell_parity(c) * 4 + (c >> 1)) * (-6.0 / (h * h));
+  for (int k = 0; k < 8; ++k) {
+    double s = 0.0;
+    for (int b = 0; b < 8; ++b) s += cell_parity(k & b) ? -f[b] : f[b];
+    fh[k] = s * 0.125;
+  }
+  for (int b = 0; b < 8; ++b) {
+    double s = 0.0;
+    for (int k = 1; k < 8; ++k) {
+      const int odd = (k & 1) + ((k >> 1) & 1) + ((k >> 2) & 1);
+      const double x = fh[k] / (-4.0 * odd / (h * h));
+      s += cell_parity(k & b) ? -x : x;
+    }
+    phi[(int64_t)cell_parity(b) * n_alloc * 4 + (b >> 1)] = (T)s;
+  }
+}
+
+}  // namespace dev
+}  // namespace cmg

@@ -109,10 +109,32 @@ bool coarse_needs_zero(const cmg_level *L, int m, const cmg_solve_params *p) {
   return !L->exact_coarse && p->coarse_sweeps == 0;
 }
 
+// First MG level (>= 1) from which every level down to the coarsest has at
+// most the schedule's tail size: those levels run in one tail launch.
+template <typename T>
+int tail_start(const cmg_level *L) {
+  const int64_t lim = sizeof(T) == 8 ? L->tail_octs_fp64 : L->tail_octs_fp32;
+  if (lim <= 0) return -1;
+  int m0 = -1;
+  for (int m = (int)L->mg.size() - 1; m >= 1; --m) {
+    if (L->mg[m].n > lim) break;
+    m0 = m;
+  }
+  return m0;
+}
+
 template <typename T>
 void vcycle(cmg_level *L, int m, const cmg_solve_params *p, bool zero_top, int64_t *updates) {
   const int last = (int)L->mg.size() - 1;
   const int prec = sizeof(T) == 8 ? CMG_PREC_FP64 : CMG_PREC_MIXED;
+  if (m > 0 && m == tail_start<T>(L)) {
+    bool zc[64] = {};
+    for (int j = m; j < last && j < 64; ++j) zc[j] = coarse_needs_zero(L, j, p);
+    tail_vcycle<T>(L, m, p, zc);
+    for (int j = m; j < last; ++j) *updates += (int64_t)(p->n_pre + p->n_post) * 8 * L->mg[j].n;
+    if (!L->exact_coarse) *updates += (int64_t)p->coarse_sweeps * 8 * L->mg[last].n;
+    return;
+  }
   if (m == last) {
     coarse_solve(L, prec, p->coarse_sweeps);
     if (!L->exact_coarse) *updates += (int64_t)p->coarse_sweeps * 8 * L->mg[m].n;
