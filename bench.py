@@ -116,7 +116,7 @@ def traffic_for(kernel):
     return e.get("dram_bytes_per_launch")
 
 
-def cycle_updates(n_octs_per_mg, n_pre=2, n_post=2, coarse_sweeps=32, exact_coarse=True):
+def cycle_updates(n_octs_per_mg, n_pre=2, n_post=2, coarse_sweeps=4, exact_coarse=True):
     u = sum((n_pre + n_post) * 8 * n for n in n_octs_per_mg[:-1])
     if not exact_coarse:
         u += coarse_sweeps * 8 * n_octs_per_mg[-1]

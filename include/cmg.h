@@ -158,8 +158,9 @@ int cmg_level_solve(cmg_level *lvl, const cmg_solve_params *params, cmg_solve_st
 /* Execution schedule of the V-cycle (no effect on the arithmetic): MG levels
  * with at most tail_octs_fp64 (FP64 cycles) / tail_octs_fp32 (FP32 inner
  * cycles) octs, together with every coarser level, run in one thread-block-
- * cluster launch instead of one launch per operation; 0 disables.  Defaults
- * 2048 / 16384.  Negative values leave the current setting. */
+ * cluster launch instead of one launch per operation; 0 disables (the
+ * default: on GB300 a cluster pass over a small level is as slow as a launch).
+ * Negative values leave the current setting. */
 int cmg_level_set_schedule(cmg_level *lvl, int64_t tail_octs_fp64, int64_t tail_octs_fp32);
 
 /* ---- multigrid hierarchy introspection and single steps (for tests) ----

@@ -113,7 +113,7 @@ def hash_capacity_for(n):
     return lib().or_hash_capacity_for(int(n))
 
 
-def params(tol=1e-10, max_cycles=100, n_pre=2, n_post=2, coarse_sweeps=32, fixed_cycles=0):
+def params(tol=1e-10, max_cycles=100, n_pre=2, n_post=2, coarse_sweeps=4, fixed_cycles=0):
     return OrParams(tol, max_cycles, n_pre, n_post, coarse_sweeps, fixed_cycles)
 
 
@@ -248,10 +248,10 @@ class Level:
     def prolong(self, m):
         lib().or_prolong(self._h, m)
 
-    def coarse_solve(self, coarse_sweeps=32):
+    def coarse_solve(self, coarse_sweeps=4):
         lib().or_coarse_solve(self._h, coarse_sweeps)
 
-    def solve(self, tol=1e-10, max_cycles=100, n_pre=2, n_post=2, coarse_sweeps=32, fixed_cycles=0,
+    def solve(self, tol=1e-10, max_cycles=100, n_pre=2, n_post=2, coarse_sweeps=4, fixed_cycles=0,
               raise_on_error=True):
         p = params(tol, max_cycles, n_pre, n_post, coarse_sweeps, fixed_cycles)
         st = OrStats()
@@ -260,7 +260,7 @@ class Level:
             raise OracleError(rc, "or_level_solve")
         return rc, _stats_dict(st)
 
-    def solve_mixed(self, tol=1e-10, max_cycles=100, n_pre=2, n_post=2, coarse_sweeps=32, fixed_cycles=0,
+    def solve_mixed(self, tol=1e-10, max_cycles=100, n_pre=2, n_post=2, coarse_sweeps=4, fixed_cycles=0,
                     inner_cycles=1, raise_on_error=True):
         p = params(tol, max_cycles, n_pre, n_post, coarse_sweeps, fixed_cycles)
         st = OrStats()

@@ -265,8 +265,8 @@ struct cmg_level {
   bool has32 = false;
   // schedule: MG levels with at most this many octs (and all coarser ones) run
   // in one cluster "tail" launch; 0 = one launch per operation everywhere
-  int64_t tail_octs_fp64 = 2048;
-  int64_t tail_octs_fp32 = 16384;
+  int64_t tail_octs_fp64 = 0;
+  int64_t tail_octs_fp32 = 0;
   cmg::DeviceBuffers mem;
 };
 
@@ -275,6 +275,32 @@ namespace cmg {
 constexpr int kThreads = 256;
 
 inline unsigned blocks_for(int64_t n, int t = kThreads) { return (unsigned)((n + t - 1) / t); }
+
+// Launch with programmatic dependent launch allowed: the next kernel on the
+// stream (or in the captured graph) may be scheduled while this one drains.
+// Every kernel launched this way starts with pdl_enter(), which waits for the
+// preceding grid to complete before touching memory.
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cuda_check(cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...), "cudaLaunchKernelEx");
+}
+
+__device__ __forceinline__ void pdl_enter() {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
+  cudaTriggerProgrammaticLaunchCompletion();
+  cudaGridDependencySynchronize();
+#endif
+}
 
 // scan.cu
 void scan_exclusive(const int32_t *in, int32_t *out, int64_t n, int32_t *d_total, int32_t *scratch,

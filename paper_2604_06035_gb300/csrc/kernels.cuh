@@ -32,6 +32,7 @@ template <typename T, int P, bool ZERO, bool MASK>
 __global__ void __launch_bounds__(kThreads) k_sweep(const int32_t *__restrict__ nbr, const T *__restrict__ src,
                                                    T *__restrict__ dst, const T *__restrict__ g,
                                                    const uint8_t *__restrict__ active, int64_t n) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   dev::sweep_oct<T, P, ZERO, MASK, false>(i, nbr, src, dst, g, active, n);
@@ -45,6 +46,7 @@ __global__ void __launch_bounds__(kThreads) k_resid(const int32_t *__restrict__ 
                                                    int64_t cn_alloc, int zero_cphi, double *__restrict__ partials,
                                                    float *__restrict__ g32, const double *__restrict__ emit_scale,
                                                    double *__restrict__ rout, double rscale) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double acc = 0.0;
   if (i < n) {
@@ -61,6 +63,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const uint64_t *__restrict
                                                      int64_t n, int64_t n_alloc, T *__restrict__ phi,
                                                      const uint8_t *__restrict__ active,
                                                      const T *__restrict__ cphi, int64_t cn_alloc) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   dev::prolong_oct<T, MASK, false>(i, keys, blk, n, n_alloc, phi, active, cphi, cn_alloc);
@@ -71,6 +74,7 @@ __global__ void __launch_bounds__(kThreads) k_ghost_fill(const uint64_t *__restr
                                                         const uint32_t *__restrict__ gmask, int64_t n_ghost,
                                                         int64_t n, int64_t n_alloc, double *__restrict__ phi,
                                                         const double *__restrict__ pphi, int64_t pn_alloc) {
+  pdl_enter();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= n_ghost) return;
   const int cc = (int)(gkeys[t] & 7);
@@ -96,6 +100,7 @@ __global__ void __launch_bounds__(kThreads) k_ghost_fill(const uint64_t *__restr
 // Ghost values in the [n][6][4] API layout (NaN where the neighbour exists).
 __global__ void k_get_ghosts(const int32_t *__restrict__ nbr, int64_t n, int64_t n_ghost, int64_t n_alloc,
                              const double *__restrict__ phi, double *__restrict__ out) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   for (int d = 0; d < 6; ++d) {
@@ -115,12 +120,14 @@ __global__ void k_get_ghosts(const int32_t *__restrict__ nbr, int64_t n, int64_t
 
 template <typename T>
 __global__ void k_wht(const T *__restrict__ g, T *__restrict__ phi, int64_t n_alloc, double h) {
+  pdl_enter();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   dev::wht_solve<T, T, false>(g, phi, n_alloc, h);
 }
 
 __global__ void k_set_density(const double *__restrict__ rho, int64_t n, double rho_bar, double scale,
                               double *__restrict__ g) {
+  pdl_enter();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= 8 * n) return;
   const int64_t i = t >> 3;
@@ -131,6 +138,7 @@ __global__ void k_set_density(const double *__restrict__ rho, int64_t n, double 
 // oct-major [n][8] <-> planar [2][stride][4], with a scale factor
 template <typename S, typename D>
 __global__ void k_pack(const S *__restrict__ in, int64_t n, int64_t stride, double scale, D *__restrict__ out) {
+  pdl_enter();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= 8 * n) return;
   const int64_t i = t >> 3;
@@ -140,6 +148,7 @@ __global__ void k_pack(const S *__restrict__ in, int64_t n, int64_t stride, doub
 
 template <typename S, typename D>
 __global__ void k_unpack(const S *__restrict__ in, int64_t n, int64_t stride, double scale, D *__restrict__ out) {
+  pdl_enter();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= 8 * n) return;
   const int64_t i = t >> 3;
@@ -148,6 +157,7 @@ __global__ void k_unpack(const S *__restrict__ in, int64_t n, int64_t stride, do
 }
 
 __global__ void k_sum_phi(const double *__restrict__ phi, int64_t n, int64_t n_alloc, double *__restrict__ partials) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double acc = 0.0;
   if (i < n) {
@@ -160,6 +170,7 @@ __global__ void k_sum_phi(const double *__restrict__ phi, int64_t n, int64_t n_a
 }
 
 __global__ void k_sub_scalar(double *__restrict__ phi, int64_t n, int64_t n_alloc, const double *__restrict__ s) {
+  pdl_enter();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= 8 * n) return;
   const int64_t i = t >> 3;
@@ -171,6 +182,7 @@ __global__ void k_sub_scalar(double *__restrict__ phi, int64_t n, int64_t n_allo
 // phi64 += S * phi32 on the real octs (solution accumulation, FP64)
 __global__ void k_accumulate(double *__restrict__ phi, const float *__restrict__ e, int64_t n, int64_t n_alloc,
                              const double *__restrict__ scale) {
+  pdl_enter();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= 2 * n) return;
   const int p = (int)(t / n);
@@ -188,6 +200,7 @@ __global__ void k_accumulate(double *__restrict__ phi, const float *__restrict__
 // Sum partials in a fixed order; out[0] = scale * sum (and its sqrt to out[1]).
 __global__ void k_finalize(const double *__restrict__ partials, int np, double scale, double *__restrict__ out,
                            int with_sqrt) {
+  pdl_enter();
   __shared__ double ws[32];
   double v = 0.0;
   for (int t = threadIdx.x; t < np; t += blockDim.x) v += partials[t];
@@ -207,10 +220,12 @@ __global__ void k_finalize(const double *__restrict__ partials, int np, double s
 }
 
 __global__ void k_copy_convert_f2d(const float *__restrict__ a, double *__restrict__ b, int64_t m) {
+  pdl_enter();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t < m) b[t] = (double)a[t];
 }
 __global__ void k_copy_convert_d2f(const double *__restrict__ a, float *__restrict__ b, int64_t m) {
+  pdl_enter();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t < m) b[t] = (float)a[t];
 }

@@ -28,7 +28,7 @@ void sweep(cmg_level *L, int m, bool zero_init) {
 #define CMG_SWEEP(P, Z, M)                                                                                  \
   do {                                                                                                      \
     LaunchScope ls(L->ctx, cls, (Z) ? 2.0 * u * sizeof(T) : full_bytes, (Z) ? 0.0 : full_flops);            \
-    k_sweep<T, P, Z, M><<<nb, kThreads, 0, s>>>(g.nbr, phi + (1 - P) * st, phi + P * st, gg + P * g.n * 4, \
+    launch_k(k_sweep<T, P, Z, M>, nb, kThreads, s, g.nbr, phi + (1 - P) * st, phi + P * st, gg + P * g.n * 4, \
                                                 g.active, g.n);                                             \
   } while (0)
   if (mask) {
@@ -63,19 +63,19 @@ void resid_restrict(cmg_level *L, int m, bool restrict_to_coarse, bool norm, boo
   if (g.n > 0) {
     LaunchScope ls(L->ctx, cls, bytes, flops);
     if (restrict_to_coarse && !norm && !emit_scale)
-      k_resid<T, false, true, false, false, false><<<nb, kThreads, 0, s>>>(
+      launch_k(k_resid<T, false, true, false, false, false>, nb, kThreads, s, 
           g.nbr, phi_of<T>(g), g_of<T>(g), act, g.n, g.n_alloc, g.father, cg, cphi, cn, cna, zero_coarse_phi,
           nullptr, nullptr, nullptr, nullptr, 0.0);
     else if (restrict_to_coarse && norm && !emit_scale)
-      k_resid<T, true, true, false, false, false><<<nb, kThreads, 0, s>>>(
+      launch_k(k_resid<T, true, true, false, false, false>, nb, kThreads, s, 
           g.nbr, phi_of<T>(g), g_of<T>(g), act, g.n, g.n_alloc, g.father, cg, cphi, cn, cna, zero_coarse_phi,
           L->partials, nullptr, nullptr, nullptr, 0.0);
     else if (!restrict_to_coarse && norm && !emit_scale)
-      k_resid<T, true, false, false, false, false><<<nb, kThreads, 0, s>>>(
+      launch_k(k_resid<T, true, false, false, false, false>, nb, kThreads, s, 
           g.nbr, phi_of<T>(g), g_of<T>(g), act, g.n, g.n_alloc, nullptr, nullptr, nullptr, 0, 0, 0, L->partials,
           nullptr, nullptr, nullptr, 0.0);
     else if (!restrict_to_coarse && norm && emit_scale)
-      k_resid<T, true, false, true, false, false><<<nb, kThreads, 0, s>>>(
+      launch_k(k_resid<T, true, false, true, false, false>, nb, kThreads, s, 
           g.nbr, phi_of<T>(g), g_of<T>(g), act, g.n, g.n_alloc, nullptr, nullptr, nullptr, 0, 0, 0, L->partials,
           g.g32, emit_scale, nullptr, 0.0);
     else
@@ -88,7 +88,7 @@ void resid_restrict(cmg_level *L, int m, bool restrict_to_coarse, bool norm, boo
       CMG_CUDA(cudaMemsetAsync(norm_out, 0, 2 * sizeof(double), s));
     } else {
       LaunchScope ls(L->ctx, K_REDUCE, nb * 8.0, nb);
-      k_finalize<<<1, 1024, 0, s>>>(L->partials, (int)nb, scale, norm_out, 1);
+      launch_k(k_finalize, 1, 1024, s, L->partials, (int)nb, scale, norm_out, 1);
       CMG_CUDA(cudaGetLastError());
     }
   }
@@ -104,11 +104,11 @@ void residual_out(cmg_level *L, int m, int prec, double *out) {
   const double rscale = -6.0 / (g.h * g.h);
   LaunchScope ls(L->ctx, prec == CMG_PREC_FP64 ? K_RESID64 : K_RESID32, 8.0 * g.n * 24.0, 8.0 * g.n * 9.0);
   if (prec == CMG_PREC_FP64)
-    k_resid<double, false, false, false, true, false><<<blocks_for(g.n), kThreads, 0, s>>>(
+    launch_k(k_resid<double, false, false, false, true, false>, blocks_for(g.n), kThreads, s, 
         g.nbr, g.phi, g.g, act, g.n, g.n_alloc, nullptr, nullptr, nullptr, 0, 0, 0, nullptr, nullptr, nullptr, out,
         rscale);
   else
-    k_resid<float, false, false, false, true, false><<<blocks_for(g.n), kThreads, 0, s>>>(
+    launch_k(k_resid<float, false, false, false, true, false>, blocks_for(g.n), kThreads, s, 
         g.nbr, g.phi32, g.g32, act, g.n, g.n_alloc, nullptr, nullptr, nullptr, 0, 0, 0, nullptr, nullptr, nullptr,
         out, rscale);
   CMG_CUDA(cudaGetLastError());
@@ -125,13 +125,13 @@ void zero_phi_norm(cmg_level *L, double *out) {
   }
   {
     LaunchScope ls(L->ctx, K_RESID64, 8.0 * g.n * 8.0, 8.0 * g.n * 9.0);
-    k_resid<double, true, false, false, false, true><<<nb, kThreads, 0, s>>>(
+    launch_k(k_resid<double, true, false, false, false, true>, nb, kThreads, s, 
         g.nbr, g.phi, g.g, nullptr, g.n, g.n_alloc, nullptr, nullptr, nullptr, 0, 0, 0, L->partials, nullptr,
         nullptr, nullptr, 0.0);
   }
   {
     LaunchScope ls(L->ctx, K_REDUCE, nb * 8.0, nb);
-    k_finalize<<<1, 1024, 0, s>>>(L->partials, (int)nb, 36.0 / (g.h * g.h * g.h * g.h), out, 1);
+    launch_k(k_finalize, 1, 1024, s, L->partials, (int)nb, 36.0 / (g.h * g.h * g.h * g.h), out, 1);
   }
   CMG_CUDA(cudaGetLastError());
 }
@@ -145,10 +145,10 @@ void prolong(cmg_level *L, int m) {
   LaunchScope ls(L->ctx, sizeof(T) == 8 ? K_PROLONG64 : K_PROLONG32,
                  g.n * 17.0 * sizeof(T), g.n * 128.0);
   if (g.all_active)
-    k_prolong<T, false><<<blocks_for(g.n), kThreads, 0, s>>>(g.keys, g.blk, g.n, g.n_alloc, phi_of<T>(g), g.active,
+    launch_k(k_prolong<T, false>, blocks_for(g.n), kThreads, s, g.keys, g.blk, g.n, g.n_alloc, phi_of<T>(g), g.active,
                                                              phi_of<T>(c), c.n_alloc);
   else
-    k_prolong<T, true><<<blocks_for(g.n), kThreads, 0, s>>>(g.keys, g.blk, g.n, g.n_alloc, phi_of<T>(g), g.active,
+    launch_k(k_prolong<T, true>, blocks_for(g.n), kThreads, s, g.keys, g.blk, g.n, g.n_alloc, phi_of<T>(g), g.active,
                                                             phi_of<T>(c), c.n_alloc);
   CMG_CUDA(cudaGetLastError());
 }
@@ -180,9 +180,9 @@ void coarse_solve(cmg_level *L, int prec, int coarse_sweeps) {
   if (L->exact_coarse) {
     LaunchScope ls(L->ctx, K_COARSE, 128.0, 256.0);
     if (prec == CMG_PREC_FP64)
-      k_wht<double><<<1, 32, 0, s>>>(g.g, g.phi, g.n_alloc, g.h);
+      launch_k(k_wht<double>, 1, 32, s, g.g, g.phi, g.n_alloc, g.h);
     else
-      k_wht<float><<<1, 32, 0, s>>>(g.g32, g.phi32, g.n_alloc, g.h);
+      launch_k(k_wht<float>, 1, 32, s, g.g32, g.phi32, g.n_alloc, g.h);
     CMG_CUDA(cudaGetLastError());
     return;
   }
@@ -194,17 +194,17 @@ void coarse_solve(cmg_level *L, int prec, int coarse_sweeps) {
   const int64_t mg = 8 * g.n, ma = 8 * g.n_alloc;
   {
     LaunchScope ls(L->ctx, K_CONVERT, 12.0 * (mg + ma), 0.0);
-    k_copy_convert_f2d<<<blocks_for(mg), kThreads, 0, s>>>(g.g32, g.g, mg);
+    launch_k(k_copy_convert_f2d, blocks_for(mg), kThreads, s, g.g32, g.g, mg);
   }
   {
     LaunchScope ls(L->ctx, K_CONVERT, 12.0 * ma, 0.0);
-    k_copy_convert_f2d<<<blocks_for(ma), kThreads, 0, s>>>(g.phi32, g.phi, ma);
+    launch_k(k_copy_convert_f2d, blocks_for(ma), kThreads, s, g.phi32, g.phi, ma);
   }
   CMG_CUDA(cudaGetLastError());
   for (int k = 0; k < coarse_sweeps; ++k) sweep<double>(L, m, k == 0 && m > 0);
   {
     LaunchScope ls(L->ctx, K_CONVERT, 12.0 * ma, 0.0);
-    k_copy_convert_d2f<<<blocks_for(ma), kThreads, 0, s>>>(g.phi, g.phi32, ma);
+    launch_k(k_copy_convert_d2f, blocks_for(ma), kThreads, s, g.phi, g.phi32, ma);
   }
   CMG_CUDA(cudaGetLastError());
 }
@@ -216,15 +216,15 @@ void subtract_mean(cmg_level *L) {
   const unsigned nb = blocks_for(g.n);
   {
     LaunchScope ls(L->ctx, K_REDUCE, 64.0 * g.n, 8.0 * g.n);
-    k_sum_phi<<<nb, kThreads, 0, s>>>(g.phi, g.n, g.n_alloc, L->partials);
+    launch_k(k_sum_phi, nb, kThreads, s, g.phi, g.n, g.n_alloc, L->partials);
   }
   {
     LaunchScope ls(L->ctx, K_REDUCE, nb * 8.0, nb);
-    k_finalize<<<1, 1024, 0, s>>>(L->partials, (int)nb, 1.0 / (8.0 * (double)g.n), L->scal + 6, 0);
+    launch_k(k_finalize, 1, 1024, s, L->partials, (int)nb, 1.0 / (8.0 * (double)g.n), L->scal + 6, 0);
   }
   {
     LaunchScope ls(L->ctx, K_CONVERT, 128.0 * g.n, 8.0 * g.n);
-    k_sub_scalar<<<blocks_for(8 * g.n), kThreads, 0, s>>>(g.phi, g.n, g.n_alloc, L->scal + 6);
+    launch_k(k_sub_scalar, blocks_for(8 * g.n), kThreads, s, g.phi, g.n, g.n_alloc, L->scal + 6);
   }
   CMG_CUDA(cudaGetLastError());
 }
@@ -233,7 +233,7 @@ void accumulate(cmg_level *L, const double *scale) {
   MgLev &g = L->mg[0];
   if (g.n == 0) return;
   LaunchScope ls(L->ctx, K_CONVERT, g.n * 8.0 * (16.0 + 4.0), g.n * 16.0);
-  k_accumulate<<<blocks_for(2 * g.n), kThreads, 0, L->ctx->stream>>>(g.phi, g.phi32, g.n, g.n_alloc, scale);
+  launch_k(k_accumulate, blocks_for(2 * g.n), kThreads, L->ctx->stream, g.phi, g.phi32, g.n, g.n_alloc, scale);
   CMG_CUDA(cudaGetLastError());
 }
 
@@ -265,9 +265,9 @@ void pack_field(cmg_level *L, int m, int field, int prec, const void *in) {
   const unsigned nb = blocks_for(8 * g.n);
   LaunchScope ls(L->ctx, K_CONVERT, g.n * 8.0 * 2.0 * (prec == CMG_PREC_FP64 ? 8.0 : 4.0), 0.0);
   if (prec == CMG_PREC_FP64)
-    k_pack<double, double><<<nb, kThreads, 0, s>>>((const double *)in, g.n, stride, scale, field == 0 ? g.phi : g.g);
+    launch_k(k_pack<double, double>, nb, kThreads, s, (const double *)in, g.n, stride, scale, field == 0 ? g.phi : g.g);
   else
-    k_pack<float, float><<<nb, kThreads, 0, s>>>((const float *)in, g.n, stride, scale, field == 0 ? g.phi32 : g.g32);
+    launch_k(k_pack<float, float>, nb, kThreads, s, (const float *)in, g.n, stride, scale, field == 0 ? g.phi32 : g.g32);
   CMG_CUDA(cudaGetLastError());
 }
 
@@ -280,9 +280,9 @@ void unpack_field(cmg_level *L, int m, int field, int prec, void *out) {
   const unsigned nb = blocks_for(8 * g.n);
   LaunchScope ls(L->ctx, K_CONVERT, g.n * 8.0 * 2.0 * (prec == CMG_PREC_FP64 ? 8.0 : 4.0), 0.0);
   if (prec == CMG_PREC_FP64)
-    k_unpack<double, double><<<nb, kThreads, 0, s>>>(field == 0 ? g.phi : g.g, g.n, stride, scale, (double *)out);
+    launch_k(k_unpack<double, double>, nb, kThreads, s, field == 0 ? g.phi : g.g, g.n, stride, scale, (double *)out);
   else
-    k_unpack<float, float><<<nb, kThreads, 0, s>>>(field == 0 ? g.phi32 : g.g32, g.n, stride, scale, (float *)out);
+    launch_k(k_unpack<float, float>, nb, kThreads, s, field == 0 ? g.phi32 : g.g32, g.n, stride, scale, (float *)out);
   CMG_CUDA(cudaGetLastError());
 }
 
