@@ -188,6 +188,59 @@ typedef enum {
 } cmg_op;
 int cmg_level_mg_step(cmg_level *lvl, int m, int op, int precision, int n, double *norm2);
 
+/* ---- batched solve of many independent patches (no counterpart in the paper;
+ * its nearest idea is the batched grid buffering of the GPU offload section,
+ * "Batched Grid Buffering") ----
+ * A batch is a built level whose octs form n_patches independent patches:
+ * patch k is octs [offsets[k], offsets[k+1]) of the level (host array,
+ * offsets[0] = 0, offsets[n_patches] = n_octs), and no same-level neighbour
+ * link, at any multigrid level, joins two patches (else CMG_ERR_INVALID_ARG).
+ * cmg_batch_solve runs the whole solve of all patches -- every cycle, every
+ * multigrid level, the per-patch residual norms and the stopping test -- in
+ * ONE persistent cooperative kernel launch, recorded in a CUDA graph.  Grid
+ * barriers inside the kernel spin with a bounded budget; if a barrier gives
+ * up the solve returns CMG_ERR_TIMEOUT and the context stays usable.
+ * Each patch stops counting when its own relative residual reaches tol;
+ * all patches iterate until the slowest one has.  With MIXED precision the
+ * cycles are FP32 V-cycles inside FP64 refinement, scaled per patch.
+ * The coarsest solve of every patch is n_pre + n_post red-black sweeps (the
+ * schedule's), so a patch's result equals the solve of that patch alone. */
+typedef struct cmg_batch cmg_batch;
+typedef struct {
+  int threads;        /* threads per block of the persistent kernel (multiple of 32, <= 1024) */
+  int blocks_per_sm;  /* resident blocks per SM: grid = SMs x this (capped by occupancy) */
+  int n_pre, n_post;  /* red-black sweeps before / after the coarse correction */
+  int inner_cycles;   /* MIXED: FP32 V-cycles per FP64 refinement step */
+} cmg_batch_schedule;
+typedef struct {
+  int cycles;          /* V-cycles (FP64) or refinement steps (MIXED) run */
+  int status;
+  int n_patches;
+  int n_converged;     /* patches at or below tol */
+  double rel_max;      /* largest per-patch relative residual at return */
+  double ms;           /* device time of the solve */
+  int64_t cell_updates;
+  int64_t grid_barriers;
+} cmg_batch_stats;
+int cmg_batch_create(cmg_level *lvl, const int64_t *offsets, int n_patches, cmg_batch **out);
+int cmg_batch_destroy(cmg_batch *batch);
+int cmg_batch_set_schedule(cmg_batch *batch, const cmg_batch_schedule *schedule);
+int cmg_batch_get_schedule(cmg_batch *batch, cmg_batch_schedule *schedule);
+/* Spin budget of the grid barriers in SM clock cycles (default 2e9, ~1 s). */
+int cmg_batch_set_spin_budget(cmg_batch *batch, int64_t cycles);
+/* params: tol, max_cycles, fixed_cycles and precision are used; the sweep
+ * counts come from the batch schedule. */
+int cmg_batch_solve(cmg_batch *batch, const cmg_solve_params *params, cmg_batch_stats *stats);
+/* Per-patch results of the last solve (host arrays of n_patches; any may be
+ * NULL): relative residual, cycle at which the patch reached tol (-1 if it
+ * did not), and ||f - L 0|| of the patch. */
+int cmg_batch_patch_stats(cmg_batch *batch, double *rel, int32_t *converged_at, double *norm0);
+/* Times candidate schedules (block shape x sweep schedule x inner cycles)
+ * with full solves on the batch's current data, keeps the fastest and sets
+ * it; phi of the level is restored afterwards.  best / best_ms may be NULL. */
+int cmg_batch_autotune(cmg_batch *batch, const cmg_solve_params *params, cmg_batch_schedule *best,
+                       double *best_ms);
+
 /* ---- residual norm without allocation (the paper has no counterpart) ----
  * The level objects above allocate device memory when they are built, and
  * their residual norm reduces through scratch the level owns.  Callers that

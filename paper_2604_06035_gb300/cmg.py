@@ -53,6 +53,17 @@ class cmg_kernel_profile(C.Structure):
                 ("flops", C.c_double)]
 
 
+class cmg_batch_schedule(C.Structure):
+    _fields_ = [("threads", C.c_int), ("blocks_per_sm", C.c_int), ("n_pre", C.c_int), ("n_post", C.c_int),
+                ("inner_cycles", C.c_int)]
+
+
+class cmg_batch_stats(C.Structure):
+    _fields_ = [("cycles", C.c_int), ("status", C.c_int), ("n_patches", C.c_int), ("n_converged", C.c_int),
+                ("rel_max", C.c_double), ("ms", C.c_double), ("cell_updates", C.c_int64),
+                ("grid_barriers", C.c_int64)]
+
+
 class CmgError(RuntimeError):
     def __init__(self, code, fn, msg):
         super().__init__("%s failed (status %d): %s" % (fn, code, msg))
@@ -96,6 +107,14 @@ _SIGS = {
     "cmg_level_mg_set": (_I, [_P, _I, _I, _I, _P, _I]),
     "cmg_level_mg_step": (_I, [_P, _I, _I, _I, _I, C.POINTER(C.c_double)]),
     "cmg_residual_norm2_noalloc": (_I, [_P, _P, _P, _P, _I64, C.c_double, _P, _P]),
+    "cmg_batch_create": (_I, [_P, _P, _I, C.POINTER(_P)]),
+    "cmg_batch_destroy": (_I, [_P]),
+    "cmg_batch_set_schedule": (_I, [_P, _P]),
+    "cmg_batch_get_schedule": (_I, [_P, _P]),
+    "cmg_batch_set_spin_budget": (_I, [_P, _I64]),
+    "cmg_batch_solve": (_I, [_P, C.POINTER(cmg_solve_params), _P]),
+    "cmg_batch_patch_stats": (_I, [_P, _P, _P, _P]),
+    "cmg_batch_autotune": (_I, [_P, C.POINTER(cmg_solve_params), _P, C.POINTER(C.c_double)]),
 }
 
 _lib = None
@@ -302,8 +321,86 @@ def cmg_level_build(ctx, level, keys, parent=None, nx=1, periodic_mask=7):
 
 def cmg_level_destroy(lvl):
     if lvl.h:
+        for ref in getattr(lvl, "batches", []):
+            b = ref()
+            if b is not None and b.h:
+                cmg_batch_destroy(b)
         _check(lib().cmg_level_destroy(lvl.h), "cmg_level_destroy")
         lvl.h = None
+
+
+class BatchHandle:
+    """Owns a cmg_batch* and keeps its level alive; destroyed before it."""
+
+    def __init__(self, h, lvl, n_patches):
+        import weakref
+        self.h = h
+        self.lvl = lvl
+        self.n_patches = n_patches
+        if not hasattr(lvl, "batches"):
+            lvl.batches = []
+        lvl.batches.append(weakref.ref(self))
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            h, self.h = self.h, None
+            _lib.cmg_batch_destroy(h)
+
+
+def cmg_batch_create(lvl, offsets):
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    h = C.c_void_p()
+    _check(lib().cmg_batch_create(lvl.h, off.ctypes.data_as(C.c_void_p), len(off) - 1, C.byref(h)),
+           "cmg_batch_create")
+    return BatchHandle(h, lvl, len(off) - 1)
+
+
+def cmg_batch_destroy(b):
+    if b.h:
+        h, b.h = b.h, None
+        _check(lib().cmg_batch_destroy(h), "cmg_batch_destroy")
+
+
+def cmg_batch_set_schedule(b, threads=256, blocks_per_sm=2, n_pre=2, n_post=2, inner_cycles=1):
+    s = cmg_batch_schedule(threads, blocks_per_sm, n_pre, n_post, inner_cycles)
+    _check(lib().cmg_batch_set_schedule(b.h, C.byref(s)), "cmg_batch_set_schedule")
+
+
+def cmg_batch_get_schedule(b):
+    s = cmg_batch_schedule()
+    _check(lib().cmg_batch_get_schedule(b.h, C.byref(s)), "cmg_batch_get_schedule")
+    return {f: getattr(s, f) for f, _ in s._fields_}
+
+
+def cmg_batch_set_spin_budget(b, cycles):
+    _check(lib().cmg_batch_set_spin_budget(b.h, int(cycles)), "cmg_batch_set_spin_budget")
+
+
+def cmg_batch_solve(b, params=None, raise_on_error=True, **kw):
+    prm = params if params is not None else solve_params(**kw)
+    st = cmg_batch_stats()
+    rc = lib().cmg_batch_solve(b.h, C.byref(prm), C.byref(st))
+    if raise_on_error:
+        _check(rc, "cmg_batch_solve")
+    return rc, {f: getattr(st, f) for f, _ in st._fields_}
+
+
+def cmg_batch_patch_stats(b):
+    n = b.n_patches
+    rel = np.empty(n)
+    conv = np.empty(n, dtype=np.int32)
+    n0 = np.empty(n)
+    _check(lib().cmg_batch_patch_stats(b.h, rel.ctypes.data_as(C.c_void_p), conv.ctypes.data_as(C.c_void_p),
+                                       n0.ctypes.data_as(C.c_void_p)), "cmg_batch_patch_stats")
+    return rel, conv, n0
+
+
+def cmg_batch_autotune(b, params=None, **kw):
+    prm = params if params is not None else solve_params(**kw)
+    s = cmg_batch_schedule()
+    ms = C.c_double()
+    _check(lib().cmg_batch_autotune(b.h, C.byref(prm), C.byref(s), C.byref(ms)), "cmg_batch_autotune")
+    return {f: getattr(s, f) for f, _ in s._fields_}, ms.value
 
 
 def cmg_level_n_octs(lvl):

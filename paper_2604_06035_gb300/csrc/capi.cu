@@ -386,6 +386,82 @@ int cmg_level_set_schedule(cmg_level *lvl, int64_t tail_octs_fp64, int64_t tail_
   });
 }
 
+int cmg_batch_create(cmg_level *lvl, const int64_t *offsets, int n_patches, cmg_batch **out) {
+  return guard([&] {
+    need(out != nullptr, "out is NULL");
+    *out = nullptr;
+    need(lvl && offsets && n_patches >= 1, "bad batch arguments");
+    DeviceScope ds(lvl->device);
+    cmg::batch_create(lvl, offsets, n_patches, out);
+    return CMG_OK;
+  });
+}
+
+int cmg_batch_destroy(cmg_batch *batch) {
+  if (!batch) return CMG_OK;
+  return guard([&] {
+    cmg::batch_destroy(batch);
+    return CMG_OK;
+  });
+}
+
+int cmg_batch_set_schedule(cmg_batch *batch, const cmg_batch_schedule *schedule) {
+  return guard([&] {
+    need(batch && schedule, "NULL argument");
+    need(schedule->threads <= 512, "batch kernels use at most 512 threads per block");
+    need(schedule->n_pre >= 1, "the batch schedule needs n_pre >= 1");
+    cmg::batch_set_schedule(batch, schedule);
+    return CMG_OK;
+  });
+}
+
+int cmg_batch_get_schedule(cmg_batch *batch, cmg_batch_schedule *schedule) {
+  return guard([&] {
+    need(batch && schedule, "NULL argument");
+    *schedule = batch->sched;
+    return CMG_OK;
+  });
+}
+
+int cmg_batch_set_spin_budget(cmg_batch *batch, int64_t cycles) {
+  return guard([&] {
+    need(batch && cycles >= 0, "bad spin budget");
+    batch->spin_budget = cycles;
+    return CMG_OK;
+  });
+}
+
+int cmg_batch_solve(cmg_batch *batch, const cmg_solve_params *params, cmg_batch_stats *stats) {
+  return guard([&] {
+    need(batch && params, "NULL argument");
+    DeviceScope ds(batch->lvl->device);
+    const int st = cmg::batch_solve(batch, params, stats);
+    if (st == CMG_ERR_TIMEOUT) g_last_error = "a grid barrier of the persistent kernel gave up (spin budget)";
+    if (st == CMG_ERR_NOT_CONVERGED) g_last_error = "max_cycles reached above tol";
+    if (st == CMG_ERR_DIVERGED) g_last_error = "residual diverged";
+    return st;
+  });
+}
+
+int cmg_batch_patch_stats(cmg_batch *batch, double *rel, int32_t *converged_at, double *norm0) {
+  return guard([&] {
+    need(batch != nullptr, "NULL batch");
+    DeviceScope ds(batch->lvl->device);
+    cmg::batch_patch_stats(batch, rel, converged_at, norm0);
+    return CMG_OK;
+  });
+}
+
+int cmg_batch_autotune(cmg_batch *batch, const cmg_solve_params *params, cmg_batch_schedule *best,
+                       double *best_ms) {
+  return guard([&] {
+    need(batch && params, "NULL argument");
+    DeviceScope ds(batch->lvl->device);
+    cmg::batch_autotune(batch, params, best, best_ms);
+    return CMG_OK;
+  });
+}
+
 int cmg_level_mg_depth(const cmg_level *lvl, int *depth) {
   return guard([&] {
     need(lvl && depth, "NULL argument");

@@ -270,6 +270,26 @@ struct cmg_level {
   cmg::DeviceBuffers mem;
 };
 
+struct cmg_batch {
+  cmg_level *lvl = nullptr;
+  int n_patches = 0;
+  cmg_batch_schedule sched = {256, 2, 2, 2, 1};
+  long long spin_budget = 2000000000ll;
+  std::vector<int32_t *> pid;  // patch of each oct, per MG level
+  double *pstate = nullptr;    // n0, norm, s_emit, s_acc, rel: 5 x n_patches
+  int32_t *conv_at = nullptr;
+  int *ctrl = nullptr;         // 8 ints
+  unsigned *bar = nullptr;     // grid barrier words
+  int *h_ctrl = nullptr;       // pinned copy of ctrl
+  cmg::DeviceBuffers mem;
+  // the recorded solve graph and what it was recorded for
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  cmg_batch_schedule g_sched = {};
+  cmg_solve_params g_params = {};
+  int g_grid = 0;
+};
+
 namespace cmg {
 
 constexpr int kThreads = 256;
@@ -341,6 +361,14 @@ void finalize_norm(cmg_level *L, int n_partials, double scale, double *out);
 // tail.cu
 template <typename T>
 void tail_vcycle(cmg_level *L, int m0, const cmg_solve_params *p, const bool *zero_coarse);
+
+// batch.cu
+void batch_create(cmg_level *L, const int64_t *offsets, int n_patches, cmg_batch **out);
+void batch_destroy(cmg_batch *b);
+int batch_solve(cmg_batch *b, const cmg_solve_params *p, cmg_batch_stats *st);
+void batch_patch_stats(cmg_batch *b, double *rel, int32_t *conv, double *norm0);
+void batch_set_schedule(cmg_batch *b, const cmg_batch_schedule *s);
+void batch_autotune(cmg_batch *b, const cmg_solve_params *p, cmg_batch_schedule *best, double *best_ms);
 
 // solve.cu
 int solve(cmg_level *L, const cmg_solve_params *p, cmg_solve_stats *st);

@@ -173,6 +173,81 @@ def two_level_amr(base_level=7, sigma=1.5, seed=2):
     return amr_lognormal(base_level, 1, sigma, seed)
 
 
+def batched_patches(n_patches=512, n_min=64, n_max=200000, seed=4, level=11, sigma=1.5):
+    """Independent refined patches for the batched solve.
+
+    Patch sizes are log-uniform in [n_min, n_max] octs.  Patch k lives in its
+    own cube of 128 octs per side (an 8 x 8 x 8 arrangement at `level`, whose
+    box is 1024 octs wide) and is the compact, irregular set of the n_k octs
+    of the central 64^3 sub-cube nearest to the sub-cube centre (distances
+    perturbed by a seeded jitter), so patches are separated by at least 64
+    octs and their multigrid hierarchies never touch.  Each patch has its own
+    lognormal density (sigma_ln rho = sigma, k^-2 GRF on the 64^3 sub-cube;
+    the patches draw from 16 seeded fields, each patch with its own seeded
+    periodic shift and sign).  The parent level (level - 1) holds the parents
+    of every patch oct dilated by one oct, with phi = a seeded sum of 8 low-k
+    (|k| <= 4) sine modes at the parent cell centres (the smooth coarse field
+    of the Dirichlet values).
+
+    Returns dict(level, coords [N,3] uint32 (patches contiguous), offsets
+    [n_patches+1], rho [N,8], parent_coords, parent_phi [M,8])."""
+    if n_patches > 512:
+        raise ValueError("at most 512 patches fit the 8^3 cube arrangement")
+    rng = np.random.default_rng(seed)
+    sizes = np.rint(np.exp(rng.uniform(np.log(n_min), np.log(n_max), n_patches))).astype(np.int64)
+    sizes = np.clip(sizes, n_min, min(n_max, 64 ** 3))
+    r = np.arange(64)
+    z, y, x = np.meshgrid(r, r, r, indexing="ij")
+    sub = np.stack([x.ravel(), y.ravel(), z.ravel()], 1)
+    d2 = ((sub - 31.5) ** 2).sum(axis=1)
+    n_shapes = 8
+    orders = [np.argsort(d2 + np.random.default_rng([seed, s, 2]).uniform(0.0, 40.0, len(d2)), kind="stable")
+              for s in range(n_shapes)]
+    fields = []
+    for s in range(16):
+        e = np.exp(sigma * grf(64, 1.0, [seed, s, 1]))
+        fields.append(e / e.mean())
+    coords, rho, offsets, parents = [], [], [0], []
+    for k in range(n_patches):
+        prng = np.random.default_rng([seed, k])
+        cells = sub[orders[k % n_shapes][:sizes[k]]]
+        cube = np.array([k % 8, (k // 8) % 8, k // 64]) * 128 + 32
+        coords.append((cells + cube).astype(np.uint32))
+        shift = prng.integers(0, 64, size=3)
+        sign = 1.0 if prng.uniform() < 0.5 else -1.0
+        e = np.roll(fields[k % 16], tuple(shift), axis=(0, 1, 2))
+        if sign < 0:
+            e = 1.0 / e
+            e /= e.mean()
+        rho.append(child_density(e[cells[:, 0], cells[:, 1], cells[:, 2]], seed * 1000 + k, level, 0.5))
+        offsets.append(offsets[-1] + sizes[k])
+        # parent octs of the patch (a 32^3 window of level - 1), dilated by one oct
+        m = np.zeros((34, 34, 34), dtype=bool)
+        pc = cells >> 1
+        m[pc[:, 0] + 1, pc[:, 1] + 1, pc[:, 2] + 1] = True
+        d = m.copy()
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dz in (-1, 0, 1):
+                    d |= np.roll(m, (dx, dy, dz), axis=(0, 1, 2))
+        parents.append(np.argwhere(d) - 1 + cube // 2)
+    coords = np.concatenate(coords)
+    rho = np.concatenate(rho)
+    parent = np.concatenate(parents).astype(np.uint32)
+    off = child_offsets()
+    hp = 1.0 / (1 << (level - 1))
+    X = (2 * parent[:, None, :].astype(np.float64) + off[None] + 0.5) * hp
+    phi = np.zeros(X.shape[:2])
+    for _ in range(8):
+        kv = rng.integers(-4, 5, size=3)
+        while not kv.any() or np.sqrt((kv ** 2).sum()) > 4:
+            kv = rng.integers(-4, 5, size=3)
+        amp, ph = rng.normal(0.0, 1.0), rng.uniform(0, 2 * np.pi)
+        phi += amp * np.sin(2 * np.pi * (X @ kv) + ph)
+    return {"level": level, "coords": coords, "offsets": np.array(offsets, dtype=np.int64), "rho": rho,
+            "parent_coords": parent, "parent_phi": phi, "sizes": sizes}
+
+
 def mixed_amr(base_level=8, n_refine=3, sigma=2.0, seed=3):
     """Periodic lognormal base (sigma_ln rho = 2) plus three refined levels at
     threshold 8 rho_bar each (the 256^3 mixed-precision workload)."""
