@@ -471,6 +471,7 @@ void record(cmg_batch *b, const cmg_solve_params *p) {
   b->g_sched = b->sched;
   b->g_params = *p;
   b->g_grid = grid;
+  b->g_budget = b->spin_budget;
 }
 
 int64_t updates_per_cycle(const cmg_batch *b, bool mixed) {
@@ -498,7 +499,9 @@ int batch_solve(cmg_batch *b, const cmg_solve_params *p, cmg_batch_stats *st) {
   cmg_ctx *ctx = L->ctx;
   const bool mixed = p->precision == CMG_PREC_MIXED;
   if (mixed) ensure_fp32(L);
-  if (!b->exec || !same_sched(b->sched, b->g_sched) || !same_params(*p, b->g_params)) record(b, p);
+  if (!b->exec || !same_sched(b->sched, b->g_sched) || !same_params(*p, b->g_params) ||
+      b->spin_budget != b->g_budget)
+    record(b, p);
   CMG_CUDA(cudaEventRecord(ctx->ev0, ctx->stream));
   CMG_CUDA(cudaGraphLaunch(b->exec, ctx->stream));
   CMG_CUDA(cudaEventRecord(ctx->ev1, ctx->stream));

@@ -288,6 +288,7 @@ struct cmg_batch {
   cmg_batch_schedule g_sched = {};
   cmg_solve_params g_params = {};
   int g_grid = 0;
+  long long g_budget = 0;
 };
 
 namespace cmg {
