@@ -233,7 +233,7 @@ def batched_patches(n_patches=512, n_min=64, n_max=200000, seed=4, level=11, sig
         parents.append(np.argwhere(d) - 1 + cube // 2)
     coords = np.concatenate(coords)
     rho = np.concatenate(rho)
-    parent = np.concatenate(parents).astype(np.uint32)
+    parent = np.ascontiguousarray(np.concatenate(parents), dtype=np.uint32)
     off = child_offsets()
     hp = 1.0 / (1 << (level - 1))
     X = (2 * parent[:, None, :].astype(np.float64) + off[None] + 0.5) * hp
