@@ -241,6 +241,44 @@ int cmg_batch_patch_stats(cmg_batch *batch, double *rel, int32_t *converged_at, 
 int cmg_batch_autotune(cmg_batch *batch, const cmg_solve_params *params, cmg_batch_schedule *best,
                        double *best_ms);
 
+/* ---- learned warm start (no counterpart in the paper) ----
+ * A 3-level 3-D U-Net (16/32/64 channels) on periodic D^3 blocks predicts
+ * phi from (rho, phi_prev); its prediction is the initial guess of a level
+ * solve.  Layers (3x3x3 convs with circular padding, bias and ReLU):
+ *   enc0a 16->16, enc0b 16->16 (D) | pool | enc1a 16->32, enc1b 32->32 (D/2) |
+ *   pool | bota 32->64, botb 64->64 (D/4) | up x2, concat with enc1b |
+ *   dec1a 96->32, dec1b 32->32 | up x2, concat with enc0b | dec0a 48->16,
+ *   dec0b 16->16 | head 1x1x1 16->1 (linear) = delta.
+ * Input channels: (rho - mean)/std, phi_prev/rms(phi_prev), 14 zeros;
+ * phi_pred = phi_prev + rms(phi_prev) * delta.  Parameters: FP32 master
+ * vector (per layer [Cout][27][Cin] weights then biases; head 16 + 1);
+ * convolutions run on BF16 weights and BF16 activations with FP32
+ * accumulation (tensor cores), the head and the optimiser in FP32.
+ * Fields are dense [batch][D][D][D] (z, y, x) FP32 arrays in `mem`. */
+typedef struct cmg_unet cmg_unet;
+/* grid_dim: multiple of 16; max_batch: samples per call. */
+int cmg_unet_create(cmg_ctx *ctx, int grid_dim, int max_batch, cmg_unet **out);
+int cmg_unet_destroy(cmg_unet *net);
+int cmg_unet_n_params(const cmg_unet *net, int64_t *n);
+/* Replace the master parameters (resets the Adam moments). */
+int cmg_unet_set_params(cmg_unet *net, const float *params, cmg_mem mem);
+int cmg_unet_get_params(cmg_unet *net, float *out, cmg_mem mem);
+/* Inference: phi_pred and/or delta (either may be NULL). */
+int cmg_unet_forward(cmg_unet *net, const float *rho, const float *phi_prev, int batch, float *phi_pred,
+                     float *delta, cmg_mem mem);
+/* Loss = mean over all voxels of (delta - (phi_next - phi_prev)/rms)^2 and its
+ * gradient (kept inside for cmg_unet_adam_step; copied to grads if not NULL;
+ * loss is written as a host double when mem is HOST, else it is the device
+ * sum of squared errors). */
+int cmg_unet_gradients(cmg_unet *net, const float *rho, const float *phi_prev, const float *phi_next, int batch,
+                       float *grads, double *loss, cmg_mem mem);
+/* One Adam step on the master parameters with the last gradients. */
+int cmg_unet_adam_step(cmg_unet *net, float lr, float beta1, float beta2, float eps);
+/* Device copy between a dense [D][D][D] (z, y, x) FP64 field and the oct-major
+ * [n][8] field of the full periodic level whose octs are listed x fastest
+ * (to_octs = 1: dense -> octs; 0: octs -> dense).  Both device pointers. */
+int cmg_dense_octs(cmg_ctx *ctx, const double *src, int grid_dim, double *dst, int to_octs);
+
 /* ---- residual norm without allocation (the paper has no counterpart) ----
  * The level objects above allocate device memory when they are built, and
  * their residual norm reduces through scratch the level owns.  Callers that

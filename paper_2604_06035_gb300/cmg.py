@@ -115,6 +115,15 @@ _SIGS = {
     "cmg_batch_solve": (_I, [_P, C.POINTER(cmg_solve_params), _P]),
     "cmg_batch_patch_stats": (_I, [_P, _P, _P, _P]),
     "cmg_batch_autotune": (_I, [_P, C.POINTER(cmg_solve_params), _P, C.POINTER(C.c_double)]),
+    "cmg_unet_create": (_I, [_P, _I, _I, C.POINTER(_P)]),
+    "cmg_unet_destroy": (_I, [_P]),
+    "cmg_unet_n_params": (_I, [_P, C.POINTER(_I64)]),
+    "cmg_unet_set_params": (_I, [_P, _P, _I]),
+    "cmg_unet_get_params": (_I, [_P, _P, _I]),
+    "cmg_unet_forward": (_I, [_P, _P, _P, _I, _P, _P, _I]),
+    "cmg_unet_gradients": (_I, [_P, _P, _P, _P, _I, _P, C.POINTER(C.c_double), _I]),
+    "cmg_unet_adam_step": (_I, [_P, C.c_float, C.c_float, C.c_float, C.c_float]),
+    "cmg_dense_octs": (_I, [_P, _P, _I, _P, _I]),
 }
 
 _lib = None
@@ -233,9 +242,12 @@ class CtxHandle:
 
 
 def cmg_ctx_destroy(ctx):
-    import weakref  # noqa: F401
     if not ctx.h:
         return
+    for ref in getattr(ctx, "unets", []):
+        u = ref()
+        if u is not None and u.h:
+            cmg_unet_destroy(u)
     for ref in reversed(ctx.levels):
         lv = ref()
         if lv is not None and lv.h:
@@ -530,6 +542,109 @@ def cmg_level_mg_step(lvl, m, op, precision=CMG_PREC_FP64, n=1):
     v = C.c_double(0.0)
     _check(lib().cmg_level_mg_step(lvl.h, m, op, precision, n, C.byref(v)), "cmg_level_mg_step")
     return v.value
+
+
+class UnetHandle:
+    """Owns a cmg_unet*; destroyed before its context."""
+
+    def __init__(self, h, ctx, grid_dim, max_batch):
+        import weakref
+        self.h = h
+        self.ctx = ctx
+        self.D = grid_dim
+        self.max_batch = max_batch
+        if not hasattr(ctx, "unets"):
+            ctx.unets = []
+        ctx.unets.append(weakref.ref(self))
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            h, self.h = self.h, None
+            _lib.cmg_unet_destroy(h)
+
+
+def cmg_unet_create(ctx, grid_dim=64, max_batch=4):
+    h = C.c_void_p()
+    _check(lib().cmg_unet_create(ctx, grid_dim, max_batch, C.byref(h)), "cmg_unet_create")
+    return UnetHandle(h, ctx, grid_dim, max_batch)
+
+
+def cmg_unet_destroy(net):
+    if net.h:
+        h, net.h = net.h, None
+        _check(lib().cmg_unet_destroy(h), "cmg_unet_destroy")
+
+
+def cmg_unet_n_params(net):
+    v = C.c_int64()
+    _check(lib().cmg_unet_n_params(net.h, C.byref(v)), "cmg_unet_n_params")
+    return v.value
+
+
+def cmg_unet_set_params(net, params):
+    p, mem, keep = _in(params, np.float32)
+    _check(lib().cmg_unet_set_params(net.h, p, mem), "cmg_unet_set_params")
+
+
+def cmg_unet_get_params(net, device=False):
+    o, mem, res = _out((cmg_unet_n_params(net),), np.float32, device=device)
+    _check(lib().cmg_unet_get_params(net.h, o, mem), "cmg_unet_get_params")
+    return res
+
+
+def _batch_of(net, x):
+    n = x.numel() if _is_torch(x) else np.asarray(x).size
+    return n // (net.D ** 3)
+
+
+def cmg_unet_forward(net, rho, phi_prev, delta=False):
+    """phi_pred (and delta if asked) for a batch of dense [B][D][D][D] fields."""
+    pr, mem, k1 = _in(rho, np.float32)
+    pp, mem2, k2 = _in(phi_prev, np.float32)
+    _same_mem(mem, mem2, "cmg_unet_forward")
+    B = _batch_of(net, rho)
+    shape = (B, net.D, net.D, net.D)
+    po, _, out = _out(shape, np.float32, device=(mem == CMG_MEM_DEVICE))
+    pd, dres = None, None
+    if delta:
+        pd, _, dres = _out(shape, np.float32, device=(mem == CMG_MEM_DEVICE))
+    _check(lib().cmg_unet_forward(net.h, pr, pp, B, po, pd, mem), "cmg_unet_forward")
+    return (out, dres) if delta else out
+
+
+def cmg_unet_gradients(net, rho, phi_prev, phi_next, grads=True):
+    """(loss, gradient or None).  Host inputs give the mean loss; device inputs
+    return the loss as a device sum of squares (see include/cmg.h)."""
+    pr, mem, k1 = _in(rho, np.float32)
+    pp, _, k2 = _in(phi_prev, np.float32)
+    pn, _, k3 = _in(phi_next, np.float32)
+    B = _batch_of(net, rho)
+    pg, res = None, None
+    if grads:
+        pg, _, res = _out((cmg_unet_n_params(net),), np.float32, device=(mem == CMG_MEM_DEVICE))
+    loss = C.c_double(0.0)
+    if mem == CMG_MEM_DEVICE:
+        import torch
+        lt = torch.zeros(1, dtype=torch.float64, device="cuda")
+        _check(lib().cmg_unet_gradients(net.h, pr, pp, pn, B, pg, C.cast(C.c_void_p(lt.data_ptr()),
+                                                                         C.POINTER(C.c_double)), mem),
+               "cmg_unet_gradients")
+        return lt, res
+    _check(lib().cmg_unet_gradients(net.h, pr, pp, pn, B, pg, C.byref(loss), mem), "cmg_unet_gradients")
+    return loss.value, res
+
+
+def cmg_unet_adam_step(net, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    _check(lib().cmg_unet_adam_step(net.h, lr, beta1, beta2, eps), "cmg_unet_adam_step")
+
+
+def cmg_dense_octs(ctx, src, grid_dim, dst, to_octs):
+    """Device copy dense [D^3] <-> oct-major [n][8] of a full periodic level (x-fastest octs)."""
+    ps, ms, _ = _in(src, np.float64)
+    pd, md, _ = _in(dst, np.float64)
+    _same_mem(ms, CMG_MEM_DEVICE, "cmg_dense_octs")
+    _same_mem(md, CMG_MEM_DEVICE, "cmg_dense_octs")
+    _check(lib().cmg_dense_octs(ctx, ps, grid_dim, pd, int(to_octs)), "cmg_dense_octs")
 
 
 def cmg_residual_norm2_noalloc(neighbors, ghosts, phi, f, h, norm2, stream=0):

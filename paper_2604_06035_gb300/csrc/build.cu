@@ -36,6 +36,7 @@ void DeviceBuffers::release() {
 
 template uint64_t *DeviceBuffers::alloc<uint64_t>(int64_t, bool, cudaStream_t);
 template int64_t *DeviceBuffers::alloc<int64_t>(int64_t, bool, cudaStream_t);
+template uint16_t *DeviceBuffers::alloc<uint16_t>(int64_t, bool, cudaStream_t);
 template int32_t *DeviceBuffers::alloc<int32_t>(int64_t, bool, cudaStream_t);
 template uint32_t *DeviceBuffers::alloc<uint32_t>(int64_t, bool, cudaStream_t);
 template uint8_t *DeviceBuffers::alloc<uint8_t>(int64_t, bool, cudaStream_t);
