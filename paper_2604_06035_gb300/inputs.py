@@ -248,6 +248,21 @@ def batched_patches(n_patches=512, n_min=64, n_max=200000, seed=4, level=11, sig
             "parent_coords": parent, "parent_phi": phi, "sizes": sizes}
 
 
+def warmstart_trajectory(D=64, n_steps=20, sigma=1.5, eps=0.05, seed=5, traj=0):
+    """Densities of one evolving periodic block for the learned warm start:
+    ln rho_0 = sigma g_0, ln rho_{t+1} = ln rho_t + eps g_{t+1} (g unit-rms
+    k^-2 GRFs seeded by (seed, traj, t)), each rho renormalised to mean 1.
+    Returns float64 [n_steps + 1, D, D, D] indexed [t, z, y, x]."""
+    out = np.empty((n_steps + 1, D, D, D))
+    lnr = sigma * grf(D, 1.0, [seed, traj, 0])
+    for t in range(n_steps + 1):
+        if t:
+            lnr = lnr + eps * grf(D, 1.0, [seed, traj, t])
+        e = np.exp(lnr)
+        out[t] = (e / e.mean()).transpose(2, 1, 0)
+    return out
+
+
 def mixed_amr(base_level=8, n_refine=3, sigma=2.0, seed=3):
     """Periodic lognormal base (sigma_ln rho = 2) plus three refined levels at
     threshold 8 rho_bar each (the 256^3 mixed-precision workload)."""
