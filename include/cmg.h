@@ -249,8 +249,11 @@ int cmg_batch_autotune(cmg_batch *batch, const cmg_solve_params *params, cmg_bat
  *   pool | bota 32->64, botb 64->64 (D/4) | up x2, concat with enc1b |
  *   dec1a 96->32, dec1b 32->32 | up x2, concat with enc0b | dec0a 48->16,
  *   dec0b 16->16 | head 1x1x1 16->1 (linear) = delta.
- * Input channels: (rho - mean)/std, phi_prev/rms(phi_prev), 14 zeros;
- * phi_pred = phi_prev + rms(phi_prev) * delta.  Parameters: FP32 master
+ * Input channels: (rho - mean)/std, field/rms(field), 14 zeros; the
+ * prediction is base + rms(field) * delta (base defaults to field).  For the
+ * warm start, field = the FP64 residual f - L phi_prev of the previous
+ * potential for the new density and base = phi_prev, so the network learns
+ * the correction of phi_prev.  Parameters: FP32 master
  * vector (per layer [Cout][27][Cin] weights then biases; head 16 + 1);
  * convolutions run on BF16 weights and BF16 activations with FP32
  * accumulation (tensor cores), the head and the optimiser in FP32.
@@ -263,15 +266,15 @@ int cmg_unet_n_params(const cmg_unet *net, int64_t *n);
 /* Replace the master parameters (resets the Adam moments). */
 int cmg_unet_set_params(cmg_unet *net, const float *params, cmg_mem mem);
 int cmg_unet_get_params(cmg_unet *net, float *out, cmg_mem mem);
-/* Inference: phi_pred and/or delta (either may be NULL). */
-int cmg_unet_forward(cmg_unet *net, const float *rho, const float *phi_prev, int batch, float *phi_pred,
-                     float *delta, cmg_mem mem);
-/* Loss = mean over all voxels of (delta - (phi_next - phi_prev)/rms)^2 and its
+/* Inference: prediction and/or delta (either may be NULL); base may be NULL. */
+int cmg_unet_forward(cmg_unet *net, const float *rho, const float *field, const float *base, int batch,
+                     float *pred, float *delta, cmg_mem mem);
+/* Loss = mean over all voxels of (delta - (target - base)/rms(field))^2 and its
  * gradient (kept inside for cmg_unet_adam_step; copied to grads if not NULL;
  * loss is written as a host double when mem is HOST, else it is the device
  * sum of squared errors). */
-int cmg_unet_gradients(cmg_unet *net, const float *rho, const float *phi_prev, const float *phi_next, int batch,
-                       float *grads, double *loss, cmg_mem mem);
+int cmg_unet_gradients(cmg_unet *net, const float *rho, const float *field, const float *base, const float *target,
+                       int batch, float *grads, double *loss, cmg_mem mem);
 /* One Adam step on the master parameters with the last gradients. */
 int cmg_unet_adam_step(cmg_unet *net, float lr, float beta1, float beta2, float eps);
 /* Device copy between a dense [D][D][D] (z, y, x) FP64 field and the oct-major

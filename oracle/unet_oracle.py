@@ -116,20 +116,23 @@ def up_bwd(d):
     return d.reshape(D, 2, D, 2, D, 2, -1).sum(axis=(1, 3, 5))
 
 
-def inputs(rho, phi_prev):
-    """Network input [D,D,D,16] and the phi scale (rms of phi_prev)."""
-    s = np.sqrt(np.mean(phi_prev ** 2))
+def inputs(rho, field):
+    """Network input [D,D,D,16] and the output scale (rms of field)."""
+    s = np.sqrt(np.mean(field ** 2))
     x = np.zeros(rho.shape + (16,))
     x[..., 0] = (rho - rho.mean()) / rho.std()
-    x[..., 1] = phi_prev / s
+    x[..., 1] = field / s
     return x, s
 
 
-def forward(params, rho, phi_prev, bf=False):
-    """Returns (delta [D,D,D], phi_pred, cache)."""
+def forward(params, rho, field, base=None, bf=False):
+    """Returns (delta [D,D,D], base + rms(field) * delta, cache); base
+    defaults to field."""
     P = unpack(params)
     R = bf16 if bf else (lambda a: a)
-    x, s = inputs(rho, phi_prev)
+    if base is None:
+        base = field
+    x, s = inputs(rho, field)
     x = R(x)
     cache = {"x": x, "s": s}
 
@@ -147,16 +150,18 @@ def forward(params, rho, phi_prev, bf=False):
     hw, hb = P["head"]
     delta = d0 @ hw + hb
     cache["d0"] = d0
-    return delta, phi_prev + s * delta, cache
+    return delta, base + s * delta, cache
 
 
-def loss_and_grads(params, rho, phi_prev, phi_next, bf=False):
-    """MSE between delta and (phi_next - phi_prev) / rms(phi_prev) over the
-    voxels; returns (loss, flat gradient)."""
+def loss_and_grads(params, rho, field, target, base=None, bf=False):
+    """MSE between delta and (target - base) / rms(field) over the voxels
+    (base defaults to field); returns (loss, flat gradient)."""
     P = unpack(params)
     R = bf16 if bf else (lambda a: a)
-    delta, _, c = forward(params, rho, phi_prev, bf)
-    target = (phi_next - phi_prev) / c["s"]
+    if base is None:
+        base = field
+    delta, _, c = forward(params, rho, field, base, bf)
+    target = (target - base) / c["s"]
     V = delta.size
     loss = np.mean((delta - target) ** 2)
     g = {}

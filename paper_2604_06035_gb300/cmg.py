@@ -120,8 +120,8 @@ _SIGS = {
     "cmg_unet_n_params": (_I, [_P, C.POINTER(_I64)]),
     "cmg_unet_set_params": (_I, [_P, _P, _I]),
     "cmg_unet_get_params": (_I, [_P, _P, _I]),
-    "cmg_unet_forward": (_I, [_P, _P, _P, _I, _P, _P, _I]),
-    "cmg_unet_gradients": (_I, [_P, _P, _P, _P, _I, _P, C.POINTER(C.c_double), _I]),
+    "cmg_unet_forward": (_I, [_P, _P, _P, _P, _I, _P, _P, _I]),
+    "cmg_unet_gradients": (_I, [_P, _P, _P, _P, _P, _I, _P, C.POINTER(C.c_double), _I]),
     "cmg_unet_adam_step": (_I, [_P, C.c_float, C.c_float, C.c_float, C.c_float]),
     "cmg_dense_octs": (_I, [_P, _P, _I, _P, _I]),
 }
@@ -597,27 +597,34 @@ def _batch_of(net, x):
     return n // (net.D ** 3)
 
 
-def cmg_unet_forward(net, rho, phi_prev, delta=False):
-    """phi_pred (and delta if asked) for a batch of dense [B][D][D][D] fields."""
+def cmg_unet_forward(net, rho, field, base=None, delta=False):
+    """Prediction base + rms(field) delta (and delta if asked) for a batch of
+    dense [B][D][D][D] fields; base defaults to field."""
     pr, mem, k1 = _in(rho, np.float32)
-    pp, mem2, k2 = _in(phi_prev, np.float32)
+    pp, mem2, k2 = _in(field, np.float32)
     _same_mem(mem, mem2, "cmg_unet_forward")
+    pb, k4 = None, None
+    if base is not None:
+        pb, _, k4 = _in(base, np.float32)
     B = _batch_of(net, rho)
     shape = (B, net.D, net.D, net.D)
     po, _, out = _out(shape, np.float32, device=(mem == CMG_MEM_DEVICE))
     pd, dres = None, None
     if delta:
         pd, _, dres = _out(shape, np.float32, device=(mem == CMG_MEM_DEVICE))
-    _check(lib().cmg_unet_forward(net.h, pr, pp, B, po, pd, mem), "cmg_unet_forward")
+    _check(lib().cmg_unet_forward(net.h, pr, pp, pb, B, po, pd, mem), "cmg_unet_forward")
     return (out, dres) if delta else out
 
 
-def cmg_unet_gradients(net, rho, phi_prev, phi_next, grads=True):
+def cmg_unet_gradients(net, rho, field, target, base=None, grads=True):
     """(loss, gradient or None).  Host inputs give the mean loss; device inputs
     return the loss as a device sum of squares (see include/cmg.h)."""
     pr, mem, k1 = _in(rho, np.float32)
-    pp, _, k2 = _in(phi_prev, np.float32)
-    pn, _, k3 = _in(phi_next, np.float32)
+    pp, _, k2 = _in(field, np.float32)
+    pn, _, k3 = _in(target, np.float32)
+    pb, k4 = None, None
+    if base is not None:
+        pb, _, k4 = _in(base, np.float32)
     B = _batch_of(net, rho)
     pg, res = None, None
     if grads:
@@ -626,11 +633,11 @@ def cmg_unet_gradients(net, rho, phi_prev, phi_next, grads=True):
     if mem == CMG_MEM_DEVICE:
         import torch
         lt = torch.zeros(1, dtype=torch.float64, device="cuda")
-        _check(lib().cmg_unet_gradients(net.h, pr, pp, pn, B, pg, C.cast(C.c_void_p(lt.data_ptr()),
-                                                                         C.POINTER(C.c_double)), mem),
+        _check(lib().cmg_unet_gradients(net.h, pr, pp, pb, pn, B, pg,
+                                        C.cast(C.c_void_p(lt.data_ptr()), C.POINTER(C.c_double)), mem),
                "cmg_unet_gradients")
         return lt, res
-    _check(lib().cmg_unet_gradients(net.h, pr, pp, pn, B, pg, C.byref(loss), mem), "cmg_unet_gradients")
+    _check(lib().cmg_unet_gradients(net.h, pr, pp, pb, pn, B, pg, C.byref(loss), mem), "cmg_unet_gradients")
     return loss.value, res
 
 

@@ -492,7 +492,9 @@ struct cmg_unet {
   __nv_bfloat16 *gp = nullptr, *gu = nullptr;
   float *delta = nullptr, *norm = nullptr;
   double *stats = nullptr, *loss = nullptr;
-  float *in_rho = nullptr, *in_phi = nullptr, *in_next = nullptr, *out_phi = nullptr;
+  // inputs: rho, field (its rms scales the output), base (the output is
+  // base + rms(field) delta), target (training); out = the prediction
+  float *in_rho = nullptr, *in_phi = nullptr, *in_base = nullptr, *in_next = nullptr, *out_phi = nullptr;
   int adam_t = 0;
   bool weights_ready = false;
   cmg::DeviceBuffers mem;
@@ -615,7 +617,7 @@ void forward(cmg_unet *U, int B, float *phi_pred) {
   layer(8, U->c0, U->a[8]);
   layer(9, U->a[8], U->a[9]);
   const float *hw = U->params + layer_offset(10);
-  k_head<<<gsz(B * V0), 256, 0, s>>>(U->a[9], hw, hw + 16, U->in_phi, U->norm, V0, B, U->delta, phi_pred);
+  k_head<<<gsz(B * V0), 256, 0, s>>>(U->a[9], hw, hw + 16, U->in_base, U->norm, V0, B, U->delta, phi_pred);
   CMG_CUDA(cudaGetLastError());
   (void)D2;
 }
@@ -629,7 +631,7 @@ void backward(cmg_unet *U, int B) {
   CMG_CUDA(cudaMemsetAsync(U->grads, 0, sizeof(float) * U->np, s));
   CMG_CUDA(cudaMemsetAsync(U->loss, 0, sizeof(double), s));
   float *ghw = U->grads + layer_offset(10);
-  k_head_grad<<<gsz(B * V0), 256, 0, s>>>(U->a[9], U->params + layer_offset(10), U->delta, U->in_phi, U->in_next,
+  k_head_grad<<<gsz(B * V0), 256, 0, s>>>(U->a[9], U->params + layer_offset(10), U->delta, U->in_base, U->in_next,
                                           U->norm, V0, B, U->g0, ghw, ghw + 16, U->loss);
   CMG_CUDA(cudaGetLastError());
   // back through layer l: g (grad of its output, bf16) -> grad of its input
@@ -742,6 +744,7 @@ int cmg_unet_create(cmg_ctx *ctx, int grid_dim, int max_batch, cmg_unet **out) {
       U->loss = M.alloc<double>(1);
       U->in_rho = M.alloc<float>(B * V0);
       U->in_phi = M.alloc<float>(B * V0);
+      U->in_base = M.alloc<float>(B * V0);
       U->in_next = M.alloc<float>(B * V0);
       U->out_phi = M.alloc<float>(B * V0);
       CMG_CUDA(cudaStreamSynchronize(s));
@@ -797,15 +800,16 @@ int cmg_unet_get_params(cmg_unet *U, float *out, cmg_mem mem) {
   });
 }
 
-int cmg_unet_forward(cmg_unet *U, const float *rho, const float *phi_prev, int batch, float *phi_pred, float *delta,
-                     cmg_mem mem) {
+int cmg_unet_forward(cmg_unet *U, const float *rho, const float *field, const float *base, int batch,
+                     float *phi_pred, float *delta, cmg_mem mem) {
   return unet_guard([&] {
-    if (!U || !rho || !phi_prev || batch < 1 || batch > U->max_batch) return (int)CMG_ERR_INVALID_ARG;
+    if (!U || !rho || !field || batch < 1 || batch > U->max_batch) return (int)CMG_ERR_INVALID_ARG;
     cudaSetDevice(U->ctx->device);
     const int64_t n = (int64_t)batch * U->D * U->D * U->D;
     cudaStream_t s = U->ctx->stream;
     cmg::copy_in(U, U->in_rho, rho, n, mem);
-    cmg::copy_in(U, U->in_phi, phi_prev, n, mem);
+    cmg::copy_in(U, U->in_phi, field, n, mem);
+    cmg::copy_in(U, U->in_base, base ? base : field, n, mem);
     cmg::forward(U, batch, U->out_phi);
     const cudaMemcpyKind k = mem == CMG_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     if (phi_pred) CMG_CUDA(cudaMemcpyAsync(phi_pred, U->out_phi, sizeof(float) * n, k, s));
@@ -815,16 +819,17 @@ int cmg_unet_forward(cmg_unet *U, const float *rho, const float *phi_prev, int b
   });
 }
 
-int cmg_unet_gradients(cmg_unet *U, const float *rho, const float *phi_prev, const float *phi_next, int batch,
-                       float *grads, double *loss, cmg_mem mem) {
+int cmg_unet_gradients(cmg_unet *U, const float *rho, const float *field, const float *base, const float *target,
+                       int batch, float *grads, double *loss, cmg_mem mem) {
   return unet_guard([&] {
-    if (!U || !rho || !phi_prev || !phi_next || batch < 1 || batch > U->max_batch) return (int)CMG_ERR_INVALID_ARG;
+    if (!U || !rho || !field || !target || batch < 1 || batch > U->max_batch) return (int)CMG_ERR_INVALID_ARG;
     cudaSetDevice(U->ctx->device);
     const int64_t n = (int64_t)batch * U->D * U->D * U->D;
     cudaStream_t s = U->ctx->stream;
     cmg::copy_in(U, U->in_rho, rho, n, mem);
-    cmg::copy_in(U, U->in_phi, phi_prev, n, mem);
-    cmg::copy_in(U, U->in_next, phi_next, n, mem);
+    cmg::copy_in(U, U->in_phi, field, n, mem);
+    cmg::copy_in(U, U->in_base, base ? base : field, n, mem);
+    cmg::copy_in(U, U->in_next, target, n, mem);
     cmg::forward(U, batch, nullptr);
     cmg::backward(U, batch);
     const cudaMemcpyKind k = mem == CMG_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;

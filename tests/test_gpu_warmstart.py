@@ -44,8 +44,8 @@ def test_warmstart_trains_and_helps(cmg):
         S = W.PeriodicSolver(ctx, 32)
         rho, prev = data["rho"][10, 5], data["phi"][10, 4]
         a, _ = S.solve(rho, prev, 1e-12)
-        pred = cmg.cmg_unet_forward(net, rho[None].contiguous(), prev[None].contiguous())
-        b, _ = S.solve(rho, pred[0], 1e-12)
+        pred = W.predict(S, net, rho, prev)
+        b, _ = S.solve(rho, pred, 1e-12)
         assert float((a - b).abs().max() / a.abs().max()) <= 1e-9
         del net, S
         torch.cuda.synchronize()
