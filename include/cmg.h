@@ -250,7 +250,8 @@ int cmg_batch_autotune(cmg_batch *batch, const cmg_solve_params *params, cmg_bat
  *   dec1a 96->32, dec1b 32->32 | up x2, concat with enc0b | dec0a 48->16,
  *   dec0b 16->16 | head 1x1x1 16->1 (linear) = delta.
  * Input channels: (rho - mean)/std, field/rms(field), 14 zeros; the
- * prediction is base + rms(field) * delta (base defaults to field).  For the
+ * prediction is base + c * rms(field) * delta (base defaults to field; c is
+ * the output scale, 1 unless set).  For the
  * warm start, field = the FP64 residual f - L phi_prev of the previous
  * potential for the new density and base = phi_prev, so the network learns
  * the correction of phi_prev.  Parameters: FP32 master
@@ -266,10 +267,15 @@ int cmg_unet_n_params(const cmg_unet *net, int64_t *n);
 /* Replace the master parameters (resets the Adam moments). */
 int cmg_unet_set_params(cmg_unet *net, const float *params, cmg_mem mem);
 int cmg_unet_get_params(cmg_unet *net, float *out, cmg_mem mem);
+/* Output scale c > 0 (finite), kept with the network: the trainer sets it to
+ * the typical size of (target - base)/rms(field) so that delta is O(1).
+ * CMG_ERR_INVALID_ARG otherwise. */
+int cmg_unet_set_output_scale(cmg_unet *net, float scale);
+int cmg_unet_get_output_scale(const cmg_unet *net, float *scale);
 /* Inference: prediction and/or delta (either may be NULL); base may be NULL. */
 int cmg_unet_forward(cmg_unet *net, const float *rho, const float *field, const float *base, int batch,
                      float *pred, float *delta, cmg_mem mem);
-/* Loss = mean over all voxels of (delta - (target - base)/rms(field))^2 and its
+/* Loss = mean over all voxels of (delta - (target - base)/(c rms(field)))^2 and its
  * gradient (kept inside for cmg_unet_adam_step; copied to grads if not NULL;
  * loss is written as a host double when mem is HOST, else it is the device
  * sum of squared errors). */

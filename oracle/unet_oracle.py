@@ -16,8 +16,9 @@ periodic D^3 block, inputs (rho, phi_prev), output the change of phi.
   head 1x1x1 16->1 (linear): delta
 
 Every 3x3x3 convolution has circular padding, a bias and a ReLU.  Input
-channels: 0 = (rho - mean rho) / std rho, 1 = phi_prev / rms phi_prev, 2..15
-zero.  phi_pred = phi_prev + rms(phi_prev) * delta.
+channels: 0 = (rho - mean rho) / std rho, 1 = field / rms field, 2..15 zero.
+The prediction is base + c rms(field) delta (base defaults to field, c is the
+output scale).
 
 Activations are channels-last arrays [D, D, D, C] indexed [z, y, x, c]; conv
 weights are [Cout, 27, Cin] with tap t = 9 (dz+1) + 3 (dy+1) + (dx+1); the
@@ -125,14 +126,15 @@ def inputs(rho, field):
     return x, s
 
 
-def forward(params, rho, field, base=None, bf=False):
-    """Returns (delta [D,D,D], base + rms(field) * delta, cache); base
+def forward(params, rho, field, base=None, bf=False, scale=1.0):
+    """Returns (delta [D,D,D], base + scale rms(field) delta, cache); base
     defaults to field."""
     P = unpack(params)
     R = bf16 if bf else (lambda a: a)
     if base is None:
         base = field
     x, s = inputs(rho, field)
+    s = s * scale
     x = R(x)
     cache = {"x": x, "s": s}
 
@@ -153,14 +155,14 @@ def forward(params, rho, field, base=None, bf=False):
     return delta, base + s * delta, cache
 
 
-def loss_and_grads(params, rho, field, target, base=None, bf=False):
-    """MSE between delta and (target - base) / rms(field) over the voxels
-    (base defaults to field); returns (loss, flat gradient)."""
+def loss_and_grads(params, rho, field, target, base=None, bf=False, scale=1.0):
+    """MSE between delta and (target - base) / (scale rms(field)) over the
+    voxels (base defaults to field); returns (loss, flat gradient)."""
     P = unpack(params)
     R = bf16 if bf else (lambda a: a)
     if base is None:
         base = field
-    delta, _, c = forward(params, rho, field, base, bf)
+    delta, _, c = forward(params, rho, field, base, bf, scale)
     target = (target - base) / c["s"]
     V = delta.size
     loss = np.mean((delta - target) ** 2)

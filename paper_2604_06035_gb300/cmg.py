@@ -120,6 +120,8 @@ _SIGS = {
     "cmg_unet_n_params": (_I, [_P, C.POINTER(_I64)]),
     "cmg_unet_set_params": (_I, [_P, _P, _I]),
     "cmg_unet_get_params": (_I, [_P, _P, _I]),
+    "cmg_unet_set_output_scale": (_I, [_P, C.c_float]),
+    "cmg_unet_get_output_scale": (_I, [_P, C.POINTER(C.c_float)]),
     "cmg_unet_forward": (_I, [_P, _P, _P, _P, _I, _P, _P, _I]),
     "cmg_unet_gradients": (_I, [_P, _P, _P, _P, _P, _I, _P, C.POINTER(C.c_double), _I]),
     "cmg_unet_adam_step": (_I, [_P, C.c_float, C.c_float, C.c_float, C.c_float]),
@@ -597,8 +599,18 @@ def _batch_of(net, x):
     return n // (net.D ** 3)
 
 
+def cmg_unet_set_output_scale(net, scale):
+    _check(lib().cmg_unet_set_output_scale(net.h, float(scale)), "cmg_unet_set_output_scale")
+
+
+def cmg_unet_get_output_scale(net):
+    v = C.c_float(0.0)
+    _check(lib().cmg_unet_get_output_scale(net.h, C.byref(v)), "cmg_unet_get_output_scale")
+    return v.value
+
+
 def cmg_unet_forward(net, rho, field, base=None, delta=False):
-    """Prediction base + rms(field) delta (and delta if asked) for a batch of
+    """Prediction base + c rms(field) delta (c: the output scale) (and delta if asked) for a batch of
     dense [B][D][D][D] fields; base defaults to field."""
     pr, mem, k1 = _in(rho, np.float32)
     pp, mem2, k2 = _in(field, np.float32)

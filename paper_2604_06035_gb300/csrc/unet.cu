@@ -242,9 +242,10 @@ __global__ void k_stats(const float *__restrict__ rho, const float *__restrict__
 }
 
 // x[b][v][0] = (rho - mean) / std, x[..][1] = phi / rms, channels 2..15 = 0;
-// norm[b] = {mean, 1/std, rms}
+// norm[b] = {mean, 1/std, out_scale * rms}
 __global__ void k_input(const float *__restrict__ rho, const float *__restrict__ phi, int64_t V,
-                        const double *__restrict__ stats, float *__restrict__ norm, bf16 *__restrict__ x) {
+                        const double *__restrict__ stats, float out_scale, float *__restrict__ norm,
+                        bf16 *__restrict__ x) {
   const int b = blockIdx.y;
   const double n = (double)V;
   const double mean = stats[3 * b] / n;
@@ -254,7 +255,7 @@ __global__ void k_input(const float *__restrict__ rho, const float *__restrict__
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     norm[3 * b] = fmean;
     norm[3 * b + 1] = inv_std;
-    norm[3 * b + 2] = (float)rms;
+    norm[3 * b + 2] = (float)(out_scale * rms);
   }
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
     __align__(16) bf16 row[16];
@@ -495,6 +496,8 @@ struct cmg_unet {
   // inputs: rho, field (its rms scales the output), base (the output is
   // base + rms(field) delta), target (training); out = the prediction
   float *in_rho = nullptr, *in_phi = nullptr, *in_base = nullptr, *in_next = nullptr, *out_phi = nullptr;
+  // the prediction is base + out_scale * rms(field) * delta
+  float out_scale = 1.f;
   int adam_t = 0;
   bool weights_ready = false;
   cmg::DeviceBuffers mem;
@@ -595,7 +598,7 @@ void forward(cmg_unet *U, int B, float *phi_pred) {
   const int64_t V0 = vox(U, 0);
   CMG_CUDA(cudaMemsetAsync(U->stats, 0, sizeof(double) * 3 * B, s));
   k_stats<<<dim3(64, B), 256, 0, s>>>(U->in_rho, U->in_phi, V0, U->stats);
-  k_input<<<dim3(gsz(V0), B), 256, 0, s>>>(U->in_rho, U->in_phi, V0, U->stats, U->norm, U->x);
+  k_input<<<dim3(gsz(V0), B), 256, 0, s>>>(U->in_rho, U->in_phi, V0, U->stats, U->out_scale, U->norm, U->x);
   CMG_CUDA(cudaGetLastError());
   const int D0 = dim_of(U, 0), D1 = dim_of(U, 1), D2 = dim_of(U, 2);
   auto layer = [&](int l, const bf16 *in, bf16 *out) {
@@ -786,6 +789,18 @@ int cmg_unet_set_params(cmg_unet *U, const float *params, cmg_mem mem) {
     CMG_CUDA(cudaStreamSynchronize(s));
     return (int)CMG_OK;
   });
+}
+
+int cmg_unet_set_output_scale(cmg_unet *U, float scale) {
+  if (!U || !(scale > 0.f) || !std::isfinite(scale)) return CMG_ERR_INVALID_ARG;
+  U->out_scale = scale;
+  return CMG_OK;
+}
+
+int cmg_unet_get_output_scale(const cmg_unet *U, float *scale) {
+  if (!U || !scale) return CMG_ERR_INVALID_ARG;
+  *scale = U->out_scale;
+  return CMG_OK;
 }
 
 int cmg_unet_get_params(cmg_unet *U, float *out, cmg_mem mem) {

@@ -108,11 +108,27 @@ def _batch(data, pairs):
             data["phi"][k, t].contiguous(), data["phi"][k, t + 1].contiguous())
 
 
-def train(net, data, train_trajs, epochs=10, batch=4, lr=1e-3, seconds=None, seed=0):
+def output_scale(data, trajs):
+    """The rms over the pairs of (phi_{t+1} - phi_t) / rms(r_t): the network's
+    output scale, so that the delta it regresses is O(1)."""
+    import torch
+    acc = 0.0
+    pairs = _pairs(data, trajs)
+    for k, t in pairs:
+        r = data["res"][k, t].double()
+        d = (data["phi"][k, t + 1] - data["phi"][k, t]).double()
+        acc += float((d.pow(2).mean() / r.pow(2).mean()).item())
+    return float(np.sqrt(acc / len(pairs)))
+
+
+def train(net, data, train_trajs, epochs=10, batch=4, lr=1e-3, seconds=None, seed=0, calibrate=True):
     """Adam on the mean squared error of delta with a cosine learning-rate
-    decay; returns the per-epoch mean loss."""
+    decay (after setting the output scale from the training pairs when
+    calibrate); returns the per-epoch mean loss."""
     rng = np.random.default_rng(seed)
     pairs = _pairs(data, train_trajs)
+    if calibrate:
+        cmg.cmg_unet_set_output_scale(net, output_scale(data, train_trajs))
     losses = []
     t0 = time.perf_counter()
     steps_total = epochs * ((len(pairs) + batch - 1) // batch)
@@ -143,11 +159,18 @@ def predict(S, net, rho, prev):
     return pred[0]
 
 
+def _rel_err(a, ref):
+    """Relative L2 error of a against ref, constants removed (they are the
+    periodic operator's null space)."""
+    d = (a - a.mean()) - (ref - ref.mean())
+    return float((d.norm() / (ref - ref.mean()).norm()).item())
+
+
 def evaluate(ctx, net, data, test_trajs, tol=1e-10, precision=cmg.CMG_PREC_FP64):
     """Per held-out pair: V-cycles, device ms and initial relative residual of
     the solve started from phi_t and from the network's prediction (and from
-    zero); the warm start's own cost (residual + network) is timed with CUDA
-    events."""
+    zero), and the error of both starts against phi_{t+1}; the warm start's
+    own cost (residual + network) is timed with CUDA events."""
     import torch
     S = PeriodicSolver(ctx, data["D"])
     rows = []
@@ -160,13 +183,15 @@ def evaluate(ctx, net, data, test_trajs, tol=1e-10, precision=cmg.CMG_PREC_FP64)
         pred = predict(S, net, rho, prev)
         e1.record()
         torch.cuda.synchronize()
+        nxt = data["phi"][k, t + 1].double()
+        err_prev, err_net = _rel_err(prev.double(), nxt), _rel_err(pred.double(), nxt)
         _, st_net = S.solve(rho, pred, tol, precision)
         _, st_zero = S.solve(rho, None, tol, precision)
         rows.append({"cycles_prev": st_prev["cycles"], "cycles_net": st_net["cycles"],
                      "cycles_zero": st_zero["cycles"], "ms_prev": st_prev["ms"], "ms_net": st_net["ms"],
                      "ms_zero": st_zero["ms"], "ms_infer": e0.elapsed_time(e1),
                      "rel0_prev": st_prev["rel_initial"], "rel0_net": st_net["rel_initial"],
-                     "rel_final_net": st_net["rel_final"]})
+                     "rel_final_net": st_net["rel_final"], "err_prev": err_prev, "err_net": err_net})
     keys = rows[0].keys()
     mean = {k: float(np.mean([r[k] for r in rows])) for k in keys}
     mean["pairs"] = len(rows)

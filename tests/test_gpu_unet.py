@@ -108,27 +108,33 @@ def test_gradients_match_reference(cmg, ctx):
 
 
 def test_separate_base(cmg, ctx):
-    """prediction = base + rms(field) delta with base != field (the warm
-    start's form: field = residual of phi_prev, base = phi_prev)."""
+    """prediction = base + c rms(field) delta with base != field and an output
+    scale c (the warm start's form: field = residual of phi_prev, base =
+    phi_prev)."""
     D = 16
     net = cmg.cmg_unet_create(ctx, D, 1)
     p = _params(13)
     cmg.cmg_unet_set_params(net, p)
+    cmg.cmg_unet_set_output_scale(net, 0.25)
+    assert cmg.cmg_unet_get_output_scale(net) == 0.25
+    with pytest.raises(cmg.CmgError):
+        cmg.cmg_unet_set_output_scale(net, -1.0)
     rho, field, target = _sample(D, 14)
     base = (np.roll(field, 3, axis=0) * 2.5 + 0.1).astype(np.float32)
     pred = cmg.cmg_unet_forward(net, rho[None], field[None], base=base[None])
     p64 = p.astype(np.float64)
-    _, ref_pred, _ = U.forward(p64, rho.astype(np.float64), field.astype(np.float64), base.astype(np.float64), bf=True)
+    _, ref_pred, _ = U.forward(p64, rho.astype(np.float64), field.astype(np.float64), base.astype(np.float64),
+                               bf=True, scale=0.25)
     assert _rel(pred[0] - base, ref_pred - base) <= 1e-2
     loss, g = cmg.cmg_unet_gradients(net, rho[None], field[None], target[None], base=base[None])
     l_ref, g_ref = U.loss_and_grads(p64, rho.astype(np.float64), field.astype(np.float64),
-                                    target.astype(np.float64), base.astype(np.float64), bf=True)
+                                    target.astype(np.float64), base.astype(np.float64), bf=True, scale=0.25)
     assert abs(loss - l_ref) <= 1e-2 * l_ref
     assert _rel(g, g_ref) <= 2e-2
     # the base enters the loss: a different base changes it
     l_default, _ = cmg.cmg_unet_gradients(net, rho[None], field[None], target[None], grads=False)
     l_ref_default, _ = U.loss_and_grads(p64, rho.astype(np.float64), field.astype(np.float64),
-                                        target.astype(np.float64), bf=True)
+                                        target.astype(np.float64), bf=True, scale=0.25)
     assert abs(l_default - l_ref_default) <= 1e-2 * l_ref_default
     assert abs(l_default - loss) > 0.1 * loss
 

@@ -4,8 +4,11 @@ the network's prediction against those started from the previous phi.
 
 What the network gains is measured, not assumed: the test requires that
 training lowers the loss, that the solves from the prediction reach the same
-tolerance and the same discrete solution, and that the prediction is a
-better initial guess (smaller initial residual) than the previous phi."""
+tolerance and the same discrete solution, that the prediction is closer to
+the new solution than the previous phi, and that its solves take no more
+V-cycles.  (The initial residual is not the criterion: the prediction's BF16
+rounding noise is high-frequency, which the Laplacian amplifies and the first
+smoothing sweep removes.)"""
 import numpy as np
 import pytest
 
@@ -39,7 +42,9 @@ def test_warmstart_trains_and_helps(cmg):
         # the untrained network is exactly the previous phi
         assert abs(before["rel0_net"] - before["rel0_prev"]) <= 1e-6 * before["rel0_prev"]
         # the trained network is a better starting point than the previous phi
-        assert after["rel0_net"] < after["rel0_prev"]
+        assert abs(before["err_net"] - before["err_prev"]) <= 1e-6 * before["err_prev"]
+        assert after["err_net"] < 0.7 * after["err_prev"]
+        assert after["cycles_net"] <= after["cycles_prev"]
         # both starts converge to the same discrete solution
         S = W.PeriodicSolver(ctx, 32)
         rho, prev = data["rho"][10, 5], data["phi"][10, 4]

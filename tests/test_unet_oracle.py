@@ -90,6 +90,35 @@ def test_gradient_finite_differences():
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)) + 1e-5 * abs(fd), (i, fd, g[i])
 
 
+def test_base_and_output_scale():
+    """delta depends on (rho, field) only; the prediction is base + c rms(field)
+    delta; a loss with scale c equals the scale-1 loss of the target pulled
+    toward base by 1/c; finite differences still hold with base and c."""
+    rho, field, target = _sample(seed=9)
+    base = np.random.default_rng(10).standard_normal(field.shape)
+    p = U.init_params(11)
+    p[-17:-1] = np.random.default_rng(12).normal(0, 0.5, 16)
+    d1, pred1, _ = U.forward(p, rho, field)
+    d2, pred2, _ = U.forward(p, rho, field, base, scale=3.0)
+    assert np.array_equal(d1, d2)
+    rms = np.sqrt(np.mean(field ** 2))
+    assert np.allclose(pred1, field + rms * d1, rtol=0, atol=1e-12)
+    assert np.allclose(pred2, base + 3.0 * rms * d1, rtol=0, atol=1e-12)
+    l3, g3 = U.loss_and_grads(p, rho, field, target, base, scale=3.0)
+    l1, g1 = U.loss_and_grads(p, rho, field, base + (target - base) / 3.0, base)
+    assert abs(l3 - l1) <= 1e-12 * l1
+    assert np.allclose(g3, g1, rtol=1e-10, atol=1e-14)
+    eps = 1e-6
+    for i in [5, 1000, len(p) - 3, len(p) - 1]:
+        q = p.copy()
+        q[i] += eps
+        lp, _ = U.loss_and_grads(q, rho, field, target, base, scale=3.0)
+        q[i] -= 2 * eps
+        lm, _ = U.loss_and_grads(q, rho, field, target, base, scale=3.0)
+        fd = (lp - lm) / (2 * eps)
+        assert abs(fd - g3[i]) <= 1e-6 * max(1.0, abs(fd)) + 1e-5 * abs(fd), (i, fd, g3[i])
+
+
 def _is_zero_padding(i):
     # first-layer weights on the zero input channels 2..15: gradient exactly 0
     if i >= 16 * 27 * 16:
