@@ -43,6 +43,10 @@ def parse():
     ap.add_argument("--workload", default="two_level_128", choices=["two_level_128"])
     ap.add_argument("--quick", action="store_true", help="timed steps only (profiling runs)")
     ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--learned-traj", type=int, default=128,
+                    help="trajectories of 8 steps for the learned warm start (1/16 held out)")
+    ap.add_argument("--train-seconds", type=float, default=60.0, help="U-Net training budget")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start block")
     return ap.parse_args()
 
 
@@ -114,6 +118,21 @@ def traffic_for(kernel):
     if e.get("source_sha") != _b.source_digest():
         return None
     return e.get("dram_bytes_per_launch")
+
+
+def read_peaks():
+    """HBM GB/s and dense BF16 TFLOP/s (burst) from MEASURED_PEAKS.json, else
+    the profiling recipe's fallback figures."""
+    out = {"hbm": 6800.0, "hbm_src": "fallback", "bf16": 1900.0, "bf16_src": "fallback"}
+    try:
+        rec = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return out
+    if "hbm_gbs" in rec:
+        out["hbm"], out["hbm_src"] = float(rec["hbm_gbs"]), "measured"
+    if "bf16_tflops" in rec:
+        out["bf16"], out["bf16_src"] = float(rec["bf16_tflops"]), "measured (burst)"
+    return out
 
 
 def cycle_updates(n_octs_per_mg, n_pre=2, n_post=2, coarse_sweeps=4, exact_coarse=True):
@@ -233,6 +252,89 @@ def bench_batched(cmg, ctx, dev, stream, args):
     return res
 
 
+def bench_learned(cmg, ctx, dev, args, peaks):
+    """Learned warm start on 64^3 periodic blocks: dataset from the FP64
+    solver (lognormal trajectories), U-Net training with the library's BF16
+    kernels for a fixed wall-clock budget, then on held-out trajectories the
+    V-cycles and device time to rel. residual tol from phi_prev and from the
+    network's prediction (FP64 and mixed precision), the warm start's own
+    cost, and the forward convolutions' tensor-core rate."""
+    import numpy as np
+    import torch
+    from paper_2604_06035_gb300 import warmstart as W
+    D, n_steps = 64, 8
+    n_traj = args.learned_traj
+    n_test = max(2, n_traj // 16)
+    t0 = time.perf_counter()
+    data = W.build_dataset(ctx, n_traj=n_traj, n_steps=n_steps, D=D, seed=5)
+    gen_s = time.perf_counter() - t0
+    net = cmg.cmg_unet_create(ctx, D, 8)
+    # delta = 0 at the start: the untrained network returns phi_prev
+    cmg.cmg_unet_set_params(net, W.init_params(12))
+    train_trajs = list(range(n_traj - n_test))
+    test_trajs = list(range(n_traj - n_test, n_traj))
+    t0 = time.perf_counter()
+    losses = W.train(net, data, train_trajs, batch=4, lr=2e-3, seconds=args.train_seconds)
+    train_s = time.perf_counter() - t0
+    res = {"grid": "%d^3 periodic" % D, "pairs_train": len(train_trajs) * n_steps,
+           "pairs_test": len(test_trajs) * n_steps, "dataset_s": gen_s, "train_s": train_s,
+           "epochs": len(losses), "loss_first_epoch": losses[0], "loss_last_epoch": losses[-1],
+           "output_scale": cmg.cmg_unet_get_output_scale(net)}
+    for name, prec in (("fp64", cmg.CMG_PREC_FP64), ("mixed", cmg.CMG_PREC_MIXED)):
+        W.evaluate(ctx, net, data, test_trajs[:1], tol=args.tol, precision=prec)  # warm the graphs
+        m, _ = W.evaluate(ctx, net, data, test_trajs, tol=args.tol, precision=prec)
+        res[name] = {k: m[k] for k in ("cycles_prev", "cycles_net", "cycles_zero", "ms_prev", "ms_net", "ms_zero",
+                                       "rel_final_net", "err_prev", "err_net")}
+    # the warm start's cost: residual of phi_prev + forward (batch 1), and the
+    # forward alone, on device inputs
+    S = W.PeriodicSolver(ctx, D)
+    k, t = test_trajs[0], 0
+    rho, prev = data["rho"][k, t + 1], data["phi"][k, t]
+    r = data["res"][k, t][None].contiguous()
+    rho1, prev1 = rho[None].contiguous(), prev[None].contiguous()
+
+    def ev_time(fn, reps=20):
+        for _ in range(3):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    res["ms_warm_start"] = ev_time(lambda: W.predict(S, net, rho, prev))
+    res["ms_forward_b1"] = ev_time(lambda: cmg.cmg_unet_forward(net, rho1, r, base=prev1))
+    rho8 = data["rho"][k, 1:9].contiguous()
+    r8 = data["res"][k, 0:8].contiguous()
+    prev8 = data["phi"][k, 0:8].contiguous()
+    res["ms_forward_per_block_b8"] = ev_time(lambda: cmg.cmg_unet_forward(net, rho8, r8, base=prev8)) / 8
+    cmg.cmg_ctx_reset_profile(ctx)
+    cmg.cmg_ctx_set_profiling(ctx, True)
+    for _ in range(5):
+        cmg.cmg_unet_forward(net, rho8, r8, base=prev8)
+    torch.cuda.synchronize()
+    cmg.cmg_ctx_set_profiling(ctx, False)
+    conv = cmg.cmg_ctx_get_profile(ctx)["conv_fwd"]
+    tf = conv["flops"] / (conv["ms"] / 1e3) / 1e12
+    res["roofline_conv_fwd"] = {"bound": "tensor", "achieved": tf, "peak": peaks["bf16"], "unit": "TFLOP/s",
+                                "frac": tf / peaks["bf16"], "peak_source": peaks["bf16_src"],
+                                "launches": conv["launches"], "ms": conv["ms"],
+                                "flops_per_block": conv["flops"] / (5 * 8)}
+    f, m = res["fp64"], res["mixed"]
+    res["summary"] = {
+        "fp64_ms_prev": f["ms_prev"], "fp64_ms_net_plus_warm_start": f["ms_net"] + res["ms_warm_start"],
+        "mixed_ms_prev": m["ms_prev"], "mixed_ms_net_plus_warm_start": m["ms_net"] + res["ms_warm_start"],
+        "cycles_saved_fp64": f["cycles_prev"] - f["cycles_net"]}
+    del S, net
+    del data
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_ours(args, rank, local, world):
     import numpy as np
     import torch
@@ -325,12 +427,8 @@ def run_ours(args, rank, local, world):
     dname, d = dom
     achieved_tflops = d["flops"] / (d["ms"] / 1e3) / 1e12
     achieved_gbs = d["bytes"] / (d["ms"] / 1e3) / 1e9
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        hbm = float(peaks["hbm_gbs"])
-        hbm_src = "measured"
-    except (OSError, ValueError, KeyError):
-        hbm, hbm_src = 6800.0, "fallback"
+    peaks = read_peaks()
+    hbm, hbm_src = peaks["hbm"], peaks["hbm_src"]
     fp64 = dname.endswith("fp64")
     if fp64:
         roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -381,6 +479,22 @@ def run_ours(args, rank, local, world):
             mixed_ms += a.elapsed_time(b)
             mixed_upd += sum(s["cell_updates"] for s in sm)
         phi_mixed_f = cmg.cmg_level_get_phi(F)
+        cmg.cmg_ctx_reset_profile(ctx)
+        cmg.cmg_ctx_set_profiling(ctx, True)
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            step(cmg.CMG_PREC_MIXED)
+        torch.cuda.synchronize()
+        cmg.cmg_ctx_set_profiling(ctx, False)
+        mprof = cmg.cmg_ctx_get_profile(ctx)
+        sw = mprof.get("rbgs_fp32")
+        mixed_roof = None
+        if sw and sw["ms"] > 0:
+            gbs = sw["bytes"] / (sw["ms"] / 1e3) / 1e9
+            mixed_roof = {"bound": "hbm", "kernel": "rbgs_fp32", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                          "frac": gbs / hbm, "peak_source": hbm_src, "launches": sw["launches"],
+                          "share_of_kernel_ms": sw["ms"] / sum(v["ms"] for v in mprof.values()),
+                          "traffic": traffic_for("rbgs_fp32")}
         step()
         phi_fp64_f = cmg.cmg_level_get_phi(F)
         out["mixed"] = {"ms_per_step": mixed_ms / args.steps,
@@ -388,7 +502,11 @@ def run_ours(args, rank, local, world):
                         "time_to_tol_ms": {"base": sm[0]["ms"], "fine": sm[1]["ms"]},
                         "refinement_steps": {"base": sm[0]["cycles"], "fine": sm[1]["cycles"]},
                         "phi_rel_diff_vs_fp64_gpu": float(np.max(np.abs(phi_mixed_f - phi_fp64_f)) /
-                                                          np.max(np.abs(phi_fp64_f)))}
+                                                          np.max(np.abs(phi_fp64_f))),
+                        "roofline_smoother": mixed_roof,
+                        "kernels": {k: {"launches": v["launches"], "ms": v["ms"],
+                                        "GB/s": v["bytes"] / v["ms"] / 1e6 if v["ms"] else None}
+                                    for k, v in mprof.items()}}
 
         # end to end through the C ABI with host buffers (pinned): H2D densities,
         # both solves, D2H of both phi arrays
@@ -412,6 +530,8 @@ def run_ours(args, rank, local, world):
         out["e2e"] = {"value": e2e_upd * world / (e2e_ms / 1e3) / 1e6, "unit": "Mcell-updates/s",
                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps}
         out["batched"] = bench_batched(cmg, ctx, dev, stream, args)
+        if not args.no_learned:
+            out["learned"] = bench_learned(cmg, ctx, dev, args, peaks)
         if rank == 0 and world == 1:
             out["cpu_baseline"] = cpu_baseline_sample()
     else:

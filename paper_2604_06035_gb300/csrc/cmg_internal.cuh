@@ -197,7 +197,7 @@ struct DeviceBuffers {
 namespace cmg {
 enum KernelClass {
   K_SWEEP64 = 0, K_SWEEP32, K_RESID64, K_RESID32, K_PROLONG64, K_PROLONG32, K_GHOST, K_COARSE, K_REDUCE,
-  K_CONVERT, K_NCLASS
+  K_CONVERT, K_CONV_FWD, K_CONV_DGRAD, K_CONV_WGRAD, K_NCLASS
 };
 struct ProfClass {
   int64_t launches = 0;

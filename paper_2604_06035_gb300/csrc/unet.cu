@@ -517,7 +517,7 @@ void conv_launch(cmg_unet *U, const bf16 *in, int K, const bf16 *W, const float 
     attr = true;
   }
   const int nb = (D / 4) * (D / 4) * (D / 4);
-  LaunchScope ls(U->ctx, K_CONVERT, 0.0, 2.0 * 27 * K * NT * 8 * (double)D * D * D * B);
+  LaunchScope ls(U->ctx, SIGN > 0 ? K_CONV_FWD : K_CONV_DGRAD, 0.0, 2.0 * 27 * K * NT * 8 * (double)D * D * D * B);
   k_conv<NT, SIGN, BR><<<dim3(nb, B), kConvThreads, smem, U->ctx->stream>>>(in, K, W, bias, out, D);
   CMG_CUDA(cudaGetLastError());
 }
@@ -551,7 +551,7 @@ void wgrad_launch(cmg_unet *U, const bf16 *dout, int Cout, const bf16 *in, float
   const int nbricks = B * (D / 4) * (D / 4) * (D / 4);
   const int per_block = std::max(1, std::min(32, nbricks / 64));
   const int blocks = (nbricks + per_block - 1) / per_block;
-  LaunchScope ls(U->ctx, K_CONVERT, 0.0, 2.0 * 27 * Cout * NTI * 8 * (double)D * D * D * B);
+  LaunchScope ls(U->ctx, K_CONV_WGRAD, 0.0, 2.0 * 27 * Cout * NTI * 8 * (double)D * D * D * B);
   k_conv_wgrad<NTI><<<dim3(blocks, 27), kConvThreads, smem, U->ctx->stream>>>(dout, Cout, in, dW, D, nbricks,
                                                                                per_block);
   CMG_CUDA(cudaGetLastError());

@@ -25,6 +25,28 @@ import numpy as np
 from . import cmg, inputs
 
 
+# (name, input channels, output channels) of the ten 3x3x3 convolutions in
+# the order of the parameter vector (include/cmg.h), then the 16 + 1 head.
+LAYERS = [("enc0a", 16, 16), ("enc0b", 16, 16), ("enc1a", 16, 32), ("enc1b", 32, 32), ("bota", 32, 64),
+          ("botb", 64, 64), ("dec1a", 96, 32), ("dec1b", 32, 32), ("dec0a", 48, 16), ("dec0b", 16, 16)]
+
+
+def init_params(seed, zero_head=True):
+    """He-normal convolution weights, zero biases, the first layer's unused
+    input channels 2..15 zero; the head zero when zero_head (the untrained
+    network then returns its base, i.e. phi_prev).  FP32 vector."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for name, ci, co in LAYERS:
+        w = rng.normal(0.0, np.sqrt(2.0 / (27 * ci)), size=(co, 27, ci))
+        if name == "enc0a":
+            w[:, :, 2:] = 0.0
+        parts += [w.ravel(), np.zeros(co)]
+    head = np.zeros(16) if zero_head else rng.normal(0.0, 0.05, size=16)
+    parts += [head, np.zeros(1)]
+    return np.concatenate(parts).astype(np.float32)
+
+
 class PeriodicSolver:
     """A full periodic level of D^3 cells, with dense [D, D, D] (z, y, x)
     device fields in and out (converted to octs by cmg_dense_octs)."""
@@ -123,8 +145,9 @@ def output_scale(data, trajs):
 
 def train(net, data, train_trajs, epochs=10, batch=4, lr=1e-3, seconds=None, seed=0, calibrate=True):
     """Adam on the mean squared error of delta with a cosine learning-rate
-    decay (after setting the output scale from the training pairs when
-    calibrate); returns the per-epoch mean loss."""
+    decay over `epochs`, or over a wall-clock budget of `seconds` when given
+    (then as many epochs as fit); the output scale is set from the training
+    pairs first when calibrate.  Returns the per-epoch mean loss."""
     rng = np.random.default_rng(seed)
     pairs = _pairs(data, train_trajs)
     if calibrate:
@@ -133,19 +156,29 @@ def train(net, data, train_trajs, epochs=10, batch=4, lr=1e-3, seconds=None, see
     t0 = time.perf_counter()
     steps_total = epochs * ((len(pairs) + batch - 1) // batch)
     step = 0
-    for ep in range(epochs):
+    ep = 0
+    while True:
+        if seconds is None and ep >= epochs:
+            break
         order = rng.permutation(len(pairs))
         acc, nb = 0.0, 0
         for i in range(0, len(pairs), batch):
+            if seconds is not None:
+                progress = min(1.0, (time.perf_counter() - t0) / seconds)
+            else:
+                progress = step / steps_total
             chunk = [pairs[j] for j in order[i:i + batch]]
             rho, r, prev, nxt = _batch(data, chunk)
             loss, _ = cmg.cmg_unet_gradients(net, rho, r, nxt, base=prev, grads=False)
-            cmg.cmg_unet_adam_step(net, lr * 0.5 * (1 + np.cos(np.pi * step / steps_total)))
+            cmg.cmg_unet_adam_step(net, lr * 0.5 * (1 + np.cos(np.pi * progress)))
             step += 1
             acc += loss / len(chunk)
             nb += 1
+            if seconds is not None and progress >= 1.0:
+                break
         losses.append(float((acc / (nb * data["D"] ** 3)).item()))
-        if seconds is not None and time.perf_counter() - t0 > seconds:
+        ep += 1
+        if seconds is not None and time.perf_counter() - t0 >= seconds:
             break
     return losses
 
