@@ -47,6 +47,9 @@ def parse():
                     help="trajectories of 8 steps for the learned warm start (1/16 held out)")
     ap.add_argument("--train-seconds", type=float, default=60.0, help="U-Net training budget")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start block")
+    ap.add_argument("--block", choices=["smoother", "learned"], default=None,
+                    help="run one sub-benchmark alone and print its JSON (profiling runs)")
+    ap.add_argument("--smoother-level", type=int, default=9, help="level of the full periodic grid (9 = 512^3)")
     return ap.parse_args()
 
 
@@ -248,6 +251,46 @@ def bench_batched(cmg, ctx, dev, stream, args):
     cmg.cmg_level_destroy(F)
     cmg.cmg_level_destroy(P)
     del zeros
+    torch.cuda.empty_cache()
+    return res
+
+
+def bench_smoother(cmg, ctx, dev, peaks, lev=9, sweeps=10):
+    """The smoother and residual kernels alone on a full periodic 512^3 level
+    (16.8 M octs; every field far larger than L2): per-launch CUDA events on
+    the library stream, algorithmic bytes per launch (FP32: 3 x 4 cells x 4 B
+    per oct and colour; the neighbour indices are not counted) against the
+    measured HBM copy rate."""
+    import torch
+    from paper_2604_06035_gb300 import inputs
+    coords = torch.from_numpy(inputs.uniform_oct_coords(lev)).to(dev)
+    L = cmg.cmg_level_build(ctx, lev, cmg.cmg_morton_encode(ctx, coords))
+    del coords
+    n = cmg.cmg_level_n_octs(L)
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    rho = torch.rand((n, 8), dtype=torch.float64, device=dev, generator=g) + 0.5
+    cmg.cmg_level_set_density(L, rho, float(rho.mean().item()))
+    del rho
+    cmg.cmg_level_set_phi(L, torch.zeros((n, 8), dtype=torch.float64, device=dev))
+    res = {"grid": "%d^3 periodic (%d octs)" % (1 << lev, n), "sweeps": sweeps}
+    for name, prec in (("fp32", cmg.CMG_PREC_MIXED), ("fp64", cmg.CMG_PREC_FP64)):
+        cmg.cmg_level_mg_step(L, 0, cmg.CMG_OP_SWEEP, prec, 2)
+        cmg.cmg_ctx_reset_profile(ctx)
+        cmg.cmg_ctx_set_profiling(ctx, True)
+        cmg.cmg_level_mg_step(L, 0, cmg.CMG_OP_SWEEP, prec, sweeps)
+        cmg.cmg_level_mg_step(L, 0, cmg.CMG_OP_RESIDUAL, prec)
+        cmg.cmg_ctx_set_profiling(ctx, False)
+        prof = cmg.cmg_ctx_get_profile(ctx)
+        for fam in ("rbgs_" + name, "residual_" + name):
+            d = prof[fam]
+            gbs = d["bytes"] / (d["ms"] / 1e3) / 1e9
+            res[fam] = {"launches": d["launches"], "ms_per_launch": d["ms"] / d["launches"],
+                        "bytes_per_launch": d["bytes"] / d["launches"], "achieved_GBs": gbs,
+                        "frac_of_hbm": gbs / peaks["hbm"], "hbm_source": peaks["hbm_src"],
+                        "TFLOPs": d["flops"] / (d["ms"] / 1e3) / 1e12, "traffic": traffic_for(fam + "_512")}
+    cmg.cmg_level_destroy(L)
+    torch.cuda.synchronize()
     torch.cuda.empty_cache()
     return res
 
@@ -530,6 +573,7 @@ def run_ours(args, rank, local, world):
         out["e2e"] = {"value": e2e_upd * world / (e2e_ms / 1e3) / 1e6, "unit": "Mcell-updates/s",
                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps}
         out["batched"] = bench_batched(cmg, ctx, dev, stream, args)
+        out["smoother_512"] = bench_smoother(cmg, ctx, dev, peaks)
         if not args.no_learned:
             out["learned"] = bench_learned(cmg, ctx, dev, args, peaks)
         if rank == 0 and world == 1:
@@ -546,10 +590,31 @@ def run_ours(args, rank, local, world):
         dist.destroy_process_group()
 
 
+def run_block(args):
+    """One sub-benchmark alone on cuda:0 (for profiler captures)."""
+    import torch
+
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2604_06035_gb300 import cmg
+    dev = torch.device("cuda", 0)
+    ctx = cmg.cmg_ctx_create(0, stream=torch.cuda.current_stream(dev).cuda_stream)
+    peaks = read_peaks()
+    if args.block == "smoother":
+        out = bench_smoother(cmg, ctx, dev, peaks, lev=args.smoother_level)
+    else:
+        out = bench_learned(cmg, ctx, dev, args, peaks)
+    print(json.dumps({"block": args.block, **out}), flush=True)
+    torch.cuda.synchronize()
+    cmg.cmg_ctx_destroy(ctx)
+
+
 def main():
     args = parse()
     rank, local, world = dist_env()
-    if args.impl == "reference":
+    if args.block is not None and args.impl == "ours":
+        run_block(args)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_ours(args, rank, local, world)
