@@ -118,7 +118,7 @@ def traffic_for(kernel):
     if not e:
         return None
     from paper_2604_06035_gb300 import build as _b
-    if e.get("source_sha") != _b.source_digest():
+    if e.get("source_sha") != _b.source_digest(tuple(e.get("sources", ())) or None):
         return None
     return e.get("dram_bytes_per_launch")
 

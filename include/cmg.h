@@ -267,12 +267,20 @@ int cmg_unet_n_params(const cmg_unet *net, int64_t *n);
 /* Replace the master parameters (resets the Adam moments). */
 int cmg_unet_set_params(cmg_unet *net, const float *params, cmg_mem mem);
 int cmg_unet_get_params(cmg_unet *net, float *out, cmg_mem mem);
+/* Convolution kernels: 1 (default) = tcgen05 tensor-core kernels with TMEM
+ * accumulators on every grid whose size is a multiple of 16 (the warp-level
+ * mma.sync kernels below that); 0 = the warp-level mma.sync kernels
+ * everywhere.  Both compute the same convolutions in BF16 x BF16 -> FP32. */
+int cmg_unet_set_kernels(cmg_unet *net, int tensor_path);
 /* Output scale c > 0 (finite), kept with the network: the trainer sets it to
  * the typical size of (target - base)/rms(field) so that delta is O(1).
  * CMG_ERR_INVALID_ARG otherwise. */
 int cmg_unet_set_output_scale(cmg_unet *net, float scale);
 int cmg_unet_get_output_scale(const cmg_unet *net, float *scale);
-/* Inference: prediction and/or delta (either may be NULL); base may be NULL. */
+/* Inference: prediction and/or delta (either may be NULL); base may be NULL.
+ * Every wait inside the tensor-core kernels is bounded; an expired wait is
+ * reported as CMG_ERR_TIMEOUT by the next call that synchronises (host
+ * buffers, or cmg_unet_gradients with a loss). */
 int cmg_unet_forward(cmg_unet *net, const float *rho, const float *field, const float *base, int batch,
                      float *pred, float *delta, cmg_mem mem);
 /* Loss = mean over all voxels of (delta - (target - base)/(c rms(field)))^2 and its

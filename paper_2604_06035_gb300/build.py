@@ -40,12 +40,19 @@ def _deps():
     return files
 
 
-def source_digest():
-    """sha256 of the CUDA sources and headers (keys recorded profiler data to
-    the kernel version it was taken on)."""
+# the sources each kernel family is built from (for source_digest)
+STENCIL_SOURCES = ("cmg_internal.cuh", "oct_ops.cuh", "kernels.cuh", "launch.cu")
+UNET_SOURCES = ("cmg_internal.cuh", "conv_tc.cuh", "unet.cu")
+
+
+def source_digest(files=None):
+    """sha256 of the CUDA sources and headers, or of the named ones only
+    (keys recorded profiler data to the kernel version it was taken on)."""
     import hashlib
     h = hashlib.sha256()
     for f in sorted(_deps()):
+        if files is not None and os.path.basename(f) not in files:
+            continue
         if f.endswith((".cu", ".cuh", ".h")):
             h.update(os.path.basename(f).encode())
             h.update(open(f, "rb").read())

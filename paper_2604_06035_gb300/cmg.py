@@ -120,6 +120,7 @@ _SIGS = {
     "cmg_unet_n_params": (_I, [_P, C.POINTER(_I64)]),
     "cmg_unet_set_params": (_I, [_P, _P, _I]),
     "cmg_unet_get_params": (_I, [_P, _P, _I]),
+    "cmg_unet_set_kernels": (_I, [_P, _I]),
     "cmg_unet_set_output_scale": (_I, [_P, C.c_float]),
     "cmg_unet_get_output_scale": (_I, [_P, C.POINTER(C.c_float)]),
     "cmg_unet_forward": (_I, [_P, _P, _P, _P, _I, _P, _P, _I]),
@@ -597,6 +598,11 @@ def cmg_unet_get_params(net, device=False):
 def _batch_of(net, x):
     n = x.numel() if _is_torch(x) else np.asarray(x).size
     return n // (net.D ** 3)
+
+
+def cmg_unet_set_kernels(net, tensor_path):
+    """1 = tcgen05 convolutions where the grid allows (default), 0 = mma.sync."""
+    _check(lib().cmg_unet_set_kernels(net.h, int(tensor_path)), "cmg_unet_set_kernels")
 
 
 def cmg_unet_set_output_scale(net, scale):

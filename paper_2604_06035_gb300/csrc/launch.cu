@@ -10,7 +10,10 @@ namespace cmg {
 
 // ------------------------------------------------------------ launchers
 // Algorithmic work per launch (for the profile): bytes are the minimum
-// traffic of the operation, flops its floating-point operations (FMA = 2).
+// traffic of the operation with perfect reuse, flops its floating-point
+// operations (FMA = 2).  The neighbour cache counts 24 B per oct per full
+// red-black sweep (6 int32; 12 B per colour pass) and 24 B per oct per
+// residual evaluation.
 
 template <typename T>
 void sweep(cmg_level *L, int m, bool zero_init) {
@@ -24,10 +27,11 @@ void sweep(cmg_level *L, int m, bool zero_init) {
   const bool mask = !g.all_active;
   const int cls = sizeof(T) == 8 ? K_SWEEP64 : K_SWEEP32;
   const double u = 4.0 * (double)g.n;  // cells updated per colour pass
-  const double full_bytes = 3.0 * u * sizeof(T), full_flops = 7.0 * u;
+  const double nbr_bytes = 12.0 * (double)g.n;
+  const double full_bytes = 3.0 * u * sizeof(T) + nbr_bytes, full_flops = 7.0 * u;
 #define CMG_SWEEP(P, Z, M)                                                                                  \
   do {                                                                                                      \
-    LaunchScope ls(L->ctx, cls, (Z) ? 2.0 * u * sizeof(T) : full_bytes, (Z) ? 0.0 : full_flops);            \
+    LaunchScope ls(L->ctx, cls, (Z) ? 2.0 * u * sizeof(T) + nbr_bytes : full_bytes, (Z) ? 0.0 : full_flops); \
     launch_k(k_sweep<T, P, Z, M>, nb, kThreads, s, g.nbr, phi + (1 - P) * st, phi + P * st, gg + P * g.n * 4, \
                                                 g.active, g.n);                                             \
   } while (0)
@@ -56,7 +60,7 @@ void resid_restrict(cmg_level *L, int m, bool restrict_to_coarse, bool norm, boo
   const int64_t cn = c ? c->n : 0, cna = c ? c->n_alloc : 0;
   const uint8_t *act = g.all_active ? nullptr : g.active;
   const double cells = 8.0 * (double)g.n;
-  const double bytes = cells * 2.0 * sizeof(T) + (restrict_to_coarse ? g.n * sizeof(T) : 0.0) +
+  const double bytes = cells * 2.0 * sizeof(T) + 24.0 * g.n + (restrict_to_coarse ? g.n * sizeof(T) : 0.0) +
                        (emit_scale ? cells * 4.0 : 0.0);
   const double flops = cells * (8.0 + (norm ? 2.0 : 0.0) + (restrict_to_coarse ? 1.0 : 0.0));
   const int cls = sizeof(T) == 8 ? K_RESID64 : K_RESID32;

@@ -21,6 +21,7 @@
 #include <cstring>
 
 #include "cmg_internal.cuh"
+#include "conv_tc.cuh"
 
 namespace cmg {
 namespace {
@@ -487,6 +488,10 @@ struct cmg_unet {
   int64_t np = 0;
   float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
   __nv_bfloat16 *W[10] = {}, *WT[10] = {};
+  // the same weights arranged for the tcgen05 kernels (conv_tc.cuh)
+  __nv_bfloat16 *WI[10] = {}, *WTI[10] = {};
+  int *d_err = nullptr;  // device status word of the bounded waits
+  bool use_tc = true;    // tcgen05 convolutions where the grid allows
   // activations (bf16) and their gradients, per batch sample
   __nv_bfloat16 *x = nullptr, *a[10] = {}, *p0 = nullptr, *p1 = nullptr, *c1 = nullptr, *c0 = nullptr;
   __nv_bfloat16 *g0 = nullptr, *g1 = nullptr, *gc = nullptr, *gx = nullptr, *gs0 = nullptr, *gs1 = nullptr;
@@ -508,6 +513,22 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
+template <int N, int ZB, int SIGN, bool BR>
+void conv_tc_launch(cmg_unet *U, const bf16 *in, int K, const bf16 *WI, const float *bias, bf16 *out, int D, int B) {
+  using G = tc::ConvGeom<N, ZB>;
+  static int attr_dev = -1;
+  if (attr_dev != U->ctx->device) {
+    CMG_CUDA(cudaFuncSetAttribute(tc::k_conv_tc<N, ZB, SIGN, BR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  G::kSmemBytes));
+    attr_dev = U->ctx->device;
+  }
+  const int nb = (D / 8) * (D / 16) * (D / ZB);
+  LaunchScope ls(U->ctx, SIGN > 0 ? K_CONV_FWD : K_CONV_DGRAD, 0.0, 2.0 * 27 * K * N * (double)D * D * D * B);
+  tc::k_conv_tc<N, ZB, SIGN, BR><<<dim3(nb, B), tc::kThreads, G::kSmemBytes, U->ctx->stream>>>(in, K, WI, bias, out,
+                                                                                               D, U->d_err);
+  CMG_CUDA(cudaGetLastError());
+}
+
 template <int NT, int SIGN, bool BR>
 void conv_launch(cmg_unet *U, const bf16 *in, int K, const bf16 *W, const float *bias, bf16 *out, int D, int B) {
   const size_t smem = (216 * 16 + (size_t)NT * 8 * 27 * 16) * sizeof(bf16);
@@ -522,8 +543,37 @@ void conv_launch(cmg_unet *U, const bf16 *in, int K, const bf16 *W, const float 
   CMG_CUDA(cudaGetLastError());
 }
 
-void conv(cmg_unet *U, const bf16 *in, int K, const bf16 *W, const float *bias, bf16 *out, int N, int D, int B,
-          bool fwd) {
+// The tcgen05 path needs bricks of 8 x 16 x ZB voxels: D a multiple of 16.
+bool tc_eligible(const cmg_unet *U, int N, int D) {
+  return U->use_tc && D >= 16 && D % 16 == 0 && (N == 16 || N == 32 || N == 48 || N == 64 || N == 96);
+}
+
+void conv_tc(cmg_unet *U, const bf16 *in, int K, const bf16 *WI, const float *bias, bf16 *out, int N, int D, int B,
+             bool fwd) {
+#define CMG_CONV_TC(NN, ZB)                                                          \
+  case NN:                                                                           \
+    if (fwd) conv_tc_launch<NN, ZB, 1, true>(U, in, K, WI, bias, out, D, B);         \
+    else conv_tc_launch<NN, ZB, -1, false>(U, in, K, WI, nullptr, out, D, B);        \
+    break;
+  switch (N) {
+    CMG_CONV_TC(16, 4)
+    CMG_CONV_TC(32, 4)
+    CMG_CONV_TC(48, 2)
+    CMG_CONV_TC(64, 2)
+    CMG_CONV_TC(96, 2)
+    default: throw Error(CMG_ERR_INVALID_ARG, "unsupported channel count");
+  }
+#undef CMG_CONV_TC
+}
+
+// Convolution of layer l: forward (in = activations, N = cout) or input
+// gradient (in = output gradient, N = cin).
+void conv(cmg_unet *U, int l, const bf16 *in, int K, const float *bias, bf16 *out, int N, int D, int B, bool fwd) {
+  if (tc_eligible(U, N, D)) {
+    conv_tc(U, in, K, fwd ? U->WI[l] : U->WTI[l], bias, out, N, D, B, fwd);
+    return;
+  }
+  const bf16 *W = fwd ? U->W[l] : U->WT[l];
 #define CMG_CONV(NT)                                                             \
   case NT:                                                                       \
     if (fwd) conv_launch<NT, 1, true>(U, in, K, W, bias, out, D, B);             \
@@ -568,6 +618,17 @@ void wgrad(cmg_unet *U, const bf16 *dout, int Cout, const bf16 *in, int Cin, flo
   }
 }
 
+// After a synchronisation: a bounded wait that expired in a tcgen05
+// convolution is reported (and the status word cleared).
+void check_status(cmg_unet *U) {
+  int e = 0;
+  CMG_CUDA(cudaMemcpy(&e, U->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e != 0) {
+    CMG_CUDA(cudaMemset(U->d_err, 0, sizeof(int)));
+    throw Error(e, "U-Net convolution: a bounded wait expired (tensor-core pipeline stalled)");
+  }
+}
+
 int dim_of(const cmg_unet *U, int lvl) { return U->D >> lvl; }
 int64_t vox(const cmg_unet *U, int lvl) {
   const int64_t d = dim_of(U, lvl);
@@ -579,8 +640,10 @@ void prepare_weights(cmg_unet *U) {
   cudaStream_t s = U->ctx->stream;
   for (int l = 0; l < 10; ++l) {
     const LayerSpec &L = kLayers[l];
-    k_cast_w<<<gsz((int64_t)L.cout * 27 * L.cin), 256, 0, s>>>(U->params + layer_offset(l), L.cout, L.cin, U->W[l],
-                                                                U->WT[l]);
+    const int64_t n = (int64_t)L.cout * 27 * L.cin;
+    k_cast_w<<<gsz(n), 256, 0, s>>>(U->params + layer_offset(l), L.cout, L.cin, U->W[l], U->WT[l]);
+    tc::k_weight_image<<<gsz(n), 256, 0, s>>>(U->W[l], L.cout, L.cin, U->WI[l]);
+    tc::k_weight_image<<<gsz(n), 256, 0, s>>>(U->WT[l], L.cin, L.cout, U->WTI[l]);
   }
   CMG_CUDA(cudaGetLastError());
   U->weights_ready = true;
@@ -603,7 +666,7 @@ void forward(cmg_unet *U, int B, float *phi_pred) {
   const int D0 = dim_of(U, 0), D1 = dim_of(U, 1), D2 = dim_of(U, 2);
   auto layer = [&](int l, const bf16 *in, bf16 *out) {
     const LayerSpec &L = kLayers[l];
-    conv(U, in, L.cin, U->W[l], bias_of(U, l), out, L.cout, dim_of(U, L.lvl), B, true);
+    conv(U, l, in, L.cin, bias_of(U, l), out, L.cout, dim_of(U, L.lvl), B, true);
   };
   layer(0, U->x, U->a[0]);
   layer(1, U->a[0], U->a[1]);  // s0
@@ -647,7 +710,7 @@ void backward(cmg_unet *U, int B) {
     k_bias_grad<<<256, 256, 0, s>>>(g, rows, L.cout, gw + (int64_t)L.cout * 27 * L.cin);
     CMG_CUDA(cudaGetLastError());
     wgrad(U, g, L.cout, in, L.cin, gw, D, B);
-    if (gin) conv(U, g, L.cout, U->WT[l], nullptr, gin, L.cin, D, B, false);
+    if (gin) conv(U, l, g, L.cout, nullptr, gin, L.cin, D, B, false);
   };
   // decoder level 0
   back(9, U->g0, U->a[8], U->g1);            // g1 = grad a8 (16 ch, V0)
@@ -721,6 +784,8 @@ int cmg_unet_create(cmg_ctx *ctx, int grid_dim, int max_batch, cmg_unet **out) {
         const int64_t n = (int64_t)kLayers[l].cout * 27 * kLayers[l].cin;
         U->W[l] = reinterpret_cast<__nv_bfloat16 *>(M.alloc<uint16_t>(n));
         U->WT[l] = reinterpret_cast<__nv_bfloat16 *>(M.alloc<uint16_t>(n));
+        U->WI[l] = reinterpret_cast<__nv_bfloat16 *>(M.alloc<uint16_t>(n));
+        U->WTI[l] = reinterpret_cast<__nv_bfloat16 *>(M.alloc<uint16_t>(n));
       }
       const int64_t B = max_batch;
       const int64_t V0 = (int64_t)grid_dim * grid_dim * grid_dim, V1 = V0 / 8, V2 = V0 / 64;
@@ -745,6 +810,7 @@ int cmg_unet_create(cmg_ctx *ctx, int grid_dim, int max_batch, cmg_unet **out) {
       U->norm = M.alloc<float>(3 * B);
       U->stats = M.alloc<double>(3 * B);
       U->loss = M.alloc<double>(1);
+      U->d_err = M.alloc<int32_t>(1, true, s);
       U->in_rho = M.alloc<float>(B * V0);
       U->in_phi = M.alloc<float>(B * V0);
       U->in_base = M.alloc<float>(B * V0);
@@ -791,6 +857,12 @@ int cmg_unet_set_params(cmg_unet *U, const float *params, cmg_mem mem) {
   });
 }
 
+int cmg_unet_set_kernels(cmg_unet *U, int tensor_path) {
+  if (!U || (tensor_path != 0 && tensor_path != 1)) return CMG_ERR_INVALID_ARG;
+  U->use_tc = tensor_path == 1;
+  return CMG_OK;
+}
+
 int cmg_unet_set_output_scale(cmg_unet *U, float scale) {
   if (!U || !(scale > 0.f) || !std::isfinite(scale)) return CMG_ERR_INVALID_ARG;
   U->out_scale = scale;
@@ -829,7 +901,10 @@ int cmg_unet_forward(cmg_unet *U, const float *rho, const float *field, const fl
     const cudaMemcpyKind k = mem == CMG_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     if (phi_pred) CMG_CUDA(cudaMemcpyAsync(phi_pred, U->out_phi, sizeof(float) * n, k, s));
     if (delta) CMG_CUDA(cudaMemcpyAsync(delta, U->delta, sizeof(float) * n, k, s));
-    if (mem == CMG_MEM_HOST) CMG_CUDA(cudaStreamSynchronize(s));
+    if (mem == CMG_MEM_HOST) {
+      CMG_CUDA(cudaStreamSynchronize(s));
+      cmg::check_status(U);
+    }
     return (int)CMG_OK;
   });
 }
@@ -852,7 +927,10 @@ int cmg_unet_gradients(cmg_unet *U, const float *rho, const float *field, const 
     if (loss) {
       CMG_CUDA(cudaMemcpyAsync(loss, U->loss, sizeof(double), k, s));
     }
-    if (mem == CMG_MEM_HOST || loss) CMG_CUDA(cudaStreamSynchronize(s));
+    if (mem == CMG_MEM_HOST || loss) {
+      CMG_CUDA(cudaStreamSynchronize(s));
+      cmg::check_status(U);
+    }
     if (loss && mem == CMG_MEM_HOST) *loss /= (double)n;
     return (int)CMG_OK;
   });

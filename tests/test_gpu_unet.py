@@ -57,7 +57,7 @@ def _rel(a, b):
     return np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b))
 
 
-@pytest.mark.parametrize("D", [16, 32])
+@pytest.mark.parametrize("D", [16, 32, 64])
 def test_forward_matches_reference(cmg, ctx, D):
     net = cmg.cmg_unet_create(ctx, D, 1)
     p = _params(3)
@@ -83,8 +83,8 @@ def _layer_slices():
     return out
 
 
-def test_gradients_match_reference(cmg, ctx):
-    D = 16
+@pytest.mark.parametrize("D", [16, 32])
+def test_gradients_match_reference(cmg, ctx, D):
     net = cmg.cmg_unet_create(ctx, D, 2)
     p = _params(5)
     cmg.cmg_unet_set_params(net, p)
@@ -137,6 +137,31 @@ def test_separate_base(cmg, ctx):
                                         target.astype(np.float64), bf=True, scale=0.25)
     assert abs(l_default - l_ref_default) <= 1e-2 * l_ref_default
     assert abs(l_default - loss) > 0.1 * loss
+
+
+def test_tcgen05_and_mma_sync_kernels_agree(cmg, ctx):
+    """The tcgen05 convolutions (grids that are multiples of 16) and the
+    warp-level mma.sync ones compute the same network: same inputs, same
+    weights, both FP32 accumulation of BF16 products."""
+    D = 32
+    net = cmg.cmg_unet_create(ctx, D, 2)
+    cmg.cmg_unet_set_params(net, _params(21))
+    s1, s2 = _sample(D, 22), _sample(D, 23)
+    rho, phi, phin = (np.stack([a, b]) for a, b in zip(s1, s2))
+    out = {}
+    for path in (1, 0):
+        cmg.cmg_unet_set_kernels(net, path)
+        _, delta = cmg.cmg_unet_forward(net, rho, phi, delta=True)
+        loss, g = cmg.cmg_unet_gradients(net, rho, phi, phin)
+        out[path] = (delta, loss, g)
+    cmg.cmg_unet_set_kernels(net, 1)
+    assert _rel(out[1][0], out[0][0]) <= 1e-2
+    assert abs(out[1][1] - out[0][1]) <= 1e-2 * out[0][1]
+    for name, sl in _layer_slices():
+        a, b = out[1][2][sl], out[0][2][sl]
+        if not np.any(b):
+            continue
+        assert _rel(a, b) <= 2e-2, name
 
 
 def test_adam_step_decreases_loss(cmg, ctx):
