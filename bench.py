@@ -47,7 +47,7 @@ def parse():
                     help="trajectories of 8 steps for the learned warm start (1/16 held out)")
     ap.add_argument("--train-seconds", type=float, default=60.0, help="U-Net training budget")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start block")
-    ap.add_argument("--block", choices=["smoother", "learned"], default=None,
+    ap.add_argument("--block", choices=["smoother", "learned", "forward"], default=None,
                     help="run one sub-benchmark alone and print its JSON (profiling runs)")
     ap.add_argument("--smoother-level", type=int, default=9, help="level of the full periodic grid (9 = 512^3)")
     return ap.parse_args()
@@ -292,6 +292,46 @@ def bench_smoother(cmg, ctx, dev, peaks, lev=9, sweeps=10):
     cmg.cmg_level_destroy(L)
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
+    return res
+
+
+def bench_forward(cmg, ctx, dev, peaks, D=64, batches=(1, 8), reps=20):
+    """The U-Net forward alone on random inputs (untrained He-normal weights):
+    device time per call and the convolutions' tensor-core rate."""
+    import torch
+    from paper_2604_06035_gb300 import warmstart as W
+    g = torch.Generator(device=dev)
+    g.manual_seed(3)
+    net = cmg.cmg_unet_create(ctx, D, max(batches))
+    cmg.cmg_unet_set_params(net, W.init_params(5, zero_head=False))
+    res = {"grid": "%d^3" % D}
+    for B in batches:
+        rho = torch.rand((B, D, D, D), device=dev, generator=g) + 0.5
+        field = torch.randn((B, D, D, D), device=dev, generator=g)
+        for path, name in ((1, "tcgen05"), (0, "mma_sync")):
+            cmg.cmg_unet_set_kernels(net, path)
+            for _ in range(3):
+                cmg.cmg_unet_forward(net, rho, field)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            for _ in range(reps):
+                cmg.cmg_unet_forward(net, rho, field)
+            b.record()
+            torch.cuda.synchronize()
+            cmg.cmg_ctx_reset_profile(ctx)
+            cmg.cmg_ctx_set_profiling(ctx, True)
+            for _ in range(reps):
+                cmg.cmg_unet_forward(net, rho, field)
+            torch.cuda.synchronize()
+            cmg.cmg_ctx_set_profiling(ctx, False)
+            conv = cmg.cmg_ctx_get_profile(ctx)["conv_fwd"]
+            tf = conv["flops"] / (conv["ms"] / 1e3) / 1e12
+            res["b%d_%s" % (B, name)] = {"ms_per_forward": a.elapsed_time(b) / reps,
+                                         "conv_ms_per_forward": conv["ms"] / reps, "conv_TFLOPs": tf,
+                                         "conv_frac_of_bf16": tf / peaks["bf16"]}
+    cmg.cmg_unet_set_kernels(net, 1)
+    cmg.cmg_unet_destroy(net)
     return res
 
 
@@ -602,6 +642,8 @@ def run_block(args):
     peaks = read_peaks()
     if args.block == "smoother":
         out = bench_smoother(cmg, ctx, dev, peaks, lev=args.smoother_level)
+    elif args.block == "forward":
+        out = bench_forward(cmg, ctx, dev, peaks)
     else:
         out = bench_learned(cmg, ctx, dev, args, peaks)
     print(json.dumps({"block": args.block, **out}), flush=True)

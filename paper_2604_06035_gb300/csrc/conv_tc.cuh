@@ -16,9 +16,12 @@
 // z slice are core matrices 10 rows (160 B) apart (SBO), the second K-half is
 // a plane further (LBO), and the tap offset only moves the start address --
 // no im2col copy.  One thread issues the 27 x ZB MMAs of a slice and commits
-// them to an mbarrier; the slices are double-buffered so the copies of slice
-// k+1 overlap the MMAs of slice k.  The epilogue reads TMEM (each warp its 32
-// lanes), adds the bias, applies the ReLU and stores bf16.
+// them to an mbarrier.  The kernel is persistent (one CTA per SM walking
+// (brick, slice) work items): a ring of halo stages keeps the copies two
+// items ahead of the MMAs, the accumulators are double-buffered in TMEM so
+// that a brick's epilogue (TMEM -> bias, ReLU -> bf16 stores, each warp its
+// 32 lanes) overlaps the next brick's MMAs, and the weights stay resident in
+// shared memory when they fit.
 //
 // Every wait is bounded (clock64 budget); on expiry the kernel records
 // CMG_ERR_TIMEOUT in *err, stops issuing work, frees its TMEM and returns.
@@ -118,31 +121,57 @@ __host__ __device__ constexpr int pow2_cols(int c) { return c <= 32 ? 32 : c <= 
 template <int N, int ZB>
 struct ConvGeom {
   static constexpr int kHaloRows = (ZB + 2) * 18 * 10;
-  static constexpr int kHaloBytes = kHaloRows * 32;     // two planes of 16-byte rows
-  static constexpr int kWBytes = 27 * N * 32;           // one slice, all taps
-  static constexpr int kBufBytes = kHaloBytes + kWBytes;
-  static constexpr int kBarOffset = 2 * kBufBytes;      // 4 mbarriers + TMEM slot + abort flag
-  static constexpr int kSmemBytes = kBarOffset + 64 + 1024;  // + alignment slack
-  static constexpr int kCols = pow2_cols(ZB * N);
+  static constexpr int kHaloBytes = kHaloRows * 32;  // two planes of 16-byte rows
+  static constexpr int kWBytes = 27 * N * 32;        // one 16-channel slice, all taps
+  static constexpr int kCols = pow2_cols(2 * ZB * N);  // two accumulator sets
+  static constexpr int kBarBytes = 128;
+  // Weights stay resident (one bulk copy per CTA) when they fit beside a
+  // three-stage halo ring; otherwise every stage carries its slice's weights
+  // and the ring has two stages.
+  __host__ __device__ static constexpr bool resident(int K) {
+    return 3 * kHaloBytes + (K / 16) * kWBytes + kBarBytes + 1024 <= 227 * 1024;
+  }
+  __host__ __device__ static constexpr int stages(int K) { return resident(K) ? 3 : 2; }
+  __host__ __device__ static constexpr int stage_bytes(int K) { return kHaloBytes + (resident(K) ? 0 : kWBytes); }
+  __host__ __device__ static constexpr int wres_offset(int K) { return stages(K) * stage_bytes(K); }
+  __host__ __device__ static constexpr int bar_offset(int K) {
+    return wres_offset(K) + (resident(K) ? (K / 16) * kWBytes : 0);
+  }
+  // at least 116 KB so that a single CTA fits per SM (the TMEM allocation
+  // assumes it)
+  __host__ __device__ static constexpr int smem_bytes(int K) {
+    return bar_offset(K) + kBarBytes + 1024 > 116 * 1024 ? bar_offset(K) + kBarBytes + 1024 : 116 * 1024;
+  }
 };
 
-template <int N, int ZB, int SIGN, bool BIAS_RELU>
-__global__ void __launch_bounds__(kThreads) k_conv_tc(const __nv_bfloat16 *__restrict__ in, int K,
-                                                     const __nv_bfloat16 *__restrict__ wimg,
-                                                     const float *__restrict__ bias, __nv_bfloat16 *__restrict__ out,
-                                                     int D, int *__restrict__ err) {
+// Persistent convolution: grid <= one CTA per SM, each CTA walks the work
+// items (brick, 16-channel slice) blockIdx.x, + gridDim.x, ... in order.
+// FWD: out = ReLU(conv(in, W) + bias); else out = conv^T (SIGN = -1, no bias).
+// With `skip` set (forward only) the input is the channel concatenation of
+// the nearest-upsampled `in` (K - Cb channels on the D/2 grid) and `skip`
+// (Cb channels on the D grid), read directly by the halo loader.
+template <int N, int ZB, bool FWD>
+__global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __nv_bfloat16 *__restrict__ in, int K,
+                                                        const __nv_bfloat16 *__restrict__ skip, int Cb,
+                                                        const __nv_bfloat16 *__restrict__ wimg,
+                                                        const float *__restrict__ bias,
+                                                        __nv_bfloat16 *__restrict__ out, int D, int total_bricks,
+                                                        int *__restrict__ err) {
   using G = ConvGeom<N, ZB>;
+  constexpr int SIGN = FWD ? 1 : -1;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + G::kBarOffset);  // [0,1] weights, [2,3] mma
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + G::kBarOffset + 32);
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + G::kBarOffset + 40);
+  const bool wres = G::resident(K);
+  const int NS = G::stages(K), sbytes = G::stage_bytes(K);
+  uint8_t *wres_sm = smem + G::wres_offset(K);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + G::bar_offset(K));  // [0,3) mma, [3,6) stage weights, 6 resident
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 7);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 8);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
-  const int nbx = D >> 3, nby = D >> 4;
-  const int brick = blockIdx.x;
-  const int bx = brick % nbx, by = (brick / nbx) % nby, bz = brick / (nbx * nby);
-  const int64_t sbase = (int64_t)blockIdx.y * D * D * D;
+  const int nk = K >> 4, Ca = K - Cb, Dh = D >> 1;
+  const int nbx = D >> 3, nby = D >> 4, nbps = nbx * nby * (D / ZB);
+  const int my_bricks = blockIdx.x < total_bricks ? (total_bricks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int n_items = my_bricks * nk;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
@@ -150,7 +179,7 @@ __global__ void __launch_bounds__(kThreads) k_conv_tc(const __nv_bfloat16 *__res
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int i = 0; i < 4; ++i) mbar_init(smem_addr(bars + i), 1);
+    for (int i = 0; i < 7; ++i) mbar_init(smem_addr(bars + i), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -160,16 +189,17 @@ __global__ void __launch_bounds__(kThreads) k_conv_tc(const __nv_bfloat16 *__res
   const uint32_t tbase = *tslot;
   constexpr uint32_t kIdesc = idesc_bf16(128, N);
 
-  const int nk = K >> 4;
-  for (int kc = 0; kc < nk; ++kc) {
-    const int b = kc & 1;
-    uint8_t *halo = smem + b * G::kBufBytes;
-    uint8_t *wsm = halo + G::kHaloBytes;
-    if (kc >= 2 && !mbar_wait(smem_addr(bars + 2 + b), ((kc - 2) >> 1) & 1)) *abort_flag = 1;
-    __syncthreads();
-    if (*abort_flag) break;
-    if (tid == 0)
-      bulk_load(smem_addr(wsm), wimg + (int64_t)kc * 27 * N * 16, G::kWBytes, smem_addr(bars + b));
+  if (wres && tid == 0 && n_items > 0)
+    bulk_load(smem_addr(wres_sm), wimg, (uint32_t)(nk * G::kWBytes), smem_addr(bars + 6));
+
+  // copies of work item j into its stage (halo by every thread, the
+  // slice's weights by thread 0 when they are not resident)
+  auto issue = [&](int j) {
+    const int bi = blockIdx.x + (j / nk) * gridDim.x, kc = j % nk;
+    const int sample = bi / nbps, brick = bi % nbps;
+    const int bx = brick % nbx, by = (brick / nbx) % nby, bz = brick / (nbx * nby);
+    uint8_t *halo = smem + (j % NS) * sbytes;
+    const bool up = skip != nullptr && kc * 16 < Ca;
     for (int p = tid; p < 2 * G::kHaloRows; p += kThreads) {
       const int row = p >> 1, half = p & 1;
       const int hz = row / 180, hy = (row / 10) % 18, hx = row % 10;
@@ -177,16 +207,75 @@ __global__ void __launch_bounds__(kThreads) k_conv_tc(const __nv_bfloat16 *__res
       z += z < 0 ? D : (z >= D ? -D : 0);
       y += y < 0 ? D : (y >= D ? -D : 0);
       x += x < 0 ? D : (x >= D ? -D : 0);
-      const int64_t v = sbase + ((int64_t)z * D + y) * D + x;
-      cp_async16(smem_addr(halo + half * (G::kHaloRows * 16) + row * 16), in + v * K + kc * 16 + half * 8);
+      const __nv_bfloat16 *src;
+      if (skip == nullptr) {
+        src = in + ((int64_t)sample * D * D * D + ((int64_t)z * D + y) * D + x) * K + kc * 16 + half * 8;
+      } else if (up) {
+        src = in + ((int64_t)sample * Dh * Dh * Dh + ((int64_t)(z >> 1) * Dh + (y >> 1)) * Dh + (x >> 1)) * Ca +
+              kc * 16 + half * 8;
+      } else {
+        src = skip + ((int64_t)sample * D * D * D + ((int64_t)z * D + y) * D + x) * Cb + (kc * 16 - Ca) + half * 8;
+      }
+      cp_async16(smem_addr(halo + half * (G::kHaloRows * 16) + row * 16), src);
     }
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+    if (!wres && tid == 0)
+      bulk_load(smem_addr(halo + G::kHaloBytes), wimg + (int64_t)kc * 27 * N * 16, G::kWBytes,
+                smem_addr(bars + 3 + j % NS));
+  };
+
+  // TMEM -> bias/ReLU -> bf16 stores for the brick of work item j
+  auto epilogue = [&](int j) {
+    const int bi = blockIdx.x + (j / nk) * gridDim.x;
+    const int sample = bi / nbps, brick = bi % nbps;
+    const int bx = brick % nbx, by = (brick / nbx) % nby, bz = brick / (nbx * nby);
+    const uint32_t acc = tbase + ((j / nk) & 1) * (ZB * N);
+    const int m = warp * 32 + lane;  // TMEM lane = accumulator row
+    const int y = by * 16 + (m >> 3), x = bx * 8 + (m & 7);
+#pragma unroll 1
+    for (int zz = 0; zz < ZB; ++zz) {
+      const int z = bz * ZB + zz;
+      __nv_bfloat16 *dst = out + ((int64_t)sample * D * D * D + ((int64_t)z * D + y) * D + x) * N;
+#pragma unroll 1
+      for (int c0 = 0; c0 < N; c0 += 16) {
+        float v[16];
+        tmem_ld16(acc + ((uint32_t)(warp * 32) << 16) + zz * N + c0, v);
+        __align__(16) __nv_bfloat162 o[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          float a = v[2 * q], c = v[2 * q + 1];
+          if (FWD) {
+            a = fmaxf(a + bias[c0 + 2 * q], 0.f);
+            c = fmaxf(c + bias[c0 + 2 * q + 1], 0.f);
+          }
+          o[q] = __floats2bfloat162_rn(a, c);
+        }
+        reinterpret_cast<uint4 *>(dst + c0)[0] = reinterpret_cast<const uint4 *>(o)[0];
+        reinterpret_cast<uint4 *>(dst + c0)[1] = reinterpret_cast<const uint4 *>(o)[1];
+      }
+    }
+  };
+
+  for (int s = 0; s < NS - 1; ++s) {
+    if (s < n_items) issue(s);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  bool ok = true;
+  for (int j = 0; j < n_items; ++j) {
+    const int st = j % NS, kc = j % nk;
+    // item j's halo has landed (one commit group per item, NS - 2 younger
+    // groups may still be in flight)
+    if (NS == 3) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else asm volatile("cp.async.wait_group 0;" ::: "memory");
     fence_async_shared();
     __syncthreads();
+    if (*abort_flag) { ok = false; break; }
     if (tid == 0) {
-      if (mbar_wait(smem_addr(bars + b), (kc >> 1) & 1)) {
+      const bool wready = wres ? mbar_wait(smem_addr(bars + 6), 0) : mbar_wait(smem_addr(bars + 3 + st), (j / NS) & 1);
+      if (wready) {
         tc_fence_after();
-        const uint32_t hbase = smem_addr(halo), wbase = smem_addr(wsm);
+        const uint32_t hbase = smem_addr(smem + st * sbytes);
+        const uint32_t wbase = wres ? smem_addr(wres_sm) + kc * G::kWBytes : hbase + G::kHaloBytes;
+        const uint32_t acc = tbase + ((j / nk) & 1) * (ZB * N);
 #pragma unroll 1
         for (int t = 0; t < 27; ++t) {
           const int dz = SIGN * (t / 9 - 1), dy = SIGN * ((t / 3) % 3 - 1), dx = SIGN * (t % 3 - 1);
@@ -195,49 +284,38 @@ __global__ void __launch_bounds__(kThreads) k_conv_tc(const __nv_bfloat16 *__res
           for (int zz = 0; zz < ZB; ++zz) {
             const int row0 = ((zz + dz + 1) * 18 + (dy + 1)) * 10 + (dx + 1);
             const uint64_t adesc = sdesc(hbase + row0 * 16, G::kHaloRows * 16, 160);
-            mma_bf16(tbase + zz * N, adesc, bdesc, kIdesc, (kc | t) != 0);
+            mma_bf16(acc + zz * N, adesc, bdesc, kIdesc, (kc | t) != 0);
           }
         }
       } else {
         *abort_flag = 1;
       }
-      mma_commit(smem_addr(bars + 2 + b));  // arrives even when nothing was issued
+      mma_commit(smem_addr(bars + st));  // arrives even when nothing was issued
     }
-  }
-  // all MMAs of the last slice done (each commit covers every earlier MMA)
-  if (!*abort_flag && !mbar_wait(smem_addr(bars + 2 + ((nk - 1) & 1)), ((nk - 1) >> 1) & 1)) *abort_flag = 1;
-  __syncthreads();
-  tc_fence_after();
-  if (!*abort_flag) {
-    const int m = warp * 32 + lane;  // TMEM lane = accumulator row
-    const int y = by * 16 + (m >> 3), x = bx * 8 + (m & 7);
-#pragma unroll 1
-    for (int zz = 0; zz < ZB; ++zz) {
-      const int z = bz * ZB + zz;
-      __nv_bfloat16 *dst = out + (sbase + ((int64_t)z * D + y) * D + x) * N;
-#pragma unroll 1
-      for (int c0 = 0; c0 < N; c0 += 16) {
-        float v[16];
-        tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + zz * N + c0, v);
-        __align__(16) __nv_bfloat162 o[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          float a = v[2 * j], c = v[2 * j + 1];
-          if (BIAS_RELU) {
-            a = fmaxf(a + bias[c0 + 2 * j], 0.f);
-            c = fmaxf(c + bias[c0 + 2 * j + 1], 0.f);
-          }
-          o[j] = __floats2bfloat162_rn(a, c);
-        }
-        reinterpret_cast<uint4 *>(dst + c0)[0] = reinterpret_cast<const uint4 *>(o)[0];
-        reinterpret_cast<uint4 *>(dst + c0)[1] = reinterpret_cast<const uint4 *>(o)[1];
-      }
+    __syncwarp();
+    // item j - 1's MMAs (and, through the commit, all before them) are done:
+    // the previous brick's epilogue now overlaps item j's MMAs, and item
+    // j - 1's stage is refilled with item j + NS - 1
+    if (j >= 1 && !mbar_wait(smem_addr(bars + (j - 1) % NS), ((j - 1) / NS) & 1)) *abort_flag = 1;
+    if (kc == 0 && j > 0) {
+      tc_fence_after();
+      if (!*abort_flag) epilogue(j - 1);
+      tc_fence_before();
     }
-  } else if (tid == 0) {
-    atomicExch(err, (int)CMG_ERR_TIMEOUT);
+    const int jn = j + NS - 1;
+    if (jn < n_items && !*abort_flag) issue(jn);
+    asm volatile("cp.async.commit_group;" ::: "memory");
   }
+  if (ok && n_items > 0) {
+    const int j = n_items - 1;
+    if (!mbar_wait(smem_addr(bars + j % NS), (j / NS) & 1)) *abort_flag = 1;
+    tc_fence_after();
+    if (!*abort_flag) epilogue(j);
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   tc_fence_before();
   __syncthreads();
+  if (*abort_flag && tid == 0) atomicExch(err, (int)CMG_ERR_TIMEOUT);
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(G::kCols));
 }
 

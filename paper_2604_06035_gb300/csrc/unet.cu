@@ -513,19 +513,21 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-template <int N, int ZB, int SIGN, bool BR>
-void conv_tc_launch(cmg_unet *U, const bf16 *in, int K, const bf16 *WI, const float *bias, bf16 *out, int D, int B) {
+template <int N, int ZB, bool FWD>
+void conv_tc_launch(cmg_unet *U, const bf16 *in, int K, const bf16 *skip, int Cb, const bf16 *WI, const float *bias,
+                    bf16 *out, int D, int B) {
   using G = tc::ConvGeom<N, ZB>;
   static int attr_dev = -1;
   if (attr_dev != U->ctx->device) {
-    CMG_CUDA(cudaFuncSetAttribute(tc::k_conv_tc<N, ZB, SIGN, BR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  G::kSmemBytes));
+    CMG_CUDA(cudaFuncSetAttribute(tc::k_conv_tc<N, ZB, FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  227 * 1024));
     attr_dev = U->ctx->device;
   }
-  const int nb = (D / 8) * (D / 16) * (D / ZB);
-  LaunchScope ls(U->ctx, SIGN > 0 ? K_CONV_FWD : K_CONV_DGRAD, 0.0, 2.0 * 27 * K * N * (double)D * D * D * B);
-  tc::k_conv_tc<N, ZB, SIGN, BR><<<dim3(nb, B), tc::kThreads, G::kSmemBytes, U->ctx->stream>>>(in, K, WI, bias, out,
-                                                                                               D, U->d_err);
+  const int total = (D / 8) * (D / 16) * (D / ZB) * B;
+  const int grid = std::min(total, U->ctx->num_sms);
+  LaunchScope ls(U->ctx, FWD ? K_CONV_FWD : K_CONV_DGRAD, 0.0, 2.0 * 27 * K * N * (double)D * D * D * B);
+  tc::k_conv_tc<N, ZB, FWD><<<grid, tc::kThreads, G::smem_bytes(K), U->ctx->stream>>>(in, K, skip, Cb, WI, bias, out,
+                                                                                     D, total, U->d_err);
   CMG_CUDA(cudaGetLastError());
 }
 
@@ -548,12 +550,21 @@ bool tc_eligible(const cmg_unet *U, int N, int D) {
   return U->use_tc && D >= 16 && D % 16 == 0 && (N == 16 || N == 32 || N == 48 || N == 64 || N == 96);
 }
 
-void conv_tc(cmg_unet *U, const bf16 *in, int K, const bf16 *WI, const float *bias, bf16 *out, int N, int D, int B,
-             bool fwd) {
-#define CMG_CONV_TC(NN, ZB)                                                          \
-  case NN:                                                                           \
-    if (fwd) conv_tc_launch<NN, ZB, 1, true>(U, in, K, WI, bias, out, D, B);         \
-    else conv_tc_launch<NN, ZB, -1, false>(U, in, K, WI, nullptr, out, D, B);        \
+// Deep bricks (ZB = 4 for N <= 32, 2 above) when they still give every SM a
+// brick, else one-slice bricks (four or two times as many).
+void conv_tc(cmg_unet *U, const bf16 *in, int K, const bf16 *skip, int Cb, const bf16 *WI, const float *bias,
+             bf16 *out, int N, int D, int B, bool fwd) {
+  const int zb = N <= 32 ? 4 : 2;
+  const bool deep = (D / 8) * (D / 16) * (D / zb) * B >= U->ctx->num_sms;
+#define CMG_CONV_TC(NN, ZB)                                                                           \
+  case NN:                                                                                            \
+    if (deep) {                                                                                       \
+      if (fwd) conv_tc_launch<NN, ZB, true>(U, in, K, skip, Cb, WI, bias, out, D, B);                 \
+      else conv_tc_launch<NN, ZB, false>(U, in, K, nullptr, 0, WI, nullptr, out, D, B);               \
+    } else {                                                                                          \
+      if (fwd) conv_tc_launch<NN, 1, true>(U, in, K, skip, Cb, WI, bias, out, D, B);                  \
+      else conv_tc_launch<NN, 1, false>(U, in, K, nullptr, 0, WI, nullptr, out, D, B);                \
+    }                                                                                                 \
     break;
   switch (N) {
     CMG_CONV_TC(16, 4)
@@ -570,7 +581,7 @@ void conv_tc(cmg_unet *U, const bf16 *in, int K, const bf16 *WI, const float *bi
 // gradient (in = output gradient, N = cin).
 void conv(cmg_unet *U, int l, const bf16 *in, int K, const float *bias, bf16 *out, int N, int D, int B, bool fwd) {
   if (tc_eligible(U, N, D)) {
-    conv_tc(U, in, K, fwd ? U->WI[l] : U->WTI[l], bias, out, N, D, B, fwd);
+    conv_tc(U, in, K, nullptr, 0, fwd ? U->WI[l] : U->WTI[l], bias, out, N, D, B, fwd);
     return;
   }
   const bf16 *W = fwd ? U->W[l] : U->WT[l];
@@ -655,7 +666,7 @@ const float *bias_of(cmg_unet *U, int l) {
 
 // Forward pass on U->in_rho / U->in_phi (B samples); leaves activations,
 // delta and (if phi_pred) phi_prev + rms * delta.
-void forward(cmg_unet *U, int B, float *phi_pred) {
+void forward(cmg_unet *U, int B, float *phi_pred, bool training) {
   cudaStream_t s = U->ctx->stream;
   prepare_weights(U);
   const int64_t V0 = vox(U, 0);
@@ -676,11 +687,22 @@ void forward(cmg_unet *U, int B, float *phi_pred) {
   k_pool<<<gsz(B * vox(U, 2) * 32), 256, 0, s>>>(U->a[3], D1, 32, B, U->p1);
   layer(4, U->p1, U->a[4]);
   layer(5, U->a[4], U->a[5]);
-  k_up_concat<<<gsz(B * vox(U, 1) * 96), 256, 0, s>>>(U->a[5], 64, U->a[3], 32, D1, B, U->c1);
-  layer(6, U->c1, U->a[6]);
+  // decoder convolutions: in inference the tcgen05 kernels read the
+  // upsampled coarse map and the skip map directly; training keeps the
+  // concatenation (the backward pass needs it)
+  auto up_layer = [&](int l, const bf16 *coarse, int Ca, const bf16 *skipm, int Cb, bf16 *cat, bf16 *out) {
+    const LayerSpec &L = kLayers[l];
+    const int D = dim_of(U, L.lvl);
+    if (!training && tc_eligible(U, L.cout, D)) {
+      conv_tc(U, coarse, Ca + Cb, skipm, Cb, U->WI[l], bias_of(U, l), out, L.cout, D, B, true);
+      return;
+    }
+    k_up_concat<<<gsz(B * (int64_t)D * D * D * (Ca + Cb)), 256, 0, s>>>(coarse, Ca, skipm, Cb, D, B, cat);
+    layer(l, cat, out);
+  };
+  up_layer(6, U->a[5], 64, U->a[3], 32, U->c1, U->a[6]);
   layer(7, U->a[6], U->a[7]);
-  k_up_concat<<<gsz(B * V0 * 48), 256, 0, s>>>(U->a[7], 32, U->a[1], 16, D0, B, U->c0);
-  layer(8, U->c0, U->a[8]);
+  up_layer(8, U->a[7], 32, U->a[1], 16, U->c0, U->a[8]);
   layer(9, U->a[8], U->a[9]);
   const float *hw = U->params + layer_offset(10);
   k_head<<<gsz(B * V0), 256, 0, s>>>(U->a[9], hw, hw + 16, U->in_base, U->norm, V0, B, U->delta, phi_pred);
@@ -897,7 +919,7 @@ int cmg_unet_forward(cmg_unet *U, const float *rho, const float *field, const fl
     cmg::copy_in(U, U->in_rho, rho, n, mem);
     cmg::copy_in(U, U->in_phi, field, n, mem);
     cmg::copy_in(U, U->in_base, base ? base : field, n, mem);
-    cmg::forward(U, batch, U->out_phi);
+    cmg::forward(U, batch, U->out_phi, false);
     const cudaMemcpyKind k = mem == CMG_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     if (phi_pred) CMG_CUDA(cudaMemcpyAsync(phi_pred, U->out_phi, sizeof(float) * n, k, s));
     if (delta) CMG_CUDA(cudaMemcpyAsync(delta, U->delta, sizeof(float) * n, k, s));
@@ -920,7 +942,7 @@ int cmg_unet_gradients(cmg_unet *U, const float *rho, const float *field, const 
     cmg::copy_in(U, U->in_phi, field, n, mem);
     cmg::copy_in(U, U->in_base, base ? base : field, n, mem);
     cmg::copy_in(U, U->in_next, target, n, mem);
-    cmg::forward(U, batch, nullptr);
+    cmg::forward(U, batch, nullptr, true);
     cmg::backward(U, batch);
     const cudaMemcpyKind k = mem == CMG_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     if (grads) CMG_CUDA(cudaMemcpyAsync(grads, U->grads, sizeof(float) * U->np, k, s));
