@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--block", choices=["smoother", "learned", "forward"], default=None,
                     help="run one sub-benchmark alone and print its JSON (profiling runs)")
     ap.add_argument("--smoother-level", type=int, default=9, help="level of the full periodic grid (9 = 512^3)")
+    ap.add_argument("--fwd-batches", default="1,8", help="batch sizes of --block forward")
+    ap.add_argument("--fwd-paths", default="tcgen05,mma_sync", help="kernel paths of --block forward")
     return ap.parse_args()
 
 
@@ -295,7 +297,7 @@ def bench_smoother(cmg, ctx, dev, peaks, lev=9, sweeps=10):
     return res
 
 
-def bench_forward(cmg, ctx, dev, peaks, D=64, batches=(1, 8), reps=20):
+def bench_forward(cmg, ctx, dev, peaks, D=64, batches=(1, 8), reps=20, paths=("tcgen05", "mma_sync")):
     """The U-Net forward alone on random inputs (untrained He-normal weights):
     device time per call and the convolutions' tensor-core rate."""
     import torch
@@ -309,6 +311,8 @@ def bench_forward(cmg, ctx, dev, peaks, D=64, batches=(1, 8), reps=20):
         rho = torch.rand((B, D, D, D), device=dev, generator=g) + 0.5
         field = torch.randn((B, D, D, D), device=dev, generator=g)
         for path, name in ((1, "tcgen05"), (0, "mma_sync")):
+            if name not in paths:
+                continue
             cmg.cmg_unet_set_kernels(net, path)
             for _ in range(3):
                 cmg.cmg_unet_forward(net, rho, field)
@@ -643,7 +647,8 @@ def run_block(args):
     if args.block == "smoother":
         out = bench_smoother(cmg, ctx, dev, peaks, lev=args.smoother_level)
     elif args.block == "forward":
-        out = bench_forward(cmg, ctx, dev, peaks)
+        out = bench_forward(cmg, ctx, dev, peaks, batches=[int(b) for b in args.fwd_batches.split(",")],
+                            paths=args.fwd_paths.split(","))
     else:
         out = bench_learned(cmg, ctx, dev, args, peaks)
     print(json.dumps({"block": args.block, **out}), flush=True)

@@ -124,7 +124,7 @@ struct ConvGeom {
   static constexpr int kHaloBytes = kHaloRows * 32;  // two planes of 16-byte rows
   static constexpr int kWBytes = 27 * N * 32;        // one 16-channel slice, all taps
   static constexpr int kCols = pow2_cols(2 * ZB * N);  // two accumulator sets
-  static constexpr int kBarBytes = 128;
+  static constexpr int kBarBytes = 192;  // 14 mbarriers, TMEM slot, abort flag
   // Weights stay resident (one bulk copy per CTA) when they fit beside a
   // three-stage halo ring; otherwise every stage carries its slice's weights
   // and the ring has two stages.
@@ -144,19 +144,30 @@ struct ConvGeom {
   }
 };
 
-// Persistent convolution: grid <= one CTA per SM, each CTA walks the work
-// items (brick, 16-channel slice) blockIdx.x, + gridDim.x, ... in order.
+// Persistent, warp-specialised convolution: grid <= one CTA per SM, each
+// CTA walks the work items (brick, 16-channel slice) of bricks blockIdx.x,
+// + gridDim.x, ... in order.  Warps 0-3 load the halo stages (cp.async) and
+// run the epilogues; warp 4 allocates TMEM and one of its threads issues the
+// MMAs.  The roles meet only at mbarriers:
+//   full[s]     halo of stage s landed (128 producer arrivals)
+//   empty[s]    MMAs that read stage s done (tcgen05.commit)
+//   wfull[s]    stage weights landed (bulk copy); wres: resident weights
+//   accfull[b]  a brick's accumulators in TMEM buffer b complete (commit)
+//   accempty[b] the epilogue has read TMEM buffer b (128 arrivals)
 // FWD: out = ReLU(conv(in, W) + bias); else out = conv^T (SIGN = -1, no bias).
 // With `skip` set (forward only) the input is the channel concatenation of
 // the nearest-upsampled `in` (K - Cb channels on the D/2 grid) and `skip`
 // (Cb channels on the D grid), read directly by the halo loader.
+constexpr int kConvThreads = 160;
+constexpr int kProducers = 128;
+
 template <int N, int ZB, bool FWD>
-__global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __nv_bfloat16 *__restrict__ in, int K,
-                                                        const __nv_bfloat16 *__restrict__ skip, int Cb,
-                                                        const __nv_bfloat16 *__restrict__ wimg,
-                                                        const float *__restrict__ bias,
-                                                        __nv_bfloat16 *__restrict__ out, int D, int total_bricks,
-                                                        int *__restrict__ err) {
+__global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __nv_bfloat16 *__restrict__ in, int K,
+                                                            const __nv_bfloat16 *__restrict__ skip, int Cb,
+                                                            const __nv_bfloat16 *__restrict__ wimg,
+                                                            const float *__restrict__ bias,
+                                                            __nv_bfloat16 *__restrict__ out, int D, int total_bricks,
+                                                            int *__restrict__ err) {
   using G = ConvGeom<N, ZB>;
   constexpr int SIGN = FWD ? 1 : -1;
   extern __shared__ uint8_t smem_raw[];
@@ -164,22 +175,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __nv_bfloat16 *__
   const bool wres = G::resident(K);
   const int NS = G::stages(K), sbytes = G::stage_bytes(K);
   uint8_t *wres_sm = smem + G::wres_offset(K);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + G::bar_offset(K));  // [0,3) mma, [3,6) stage weights, 6 resident
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 7);
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 8);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + G::bar_offset(K));
+  uint64_t *full = bars, *empty = bars + 3, *wfull = bars + 6, *wresb = bars + 9, *accfull = bars + 10,
+           *accempty = bars + 12;
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 14);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(bars + 15);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nk = K >> 4, Ca = K - Cb, Dh = D >> 1;
   const int nbx = D >> 3, nby = D >> 4, nbps = nbx * nby * (D / ZB);
   const int my_bricks = blockIdx.x < total_bricks ? (total_bricks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int n_items = my_bricks * nk;
 
-  if (warp == 0) {
+  if (warp == 4) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
                  "r"(G::kCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int i = 0; i < 7; ++i) mbar_init(smem_addr(bars + i), 1);
+    for (int i = 0; i < 3; ++i) {
+      mbar_init(smem_addr(full + i), kProducers);
+      mbar_init(smem_addr(empty + i), 1);
+      mbar_init(smem_addr(wfull + i), 1);
+    }
+    mbar_init(smem_addr(wresb), 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_addr(accfull + i), 1);
+      mbar_init(smem_addr(accempty + i), kProducers);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -187,136 +209,159 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __nv_bfloat16 *__
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tslot;
-  constexpr uint32_t kIdesc = idesc_bf16(128, N);
 
-  if (wres && tid == 0 && n_items > 0)
-    bulk_load(smem_addr(wres_sm), wimg, (uint32_t)(nk * G::kWBytes), smem_addr(bars + 6));
-
-  // copies of work item j into its stage (halo by every thread, the
-  // slice's weights by thread 0 when they are not resident)
-  auto issue = [&](int j) {
-    const int bi = blockIdx.x + (j / nk) * gridDim.x, kc = j % nk;
-    const int sample = bi / nbps, brick = bi % nbps;
-    const int bx = brick % nbx, by = (brick / nbx) % nby, bz = brick / (nbx * nby);
-    uint8_t *halo = smem + (j % NS) * sbytes;
-    const bool up = skip != nullptr && kc * 16 < Ca;
-    for (int p = tid; p < 2 * G::kHaloRows; p += kThreads) {
-      const int row = p >> 1, half = p & 1;
-      const int hz = row / 180, hy = (row / 10) % 18, hx = row % 10;
-      int z = bz * ZB + hz - 1, y = by * 16 + hy - 1, x = bx * 8 + hx - 1;
-      z += z < 0 ? D : (z >= D ? -D : 0);
-      y += y < 0 ? D : (y >= D ? -D : 0);
-      x += x < 0 ? D : (x >= D ? -D : 0);
-      const __nv_bfloat16 *src;
-      if (skip == nullptr) {
-        src = in + ((int64_t)sample * D * D * D + ((int64_t)z * D + y) * D + x) * K + kc * 16 + half * 8;
-      } else if (up) {
-        src = in + ((int64_t)sample * Dh * Dh * Dh + ((int64_t)(z >> 1) * Dh + (y >> 1)) * Dh + (x >> 1)) * Ca +
-              kc * 16 + half * 8;
-      } else {
-        src = skip + ((int64_t)sample * D * D * D + ((int64_t)z * D + y) * D + x) * Cb + (kc * 16 - Ca) + half * 8;
-      }
-      cp_async16(smem_addr(halo + half * (G::kHaloRows * 16) + row * 16), src);
-    }
-    if (!wres && tid == 0)
-      bulk_load(smem_addr(halo + G::kHaloBytes), wimg + (int64_t)kc * 27 * N * 16, G::kWBytes,
-                smem_addr(bars + 3 + j % NS));
-  };
-
-  // TMEM -> bias/ReLU -> bf16 stores for the brick of work item j
-  auto epilogue = [&](int j) {
-    const int bi = blockIdx.x + (j / nk) * gridDim.x;
-    const int sample = bi / nbps, brick = bi % nbps;
-    const int bx = brick % nbx, by = (brick / nbx) % nby, bz = brick / (nbx * nby);
-    const uint32_t acc = tbase + ((j / nk) & 1) * (ZB * N);
-    const int m = warp * 32 + lane;  // TMEM lane = accumulator row
-    const int y = by * 16 + (m >> 3), x = bx * 8 + (m & 7);
-#pragma unroll 1
-    for (int zz = 0; zz < ZB; ++zz) {
-      const int z = bz * ZB + zz;
-      __nv_bfloat16 *dst = out + ((int64_t)sample * D * D * D + ((int64_t)z * D + y) * D + x) * N;
-#pragma unroll 1
-      for (int c0 = 0; c0 < N; c0 += 16) {
-        float v[16];
-        tmem_ld16(acc + ((uint32_t)(warp * 32) << 16) + zz * N + c0, v);
-        __align__(16) __nv_bfloat162 o[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          float a = v[2 * q], c = v[2 * q + 1];
-          if (FWD) {
-            a = fmaxf(a + bias[c0 + 2 * q], 0.f);
-            c = fmaxf(c + bias[c0 + 2 * q + 1], 0.f);
-          }
-          o[q] = __floats2bfloat162_rn(a, c);
-        }
-        reinterpret_cast<uint4 *>(dst + c0)[0] = reinterpret_cast<const uint4 *>(o)[0];
-        reinterpret_cast<uint4 *>(dst + c0)[1] = reinterpret_cast<const uint4 *>(o)[1];
-      }
-    }
-  };
-
-  for (int s = 0; s < NS - 1; ++s) {
-    if (s < n_items) issue(s);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  }
-  bool ok = true;
-  for (int j = 0; j < n_items; ++j) {
-    const int st = j % NS, kc = j % nk;
-    // item j's halo has landed (one commit group per item, NS - 2 younger
-    // groups may still be in flight)
-    if (NS == 3) asm volatile("cp.async.wait_group 1;" ::: "memory");
-    else asm volatile("cp.async.wait_group 0;" ::: "memory");
-    fence_async_shared();
-    __syncthreads();
-    if (*abort_flag) { ok = false; break; }
-    if (tid == 0) {
-      const bool wready = wres ? mbar_wait(smem_addr(bars + 6), 0) : mbar_wait(smem_addr(bars + 3 + st), (j / NS) & 1);
-      if (wready) {
-        tc_fence_after();
-        const uint32_t hbase = smem_addr(smem + st * sbytes);
-        const uint32_t wbase = wres ? smem_addr(wres_sm) + kc * G::kWBytes : hbase + G::kHaloBytes;
-        const uint32_t acc = tbase + ((j / nk) & 1) * (ZB * N);
-#pragma unroll 1
-        for (int t = 0; t < 27; ++t) {
-          const int dz = SIGN * (t / 9 - 1), dy = SIGN * ((t / 3) % 3 - 1), dx = SIGN * (t % 3 - 1);
-          const uint64_t bdesc = sdesc(wbase + t * N * 32, N * 16, 128);
-#pragma unroll
-          for (int zz = 0; zz < ZB; ++zz) {
-            const int row0 = ((zz + dz + 1) * 18 + (dy + 1)) * 10 + (dx + 1);
-            const uint64_t adesc = sdesc(hbase + row0 * 16, G::kHaloRows * 16, 160);
-            mma_bf16(acc + zz * N, adesc, bdesc, kIdesc, (kc | t) != 0);
-          }
-        }
-      } else {
+  // bounded wait that also gives up as soon as another thread has
+  auto wait = [&](uint64_t *bar, int parity) -> bool {
+    const uint32_t a = smem_addr(bar);
+    const long long t0 = clock64();
+    while (!mbar_try(a, (uint32_t)parity)) {
+      if (*abort_flag) return false;
+      if (clock64() - t0 > kWaitBudget) {
         *abort_flag = 1;
+        return false;
       }
-      mma_commit(smem_addr(bars + st));  // arrives even when nothing was issued
     }
-    __syncwarp();
-    // item j - 1's MMAs (and, through the commit, all before them) are done:
-    // the previous brick's epilogue now overlaps item j's MMAs, and item
-    // j - 1's stage is refilled with item j + NS - 1
-    if (j >= 1 && !mbar_wait(smem_addr(bars + (j - 1) % NS), ((j - 1) / NS) & 1)) *abort_flag = 1;
-    if (kc == 0 && j > 0) {
+    return true;
+  };
+
+  if (warp < 4) {
+    // ------------------------------------------------ producers + epilogue
+    if (wres && tid == 0 && n_items > 0)
+      bulk_load(smem_addr(wres_sm), wimg, (uint32_t)(nk * G::kWBytes), smem_addr(wresb));
+    // each thread copies halo columns (hy, hx, half): slots tid, tid + 128, tid + 256 (< 360)
+    auto produce = [&](int j) {
+      const int bi = blockIdx.x + (j / nk) * gridDim.x, kc = j % nk;
+      const int sample = bi / nbps, brick = bi % nbps;
+      const int bx = brick % nbx, by = (brick / nbx) % nby, bz = brick / (nbx * nby);
+      uint8_t *halo = smem + (j % NS) * sbytes;
+      const bool up = skip != nullptr && kc * 16 < Ca;
+      const int cbase = up ? kc * 16 : (skip != nullptr ? kc * 16 - Ca : kc * 16);
+      const int cstride = up ? Ca : (skip != nullptr ? Cb : K);
+      const __nv_bfloat16 *srcT = (skip != nullptr && !up) ? skip : in;
+      const int Dg = up ? Dh : D;  // grid of the tensor read
+      const int64_t s_off = (int64_t)sample * Dg * Dg * Dg;
+      for (int slot = tid; slot < 360; slot += kProducers) {
+        const int col = slot >> 1, half = slot & 1;
+        const int hy = col / 10, hx = col % 10;
+        int y = by * 16 + hy - 1, x = bx * 8 + hx - 1;
+        y += y < 0 ? D : (y >= D ? -D : 0);
+        x += x < 0 ? D : (x >= D ? -D : 0);
+        if (up) {
+          y >>= 1;
+          x >>= 1;
+        }
+        const __nv_bfloat16 *src = srcT + (s_off + (int64_t)y * Dg + x) * cstride + cbase + half * 8;
+        const uint32_t dst = smem_addr(halo + half * (G::kHaloRows * 16) + col * 16);
+#pragma unroll
+        for (int hz = 0; hz < ZB + 2; ++hz) {
+          int z = bz * ZB + hz - 1;
+          z += z < 0 ? D : (z >= D ? -D : 0);
+          if (up) z >>= 1;
+          cp_async16(dst + hz * 180 * 16, src + (int64_t)z * Dg * Dg * cstride);
+        }
+      }
+      if (!wres && tid == 0)
+        bulk_load(smem_addr(halo + G::kHaloBytes), wimg + (int64_t)kc * 27 * N * 16, G::kWBytes,
+                  smem_addr(wfull + j % NS));
+    };
+    auto epilogue = [&](int c) {
+      const int bi = blockIdx.x + c * gridDim.x;
+      const int sample = bi / nbps, brick = bi % nbps;
+      const int bx = brick % nbx, by = (brick / nbx) % nby, bz = brick / (nbx * nby);
+      const uint32_t acc = tbase + (c & 1) * (ZB * N) + ((uint32_t)(warp * 32) << 16);
+      const int m = warp * 32 + lane;  // TMEM lane = accumulator row
+      const int y = by * 16 + (m >> 3), x = bx * 8 + (m & 7);
+#pragma unroll 1
+      for (int zz = 0; zz < ZB; ++zz) {
+        const int z = bz * ZB + zz;
+        __nv_bfloat16 *dst = out + ((int64_t)sample * D * D * D + ((int64_t)z * D + y) * D + x) * N;
+#pragma unroll
+        for (int c0 = 0; c0 < N; c0 += 16) {
+          float v[16];
+          tmem_ld16(acc + zz * N + c0, v);
+          __align__(16) __nv_bfloat162 o[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            float a = v[2 * q], b2 = v[2 * q + 1];
+            if (FWD) {
+              a = fmaxf(a + __ldg(bias + c0 + 2 * q), 0.f);
+              b2 = fmaxf(b2 + __ldg(bias + c0 + 2 * q + 1), 0.f);
+            }
+            o[q] = __floats2bfloat162_rn(a, b2);
+          }
+          reinterpret_cast<uint4 *>(dst + c0)[0] = reinterpret_cast<const uint4 *>(o)[0];
+          reinterpret_cast<uint4 *>(dst + c0)[1] = reinterpret_cast<const uint4 *>(o)[1];
+        }
+      }
+    };
+    for (int s = 0; s < NS - 1; ++s) {
+      if (s < n_items) produce(s);
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    bool ok = true;
+    for (int j = 0; j < n_items && ok; ++j) {
+      const int jn = j + NS - 1;
+      if (jn < n_items) {
+        if (jn >= NS && !wait(empty + jn % NS, ((jn - NS) / NS) & 1)) ok = false;
+        if (ok) produce(jn);
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      if (NS == 3) asm volatile("cp.async.wait_group 2;" ::: "memory");
+      else asm volatile("cp.async.wait_group 1;" ::: "memory");
+      fence_async_shared();
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(full + j % NS)) : "memory");
+      // the previous brick's epilogue, one item behind its last MMAs
+      if (ok && j > 0 && j % nk == 0) {
+        const int c = j / nk - 1;
+        if (!wait(accfull + (c & 1), (c >> 1) & 1)) ok = false;
+        tc_fence_after();
+        if (ok) epilogue(c);
+        tc_fence_before();
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(accempty + (c & 1))) : "memory");
+      }
+    }
+    if (ok && n_items > 0) {
+      const int c = n_items / nk - 1;
+      if (wait(accfull + (c & 1), (c >> 1) & 1)) {
+        tc_fence_after();
+        epilogue(c);
+      }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+  } else if (lane == 0) {
+    // ------------------------------------------------------------ MMA issue
+    constexpr uint32_t kIdesc = idesc_bf16(128, N);
+    for (int j = 0; j < n_items; ++j) {
+      const int st = j % NS, kc = j % nk, c = j / nk;
+      if (kc == 0 && c >= 2 && !wait(accempty + (c & 1), ((c - 2) >> 1) & 1)) break;
+      if (!wait(full + st, (j / NS) & 1)) break;
+      if (!(wres ? wait(wresb, 0) : wait(wfull + st, (j / NS) & 1))) break;
+      fence_async_shared();
       tc_fence_after();
-      if (!*abort_flag) epilogue(j - 1);
-      tc_fence_before();
+      const uint32_t hbase = smem_addr(smem + st * sbytes);
+      const uint32_t wbase = wres ? smem_addr(wres_sm) + kc * G::kWBytes : hbase + G::kHaloBytes;
+      const uint64_t a0 = sdesc(hbase, G::kHaloRows * 16, 160), b0 = sdesc(wbase, N * 16, 128);
+      const uint32_t acc = tbase + (c & 1) * (ZB * N);
+#pragma unroll
+      for (int t = 0; t < 27; ++t) {
+        constexpr int dummy = 0;
+        (void)dummy;
+        const int dz = SIGN * (t / 9 - 1), dy = SIGN * ((t / 3) % 3 - 1), dx = SIGN * (t % 3 - 1);
+        const int toff = ((dz + 1) * 18 + (dy + 1)) * 10 + (dx + 1);  // halo row of (0, 0, 0) at this tap
+        const uint64_t bdesc = b0 + (uint64_t)(t * N * 2);         // + t N 32 bytes (>> 4)
+#pragma unroll
+        for (int zz = 0; zz < ZB; ++zz)
+          mma_bf16(acc + zz * N, a0 + (uint64_t)(zz * 180 + toff), bdesc, kIdesc, (t > 0 || kc > 0) ? 1u : 0u);
+      }
+      mma_commit(smem_addr(empty + st));
+      if (kc == nk - 1) mma_commit(smem_addr(accfull + (c & 1)));
     }
-    const int jn = j + NS - 1;
-    if (jn < n_items && !*abort_flag) issue(jn);
-    asm volatile("cp.async.commit_group;" ::: "memory");
   }
-  if (ok && n_items > 0) {
-    const int j = n_items - 1;
-    if (!mbar_wait(smem_addr(bars + j % NS), (j / NS) & 1)) *abort_flag = 1;
-    tc_fence_after();
-    if (!*abort_flag) epilogue(j);
-  }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncwarp();
   tc_fence_before();
   __syncthreads();
   if (*abort_flag && tid == 0) atomicExch(err, (int)CMG_ERR_TIMEOUT);
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(G::kCols));
+  if (warp == 4) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(G::kCols));
 }
 
 // Weight image for k_conv_tc: src [N][27][K] (bf16) -> dst [K/16][27][2][N][8]

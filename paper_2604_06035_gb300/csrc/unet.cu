@@ -219,17 +219,19 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_wgrad(const bf16 *__restr
 }
 
 // ---- per-sample input statistics and the network input
-// stats[b] = {sum rho, sum rho^2, sum phi^2}
+// stats[b] = {sum rho, sum rho^2, sum phi^2}: per-thread FP32 partial sums,
+// combined in FP64 (GB300's FP64 rate is a small fraction of FP32's)
 __global__ void k_stats(const float *__restrict__ rho, const float *__restrict__ phi, int64_t V,
                         double *__restrict__ stats) {
   const int b = blockIdx.y;
-  double s0 = 0, s1 = 0, s2 = 0;
+  float f0 = 0.f, f1 = 0.f, f2 = 0.f;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
-    const double r = rho[b * V + v], p = phi[b * V + v];
-    s0 += r;
-    s1 += r * r;
-    s2 += p * p;
+    const float r = rho[b * V + v], p = phi[b * V + v];
+    f0 += r;
+    f1 = fmaf(r, r, f1);
+    f2 = fmaf(p, p, f2);
   }
+  double s0 = f0, s1 = f1, s2 = f2;
   for (int o = 16; o > 0; o >>= 1) {
     s0 += __shfl_down_sync(0xffffffffu, s0, o);
     s1 += __shfl_down_sync(0xffffffffu, s1, o);
@@ -242,28 +244,31 @@ __global__ void k_stats(const float *__restrict__ rho, const float *__restrict__
   }
 }
 
-// x[b][v][0] = (rho - mean) / std, x[..][1] = phi / rms, channels 2..15 = 0;
-// norm[b] = {mean, 1/std, out_scale * rms}
-__global__ void k_input(const float *__restrict__ rho, const float *__restrict__ phi, int64_t V,
-                        const double *__restrict__ stats, float out_scale, float *__restrict__ norm,
-                        bf16 *__restrict__ x) {
-  const int b = blockIdx.y;
+// norm[b] = {mean, 1/std, out_scale * rms}, plus 1/rms at norm_in[b] (one thread per sample)
+__global__ void k_norm(const double *__restrict__ stats, int64_t V, int B, float out_scale, float *__restrict__ norm,
+                       float *__restrict__ inv_rms) {
+  const int b = threadIdx.x;
+  if (b >= B) return;
   const double n = (double)V;
   const double mean = stats[3 * b] / n;
   const double var = fmax(stats[3 * b + 1] / n - mean * mean, 1e-300);
   const double rms = sqrt(stats[3 * b + 2] / n);
-  const float inv_std = (float)(1.0 / sqrt(var)), fmean = (float)mean, inv_rms = (float)(1.0 / rms);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    norm[3 * b] = fmean;
-    norm[3 * b + 1] = inv_std;
-    norm[3 * b + 2] = (float)(out_scale * rms);
-  }
+  norm[3 * b] = (float)mean;
+  norm[3 * b + 1] = (float)(1.0 / sqrt(var));
+  norm[3 * b + 2] = (float)(out_scale * rms);
+  inv_rms[b] = (float)(1.0 / rms);
+}
+
+// x[b][v][0] = (rho - mean) / std, x[..][1] = phi / rms, channels 2..15 = 0
+__global__ void k_input(const float *__restrict__ rho, const float *__restrict__ phi, int64_t V,
+                        const float *__restrict__ norm, const float *__restrict__ inv_rms, bf16 *__restrict__ x) {
+  const int b = blockIdx.y;
+  const float mean = norm[3 * b], inv_std = norm[3 * b + 1], ir = inv_rms[b];
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
-    __align__(16) bf16 row[16];
-    row[0] = __float2bfloat16_rn((rho[b * V + v] - fmean) * inv_std);
-    row[1] = __float2bfloat16_rn(phi[b * V + v] * inv_rms);
+    __align__(16) __nv_bfloat162 row[8];
+    row[0] = __floats2bfloat162_rn((rho[b * V + v] - mean) * inv_std, phi[b * V + v] * ir);
 #pragma unroll
-    for (int c = 2; c < 16; ++c) row[c] = __float2bfloat16_rn(0.f);
+    for (int c = 1; c < 8; ++c) row[c] = __floats2bfloat162_rn(0.f, 0.f);
     uint4 *dst = reinterpret_cast<uint4 *>(x + (b * V + v) * 16);
     dst[0] = reinterpret_cast<const uint4 *>(row)[0];
     dst[1] = reinterpret_cast<const uint4 *>(row)[1];
@@ -526,7 +531,7 @@ void conv_tc_launch(cmg_unet *U, const bf16 *in, int K, const bf16 *skip, int Cb
   const int total = (D / 8) * (D / 16) * (D / ZB) * B;
   const int grid = std::min(total, U->ctx->num_sms);
   LaunchScope ls(U->ctx, FWD ? K_CONV_FWD : K_CONV_DGRAD, 0.0, 2.0 * 27 * K * N * (double)D * D * D * B);
-  tc::k_conv_tc<N, ZB, FWD><<<grid, tc::kThreads, G::smem_bytes(K), U->ctx->stream>>>(in, K, skip, Cb, WI, bias, out,
+  tc::k_conv_tc<N, ZB, FWD><<<grid, tc::kConvThreads, G::smem_bytes(K), U->ctx->stream>>>(in, K, skip, Cb, WI, bias, out,
                                                                                      D, total, U->d_err);
   CMG_CUDA(cudaGetLastError());
 }
@@ -672,7 +677,8 @@ void forward(cmg_unet *U, int B, float *phi_pred, bool training) {
   const int64_t V0 = vox(U, 0);
   CMG_CUDA(cudaMemsetAsync(U->stats, 0, sizeof(double) * 3 * B, s));
   k_stats<<<dim3(64, B), 256, 0, s>>>(U->in_rho, U->in_phi, V0, U->stats);
-  k_input<<<dim3(gsz(V0), B), 256, 0, s>>>(U->in_rho, U->in_phi, V0, U->stats, U->out_scale, U->norm, U->x);
+  k_norm<<<1, (B + 31) / 32 * 32, 0, s>>>(U->stats, V0, B, U->out_scale, U->norm, U->norm + 3 * U->max_batch);
+  k_input<<<dim3(gsz(V0), B), 256, 0, s>>>(U->in_rho, U->in_phi, V0, U->norm, U->norm + 3 * U->max_batch, U->x);
   CMG_CUDA(cudaGetLastError());
   const int D0 = dim_of(U, 0), D1 = dim_of(U, 1), D2 = dim_of(U, 2);
   auto layer = [&](int l, const bf16 *in, bf16 *out) {
@@ -829,7 +835,7 @@ int cmg_unet_create(cmg_ctx *ctx, int grid_dim, int max_batch, cmg_unet **out) {
       U->gp = act(B * std::max(V1 * 16, V2 * 32));
       U->gu = act(B * std::max(V1 * 32, V2 * 64));
       U->delta = M.alloc<float>(B * V0);
-      U->norm = M.alloc<float>(3 * B);
+      U->norm = M.alloc<float>(4 * B);  // {mean, 1/std, c rms} per sample, then 1/rms per sample
       U->stats = M.alloc<double>(3 * B);
       U->loss = M.alloc<double>(1);
       U->d_err = M.alloc<int32_t>(1, true, s);
