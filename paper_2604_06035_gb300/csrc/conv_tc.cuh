@@ -147,18 +147,19 @@ struct ConvGeom {
 // Persistent, warp-specialised convolution: grid <= one CTA per SM, each
 // CTA walks the work items (brick, 16-channel slice) of bricks blockIdx.x,
 // + gridDim.x, ... in order.  Warps 0-3 load the halo stages (cp.async) and
-// run the epilogues; warp 4 allocates TMEM and one of its threads issues the
-// MMAs.  The roles meet only at mbarriers:
+// run the epilogues; warp 4 allocates TMEM, and one thread of warp 4 and
+// one of warp 5 issue the MMAs (even and odd z slices: two issuers keep the
+// tensor pipe fed at small N).  The roles meet only at mbarriers:
 //   full[s]     halo of stage s landed (128 producer arrivals)
-//   empty[s]    MMAs that read stage s done (tcgen05.commit)
+//   empty[s]    MMAs that read stage s done (tcgen05.commit of both issuers)
 //   wfull[s]    stage weights landed (bulk copy); wres: resident weights
-//   accfull[b]  a brick's accumulators in TMEM buffer b complete (commit)
+//   accfull[b]  a brick's accumulators in TMEM buffer b complete (both commits)
 //   accempty[b] the epilogue has read TMEM buffer b (128 arrivals)
 // FWD: out = ReLU(conv(in, W) + bias); else out = conv^T (SIGN = -1, no bias).
 // With `skip` set (forward only) the input is the channel concatenation of
 // the nearest-upsampled `in` (K - Cb channels on the D/2 grid) and `skip`
 // (Cb channels on the D grid), read directly by the halo loader.
-constexpr int kConvThreads = 160;
+constexpr int kConvThreads = 192;
 constexpr int kProducers = 128;
 
 template <int N, int ZB, bool FWD>
@@ -194,12 +195,12 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __nv_bfloat16
   if (tid == 0) {
     for (int i = 0; i < 3; ++i) {
       mbar_init(smem_addr(full + i), kProducers);
-      mbar_init(smem_addr(empty + i), 1);
+      mbar_init(smem_addr(empty + i), 2);
       mbar_init(smem_addr(wfull + i), 1);
     }
     mbar_init(smem_addr(wresb), 1);
     for (int i = 0; i < 2; ++i) {
-      mbar_init(smem_addr(accfull + i), 1);
+      mbar_init(smem_addr(accfull + i), 2);
       mbar_init(smem_addr(accempty + i), kProducers);
     }
     *abort_flag = 0;
@@ -300,16 +301,19 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __nv_bfloat16
     }
     bool ok = true;
     for (int j = 0; j < n_items && ok; ++j) {
+      // item j's copies landed (its group is NS - 2 groups older than the
+      // newest): hand the stage to the MMA warps at once
+      if (NS == 3) asm volatile("cp.async.wait_group 1;" ::: "memory");
+      else asm volatile("cp.async.wait_group 0;" ::: "memory");
+      fence_async_shared();
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(full + j % NS)) : "memory");
+      // refill the stage of item j - 1 once its MMAs are done
       const int jn = j + NS - 1;
       if (jn < n_items) {
         if (jn >= NS && !wait(empty + jn % NS, ((jn - NS) / NS) & 1)) ok = false;
         if (ok) produce(jn);
       }
       asm volatile("cp.async.commit_group;" ::: "memory");
-      if (NS == 3) asm volatile("cp.async.wait_group 2;" ::: "memory");
-      else asm volatile("cp.async.wait_group 1;" ::: "memory");
-      fence_async_shared();
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(full + j % NS)) : "memory");
       // the previous brick's epilogue, one item behind its last MMAs
       if (ok && j > 0 && j % nk == 0) {
         const int c = j / nk - 1;
@@ -329,7 +333,10 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __nv_bfloat16
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
   } else if (lane == 0) {
-    // ------------------------------------------------------------ MMA issue
+    // ------------------------------------------- MMA issue (warps 4 and 5)
+    // warp 4 + h issues the z slices zz = h, h + 2, ...; both commit every
+    // stage and every finished brick (the barriers count two arrivals)
+    const int h = warp - 4;
     constexpr uint32_t kIdesc = idesc_bf16(128, N);
     for (int j = 0; j < n_items; ++j) {
       const int st = j % NS, kc = j % nk, c = j / nk;
@@ -351,7 +358,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __nv_bfloat16
         const uint64_t bdesc = b0 + (uint64_t)(t * N * 2);         // + t N 32 bytes (>> 4)
 #pragma unroll
         for (int zz = 0; zz < ZB; ++zz)
-          mma_bf16(acc + zz * N, a0 + (uint64_t)(zz * 180 + toff), bdesc, kIdesc, (t > 0 || kc > 0) ? 1u : 0u);
+          if ((zz & 1) == h)
+            mma_bf16(acc + zz * N, a0 + (uint64_t)(zz * 180 + toff), bdesc, kIdesc, (t > 0 || kc > 0) ? 1u : 0u);
       }
       mma_commit(smem_addr(empty + st));
       if (kc == nk - 1) mma_commit(smem_addr(accfull + (c & 1)));
