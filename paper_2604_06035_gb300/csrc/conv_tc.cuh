@@ -3,25 +3,36 @@
 //
 // Implicit GEMM: out[v][n] = sum_t sum_k in[v + SIGN d_t][k] W[n][t][k] with
 // M = voxels, N = output channels, K = 27 taps x input channels.  A CTA owns
-// a brick of 8 (x) x 16 (y) x ZB (z) voxels: ZB accumulators of 128 rows
-// (row m = 8 y + x of one z slice) x N fp32 columns in TMEM.  Per 16-channel
+// bricks of 8 (x) x 16 (y) x ZB (z) voxels: one accumulator of 128 rows
+// (row m = 8 y + x of one z slice) per z slice, fp32 in TMEM.  Per 16-channel
 // input slice the CTA stages
 //   * the brick's periodic halo, 10 x 18 x (ZB + 2) rows of 16 channels, as
 //     two K-halves ("planes") of 16-byte rows: plane p holds channels
 //     8p..8p+7 of every halo row, rows x fastest;
-//   * the slice's weights for all 27 taps in the same canonical form (one
-//     bulk copy of a pre-arranged image, tap-major, then K-half, then n).
-// In that form every tap's A operand is a plain shared-memory descriptor:
-// eight consecutive x rows are one 128-byte core matrix, the 16 y rows of a
-// z slice are core matrices 10 rows (160 B) apart (SBO), the second K-half is
-// a plane further (LBO), and the tap offset only moves the start address --
-// no im2col copy.  One thread issues the 27 x ZB MMAs of a slice and commits
-// them to an mbarrier.  The kernel is persistent (one CTA per SM walking
-// (brick, slice) work items): a ring of halo stages keeps the copies two
-// items ahead of the MMAs, the accumulators are double-buffered in TMEM so
-// that a brick's epilogue (TMEM -> bias, ReLU -> bf16 stores, each warp its
-// 32 lanes) overlaps the next brick's MMAs, and the weights stay resident in
-// shared memory when they fit.
+//   * the slice's weights for all 27 taps in the canonical form (one bulk
+//     copy of a pre-arranged image).
+// In that form every A operand is a plain shared-memory descriptor: eight
+// consecutive x rows are one 128-byte core matrix, the 16 y rows of a z slab
+// are core matrices 10 rows (160 B) apart (SBO), the second K-half is a plane
+// further (LBO), and a tap's (dy, dx) offset only moves the start address --
+// no im2col copy.
+//
+// A z slab of the halo is the A operand of three taps (dz = -1, 0, +1 of
+// three consecutive output slices).  For N <= 32 ("stacked" form) one MMA
+// with N' = 3N covers all three: B stacks the three taps' weights, and D
+// spans three consecutive accumulators (output slices s - 2, s - 1, s for
+// halo slab s; the accumulator of slice zz sits at column (zz + 2) N, the
+// slices -2, -1, ZB, ZB + 1 are scratch).  That is 9 (ZB + 2) MMAs per slice
+// and brick instead of 27 ZB, each with three times the N -- the MMA cost
+// at small N is set by the A operand, not by N.  The accumulators are then
+// zeroed by the epilogue (tcgen05.st) instead of by the first MMA.  For
+// N >= 48 every tap is its own MMA (27 ZB per slice and brick).
+//
+// The kernel is persistent and warp-specialised: one CTA per SM walks the
+// work items (brick, slice) of bricks blockIdx.x, + gridDim.x, ...; warps
+// 0-3 load the halo stages (cp.async) and run the epilogues, warps 4 and 5
+// (one thread each) issue the MMAs of the even and the odd bricks -- each
+// into its own TMEM accumulator set, so the summation order is fixed.
 //
 // Every wait is bounded (clock64 budget); on expiry the kernel records
 // CMG_ERR_TIMEOUT in *err, stops issuing work, frees its TMEM and returns.
@@ -117,13 +128,23 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
 
 __host__ __device__ constexpr int pow2_cols(int c) { return c <= 32 ? 32 : c <= 64 ? 64 : c <= 128 ? 128 : c <= 256 ? 256 : 512; }
 
+__device__ __forceinline__ void tmem_st16_zero(uint32_t taddr) {
+  const uint32_t z = 0;
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+      "r"(z)
+      : "memory");
+}
+
 // Geometry of one configuration (shared by host and device).
 template <int N, int ZB>
 struct ConvGeom {
+  static constexpr bool kStack = N <= 32;
   static constexpr int kHaloRows = (ZB + 2) * 18 * 10;
   static constexpr int kHaloBytes = kHaloRows * 32;  // two planes of 16-byte rows
   static constexpr int kWBytes = 27 * N * 32;        // one 16-channel slice, all taps
-  static constexpr int kCols = pow2_cols(2 * ZB * N);  // two accumulator sets
+  static constexpr int kAccCols = kStack ? (ZB + 4) * N : ZB * N;  // one accumulator set
+  static constexpr int kCols = pow2_cols(2 * kAccCols);            // two sets
   static constexpr int kBarBytes = 192;  // 14 mbarriers, TMEM slot, abort flag
   // Weights stay resident (one bulk copy per CTA) when they fit beside a
   // three-stage halo ring; otherwise every stage carries its slice's weights
@@ -144,17 +165,12 @@ struct ConvGeom {
   }
 };
 
-// Persistent, warp-specialised convolution: grid <= one CTA per SM, each
-// CTA walks the work items (brick, 16-channel slice) of bricks blockIdx.x,
-// + gridDim.x, ... in order.  Warps 0-3 load the halo stages (cp.async) and
-// run the epilogues; warp 4 allocates TMEM, and one thread of warp 4 and
-// one of warp 5 issue the MMAs (even and odd z slices: two issuers keep the
-// tensor pipe fed at small N).  The roles meet only at mbarriers:
+// Barriers:
 //   full[s]     halo of stage s landed (128 producer arrivals)
-//   empty[s]    MMAs that read stage s done (tcgen05.commit of both issuers)
+//   empty[s]    MMAs that read stage s done (tcgen05.commit of its issuer)
 //   wfull[s]    stage weights landed (bulk copy); wres: resident weights
-//   accfull[b]  a brick's accumulators in TMEM buffer b complete (both commits)
-//   accempty[b] the epilogue has read TMEM buffer b (128 arrivals)
+//   accfull[b]  brick accumulators in TMEM set b complete (commit)
+//   accempty[b] the epilogue has read (and, stacked, zeroed) set b (128 arrivals)
 // FWD: out = ReLU(conv(in, W) + bias); else out = conv^T (SIGN = -1, no bias).
 // With `skip` set (forward only) the input is the channel concatenation of
 // the nearest-upsampled `in` (K - Cb channels on the D/2 grid) and `skip`
@@ -171,6 +187,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __nv_bfloat16
                                                             int *__restrict__ err) {
   using G = ConvGeom<N, ZB>;
   constexpr int SIGN = FWD ? 1 : -1;
+  constexpr bool STACK = G::kStack;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const bool wres = G::resident(K);
@@ -195,12 +212,12 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __nv_bfloat16
   if (tid == 0) {
     for (int i = 0; i < 3; ++i) {
       mbar_init(smem_addr(full + i), kProducers);
-      mbar_init(smem_addr(empty + i), 2);
+      mbar_init(smem_addr(empty + i), 1);
       mbar_init(smem_addr(wfull + i), 1);
     }
     mbar_init(smem_addr(wresb), 1);
     for (int i = 0; i < 2; ++i) {
-      mbar_init(smem_addr(accfull + i), 2);
+      mbar_init(smem_addr(accfull + i), 1);
       mbar_init(smem_addr(accempty + i), kProducers);
     }
     *abort_flag = 0;
@@ -210,6 +227,15 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __nv_bfloat16
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tslot;
+  if (STACK && warp < 4) {
+    // both accumulator sets start at zero (the MMAs always accumulate)
+    const uint32_t lanes = (uint32_t)(warp * 32) << 16;
+    for (int c0 = 0; c0 < 2 * G::kAccCols; c0 += 16) tmem_st16_zero(tbase + lanes + c0);
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
 
   // bounded wait that also gives up as soon as another thread has
   auto wait = [&](uint64_t *bar, int parity) -> bool {
@@ -269,17 +295,18 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __nv_bfloat16
       const int bi = blockIdx.x + c * gridDim.x;
       const int sample = bi / nbps, brick = bi % nbps;
       const int bx = brick % nbx, by = (brick / nbx) % nby, bz = brick / (nbx * nby);
-      const uint32_t acc = tbase + (c & 1) * (ZB * N) + ((uint32_t)(warp * 32) << 16);
+      const uint32_t set = tbase + (c & 1) * G::kAccCols + ((uint32_t)(warp * 32) << 16);
       const int m = warp * 32 + lane;  // TMEM lane = accumulator row
       const int y = by * 16 + (m >> 3), x = bx * 8 + (m & 7);
 #pragma unroll 1
       for (int zz = 0; zz < ZB; ++zz) {
         const int z = bz * ZB + zz;
         __nv_bfloat16 *dst = out + ((int64_t)sample * D * D * D + ((int64_t)z * D + y) * D + x) * N;
+        const uint32_t acc = set + (STACK ? (zz + 2) * N : zz * N);
 #pragma unroll
         for (int c0 = 0; c0 < N; c0 += 16) {
           float v[16];
-          tmem_ld16(acc + zz * N + c0, v);
+          tmem_ld16(acc + c0, v);
           __align__(16) __nv_bfloat162 o[8];
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
@@ -293,6 +320,11 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __nv_bfloat16
           reinterpret_cast<uint4 *>(dst + c0)[0] = reinterpret_cast<const uint4 *>(o)[0];
           reinterpret_cast<uint4 *>(dst + c0)[1] = reinterpret_cast<const uint4 *>(o)[1];
         }
+      }
+      if (STACK) {
+        // zero the whole set (scratch slices included) for its next brick
+        for (int c0 = 0; c0 < G::kAccCols; c0 += 16) tmem_st16_zero(set + c0);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       }
     };
     for (int s = 0; s < NS - 1; ++s) {
@@ -333,36 +365,46 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __nv_bfloat16
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
   } else if (lane == 0) {
-    // ------------------------------------------- MMA issue (warps 4 and 5)
-    // warp 4 + h issues the z slices zz = h, h + 2, ...; both commit every
-    // stage and every finished brick (the barriers count two arrivals)
+    // ------------------------------------- MMA issue: warp 4 + h, bricks c = h mod 2
     const int h = warp - 4;
-    constexpr uint32_t kIdesc = idesc_bf16(128, N);
+    constexpr uint32_t kIdesc = idesc_bf16(128, STACK ? 3 * N : N);
     for (int j = 0; j < n_items; ++j) {
       const int st = j % NS, kc = j % nk, c = j / nk;
-      if (kc == 0 && c >= 2 && !wait(accempty + (c & 1), ((c - 2) >> 1) & 1)) break;
+      if ((c & 1) != h) continue;
+      if (kc == 0 && c >= 2 && !wait(accempty + h, ((c - 2) >> 1) & 1)) break;
       if (!wait(full + st, (j / NS) & 1)) break;
       if (!(wres ? wait(wresb, 0) : wait(wfull + st, (j / NS) & 1))) break;
       fence_async_shared();
       tc_fence_after();
       const uint32_t hbase = smem_addr(smem + st * sbytes);
       const uint32_t wbase = wres ? smem_addr(wres_sm) + kc * G::kWBytes : hbase + G::kHaloBytes;
-      const uint64_t a0 = sdesc(hbase, G::kHaloRows * 16, 160), b0 = sdesc(wbase, N * 16, 128);
-      const uint32_t acc = tbase + (c & 1) * (ZB * N);
+      const uint64_t a0 = sdesc(hbase, G::kHaloRows * 16, 160);
+      const uint32_t set = tbase + h * G::kAccCols;
+      if (STACK) {
+        // B for (dy, dx) = q: the taps dz = +1, 0, -1 (times SIGN) stacked
+        const uint64_t b0 = sdesc(wbase, 3 * N * 16, 128);
 #pragma unroll
-      for (int t = 0; t < 27; ++t) {
-        constexpr int dummy = 0;
-        (void)dummy;
-        const int dz = SIGN * (t / 9 - 1), dy = SIGN * ((t / 3) % 3 - 1), dx = SIGN * (t % 3 - 1);
-        const int toff = ((dz + 1) * 18 + (dy + 1)) * 10 + (dx + 1);  // halo row of (0, 0, 0) at this tap
-        const uint64_t bdesc = b0 + (uint64_t)(t * N * 2);         // + t N 32 bytes (>> 4)
+        for (int q = 0; q < 9; ++q) {
+          const int qoff = (q / 3) * 10 + (q % 3);  // (dy + 1) * 10 + (dx + 1) in halo rows
+          const uint64_t bdesc = b0 + (uint64_t)(q * 6 * N);  // + q 3N 32 bytes (>> 4)
 #pragma unroll
-        for (int zz = 0; zz < ZB; ++zz)
-          if ((zz & 1) == h)
-            mma_bf16(acc + zz * N, a0 + (uint64_t)(zz * 180 + toff), bdesc, kIdesc, (t > 0 || kc > 0) ? 1u : 0u);
+          for (int sl = 0; sl < ZB + 2; ++sl)
+            mma_bf16(set + sl * N, a0 + (uint64_t)(sl * 180 + qoff), bdesc, kIdesc, 1u);
+        }
+      } else {
+        const uint64_t b0 = sdesc(wbase, N * 16, 128);
+#pragma unroll
+        for (int t = 0; t < 27; ++t) {
+          const int dz = SIGN * (t / 9 - 1), dy = SIGN * ((t / 3) % 3 - 1), dx = SIGN * (t % 3 - 1);
+          const int toff = ((dz + 1) * 18 + (dy + 1)) * 10 + (dx + 1);  // halo row of (0, 0, 0) at this tap
+          const uint64_t bdesc = b0 + (uint64_t)(t * N * 2);          // + t N 32 bytes (>> 4)
+#pragma unroll
+          for (int zz = 0; zz < ZB; ++zz)
+            mma_bf16(set + zz * N, a0 + (uint64_t)(zz * 180 + toff), bdesc, kIdesc, (t > 0 || kc > 0) ? 1u : 0u);
+        }
       }
       mma_commit(smem_addr(empty + st));
-      if (kc == nk - 1) mma_commit(smem_addr(accfull + (c & 1)));
+      if (kc == nk - 1) mma_commit(smem_addr(accfull + h));
     }
   }
   __syncwarp();
@@ -372,16 +414,30 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __nv_bfloat16
   if (warp == 4) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(G::kCols));
 }
 
-// Weight image for k_conv_tc: src [N][27][K] (bf16) -> dst [K/16][27][2][N][8]
-// (slice, tap, K-half, output channel, 8 channels).
-__global__ void k_weight_image(const __nv_bfloat16 *__restrict__ src, int N, int K, __nv_bfloat16 *__restrict__ dst) {
+// Weight images for k_conv_tc from src [N][27][K] (bf16):
+//   per tap (N >= 48):  [K/16][27 taps][2 K-halves][N][8]
+//   stacked (N <= 32):  [K/16][9 (dy, dx)][2 K-halves][3 (dz = +1, 0, -1)][N][8]
+// with the tap offsets of the stacked form scaled by `sign` (-1 for the
+// input-gradient convolution, whose taps are mirrored).
+__global__ void k_weight_image(const __nv_bfloat16 *__restrict__ src, int N, int K, int sign,
+                               __nv_bfloat16 *__restrict__ dst) {
   const int64_t total = (int64_t)N * 27 * K;
+  const bool stack = N <= 32;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int k = (int)(e % K);
     const int t = (int)((e / K) % 27);
     const int n = (int)(e / (27 * K));
     const int kc = k >> 4, p = (k >> 3) & 1, j = k & 7;
-    dst[((((int64_t)kc * 27 + t) * 2 + p) * N + n) * 8 + j] = src[e];
+    int64_t o;
+    if (!stack) {
+      o = ((((int64_t)kc * 27 + t) * 2 + p) * N + n) * 8 + j;
+    } else {
+      // applied offsets (dzs, dys, dxs) = sign (dz, dy, dx) of tap t
+      const int dzs = sign * (t / 9 - 1), dys = sign * ((t / 3) % 3 - 1), dxs = sign * (t % 3 - 1);
+      const int q = (dys + 1) * 3 + (dxs + 1), st = 1 - dzs;  // dzs = +1 -> 0, 0 -> 1, -1 -> 2
+      o = (((((int64_t)kc * 9 + q) * 2 + p) * 3 + st) * N + n) * 8 + j;
+    }
+    dst[o] = src[e];
   }
 }
 

@@ -555,11 +555,11 @@ bool tc_eligible(const cmg_unet *U, int N, int D) {
   return U->use_tc && D >= 16 && D % 16 == 0 && (N == 16 || N == 32 || N == 48 || N == 64 || N == 96);
 }
 
-// Deep bricks (ZB = 4 for N <= 32, 2 above) when they still give every SM a
-// brick, else one-slice bricks (four or two times as many).
+// Deep bricks (ZB = 8 for N = 16, 4 for N = 32, 2 above) when they still
+// give every SM a brick, else one-slice bricks.
 void conv_tc(cmg_unet *U, const bf16 *in, int K, const bf16 *skip, int Cb, const bf16 *WI, const float *bias,
              bf16 *out, int N, int D, int B, bool fwd) {
-  const int zb = N <= 32 ? 4 : 2;
+  const int zb = N == 16 ? 8 : N == 32 ? 4 : 2;
   const bool deep = (D / 8) * (D / 16) * (D / zb) * B >= U->ctx->num_sms;
 #define CMG_CONV_TC(NN, ZB)                                                                           \
   case NN:                                                                                            \
@@ -572,7 +572,7 @@ void conv_tc(cmg_unet *U, const bf16 *in, int K, const bf16 *skip, int Cb, const
     }                                                                                                 \
     break;
   switch (N) {
-    CMG_CONV_TC(16, 4)
+    CMG_CONV_TC(16, 8)
     CMG_CONV_TC(32, 4)
     CMG_CONV_TC(48, 2)
     CMG_CONV_TC(64, 2)
@@ -658,8 +658,8 @@ void prepare_weights(cmg_unet *U) {
     const LayerSpec &L = kLayers[l];
     const int64_t n = (int64_t)L.cout * 27 * L.cin;
     k_cast_w<<<gsz(n), 256, 0, s>>>(U->params + layer_offset(l), L.cout, L.cin, U->W[l], U->WT[l]);
-    tc::k_weight_image<<<gsz(n), 256, 0, s>>>(U->W[l], L.cout, L.cin, U->WI[l]);
-    tc::k_weight_image<<<gsz(n), 256, 0, s>>>(U->WT[l], L.cin, L.cout, U->WTI[l]);
+    tc::k_weight_image<<<gsz(n), 256, 0, s>>>(U->W[l], L.cout, L.cin, 1, U->WI[l]);
+    tc::k_weight_image<<<gsz(n), 256, 0, s>>>(U->WT[l], L.cin, L.cout, -1, U->WTI[l]);
   }
   CMG_CUDA(cudaGetLastError());
   U->weights_ready = true;
