@@ -16,6 +16,14 @@ int fail(int code, const std::string &msg) {
   return code;
 }
 
+}  // namespace
+
+namespace cmg {
+void record_error(const char *msg) { g_last_error = msg; }
+}  // namespace cmg
+
+namespace {
+
 template <class F>
 int guard(F &&f) {
   try {

@@ -153,6 +153,8 @@ __device__ inline int64_t ht_slot(const uint64_t *__restrict__ keys, uint64_t ma
 }
 
 __device__ inline void set_error(int *err, int code) { atomicCAS(err, 0, code); }
+// message returned by cmg_last_error() on this thread
+void record_error(const char *msg);
 
 // -------------------------------------------------------------- cell maps
 

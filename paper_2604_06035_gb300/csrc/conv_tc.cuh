@@ -30,9 +30,11 @@
 //
 // The kernel is persistent and warp-specialised: one CTA per SM walks the
 // work items (brick, slice) of bricks blockIdx.x, + gridDim.x, ...; warps
-// 0-3 load the halo stages (cp.async) and run the epilogues, warps 4 and 5
-// (one thread each) issue the MMAs of the even and the odd bricks -- each
-// into its own TMEM accumulator set, so the summation order is fixed.
+// 0-3 load the halo stages (cp.async) and run the epilogues, one thread of
+// warp 4 issues every MMA in work-item order (one issuer keeps each mbarrier
+// waited in phase order and the summation order fixed); the accumulators
+// are double-buffered in TMEM so that a brick's epilogue overlaps the next
+// brick's MMAs.
 //
 // Every wait is bounded (clock64 budget); on expiry the kernel records
 // CMG_ERR_TIMEOUT in *err, stops issuing work, frees its TMEM and returns.
@@ -175,7 +177,7 @@ struct ConvGeom {
 // With `skip` set (forward only) the input is the channel concatenation of
 // the nearest-upsampled `in` (K - Cb channels on the D/2 grid) and `skip`
 // (Cb channels on the D grid), read directly by the halo loader.
-constexpr int kConvThreads = 192;
+constexpr int kConvThreads = 160;
 constexpr int kProducers = 128;
 
 template <int N, int ZB, bool FWD>
@@ -365,12 +367,10 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __nv_bfloat16
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
   } else if (lane == 0) {
-    // ------------------------------------- MMA issue: warp 4 + h, bricks c = h mod 2
-    const int h = warp - 4;
+    // ------------------------------------------------------------ MMA issue
     constexpr uint32_t kIdesc = idesc_bf16(128, STACK ? 3 * N : N);
     for (int j = 0; j < n_items; ++j) {
-      const int st = j % NS, kc = j % nk, c = j / nk;
-      if ((c & 1) != h) continue;
+      const int st = j % NS, kc = j % nk, c = j / nk, h = c & 1;
       if (kc == 0 && c >= 2 && !wait(accempty + h, ((c - 2) >> 1) & 1)) break;
       if (!wait(full + st, (j / NS) & 1)) break;
       if (!(wres ? wait(wresb, 0) : wait(wfull + st, (j / NS) & 1))) break;

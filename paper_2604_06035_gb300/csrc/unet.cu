@@ -774,16 +774,16 @@ void copy_in(cmg_unet *U, float *dst, const float *src, int64_t n, int mem) {
 // ------------------------------------------------------------------ C ABI
 
 namespace {
-thread_local std::string g_unet_error;
 template <class F>
 int unet_guard(F &&f) {
   try {
+    cmg::record_error("");
     return f();
   } catch (const cmg::Error &e) {
-    g_unet_error = e.what();
+    cmg::record_error(e.what());
     return e.code;
   } catch (const std::exception &e) {
-    g_unet_error = e.what();
+    cmg::record_error(e.what());
     return CMG_ERR_CUDA;
   }
 }
