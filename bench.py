@@ -331,9 +331,20 @@ def bench_forward(cmg, ctx, dev, peaks, D=64, batches=(1, 8), reps=20, paths=("t
             cmg.cmg_ctx_set_profiling(ctx, False)
             conv = cmg.cmg_ctx_get_profile(ctx)["conv_fwd"]
             tf = conv["flops"] / (conv["ms"] / 1e3) / 1e12
+            target = field + 0.01 * torch.randn((B, D, D, D), device=dev, generator=g)
+            for _ in range(2):
+                cmg.cmg_unet_gradients(net, rho, field, target, grads=False)
+            torch.cuda.synchronize()
+            a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a2.record()
+            for _ in range(5):
+                cmg.cmg_unet_gradients(net, rho, field, target, grads=False)
+            b2.record()
+            torch.cuda.synchronize()
             res["b%d_%s" % (B, name)] = {"ms_per_forward": a.elapsed_time(b) / reps,
                                          "conv_ms_per_forward": conv["ms"] / reps, "conv_TFLOPs": tf,
-                                         "conv_frac_of_bf16": tf / peaks["bf16"]}
+                                         "conv_frac_of_bf16": tf / peaks["bf16"],
+                                         "ms_per_training_step": a2.elapsed_time(b2) / 5}
     cmg.cmg_unet_set_kernels(net, 1)
     cmg.cmg_unet_destroy(net)
     return res
@@ -392,12 +403,22 @@ def bench_learned(cmg, ctx, dev, args, peaks):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / reps
 
-    res["ms_warm_start"] = ev_time(lambda: W.predict(S, net, rho, prev))
+    res["ms_warm_start_b1_python"] = ev_time(lambda: W.predict(S, net, rho, prev))
     res["ms_forward_b1"] = ev_time(lambda: cmg.cmg_unet_forward(net, rho1, r, base=prev1))
     rho8 = data["rho"][k, 1:9].contiguous()
     r8 = data["res"][k, 0:8].contiguous()
     prev8 = data["phi"][k, 0:8].contiguous()
     res["ms_forward_per_block_b8"] = ev_time(lambda: cmg.cmg_unet_forward(net, rho8, r8, base=prev8)) / 8
+    # the residual of phi_prev on the level (density and phi are set for the
+    # solve anyway): the residual kernel and the oct -> dense copy
+    S._load(rho, prev)
+    dense = torch.empty((D, D, D), dtype=torch.float64, device=dev)
+
+    def residual_only():
+        cmg.cmg_level_get_residual(S.level, device=True, out=S.octs)
+        cmg.cmg_dense_octs(ctx, S.octs, D, dense, 0)
+    res["ms_residual_per_block"] = ev_time(residual_only)
+    res["ms_warm_start_per_block_b8"] = res["ms_forward_per_block_b8"] + res["ms_residual_per_block"]
     cmg.cmg_ctx_reset_profile(ctx)
     cmg.cmg_ctx_set_profiling(ctx, True)
     for _ in range(5):
@@ -411,9 +432,11 @@ def bench_learned(cmg, ctx, dev, args, peaks):
                                 "launches": conv["launches"], "ms": conv["ms"],
                                 "flops_per_block": conv["flops"] / (5 * 8)}
     f, m = res["fp64"], res["mixed"]
+    ws = res["ms_warm_start_per_block_b8"]
     res["summary"] = {
-        "fp64_ms_prev": f["ms_prev"], "fp64_ms_net_plus_warm_start": f["ms_net"] + res["ms_warm_start"],
-        "mixed_ms_prev": m["ms_prev"], "mixed_ms_net_plus_warm_start": m["ms_net"] + res["ms_warm_start"],
+        "warm_start_ms_per_block": ws, "fp64_ms_zero": f["ms_zero"], "fp64_ms_prev": f["ms_prev"],
+        "fp64_ms_net_plus_warm_start": f["ms_net"] + ws,
+        "mixed_ms_prev": m["ms_prev"], "mixed_ms_net_plus_warm_start": m["ms_net"] + ws,
         "cycles_saved_fp64": f["cycles_prev"] - f["cycles_net"]}
     del S, net
     del data

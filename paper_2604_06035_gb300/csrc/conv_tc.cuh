@@ -30,11 +30,12 @@
 //
 // The kernel is persistent and warp-specialised: one CTA per SM walks the
 // work items (brick, slice) of bricks blockIdx.x, + gridDim.x, ...; warps
-// 0-3 load the halo stages (cp.async) and run the epilogues, one thread of
-// warp 4 issues every MMA in work-item order (one issuer keeps each mbarrier
-// waited in phase order and the summation order fixed); the accumulators
+// 0-3 run the epilogues (TMEM -> bias, ReLU -> bf16; warp w owns TMEM lanes
+// 32w..32w+31), warps 4-7 load the halo stages (cp.async), and one thread of
+// warp 8 issues every MMA in work-item order (one issuer keeps each mbarrier
+// waited in phase order and the summation order fixed).  The accumulators
 // are double-buffered in TMEM so that a brick's epilogue overlaps the next
-// brick's MMAs.
+// brick's MMAs, and the producers never wait for an epilogue.
 //
 // Every wait is bounded (clock64 budget); on expiry the kernel records
 // CMG_ERR_TIMEOUT in *err, stops issuing work, frees its TMEM and returns.
@@ -128,6 +129,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// 16 consecutive fp32 columns of this thread's TMEM lane, without the wait
+// (several loads in flight, one tcgen05.wait::ld after them).
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, float *v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
 __host__ __device__ constexpr int pow2_cols(int c) { return c <= 32 ? 32 : c <= 64 ? 64 : c <= 128 ? 128 : c <= 256 ? 256 : 512; }
 
 __device__ __forceinline__ void tmem_st16_zero(uint32_t taddr) {
@@ -177,7 +191,7 @@ struct ConvGeom {
 // With `skip` set (forward only) the input is the channel concatenation of
 // the nearest-upsampled `in` (K - Cb channels on the D/2 grid) and `skip`
 // (Cb channels on the D grid), read directly by the halo loader.
-constexpr int kConvThreads = 160;
+constexpr int kConvThreads = 288;
 constexpr int kProducers = 128;
 
 template <int N, int ZB, bool FWD>
@@ -206,7 +220,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __nv_bfloat16
   const int my_bricks = blockIdx.x < total_bricks ? (total_bricks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int n_items = my_bricks * nk;
 
-  if (warp == 4) {
+  if (warp == 8) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
                  "r"(G::kCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -253,11 +267,12 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __nv_bfloat16
     return true;
   };
 
-  if (warp < 4) {
-    // ------------------------------------------------ producers + epilogue
-    if (wres && tid == 0 && n_items > 0)
+  if (warp >= 4 && warp < 8) {
+    // ---------------------------------------------------------- producers
+    const int ptid = tid - 128;
+    if (wres && ptid == 0 && n_items > 0)
       bulk_load(smem_addr(wres_sm), wimg, (uint32_t)(nk * G::kWBytes), smem_addr(wresb));
-    // each thread copies halo columns (hy, hx, half): slots tid, tid + 128, tid + 256 (< 360)
+    // each thread copies halo columns (hy, hx, half): slots ptid, + 128, + 256 (< 360)
     auto produce = [&](int j) {
       const int bi = blockIdx.x + (j / nk) * gridDim.x, kc = j % nk;
       const int sample = bi / nbps, brick = bi % nbps;
@@ -269,7 +284,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __nv_bfloat16
       const __nv_bfloat16 *srcT = (skip != nullptr && !up) ? skip : in;
       const int Dg = up ? Dh : D;  // grid of the tensor read
       const int64_t s_off = (int64_t)sample * Dg * Dg * Dg;
-      for (int slot = tid; slot < 360; slot += kProducers) {
+      for (int slot = ptid; slot < 360; slot += kProducers) {
         const int col = slot >> 1, half = slot & 1;
         const int hy = col / 10, hx = col % 10;
         int y = by * 16 + hy - 1, x = bx * 8 + hx - 1;
@@ -289,54 +304,17 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __nv_bfloat16
           cp_async16(dst + hz * 180 * 16, src + (int64_t)z * Dg * Dg * cstride);
         }
       }
-      if (!wres && tid == 0)
+      if (!wres && ptid == 0)
         bulk_load(smem_addr(halo + G::kHaloBytes), wimg + (int64_t)kc * 27 * N * 16, G::kWBytes,
                   smem_addr(wfull + j % NS));
-    };
-    auto epilogue = [&](int c) {
-      const int bi = blockIdx.x + c * gridDim.x;
-      const int sample = bi / nbps, brick = bi % nbps;
-      const int bx = brick % nbx, by = (brick / nbx) % nby, bz = brick / (nbx * nby);
-      const uint32_t set = tbase + (c & 1) * G::kAccCols + ((uint32_t)(warp * 32) << 16);
-      const int m = warp * 32 + lane;  // TMEM lane = accumulator row
-      const int y = by * 16 + (m >> 3), x = bx * 8 + (m & 7);
-#pragma unroll 1
-      for (int zz = 0; zz < ZB; ++zz) {
-        const int z = bz * ZB + zz;
-        __nv_bfloat16 *dst = out + ((int64_t)sample * D * D * D + ((int64_t)z * D + y) * D + x) * N;
-        const uint32_t acc = set + (STACK ? (zz + 2) * N : zz * N);
-#pragma unroll
-        for (int c0 = 0; c0 < N; c0 += 16) {
-          float v[16];
-          tmem_ld16(acc + c0, v);
-          __align__(16) __nv_bfloat162 o[8];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            float a = v[2 * q], b2 = v[2 * q + 1];
-            if (FWD) {
-              a = fmaxf(a + __ldg(bias + c0 + 2 * q), 0.f);
-              b2 = fmaxf(b2 + __ldg(bias + c0 + 2 * q + 1), 0.f);
-            }
-            o[q] = __floats2bfloat162_rn(a, b2);
-          }
-          reinterpret_cast<uint4 *>(dst + c0)[0] = reinterpret_cast<const uint4 *>(o)[0];
-          reinterpret_cast<uint4 *>(dst + c0)[1] = reinterpret_cast<const uint4 *>(o)[1];
-        }
-      }
-      if (STACK) {
-        // zero the whole set (scratch slices included) for its next brick
-        for (int c0 = 0; c0 < G::kAccCols; c0 += 16) tmem_st16_zero(set + c0);
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-      }
     };
     for (int s = 0; s < NS - 1; ++s) {
       if (s < n_items) produce(s);
       asm volatile("cp.async.commit_group;" ::: "memory");
     }
-    bool ok = true;
-    for (int j = 0; j < n_items && ok; ++j) {
+    for (int j = 0; j < n_items; ++j) {
       // item j's copies landed (its group is NS - 2 groups older than the
-      // newest): hand the stage to the MMA warps at once
+      // newest): hand the stage to the MMA warp
       if (NS == 3) asm volatile("cp.async.wait_group 1;" ::: "memory");
       else asm volatile("cp.async.wait_group 0;" ::: "memory");
       fence_async_shared();
@@ -344,29 +322,61 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __nv_bfloat16
       // refill the stage of item j - 1 once its MMAs are done
       const int jn = j + NS - 1;
       if (jn < n_items) {
-        if (jn >= NS && !wait(empty + jn % NS, ((jn - NS) / NS) & 1)) ok = false;
-        if (ok) produce(jn);
+        if (jn >= NS && !wait(empty + jn % NS, ((jn - NS) / NS) & 1)) break;
+        produce(jn);
       }
       asm volatile("cp.async.commit_group;" ::: "memory");
-      // the previous brick's epilogue, one item behind its last MMAs
-      if (ok && j > 0 && j % nk == 0) {
-        const int c = j / nk - 1;
-        if (!wait(accfull + (c & 1), (c >> 1) & 1)) ok = false;
-        tc_fence_after();
-        if (ok) epilogue(c);
-        tc_fence_before();
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(accempty + (c & 1))) : "memory");
-      }
-    }
-    if (ok && n_items > 0) {
-      const int c = n_items / nk - 1;
-      if (wait(accfull + (c & 1), (c >> 1) & 1)) {
-        tc_fence_after();
-        epilogue(c);
-      }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
-  } else if (lane == 0) {
+  } else if (warp < 4) {
+    // ----------------------------------------------------------- epilogue
+    const int m = warp * 32 + lane;  // TMEM lane = accumulator row
+    for (int c = 0; c < my_bricks; ++c) {
+      if (!wait(accfull + (c & 1), (c >> 1) & 1)) break;
+      tc_fence_after();
+      const int bi = blockIdx.x + c * gridDim.x;
+      const int sample = bi / nbps, brick = bi % nbps;
+      const int bx = brick % nbx, by = (brick / nbx) % nby, bz = brick / (nbx * nby);
+      const uint32_t set = tbase + (c & 1) * G::kAccCols + ((uint32_t)(warp * 32) << 16);
+      const int y = by * 16 + (m >> 3), x = bx * 8 + (m & 7);
+      // the ZB accumulators are ZB * N consecutive columns; 32 per wait
+      const uint32_t acc0 = set + (STACK ? 2 * N : 0);
+      const int64_t vbase = (int64_t)sample * D * D * D + (int64_t)y * D + x;
+#pragma unroll 1
+      for (int col0 = 0; col0 < ZB * N; col0 += 32) {
+        const int ng = (ZB * N - col0) >= 32 ? 2 : 1;  // 16-column groups in this chunk
+        float v[32];
+        tmem_ld16_nowait(acc0 + col0, v);
+        if (ng == 2) tmem_ld16_nowait(acc0 + col0 + 16, v + 16);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+          if (g >= ng) break;
+          const int col = col0 + 16 * g, zz = col / N, c0 = col % N;
+          __nv_bfloat16 *dst = out + (vbase + (int64_t)(bz * ZB + zz) * D * D) * N + c0;
+          __align__(16) __nv_bfloat162 o[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            float a = v[16 * g + 2 * q], b2 = v[16 * g + 2 * q + 1];
+            if (FWD) {
+              a = fmaxf(a + __ldg(bias + c0 + 2 * q), 0.f);
+              b2 = fmaxf(b2 + __ldg(bias + c0 + 2 * q + 1), 0.f);
+            }
+            o[q] = __floats2bfloat162_rn(a, b2);
+          }
+          reinterpret_cast<uint4 *>(dst)[0] = reinterpret_cast<const uint4 *>(o)[0];
+          reinterpret_cast<uint4 *>(dst)[1] = reinterpret_cast<const uint4 *>(o)[1];
+        }
+      }
+      if (STACK) {
+        // zero the whole set (scratch slices included) for its next brick
+        for (int c0 = 0; c0 < G::kAccCols; c0 += 16) tmem_st16_zero(set + c0);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      }
+      tc_fence_before();
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(accempty + (c & 1))) : "memory");
+    }
+  } else if (warp == 8 && lane == 0) {
     // ------------------------------------------------------------ MMA issue
     constexpr uint32_t kIdesc = idesc_bf16(128, STACK ? 3 * N : N);
     for (int j = 0; j < n_items; ++j) {
@@ -411,7 +421,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __nv_bfloat16
   tc_fence_before();
   __syncthreads();
   if (*abort_flag && tid == 0) atomicExch(err, (int)CMG_ERR_TIMEOUT);
-  if (warp == 4) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(G::kCols));
+  if (warp == 8) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(G::kCols));
 }
 
 // Weight images for k_conv_tc from src [N][27][K] (bf16):
