@@ -139,81 +139,91 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const bf16 *__restrict__ 
 }
 
 // dW[co][t][ci] += sum_v dout[v][co] * in[v + d_t][ci] over the bricks of
-// this block (grid.y = tap).  Warps split (co blocks of 16) x (ci tiles).
-template <int NTI>
-__global__ void __launch_bounds__(kConvThreads) k_conv_wgrad(const bf16 *__restrict__ dout, int Cout,
-                                                            const bf16 *__restrict__ in, float *__restrict__ dW,
-                                                            int D, int nbricks, int bricks_per_block) {
+// this block, for the TG taps t0 = TG blockIdx.y ... t0 + TG - 1: each
+// brick's 6x6x6 halo and output gradient are staged once and serve all TG
+// taps.  A tile is (tap, 16 output channels, 16 input channels): two
+// m16n8k16 accumulators; tiles go round-robin to the 8 warps.
+constexpr int kWgThreads = 256;
+
+template <int CIN, int COUT, int TG>
+__global__ void __launch_bounds__(kWgThreads) k_conv_wgrad(const bf16 *__restrict__ dout, const bf16 *__restrict__ in,
+                                                          float *__restrict__ dW, int D, int nbricks,
+                                                          int bricks_per_block) {
+  constexpr int NMB = COUT / 16, NJP = CIN / 16, TILES = TG * NMB * NJP, MAXT = (TILES + 7) / 8;
   extern __shared__ __align__(16) uint8_t smem[];
-  constexpr int Cin = NTI * 8;
-  bf16 *halo = reinterpret_cast<bf16 *>(smem);  // [216][Cin]
-  bf16 *dt = halo + 216 * Cin;                  // [64][Cout]
-  const int t = blockIdx.y;
-  const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+  bf16 *halo = reinterpret_cast<bf16 *>(smem);  // [216][CIN]
+  bf16 *dt = halo + 216 * CIN;                  // [64][COUT]
+  const int t0 = blockIdx.y * TG;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nmb = Cout / 16;                 // co blocks
-  const int wsplit = 4 / nmb;                // warps per co block (1, 2 or 4)
-  const int mb = warp % nmb, part = warp / nmb;
-  // this warp owns the ci tile pairs jp with jp % wsplit == part
-  float acc[NTI][4];
+  float acc[MAXT][2][4];
 #pragma unroll
-  for (int j = 0; j < NTI; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+  for (int i = 0; i < MAXT; ++i)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) acc[i][h][0] = acc[i][h][1] = acc[i][h][2] = acc[i][h][3] = 0.f;
   const int D4 = D >> 2, per = D4 * D4 * D4;
   const int b_first = blockIdx.x * bricks_per_block;
   for (int bi = b_first; bi < b_first + bricks_per_block && bi < nbricks; ++bi) {
     const int s = bi / per, brick = bi % per;
     const int bx = brick % D4, by = (brick / D4) % D4, bz = brick / (D4 * D4);
     const int64_t sbase = (int64_t)s * D * D * D;
-    const int cin16 = Cin / 8;  // 16-byte pieces per halo row
-    for (int p = threadIdx.x; p < 216 * cin16; p += kConvThreads) {
-      const int row = p / cin16, piece = p % cin16;
+    for (int p = threadIdx.x; p < 216 * (CIN / 8); p += kWgThreads) {
+      const int row = p / (CIN / 8), piece = p % (CIN / 8);
       const int hz = row / 36, hy = (row / 6) % 6, hx = row % 6;
       const int64_t g = halo_row(sbase, D, bz, by, bx, hz, hy, hx);
-      *reinterpret_cast<uint4 *>(halo + row * Cin + piece * 8) =
-          *reinterpret_cast<const uint4 *>(in + g * Cin + piece * 8);
+      *reinterpret_cast<uint4 *>(halo + row * CIN + piece * 8) =
+          *reinterpret_cast<const uint4 *>(in + g * CIN + piece * 8);
     }
-    const int co16 = Cout / 8;
-    for (int p = threadIdx.x; p < 64 * co16; p += kConvThreads) {
-      const int vi = p / co16, piece = p % co16;
-      const int64_t v =
-          sbase + ((int64_t)(bz * 4 + vi / 16) * D + by * 4 + (vi / 4) % 4) * D + bx * 4 + vi % 4;
-      *reinterpret_cast<uint4 *>(dt + vi * Cout + piece * 8) =
-          *reinterpret_cast<const uint4 *>(dout + v * Cout + piece * 8);
+    for (int p = threadIdx.x; p < 64 * (COUT / 8); p += kWgThreads) {
+      const int vi = p / (COUT / 8), piece = p % (COUT / 8);
+      const int64_t v = sbase + ((int64_t)(bz * 4 + vi / 16) * D + by * 4 + (vi / 4) % 4) * D + bx * 4 + vi % 4;
+      *reinterpret_cast<uint4 *>(dt + vi * COUT + piece * 8) =
+          *reinterpret_cast<const uint4 *>(dout + v * COUT + piece * 8);
     }
     __syncthreads();
 #pragma unroll
-    for (int k16 = 0; k16 < 4; ++k16) {
-      // A = dout^T (co x voxel) from dt [voxel][co] via ldmatrix.trans
-      const int av = k16 * 16 + (lane & 7) + ((lane >> 4) & 1) * 8;
-      const int aco = mb * 16 + ((lane >> 3) & 1) * 8;
-      uint32_t a0, a1, a2, a3;
-      ldsm_x4_t(smem_u32(dt + av * Cout + aco), a0, a1, a2, a3);
-      // B = in shifted by the tap (voxel x ci) from halo rows via ldmatrix.trans
-      const int bv = k16 * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;
-      const int hrow = ((bv / 16 + dz + 1) * 6 + ((bv / 4) % 4 + dy + 1)) * 6 + (bv % 4 + dx + 1);
+    for (int i = 0; i < MAXT; ++i) {
+      const int tile = warp + 8 * i;
+      if (tile < TILES) {
+        const int tl = tile / (NMB * NJP), r = tile % (NMB * NJP), mb = r / NJP, jp = r % NJP;
+        const int t = t0 + tl;
+        const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
 #pragma unroll
-      for (int jj = 0; jj < NTI; jj += 2) {
-        if (((jj >> 1) % wsplit) != part) continue;
-        const int ci = jj * 8 + ((lane >> 4) & 1) * 8;
-        uint32_t b0, b1, b2, b3;
-        ldsm_x4_t(smem_u32(halo + hrow * Cin + ci), b0, b1, b2, b3);
-        mma16816(acc[jj], a0, a1, a2, a3, b0, b1);
-        mma16816(acc[jj + 1], a0, a1, a2, a3, b2, b3);
+        for (int k16 = 0; k16 < 4; ++k16) {
+          // A = dout^T (co x voxel) from dt [voxel][co] via ldmatrix.trans
+          const int av = k16 * 16 + (lane & 7) + ((lane >> 4) & 1) * 8;
+          const int aco = mb * 16 + ((lane >> 3) & 1) * 8;
+          uint32_t a0, a1, a2, a3;
+          ldsm_x4_t(smem_u32(dt + av * COUT + aco), a0, a1, a2, a3);
+          // B = in shifted by the tap (voxel x ci) from halo rows via ldmatrix.trans
+          const int bv = k16 * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;
+          const int hrow = ((bv / 16 + dz + 1) * 6 + ((bv / 4) % 4 + dy + 1)) * 6 + (bv % 4 + dx + 1);
+          const int ci = jp * 16 + ((lane >> 4) & 1) * 8;
+          uint32_t b0, b1, b2, b3;
+          ldsm_x4_t(smem_u32(halo + hrow * CIN + ci), b0, b1, b2, b3);
+          mma16816(acc[i][0], a0, a1, a2, a3, b0, b1);
+          mma16816(acc[i][1], a0, a1, a2, a3, b2, b3);
+        }
       }
     }
     __syncthreads();
   }
   const int g = lane >> 2, q = lane & 3;
 #pragma unroll
-  for (int jj = 0; jj < NTI; ++jj) {
-    if (((jj >> 1) % wsplit) != part) continue;
-    const int ci = jj * 8 + q * 2;
+  for (int i = 0; i < MAXT; ++i) {
+    const int tile = warp + 8 * i;
+    if (tile >= TILES) continue;
+    const int tl = tile / (NMB * NJP), r = tile % (NMB * NJP), mb = r / NJP, jp = r % NJP;
+    const int t = t0 + tl;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int co = mb * 16 + g + h * 8;
-      float *dst = dW + ((int64_t)co * 27 + t) * Cin + ci;
-      atomicAdd(dst, acc[jj][2 * h]);
-      atomicAdd(dst + 1, acc[jj][2 * h + 1]);
+      const int ci = (2 * jp + h) * 8 + q * 2;
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int co = mb * 16 + g + hh * 8;
+        float *dst = dW + ((int64_t)co * 27 + t) * CIN + ci;
+        atomicAdd(dst, acc[i][h][2 * hh]);
+        atomicAdd(dst + 1, acc[i][h][2 * hh + 1]);
+      }
     }
   }
 }
@@ -606,32 +616,42 @@ void conv(cmg_unet *U, int l, const bf16 *in, int K, const float *bias, bf16 *ou
 #undef CMG_CONV
 }
 
-template <int NTI>
-void wgrad_launch(cmg_unet *U, const bf16 *dout, int Cout, const bf16 *in, float *dW, int D, int B) {
-  const size_t smem = ((size_t)216 * NTI * 8 + 64 * (size_t)Cout) * sizeof(bf16);
-  static bool attr = false;
-  if (!attr) {
-    CMG_CUDA(cudaFuncSetAttribute(k_conv_wgrad<NTI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-    attr = true;
+template <int CIN, int COUT, int TG>
+void wgrad_launch(cmg_unet *U, const bf16 *dout, const bf16 *in, float *dW, int D, int B) {
+  const size_t smem = ((size_t)216 * CIN + 64 * (size_t)COUT) * sizeof(bf16);
+  static int attr_dev = -1;
+  if (attr_dev != U->ctx->device) {
+    CMG_CUDA(cudaFuncSetAttribute(k_conv_wgrad<CIN, COUT, TG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+    attr_dev = U->ctx->device;
   }
   const int nbricks = B * (D / 4) * (D / 4) * (D / 4);
-  const int per_block = std::max(1, std::min(32, nbricks / 64));
+  const int gy = 27 / TG;
+  const int bx = std::max(1, std::min(nbricks, 4 * U->ctx->num_sms / gy));
+  const int per_block = (nbricks + bx - 1) / bx;
   const int blocks = (nbricks + per_block - 1) / per_block;
-  LaunchScope ls(U->ctx, K_CONV_WGRAD, 0.0, 2.0 * 27 * Cout * NTI * 8 * (double)D * D * D * B);
-  k_conv_wgrad<NTI><<<dim3(blocks, 27), kConvThreads, smem, U->ctx->stream>>>(dout, Cout, in, dW, D, nbricks,
-                                                                               per_block);
+  LaunchScope ls(U->ctx, K_CONV_WGRAD, 0.0, 2.0 * 27 * COUT * CIN * (double)D * D * D * B);
+  k_conv_wgrad<CIN, COUT, TG><<<dim3(blocks, gy), kWgThreads, smem, U->ctx->stream>>>(dout, in, dW, D, nbricks,
+                                                                                     per_block);
   CMG_CUDA(cudaGetLastError());
 }
 
+// Taps per block: as many (27, 9 or 3) as keep the accumulators of a warp
+// within 12 tiles (96 registers).
 void wgrad(cmg_unet *U, const bf16 *dout, int Cout, const bf16 *in, int Cin, float *dW, int D, int B) {
-  switch (Cin / 8) {
-    case 2: wgrad_launch<2>(U, dout, Cout, in, dW, D, B); break;
-    case 4: wgrad_launch<4>(U, dout, Cout, in, dW, D, B); break;
-    case 6: wgrad_launch<6>(U, dout, Cout, in, dW, D, B); break;
-    case 8: wgrad_launch<8>(U, dout, Cout, in, dW, D, B); break;
-    case 12: wgrad_launch<12>(U, dout, Cout, in, dW, D, B); break;
-    default: throw Error(CMG_ERR_INVALID_ARG, "unsupported channel count");
+#define CMG_WG(CI, CO, TG)                                      \
+  if (Cin == CI && Cout == CO) {                                \
+    wgrad_launch<CI, CO, TG>(U, dout, in, dW, D, B);            \
+    return;                                                     \
   }
+  CMG_WG(16, 16, 27)
+  CMG_WG(16, 32, 27)
+  CMG_WG(32, 32, 9)
+  CMG_WG(32, 64, 9)
+  CMG_WG(64, 64, 3)
+  CMG_WG(96, 32, 3)
+  CMG_WG(48, 16, 27)
+#undef CMG_WG
+  throw Error(CMG_ERR_INVALID_ARG, "unsupported channel count");
 }
 
 // After a synchronisation: a bounded wait that expired in a tcgen05
