@@ -430,7 +430,8 @@ def bench_learned(cmg, ctx, dev, args, peaks):
     res["roofline_conv_fwd"] = {"bound": "tensor", "achieved": tf, "peak": peaks["bf16"], "unit": "TFLOP/s",
                                 "frac": tf / peaks["bf16"], "peak_source": peaks["bf16_src"],
                                 "launches": conv["launches"], "ms": conv["ms"],
-                                "flops_per_block": conv["flops"] / (5 * 8)}
+                                "flops_per_block": conv["flops"] / (5 * 8),
+                                "traffic": traffic_for("conv_fwd_b8"), "traffic_unit": "DRAM bytes per launch"}
     f, m = res["fp64"], res["mixed"]
     ws = res["ms_warm_start_per_block_b8"]
     res["summary"] = {
