@@ -49,7 +49,11 @@ typedef enum { CMG_MEM_HOST = 0, CMG_MEM_DEVICE = 1 } cmg_mem;
 
 typedef enum {
   CMG_PREC_FP64 = 0,  /* every step in FP64 */
-  CMG_PREC_MIXED = 1  /* FP32 V-cycle inside FP64 iterative refinement */
+  CMG_PREC_MIXED = 1, /* FP32 V-cycle inside FP64 iterative refinement */
+  CMG_PREC_FFT = 2    /* FP32 FFT direct solve inside FP64 iterative refinement:
+                         full periodic levels of 4^3 .. 512^3 cells only (the
+                         paper's FFT base-level solve, Sec. 5.2); n_pre, n_post,
+                         coarse_sweeps and inner_cycles are ignored */
 } cmg_precision;
 
 typedef struct cmg_ctx cmg_ctx;

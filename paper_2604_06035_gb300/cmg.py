@@ -31,6 +31,7 @@ CMG_MEM_HOST = 0
 CMG_MEM_DEVICE = 1
 CMG_PREC_FP64 = 0
 CMG_PREC_MIXED = 1
+CMG_PREC_FFT = 2
 CMG_FIELD_PHI = 0
 CMG_FIELD_F = 1
 CMG_OP_SWEEP, CMG_OP_RESIDUAL, CMG_OP_RESTRICT, CMG_OP_PROLONG, CMG_OP_COARSE, CMG_OP_GHOSTS = range(6)

@@ -199,7 +199,7 @@ struct DeviceBuffers {
 namespace cmg {
 enum KernelClass {
   K_SWEEP64 = 0, K_SWEEP32, K_RESID64, K_RESID32, K_PROLONG64, K_PROLONG32, K_GHOST, K_COARSE, K_REDUCE,
-  K_CONVERT, K_CONV_FWD, K_CONV_DGRAD, K_CONV_WGRAD, K_NCLASS
+  K_CONVERT, K_CONV_FWD, K_CONV_DGRAD, K_CONV_WGRAD, K_FFT, K_NCLASS
 };
 struct ProfClass {
   int64_t launches = 0;
@@ -269,6 +269,11 @@ struct cmg_level {
   // in one cluster "tail" launch; 0 = one launch per operation everywhere
   int64_t tail_octs_fp64 = 0;
   int64_t tail_octs_fp32 = 0;
+  // FFT solve of a full periodic level (fft.cu): dense complex work array,
+  // oct-coordinate -> oct-index map, twiddles (lazy)
+  float2 *fft_buf = nullptr;
+  int32_t *fft_map = nullptr;
+  float2 *fft_tw = nullptr;
   cmg::DeviceBuffers mem;
 };
 
@@ -346,6 +351,10 @@ void unpack_field(cmg_level *L, int m, int field, int prec, void *out);
 void fill_ghosts(cmg_level *L);
 void get_ghosts(cmg_level *L, double *out);
 void ensure_fp32(cmg_level *L);
+// fft.cu
+bool fft_supported(const cmg_level *L);
+void fft_prepare(cmg_level *L);
+void fft_solve32(cmg_level *L);
 template <typename T>
 void sweep(cmg_level *L, int m, bool zero_init);
 template <typename T>

@@ -1,0 +1,243 @@
+// fft.cu -- direct FP32 FFT solve of the correction equation on a full
+// periodic level (the paper's FFT base-level solve, Sec. 5.2, here inside the
+// FP64 iterative refinement of the mixed-precision path).
+//
+// On a full periodic level the 7-point operator is diagonalised by the 3-D
+// DFT.  The FP32 inner problem of the refinement loop is the smoother's fixed
+// point e = (sum of the 6 neighbours) / 6 + g, i.e.
+//   sum_nb e - 6 e = -6 g,
+// whose symbol is -4 (sin^2(pi kx/n) + sin^2(pi ky/n) + sin^2(pi kz/n)), so
+//   e^(k) = 1.5 g^(k) / (sin^2 + sin^2 + sin^2),  e^(0) = 0 (zero mean).
+// Five passes over a dense complex FP32 array [z][y][x]: x forward (gathering
+// g from the colour-planar oct layout through an oct map), y forward, z
+// forward + scaling + z inverse (one kernel, the line stays in shared
+// memory), y inverse, x inverse (scattering e into the oct layout).  Each
+// pass runs batched radix-2 FFTs of whole lines in shared memory: forward
+// transforms decimate in time from a bit-reversed load, inverse ones
+// decimate in frequency to a bit-reversed store, so no pass reorders
+// separately.  Twiddles exp(-2 pi i k / n) come from an FP64 table rounded to
+// FP32.  Each refinement step gains ~6 digits (FP32 transform error), so the
+// FP64 loop reaches 1e-10 in two or three steps.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "cmg_internal.cuh"
+
+namespace cmg {
+namespace {
+
+constexpr int kFftThreads = 256;
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ int brev(int i, int logn) { return (int)(__brev((unsigned)i) >> (32 - logn)); }
+
+// In-place radix-2 transforms of `lines` lines of length n in shared memory
+// (line l at s + l ld).  DIT (forward, input bit-reversed, output natural)
+// with twiddles w^k; DIF (inverse, input natural, output bit-reversed) with
+// conj(w)^k.
+__device__ void fft_dit(float2 *s, int n, int ld, int lines, const float2 *tw) {
+  const int nb = lines * (n >> 1);
+  for (int len = 2; len <= n; len <<= 1) {
+    const int half = len >> 1, ts = n / len;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+      const int line = b / (n >> 1), bb = b % (n >> 1);
+      const int pos = bb % half, i = (bb / half) * len + pos, j = i + half;
+      float2 *x = s + line * ld;
+      const float2 a = x[i], c = cmul(x[j], tw[pos * ts]);
+      x[i] = make_float2(a.x + c.x, a.y + c.y);
+      x[j] = make_float2(a.x - c.x, a.y - c.y);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ void fft_dif_inv(float2 *s, int n, int ld, int lines, const float2 *tw) {
+  const int nb = lines * (n >> 1);
+  for (int len = n; len >= 2; len >>= 1) {
+    const int half = len >> 1, ts = n / len;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+      const int line = b / (n >> 1), bb = b % (n >> 1);
+      const int pos = bb % half, i = (bb / half) * len + pos, j = i + half;
+      float2 *x = s + line * ld;
+      const float2 a = x[i], c = x[j];
+      float2 w = tw[pos * ts];
+      w.y = -w.y;
+      x[i] = make_float2(a.x + c.x, a.y + c.y);
+      x[j] = cmul(make_float2(a.x - c.x, a.y - c.y), w);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ void load_tw(float2 *stw, const float2 *tw, int n) {
+  for (int k = threadIdx.x; k < (n >> 1); k += blockDim.x) stw[k] = tw[k];
+}
+
+// cell (x, y, z) of the level -> (oct, plane, slot) through the oct map
+__device__ __forceinline__ int64_t cell_index(const int32_t *map, int no, int x, int y, int z, int64_t plane_stride) {
+  const int o = map[((int64_t)(z >> 1) * no + (y >> 1)) * no + (x >> 1)];
+  const int c = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
+  return (int64_t)cell_parity(c) * plane_stride + (int64_t)o * 4 + (c >> 1);
+}
+
+// x forward: lines (y, z), `lines` per block; input g (plane stride ps)
+__global__ void k_fft_x_fwd(const float *__restrict__ g, int64_t ps, const int32_t *__restrict__ map,
+                            const float2 *__restrict__ tw, int n, int logn, int lines, float2 *__restrict__ buf) {
+  extern __shared__ float2 sm[];
+  float2 *stw = sm, *s = sm + (n >> 1);
+  load_tw(stw, tw, n);
+  const int line0 = blockIdx.x * lines, no = n >> 1;
+  for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
+    const int l = e / n, x = e % n, yz = line0 + l;
+    const int y = yz % n, z = yz / n;
+    s[l * n + brev(x, logn)] = make_float2(g[cell_index(map, no, x, y, z, ps)], 0.f);
+  }
+  __syncthreads();
+  fft_dit(s, n, n, lines, stw);
+  for (int e = threadIdx.x; e < lines * n; e += blockDim.x) buf[(int64_t)line0 * n + e] = s[e];
+}
+
+// y or z pass on tiles of `tx` consecutive x columns: AXIS 1 = y (block =
+// (z, x tile)), AXIS 2 = z (block = (y, x tile)).  MODE 0: forward;
+// 1: inverse; 2 (z only): forward, scale by the inverse symbol, inverse.
+// The tile's lines are n + 1 apart in shared memory (the load writes one
+// element of each line per thread: no bank conflicts).
+template <int AXIS, int MODE>
+__global__ void k_fft_yz(float2 *__restrict__ buf, const float2 *__restrict__ tw, int n, int logn, int tx) {
+  extern __shared__ float2 sm[];
+  float2 *stw = sm, *s = sm + (n >> 1);
+  load_tw(stw, tw, n);
+  const int ntile = n / tx;
+  const int x0 = (blockIdx.x % ntile) * tx, other = blockIdx.x / ntile;  // z (AXIS 1) or y (AXIS 2)
+  const int64_t nn = (int64_t)n * n;
+  const int ld = n + 1;
+  auto addr = [&](int a, int t) -> int64_t {  // element a along the axis, column x0 + t
+    return AXIS == 1 ? ((int64_t)other * nn + (int64_t)a * n + x0 + t) : ((int64_t)a * nn + (int64_t)other * n + x0 + t);
+  };
+  for (int e = threadIdx.x; e < tx * n; e += blockDim.x) {
+    const int a = e / tx, t = e % tx;  // consecutive threads read consecutive x
+    const float2 v = buf[addr(a, t)];
+    s[t * ld + (MODE == 1 ? a : brev(a, logn))] = v;
+  }
+  __syncthreads();
+  if (MODE == 1) {
+    fft_dif_inv(s, n, ld, tx, stw);
+  } else {
+    fft_dit(s, n, ld, tx, stw);
+    if (MODE == 2) {
+      // natural-order spectrum along z; x and y are already frequencies
+      const float sy = sinpif((float)other / (float)n);
+      for (int e = threadIdx.x; e < tx * n; e += blockDim.x) {
+        const int t = e / n, kz = e % n;
+        const float sx = sinpif((float)(x0 + t) / (float)n), sz = sinpif((float)kz / (float)n);
+        const float d = sx * sx + sy * sy + sz * sz;
+        const float f = d > 0.f ? 1.5f / d : 0.f;
+        float2 &v = s[t * ld + kz];
+        v = make_float2(v.x * f, v.y * f);
+      }
+      __syncthreads();
+      fft_dif_inv(s, n, ld, tx, stw);
+    }
+  }
+  for (int e = threadIdx.x; e < tx * n; e += blockDim.x) {
+    const int a = e / tx, t = e % tx;
+    buf[addr(a, t)] = s[t * ld + (MODE == 0 ? a : brev(a, logn))];
+  }
+}
+
+// x inverse and scatter: e = Re / n^3 into the colour-planar FP32 field
+__global__ void k_fft_x_inv(const float2 *__restrict__ buf, const int32_t *__restrict__ map,
+                            const float2 *__restrict__ tw, int n, int logn, int lines, float inv_n3,
+                            float *__restrict__ e_out, int64_t ps) {
+  extern __shared__ float2 sm[];
+  float2 *stw = sm, *s = sm + (n >> 1);
+  load_tw(stw, tw, n);
+  const int line0 = blockIdx.x * lines, no = n >> 1;
+  for (int e = threadIdx.x; e < lines * n; e += blockDim.x) s[e] = buf[(int64_t)line0 * n + e];
+  __syncthreads();
+  fft_dif_inv(s, n, n, lines, stw);
+  for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
+    const int l = e / n, x = e % n, yz = line0 + l;
+    const int y = yz % n, z = yz / n;
+    e_out[cell_index(map, no, x, y, z, ps)] = s[l * n + brev(x, logn)].x * inv_n3;
+  }
+}
+
+__global__ void k_fft_map(const uint64_t *__restrict__ keys, int64_t n_octs, int no, int32_t *__restrict__ map) {
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_octs; o += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t i, j, k;
+    morton_decode(keys[o], i, j, k);
+    map[((int64_t)k * no + j) * no + i] = (int32_t)o;
+  }
+}
+
+}  // namespace
+
+bool fft_supported(const cmg_level *L) { return L->periodic_full && L->lev >= 2 && L->lev <= 9; }
+
+void fft_prepare(cmg_level *L) {
+  if (L->fft_buf) return;
+  if (!fft_supported(L)) throw Error(CMG_ERR_INVALID_ARG, "the FFT solve needs a full periodic level of at most 512^3 cells");
+  const int n = 1 << L->lev, no = n >> 1;
+  cudaStream_t s = L->ctx->stream;
+  L->fft_buf = reinterpret_cast<float2 *>(L->mem.alloc<float>((int64_t)2 * n * n * n));
+  L->fft_map = L->mem.alloc<int32_t>((int64_t)no * no * no);
+  L->fft_tw = reinterpret_cast<float2 *>(L->mem.alloc<float>(n));
+  std::vector<float> tw(n);
+  for (int k = 0; k < n / 2; ++k) {
+    const double a = -2.0 * M_PI * (double)k / (double)n;
+    tw[2 * k] = (float)std::cos(a);
+    tw[2 * k + 1] = (float)std::sin(a);
+  }
+  CMG_CUDA(cudaMemcpyAsync(L->fft_tw, tw.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s));
+  const MgLev &g = L->mg[0];
+  k_fft_map<<<blocks_for(g.n), kThreads, 0, s>>>(g.keys, g.n, no, L->fft_map);
+  CMG_CUDA(cudaGetLastError());
+  CMG_CUDA(cudaStreamSynchronize(s));
+}
+
+// e (phi32 of MG level 0) = the FFT solution of the FP32 correction equation
+// whose right-hand side is g32 of MG level 0.
+void fft_solve32(cmg_level *L) {
+  const MgLev &g = L->mg[0];
+  const int n = 1 << L->lev, logn = L->lev;
+  cudaStream_t s = L->ctx->stream;
+  const int lines = std::max(1, std::min(2048 / n, n * n));  // x passes: <= 16 KB of lines per block
+  const int tx = std::min(n >= 512 ? 8 : 16, n);             // y / z passes: columns per block
+  const size_t smx = sizeof(float2) * ((size_t)(n / 2) + (size_t)lines * n);
+  const size_t smyz = sizeof(float2) * ((size_t)(n / 2) + (size_t)tx * (n + 1));
+  const int64_t lines_total = (int64_t)n * n;
+  const unsigned bx = (unsigned)(lines_total / lines), byz = (unsigned)((int64_t)n * (n / tx));
+  // algorithmic work per pass: one read and one write of the dense complex
+  // array (x passes: one FP32 field value per cell instead), 5 n log2 n flops
+  // per line transform
+  const double cells = (double)n * n * n, line_flops = 5.0 * cells * logn;
+  {
+    LaunchScope ls(L->ctx, K_FFT, cells * (4.0 + 4.0 + 8.0), line_flops);
+    k_fft_x_fwd<<<bx, kFftThreads, smx, s>>>(g.g32, g.n * 4, L->fft_map, L->fft_tw, n, logn, lines, L->fft_buf);
+  }
+  {
+    LaunchScope ls(L->ctx, K_FFT, cells * 16.0, line_flops);
+    k_fft_yz<1, 0><<<byz, kFftThreads, smyz, s>>>(L->fft_buf, L->fft_tw, n, logn, tx);
+  }
+  {
+    LaunchScope ls(L->ctx, K_FFT, cells * 16.0, 2.0 * line_flops + 6.0 * cells);
+    k_fft_yz<2, 2><<<byz, kFftThreads, smyz, s>>>(L->fft_buf, L->fft_tw, n, logn, tx);
+  }
+  {
+    LaunchScope ls(L->ctx, K_FFT, cells * 16.0, line_flops);
+    k_fft_yz<1, 1><<<byz, kFftThreads, smyz, s>>>(L->fft_buf, L->fft_tw, n, logn, tx);
+  }
+  {
+    LaunchScope ls(L->ctx, K_FFT, cells * (8.0 + 4.0 + 4.0), line_flops);
+    k_fft_x_inv<<<bx, kFftThreads, smx, s>>>(L->fft_buf, L->fft_map, L->fft_tw, n, logn, lines,
+                                             1.0f / ((float)n * n * n), g.phi32, g.n_alloc * 4);
+  }
+  CMG_CUDA(cudaGetLastError());
+}
+
+}  // namespace cmg

@@ -11,7 +11,7 @@ constexpr int kPoolPairs = 4096;
 const char *kNames[K_NCLASS] = {"rbgs_fp64",    "rbgs_fp32",    "residual_fp64", "residual_fp32",
                                 "prolong_fp64", "prolong_fp32", "ghost_fill",    "coarse_solve",
                                 "reduce",       "convert",      "conv_fwd",      "conv_dgrad",
-                                "conv_wgrad"};
+                                "conv_wgrad",   "fft_fp32"};
 }  // namespace
 
 const char *kernel_class_name(int cls) { return cls >= 0 && cls < K_NCLASS ? kNames[cls] : "?"; }

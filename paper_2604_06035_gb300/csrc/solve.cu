@@ -157,7 +157,7 @@ void segment_pre(cmg_level *L, const cmg_solve_params *p, cudaGraphConditionalHa
   double *scal = L->scal;
   fill_ghosts(L);
   zero_phi_norm(L, scal + 0);
-  if (p->precision == CMG_PREC_MIXED) {
+  if (p->precision != CMG_PREC_FP64) {
     LaunchScope ls(L->ctx, K_REDUCE, 16.0, 0.0);
     k_copy_scalar<<<1, 1, 0, s>>>(scal + 4, scal + 1);
     CMG_CUDA(cudaGetLastError());
@@ -170,8 +170,9 @@ void segment_pre(cmg_level *L, const cmg_solve_params *p, cudaGraphConditionalHa
   CMG_CUDA(cudaGetLastError());
 }
 
-// One iteration: a V-cycle (FP64) or an FP32 V-cycle + FP64 accumulation
-// (mixed), then the FP64 residual norm and the check.
+// One iteration: a V-cycle (FP64), or an FP32 V-cycle (mixed) or FP32 FFT
+// solve (fft) of the scaled correction equation + FP64 accumulation, then
+// the FP64 residual norm and the check.
 void segment_body(cmg_level *L, const cmg_solve_params *p, cudaGraphConditionalHandle h, int use_handle,
                   int64_t *updates) {
   cudaStream_t s = L->ctx->stream;
@@ -181,11 +182,15 @@ void segment_body(cmg_level *L, const cmg_solve_params *p, cudaGraphConditionalH
     resid_restrict<double>(L, 0, false, true, false, scal + 2);
   } else {
     MgLev &g = L->mg[0];
-    if (p->n_pre == 0) {
-      CMG_CUDA(cudaMemsetAsync(g.phi32, 0, sizeof(float) * 4 * g.n, s));
-      CMG_CUDA(cudaMemsetAsync(g.phi32 + 4 * g.n_alloc, 0, sizeof(float) * 4 * g.n, s));
+    if (p->precision == CMG_PREC_FFT) {
+      fft_solve32(L);
+    } else {
+      if (p->n_pre == 0) {
+        CMG_CUDA(cudaMemsetAsync(g.phi32, 0, sizeof(float) * 4 * g.n, s));
+        CMG_CUDA(cudaMemsetAsync(g.phi32 + 4 * g.n_alloc, 0, sizeof(float) * 4 * g.n, s));
+      }
+      for (int k = 0; k < p->inner_cycles; ++k) vcycle<float>(L, 0, p, k == 0, updates);
     }
-    for (int k = 0; k < p->inner_cycles; ++k) vcycle<float>(L, 0, p, k == 0, updates);
     accumulate(L, scal + 4);
     {
       LaunchScope ls(L->ctx, K_REDUCE, 16.0, 0.0);
@@ -320,18 +325,21 @@ void destroy_graphs(cmg_level *L) {
 int solve(cmg_level *L, const cmg_solve_params *p, cmg_solve_stats *st) {
   if (!p || p->n_pre < 0 || p->n_post < 0 || p->coarse_sweeps < 0 || p->max_cycles < 0 || p->max_cycles > 256 ||
       p->fixed_cycles < 0 || p->fixed_cycles > 256 || !(p->tol >= 0.0) ||
-      (p->precision != CMG_PREC_FP64 && p->precision != CMG_PREC_MIXED) ||
+      (p->precision != CMG_PREC_FP64 && p->precision != CMG_PREC_MIXED && p->precision != CMG_PREC_FFT) ||
       (p->precision == CMG_PREC_MIXED && p->inner_cycles < 1))
     throw Error(CMG_ERR_INVALID_ARG, "invalid solve parameters");
   if (L->periodic_full && L->nx != 1)
     throw Error(CMG_ERR_INVALID_ARG, "periodic base levels need n_x = 1 (exact 2^3 coarsest solve)");
   if (p->precision == CMG_PREC_MIXED && L->mg.size() < 2)
     throw Error(CMG_ERR_INVALID_ARG, "mixed precision needs at least two multigrid levels");
+  if (p->precision == CMG_PREC_FFT && !fft_supported(L))
+    throw Error(CMG_ERR_INVALID_ARG, "the FFT solve needs a full periodic level of 4^3 .. 512^3 cells");
   cmg_solve_stats local;
   cmg_solve_stats &S = st ? *st : local;
   S = cmg_solve_stats{};
   cmg_ctx *ctx = L->ctx;
-  if (p->precision == CMG_PREC_MIXED) ensure_fp32(L);
+  if (p->precision != CMG_PREC_FP64) ensure_fp32(L);
+  if (p->precision == CMG_PREC_FFT) fft_prepare(L);
   if (!L->ctrl) {
     L->ctrl = L->mem.alloc<uint8_t>(sizeof(SolveCtrl), true, ctx->stream);
     CMG_CUDA(cudaMallocHost(&L->h_ctrl, sizeof(SolveCtrl)));
