@@ -185,7 +185,7 @@ void fft_prepare(cmg_level *L) {
   const int n = 1 << L->lev, no = n >> 1;
   cudaStream_t s = L->ctx->stream;
   L->fft_buf = reinterpret_cast<float2 *>(L->mem.alloc<float>((int64_t)2 * n * n * n));
-  L->fft_map = L->mem.alloc<int32_t>((int64_t)no * no * no);
+  L->fft_map = L->mem.alloc<int32_t>((int64_t)no * no * no, true, s);  // zeroed: every entry a valid oct
   L->fft_tw = reinterpret_cast<float2 *>(L->mem.alloc<float>(n));
   std::vector<float> tw(n);
   for (int k = 0; k < n / 2; ++k) {
