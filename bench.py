@@ -47,7 +47,7 @@ def parse():
                     help="trajectories of 8 steps for the learned warm start (1/16 held out)")
     ap.add_argument("--train-seconds", type=float, default=60.0, help="U-Net training budget")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start block")
-    ap.add_argument("--block", choices=["smoother", "learned", "forward"], default=None,
+    ap.add_argument("--block", choices=["smoother", "learned", "forward", "fft"], default=None,
                     help="run one sub-benchmark alone and print its JSON (profiling runs)")
     ap.add_argument("--smoother-level", type=int, default=9, help="level of the full periodic grid (9 = 512^3)")
     ap.add_argument("--fwd-batches", default="1,8", help="batch sizes of --block forward")
@@ -291,6 +291,53 @@ def bench_smoother(cmg, ctx, dev, peaks, lev=9, sweeps=10):
                         "bytes_per_launch": d["bytes"] / d["launches"], "achieved_GBs": gbs,
                         "frac_of_hbm": gbs / peaks["hbm"], "hbm_source": peaks["hbm_src"],
                         "TFLOPs": d["flops"] / (d["ms"] / 1e3) / 1e12, "traffic": traffic_for(fam + "_512")}
+    cmg.cmg_level_destroy(L)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return res
+
+
+def bench_fft(cmg, ctx, dev, B, rho_b, args, peaks):
+    """Time to rel. residual tol of full periodic levels by the FFT solve
+    (FP32 FFT inside FP64 refinement) against FP64 and mixed multigrid: the
+    two-level workload's 128^3 base, and a 512^3 level (rho uniform in
+    [0.5, 1.5), seed 7)."""
+    import torch
+    from paper_2604_06035_gb300 import inputs
+
+    def time_level(L, rho, reps=5):
+        out = {}
+        n = cmg.cmg_level_n_octs(L)
+        z = torch.zeros((n, 8), dtype=torch.float64, device=dev)
+        cmg.cmg_level_set_density(L, rho, float(rho.mean().item()))
+        for name, prec in (("fp64", cmg.CMG_PREC_FP64), ("mixed", cmg.CMG_PREC_MIXED), ("fft", cmg.CMG_PREC_FFT)):
+            ms, st = [], None
+            for _ in range(reps + 1):
+                cmg.cmg_level_set_phi(L, z)
+                rc, st = cmg.cmg_level_solve(L, tol=args.tol, precision=prec)
+                ms.append(st["ms"])
+            out[name] = {"ms_to_tol": statistics.median(ms[1:]), "steps": st["cycles"], "rel_final": st["rel_final"]}
+        cmg.cmg_ctx_reset_profile(ctx)
+        cmg.cmg_ctx_set_profiling(ctx, True)
+        cmg.cmg_level_set_phi(L, z)
+        cmg.cmg_level_solve(L, tol=args.tol, precision=cmg.CMG_PREC_FFT)
+        cmg.cmg_ctx_set_profiling(ctx, False)
+        f = cmg.cmg_ctx_get_profile(ctx)["fft_fp32"]
+        gbs = f["bytes"] / (f["ms"] / 1e3) / 1e9
+        out["fft_kernels"] = {"launches": f["launches"], "ms": f["ms"], "achieved_GBs": gbs,
+                              "frac_of_hbm": gbs / peaks["hbm"], "hbm_source": peaks["hbm_src"]}
+        out["speedup_fft_vs_fp64"] = out["fp64"]["ms_to_tol"] / out["fft"]["ms_to_tol"]
+        return out
+
+    res = {"base_128": time_level(B, rho_b)}
+    coords = torch.from_numpy(inputs.uniform_oct_coords(9)).to(dev)
+    L = cmg.cmg_level_build(ctx, 9, cmg.cmg_morton_encode(ctx, coords))
+    del coords
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    rho = torch.rand((cmg.cmg_level_n_octs(L), 8), dtype=torch.float64, device=dev, generator=g) + 0.5
+    res["periodic_512"] = time_level(L, rho, reps=3)
+    del rho
     cmg.cmg_level_destroy(L)
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
@@ -642,6 +689,7 @@ def run_ours(args, rank, local, world):
                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps}
         out["batched"] = bench_batched(cmg, ctx, dev, stream, args)
         out["smoother_512"] = bench_smoother(cmg, ctx, dev, peaks)
+        out["fft"] = bench_fft(cmg, ctx, dev, B, rho[0], args, peaks)
         if not args.no_learned:
             out["learned"] = bench_learned(cmg, ctx, dev, args, peaks)
         if rank == 0 and world == 1:
@@ -670,6 +718,12 @@ def run_block(args):
     peaks = read_peaks()
     if args.block == "smoother":
         out = bench_smoother(cmg, ctx, dev, peaks, lev=args.smoother_level)
+    elif args.block == "fft":
+        from paper_2604_06035_gb300 import inputs
+        cfg = inputs.two_level_amr(base_level=7, seed=2)
+        B = cmg.cmg_level_build(ctx, 7, cmg.cmg_morton_encode(ctx, torch.from_numpy(cfg["coords"][0]).to(dev)))
+        out = bench_fft(cmg, ctx, dev, B, torch.from_numpy(cfg["rho"][0]).to(dev), args, peaks)
+        cmg.cmg_level_destroy(B)
     elif args.block == "forward":
         out = bench_forward(cmg, ctx, dev, peaks, batches=[int(b) for b in args.fwd_batches.split(",")],
                             paths=args.fwd_paths.split(","))
