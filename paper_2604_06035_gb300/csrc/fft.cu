@@ -35,19 +35,19 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 
 __device__ __forceinline__ int brev(int i, int logn) { return (int)(__brev((unsigned)i) >> (32 - logn)); }
 
-// In-place radix-2 transforms of `lines` lines of length n in shared memory
-// (line l at s + l ld).  DIT (forward, input bit-reversed, output natural)
+// In-place radix-2 transforms of `lines` lines of length n = 2^logn in
+// shared memory (line l at s + l ld); power-of-two index arithmetic only.  DIT (forward, input bit-reversed, output natural)
 // with twiddles w^k; DIF (inverse, input natural, output bit-reversed) with
 // conj(w)^k.
-__device__ void fft_dit(float2 *s, int n, int ld, int lines, const float2 *tw) {
-  const int nb = lines * (n >> 1);
-  for (int len = 2; len <= n; len <<= 1) {
-    const int half = len >> 1, ts = n / len;
+__device__ void fft_dit(float2 *s, int logn, int ld, int lines, const float2 *tw) {
+  const int n = 1 << logn, nb = lines << (logn - 1);
+  for (int st = 1; st <= logn; ++st) {
+    const int half = 1 << (st - 1), tsh = logn - st;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-      const int line = b / (n >> 1), bb = b % (n >> 1);
-      const int pos = bb % half, i = (bb / half) * len + pos, j = i + half;
+      const int line = b >> (logn - 1), bb = b & ((n >> 1) - 1);
+      const int pos = bb & (half - 1), i = ((bb >> (st - 1)) << st) | pos, j = i + half;
       float2 *x = s + line * ld;
-      const float2 a = x[i], c = cmul(x[j], tw[pos * ts]);
+      const float2 a = x[i], c = cmul(x[j], tw[pos << tsh]);
       x[i] = make_float2(a.x + c.x, a.y + c.y);
       x[j] = make_float2(a.x - c.x, a.y - c.y);
     }
@@ -55,16 +55,16 @@ __device__ void fft_dit(float2 *s, int n, int ld, int lines, const float2 *tw) {
   }
 }
 
-__device__ void fft_dif_inv(float2 *s, int n, int ld, int lines, const float2 *tw) {
-  const int nb = lines * (n >> 1);
-  for (int len = n; len >= 2; len >>= 1) {
-    const int half = len >> 1, ts = n / len;
+__device__ void fft_dif_inv(float2 *s, int logn, int ld, int lines, const float2 *tw) {
+  const int n = 1 << logn, nb = lines << (logn - 1);
+  for (int st = logn; st >= 1; --st) {
+    const int half = 1 << (st - 1), tsh = logn - st;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-      const int line = b / (n >> 1), bb = b % (n >> 1);
-      const int pos = bb % half, i = (bb / half) * len + pos, j = i + half;
+      const int line = b >> (logn - 1), bb = b & ((n >> 1) - 1);
+      const int pos = bb & (half - 1), i = ((bb >> (st - 1)) << st) | pos, j = i + half;
       float2 *x = s + line * ld;
       const float2 a = x[i], c = x[j];
-      float2 w = tw[pos * ts];
+      float2 w = tw[pos << tsh];
       w.y = -w.y;
       x[i] = make_float2(a.x + c.x, a.y + c.y);
       x[j] = cmul(make_float2(a.x - c.x, a.y - c.y), w);
@@ -92,12 +92,12 @@ __global__ void k_fft_x_fwd(const float *__restrict__ g, int64_t ps, const int32
   load_tw(stw, tw, n);
   const int line0 = blockIdx.x * lines, no = n >> 1;
   for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
-    const int l = e / n, x = e % n, yz = line0 + l;
-    const int y = yz % n, z = yz / n;
+    const int l = e >> logn, x = e & (n - 1), yz = line0 + l;
+    const int y = yz & (n - 1), z = yz >> logn;
     s[l * n + brev(x, logn)] = make_float2(g[cell_index(map, no, x, y, z, ps)], 0.f);
   }
   __syncthreads();
-  fft_dit(s, n, n, lines, stw);
+  fft_dit(s, logn, n, lines, stw);
   for (int e = threadIdx.x; e < lines * n; e += blockDim.x) buf[(int64_t)line0 * n + e] = s[e];
 }
 
@@ -107,32 +107,32 @@ __global__ void k_fft_x_fwd(const float *__restrict__ g, int64_t ps, const int32
 // The tile's lines are n + 1 apart in shared memory (the load writes one
 // element of each line per thread: no bank conflicts).
 template <int AXIS, int MODE>
-__global__ void k_fft_yz(float2 *__restrict__ buf, const float2 *__restrict__ tw, int n, int logn, int tx) {
+__global__ void k_fft_yz(float2 *__restrict__ buf, const float2 *__restrict__ tw, int n, int logn, int logtx) {
   extern __shared__ float2 sm[];
   float2 *stw = sm, *s = sm + (n >> 1);
   load_tw(stw, tw, n);
-  const int ntile = n / tx;
-  const int x0 = (blockIdx.x % ntile) * tx, other = blockIdx.x / ntile;  // z (AXIS 1) or y (AXIS 2)
+  const int tx = 1 << logtx, logtile = logn - logtx;
+  const int x0 = (blockIdx.x & ((1 << logtile) - 1)) << logtx, other = blockIdx.x >> logtile;  // z (AXIS 1) or y (AXIS 2)
   const int64_t nn = (int64_t)n * n;
   const int ld = n + 1;
   auto addr = [&](int a, int t) -> int64_t {  // element a along the axis, column x0 + t
     return AXIS == 1 ? ((int64_t)other * nn + (int64_t)a * n + x0 + t) : ((int64_t)a * nn + (int64_t)other * n + x0 + t);
   };
   for (int e = threadIdx.x; e < tx * n; e += blockDim.x) {
-    const int a = e / tx, t = e % tx;  // consecutive threads read consecutive x
+    const int a = e >> logtx, t = e & (tx - 1);  // consecutive threads read consecutive x
     const float2 v = buf[addr(a, t)];
     s[t * ld + (MODE == 1 ? a : brev(a, logn))] = v;
   }
   __syncthreads();
   if (MODE == 1) {
-    fft_dif_inv(s, n, ld, tx, stw);
+    fft_dif_inv(s, logn, ld, tx, stw);
   } else {
-    fft_dit(s, n, ld, tx, stw);
+    fft_dit(s, logn, ld, tx, stw);
     if (MODE == 2) {
       // natural-order spectrum along z; x and y are already frequencies
       const float sy = sinpif((float)other / (float)n);
       for (int e = threadIdx.x; e < tx * n; e += blockDim.x) {
-        const int t = e / n, kz = e % n;
+        const int t = e >> logn, kz = e & (n - 1);
         const float sx = sinpif((float)(x0 + t) / (float)n), sz = sinpif((float)kz / (float)n);
         const float d = sx * sx + sy * sy + sz * sz;
         const float f = d > 0.f ? 1.5f / d : 0.f;
@@ -140,11 +140,11 @@ __global__ void k_fft_yz(float2 *__restrict__ buf, const float2 *__restrict__ tw
         v = make_float2(v.x * f, v.y * f);
       }
       __syncthreads();
-      fft_dif_inv(s, n, ld, tx, stw);
+      fft_dif_inv(s, logn, ld, tx, stw);
     }
   }
   for (int e = threadIdx.x; e < tx * n; e += blockDim.x) {
-    const int a = e / tx, t = e % tx;
+    const int a = e >> logtx, t = e & (tx - 1);
     buf[addr(a, t)] = s[t * ld + (MODE == 0 ? a : brev(a, logn))];
   }
 }
@@ -159,10 +159,10 @@ __global__ void k_fft_x_inv(const float2 *__restrict__ buf, const int32_t *__res
   const int line0 = blockIdx.x * lines, no = n >> 1;
   for (int e = threadIdx.x; e < lines * n; e += blockDim.x) s[e] = buf[(int64_t)line0 * n + e];
   __syncthreads();
-  fft_dif_inv(s, n, n, lines, stw);
+  fft_dif_inv(s, logn, n, lines, stw);
   for (int e = threadIdx.x; e < lines * n; e += blockDim.x) {
-    const int l = e / n, x = e % n, yz = line0 + l;
-    const int y = yz % n, z = yz / n;
+    const int l = e >> logn, x = e & (n - 1), yz = line0 + l;
+    const int y = yz & (n - 1), z = yz >> logn;
     e_out[cell_index(map, no, x, y, z, ps)] = s[l * n + brev(x, logn)].x * inv_n3;
   }
 }
@@ -207,7 +207,9 @@ void fft_solve32(cmg_level *L) {
   const int n = 1 << L->lev, logn = L->lev;
   cudaStream_t s = L->ctx->stream;
   const int lines = std::max(1, std::min(2048 / n, n * n));  // x passes: <= 16 KB of lines per block
-  const int tx = std::min(n >= 512 ? 8 : 16, n);             // y / z passes: columns per block
+  const int tx = std::min(16, n);                           // y / z passes: columns per block (128-byte rows)
+  int logtx = 0;
+  while ((1 << logtx) < tx) ++logtx;
   const size_t smx = sizeof(float2) * ((size_t)(n / 2) + (size_t)lines * n);
   const size_t smyz = sizeof(float2) * ((size_t)(n / 2) + (size_t)tx * (n + 1));
   const int64_t lines_total = (int64_t)n * n;
@@ -216,21 +218,28 @@ void fft_solve32(cmg_level *L) {
   // array (x passes: one FP32 field value per cell instead), 5 n log2 n flops
   // per line transform
   const double cells = (double)n * n * n, line_flops = 5.0 * cells * logn;
+  static int attr_dev = -1;
+  if (attr_dev != L->ctx->device) {  // n = 512: 16 columns x 513 x 8 B > 48 KB
+    CMG_CUDA(cudaFuncSetAttribute(k_fft_yz<1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+    CMG_CUDA(cudaFuncSetAttribute(k_fft_yz<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+    CMG_CUDA(cudaFuncSetAttribute(k_fft_yz<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+    attr_dev = L->ctx->device;
+  }
   {
     LaunchScope ls(L->ctx, K_FFT, cells * (4.0 + 4.0 + 8.0), line_flops);
     k_fft_x_fwd<<<bx, kFftThreads, smx, s>>>(g.g32, g.n * 4, L->fft_map, L->fft_tw, n, logn, lines, L->fft_buf);
   }
   {
     LaunchScope ls(L->ctx, K_FFT, cells * 16.0, line_flops);
-    k_fft_yz<1, 0><<<byz, kFftThreads, smyz, s>>>(L->fft_buf, L->fft_tw, n, logn, tx);
+    k_fft_yz<1, 0><<<byz, kFftThreads, smyz, s>>>(L->fft_buf, L->fft_tw, n, logn, logtx);
   }
   {
     LaunchScope ls(L->ctx, K_FFT, cells * 16.0, 2.0 * line_flops + 6.0 * cells);
-    k_fft_yz<2, 2><<<byz, kFftThreads, smyz, s>>>(L->fft_buf, L->fft_tw, n, logn, tx);
+    k_fft_yz<2, 2><<<byz, kFftThreads, smyz, s>>>(L->fft_buf, L->fft_tw, n, logn, logtx);
   }
   {
     LaunchScope ls(L->ctx, K_FFT, cells * 16.0, line_flops);
-    k_fft_yz<1, 1><<<byz, kFftThreads, smyz, s>>>(L->fft_buf, L->fft_tw, n, logn, tx);
+    k_fft_yz<1, 1><<<byz, kFftThreads, smyz, s>>>(L->fft_buf, L->fft_tw, n, logn, logtx);
   }
   {
     LaunchScope ls(L->ctx, K_FFT, cells * (8.0 + 4.0 + 4.0), line_flops);
