@@ -36,38 +36,78 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 __device__ __forceinline__ int brev(int i, int logn) { return (int)(__brev((unsigned)i) >> (32 - logn)); }
 
 // In-place radix-2 transforms of `lines` lines of length n = 2^logn in
-// shared memory (line l at s + l ld); power-of-two index arithmetic only.  DIT (forward, input bit-reversed, output natural)
+// shared memory (line l at s + l ld), two stages per pass (each thread takes
+// four points through both in registers, halving the shared-memory round
+// trips and barriers); power-of-two index arithmetic only.  DIT (forward, input bit-reversed, output natural)
 // with twiddles w^k; DIF (inverse, input natural, output bit-reversed) with
 // conj(w)^k.
 __device__ void fft_dit(float2 *s, int logn, int ld, int lines, const float2 *tw) {
-  const int n = 1 << logn, nb = lines << (logn - 1);
-  for (int st = 1; st <= logn; ++st) {
-    const int half = 1 << (st - 1), tsh = logn - st;
+  const int n = 1 << logn;
+  int st = 1;
+  // two radix-2 stages per pass over shared memory (four points per thread)
+  for (; st + 1 <= logn; st += 2) {
+    const int h = 1 << (st - 1), ng = lines << (logn - 2);
+    for (int b = threadIdx.x; b < ng; b += blockDim.x) {
+      const int line = b >> (logn - 2), g = b & ((n >> 2) - 1);
+      const int pos = g & (h - 1), i = ((g >> (st - 1)) << (st + 1)) | pos;
+      float2 *x = s + line * ld;
+      const float2 w1 = tw[pos << (logn - st)], w2 = tw[pos << (logn - st - 1)], w3 = tw[(pos + h) << (logn - st - 1)];
+      const float2 x0 = x[i], x1 = cmul(x[i + h], w1), x2 = x[i + 2 * h], x3 = cmul(x[i + 3 * h], w1);
+      const float2 y0 = make_float2(x0.x + x1.x, x0.y + x1.y), y1 = make_float2(x0.x - x1.x, x0.y - x1.y);
+      const float2 y2 = make_float2(x2.x + x3.x, x2.y + x3.y), y3 = make_float2(x2.x - x3.x, x2.y - x3.y);
+      const float2 u = cmul(y2, w2), v = cmul(y3, w3);
+      x[i] = make_float2(y0.x + u.x, y0.y + u.y);
+      x[i + 2 * h] = make_float2(y0.x - u.x, y0.y - u.y);
+      x[i + h] = make_float2(y1.x + v.x, y1.y + v.y);
+      x[i + 3 * h] = make_float2(y1.x - v.x, y1.y - v.y);
+    }
+    __syncthreads();
+  }
+  if (st == logn) {  // odd number of stages: the last one alone
+    const int h = 1 << (st - 1), nb = lines << (logn - 1);
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
       const int line = b >> (logn - 1), bb = b & ((n >> 1) - 1);
-      const int pos = bb & (half - 1), i = ((bb >> (st - 1)) << st) | pos, j = i + half;
+      const int pos = bb & (h - 1), i = ((bb >> (st - 1)) << st) | pos;
       float2 *x = s + line * ld;
-      const float2 a = x[i], c = cmul(x[j], tw[pos << tsh]);
+      const float2 a = x[i], c = cmul(x[i + h], tw[pos << (logn - st)]);
       x[i] = make_float2(a.x + c.x, a.y + c.y);
-      x[j] = make_float2(a.x - c.x, a.y - c.y);
+      x[i + h] = make_float2(a.x - c.x, a.y - c.y);
     }
     __syncthreads();
   }
 }
 
+__device__ __forceinline__ float2 conjf2(float2 w) { return make_float2(w.x, -w.y); }
+
 __device__ void fft_dif_inv(float2 *s, int logn, int ld, int lines, const float2 *tw) {
-  const int n = 1 << logn, nb = lines << (logn - 1);
-  for (int st = logn; st >= 1; --st) {
-    const int half = 1 << (st - 1), tsh = logn - st;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-      const int line = b >> (logn - 1), bb = b & ((n >> 1) - 1);
-      const int pos = bb & (half - 1), i = ((bb >> (st - 1)) << st) | pos, j = i + half;
+  const int n = 1 << logn;
+  int st = logn;
+  for (; st - 1 >= 1; st -= 2) {
+    const int q = 1 << (st - 2), ng = lines << (logn - 2);
+    for (int b = threadIdx.x; b < ng; b += blockDim.x) {
+      const int line = b >> (logn - 2), g = b & ((n >> 2) - 1);
+      const int p = g & (q - 1), i = ((g >> (st - 2)) << st) | p;
       float2 *x = s + line * ld;
-      const float2 a = x[i], c = x[j];
-      float2 w = tw[pos << tsh];
-      w.y = -w.y;
+      const float2 wa = conjf2(tw[p << (logn - st)]), wb = conjf2(tw[(p + q) << (logn - st)]);
+      const float2 wc = conjf2(tw[p << (logn - st + 1)]);
+      const float2 x0 = x[i], x1 = x[i + q], x2 = x[i + 2 * q], x3 = x[i + 3 * q];
+      const float2 y0 = make_float2(x0.x + x2.x, x0.y + x2.y), y2 = cmul(make_float2(x0.x - x2.x, x0.y - x2.y), wa);
+      const float2 y1 = make_float2(x1.x + x3.x, x1.y + x3.y), y3 = cmul(make_float2(x1.x - x3.x, x1.y - x3.y), wb);
+      x[i] = make_float2(y0.x + y1.x, y0.y + y1.y);
+      x[i + q] = cmul(make_float2(y0.x - y1.x, y0.y - y1.y), wc);
+      x[i + 2 * q] = make_float2(y2.x + y3.x, y2.y + y3.y);
+      x[i + 3 * q] = cmul(make_float2(y2.x - y3.x, y2.y - y3.y), wc);
+    }
+    __syncthreads();
+  }
+  if (st == 1) {  // odd number of stages: the first (twiddle 1) alone
+    const int nb = lines << (logn - 1);
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+      const int line = b >> (logn - 1), i = (b & ((n >> 1) - 1)) << 1;
+      float2 *x = s + line * ld;
+      const float2 a = x[i], c = x[i + 1];
       x[i] = make_float2(a.x + c.x, a.y + c.y);
-      x[j] = cmul(make_float2(a.x - c.x, a.y - c.y), w);
+      x[i + 1] = make_float2(a.x - c.x, a.y - c.y);
     }
     __syncthreads();
   }
