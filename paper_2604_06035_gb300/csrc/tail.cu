@@ -44,7 +44,9 @@ struct TailPlan {
   TailLevel lv[kMaxTail];
 };
 
-template <typename T, bool MASK>
+// CG: loads through L2 only (another CTA of the cluster may have written the
+// data); a single-CTA tail reads through L1.
+template <typename T, bool MASK, bool CG>
 __device__ void pass(const TailLevel &L, int P, bool zero, int64_t tid, int64_t nthr) {
   T *phi = static_cast<T *>(L.phi);
   const T *g = static_cast<const T *>(L.g);
@@ -52,73 +54,71 @@ __device__ void pass(const TailLevel &L, int P, bool zero, int64_t tid, int64_t 
   for (int64_t i = tid; i < L.n; i += nthr) {
     if (P == 0) {
       if (zero)
-        dev::sweep_oct<T, 0, true, MASK, true>(i, L.nbr, phi + st, phi, g, L.active, L.n);
+        dev::sweep_oct<T, 0, true, MASK, CG>(i, L.nbr, phi + st, phi, g, L.active, L.n);
       else
-        dev::sweep_oct<T, 0, false, MASK, true>(i, L.nbr, phi + st, phi, g, L.active, L.n);
+        dev::sweep_oct<T, 0, false, MASK, CG>(i, L.nbr, phi + st, phi, g, L.active, L.n);
     } else {
-      dev::sweep_oct<T, 1, false, MASK, true>(i, L.nbr, phi, phi + st, g + L.n * 4, L.active, L.n);
+      dev::sweep_oct<T, 1, false, MASK, CG>(i, L.nbr, phi, phi + st, g + L.n * 4, L.active, L.n);
     }
   }
 }
 
-template <typename T>
+template <typename T, bool CG>
 __device__ void colour_pass(const TailLevel &L, int P, bool zero, int64_t tid, int64_t nthr) {
   if (L.all_active)
-    pass<T, false>(L, P, zero, tid, nthr);
+    pass<T, false, CG>(L, P, zero, tid, nthr);
   else
-    pass<T, true>(L, P, zero, tid, nthr);
+    pass<T, true, CG>(L, P, zero, tid, nthr);
 }
 
-template <typename T>
-__device__ void sweeps(const TailLevel &L, int n_sweeps, bool zero_first, int64_t tid, int64_t nthr,
-                       cg::cluster_group &cl) {
+template <typename T, bool CG, class Sync>
+__device__ void sweeps(const TailLevel &L, int n_sweeps, bool zero_first, int64_t tid, int64_t nthr, Sync &sync) {
   for (int k = 0; k < n_sweeps; ++k) {
-    colour_pass<T>(L, 0, zero_first && k == 0, tid, nthr);
-    cl.sync();
-    colour_pass<T>(L, 1, false, tid, nthr);
-    cl.sync();
+    colour_pass<T, CG>(L, 0, zero_first && k == 0, tid, nthr);
+    sync();
+    colour_pass<T, CG>(L, 1, false, tid, nthr);
+    sync();
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ TailPlan plan) {
-  cg::cluster_group cl = cg::this_cluster();
-  const int64_t nthr = (int64_t)cl.num_threads();
-  const int64_t tid = (int64_t)cl.block_rank() * blockDim.x + threadIdx.x;
+// The V-cycle from MG level plan.m0 down to the coarsest and back up, by
+// nthr threads (thread tid), operations separated by sync().
+template <typename T, bool CG, class Sync>
+__device__ void tail_body(const TailPlan &plan, int64_t tid, int64_t nthr, Sync &sync) {
   // descend: pre-smoothing, residual + restriction
   for (int m = plan.m0; m < plan.last; ++m) {
     const TailLevel &L = plan.lv[m];
     const TailLevel &C = plan.lv[m + 1];
-    sweeps<T>(L, plan.n_pre, true, tid, nthr, cl);
+    sweeps<T, CG>(L, plan.n_pre, true, tid, nthr, sync);
     const T *phi = static_cast<const T *>(L.phi);
     const T *g = static_cast<const T *>(L.g);
     for (int64_t i = tid; i < L.n; i += nthr)
-      dev::resid_oct<T, false, true, false, false, false, true>(
+      dev::resid_oct<T, false, true, false, false, false, CG>(
           i, L.nbr, phi, g, L.all_active ? nullptr : L.active, L.n, L.n_alloc, L.father, static_cast<T *>(C.g),
           static_cast<T *>(C.phi), C.n, C.n_alloc, L.zero_coarse, nullptr, 0.0, nullptr, 0.0);
-    cl.sync();
+    sync();
   }
   // coarsest level
   {
     const TailLevel &L = plan.lv[plan.last];
     if (plan.exact) {
-      if (tid == 0) dev::wht_solve<T, T, true>(static_cast<const T *>(L.g), static_cast<T *>(L.phi), L.n_alloc,
-                                               plan.h_last);
-      cl.sync();
+      if (tid == 0) dev::wht_solve<T, T, CG>(static_cast<const T *>(L.g), static_cast<T *>(L.phi), L.n_alloc,
+                                             plan.h_last);
+      sync();
     } else if (!plan.mixed) {
-      sweeps<T>(L, plan.coarse_sweeps, plan.last > 0, tid, nthr, cl);
+      sweeps<T, CG>(L, plan.coarse_sweeps, plan.last > 0, tid, nthr, sync);
     } else {
       // mixed precision: the coarsest level is solved in FP64
       TailLevel L64 = L;
       L64.phi = L.phi64;
       L64.g = L.g64;
       const float *g32 = static_cast<const float *>(L.g);
-      for (int64_t t = tid; t < 8 * L.n; t += nthr) L.g64[t] = (double)__ldcg(g32 + t);
-      cl.sync();
-      sweeps<double>(L64, plan.coarse_sweeps, true, tid, nthr, cl);
+      for (int64_t t = tid; t < 8 * L.n; t += nthr) L.g64[t] = (double)(CG ? __ldcg(g32 + t) : g32[t]);
+      sync();
+      sweeps<double, CG>(L64, plan.coarse_sweeps, true, tid, nthr, sync);
       float *p32 = static_cast<float *>(L.phi);
-      for (int64_t t = tid; t < 8 * L.n_alloc; t += nthr) p32[t] = (float)__ldcg(L.phi64 + t);
-      cl.sync();
+      for (int64_t t = tid; t < 8 * L.n_alloc; t += nthr) p32[t] = (float)(CG ? __ldcg(L.phi64 + t) : L.phi64[t]);
+      sync();
     }
   }
   // ascend: prolongation + correction, post-smoothing
@@ -129,13 +129,38 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     const T *cphi = static_cast<const T *>(C.phi);
     for (int64_t i = tid; i < L.n; i += nthr) {
       if (L.all_active)
-        dev::prolong_oct<T, false, true>(i, L.keys, L.blk, L.n, L.n_alloc, phi, L.active, cphi, C.n_alloc);
+        dev::prolong_oct<T, false, CG>(i, L.keys, L.blk, L.n, L.n_alloc, phi, L.active, cphi, C.n_alloc);
       else
-        dev::prolong_oct<T, true, true>(i, L.keys, L.blk, L.n, L.n_alloc, phi, L.active, cphi, C.n_alloc);
+        dev::prolong_oct<T, true, CG>(i, L.keys, L.blk, L.n, L.n_alloc, phi, L.active, cphi, C.n_alloc);
     }
-    cl.sync();
-    sweeps<T>(L, plan.n_post, false, tid, nthr, cl);
+    sync();
+    sweeps<T, CG>(L, plan.n_post, false, tid, nthr, sync);
   }
+}
+
+struct ClusterSync {
+  cg::cluster_group cl;
+  __device__ void operator()() { cl.sync(); }
+};
+struct BlockSync {
+  __device__ void operator()() { __syncthreads(); }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ TailPlan plan) {
+  ClusterSync sync{cg::this_cluster()};
+  const int64_t nthr = (int64_t)sync.cl.num_threads();
+  const int64_t tid = (int64_t)sync.cl.block_rank() * blockDim.x + threadIdx.x;
+  tail_body<T, true>(plan, tid, nthr, sync);
+}
+
+// The same V-cycle tail in one CTA: block barriers, loads through L1.  For
+// levels so small that a launch costs more than their arithmetic on one SM.
+constexpr int kTail1Threads = 1024;
+template <typename T>
+__global__ void __launch_bounds__(kTail1Threads) k_tail1(const __grid_constant__ TailPlan plan) {
+  BlockSync sync;
+  tail_body<T, false>(plan, threadIdx.x, blockDim.x, sync);
 }
 
 template <typename T>
@@ -163,6 +188,14 @@ int tail_cluster_size() {
 }
 
 }  // namespace
+
+// Largest first tail level run by one CTA: one SM does ~2 FP64 FMAs per
+// clock but ~64 FP32 ones, so the single-CTA tail pays for far larger FP32
+// levels than FP64 ones.
+template <typename T>
+int64_t tail1_max_octs() {
+  return sizeof(T) == 8 ? 64 : 4096;
+}
 
 template <typename T>
 void tail_vcycle(cmg_level *L, int m0, const cmg_solve_params *p, const bool *zero_coarse) {
@@ -194,6 +227,15 @@ void tail_vcycle(cmg_level *L, int m0, const cmg_solve_params *p, const bool *ze
     t.all_active = g.all_active ? 1 : 0;
     t.zero_coarse = (m < last && zero_coarse[m]) ? 1 : 0;
   }
+  double cells = 0.0;
+  for (int m = m0; m <= last; ++m) cells += 8.0 * L->mg[m].n;
+  LaunchScope ls(L->ctx, K_COARSE, cells * (p->n_pre + p->n_post + 2) * 3.0 * sizeof(T),
+                 cells * (p->n_pre + p->n_post) * 7.0);
+  if (L->mg[m0].n <= tail1_max_octs<T>()) {
+    k_tail1<T><<<1, kTail1Threads, 0, L->ctx->stream>>>(plan);
+    CMG_CUDA(cudaGetLastError());
+    return;
+  }
   const int cs = tail_cluster_size<T>();
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cs);
@@ -206,10 +248,6 @@ void tail_vcycle(cmg_level *L, int m0, const cmg_solve_params *p, const bool *ze
   attr.val.clusterDim.z = 1;
   cfg.attrs = &attr;
   cfg.numAttrs = 1;
-  double cells = 0.0;
-  for (int m = m0; m <= last; ++m) cells += 8.0 * L->mg[m].n;
-  LaunchScope ls(L->ctx, K_COARSE, cells * (p->n_pre + p->n_post + 2) * 3.0 * sizeof(T),
-                 cells * (p->n_pre + p->n_post) * 7.0);
   CMG_CUDA(cudaLaunchKernelEx(&cfg, k_tail<T>, plan));
 }
 

@@ -365,19 +365,24 @@ def test_device_arrays_match_host_arrays(cmg, ctx):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_tail_schedule_matches_per_operation_launches(cmg, ctx, precision):
-    """The cluster tail kernel runs the same per-oct arithmetic as the
-    one-launch-per-operation path: the schedule must not change phi."""
+    """The tail kernels (one CTA for the smallest levels, a cluster above) run
+    the same per-oct arithmetic as the one-launch-per-operation path: the
+    schedule must not change phi.  Tails from 64 octs (one CTA in FP64 and
+    FP32), 4096 (cluster in FP64, one CTA in FP32) and the whole hierarchy
+    (cluster)."""
     cfg, GB, GF, RB, RF = _two_level(cmg, ctx, 6)
     out = {}
-    for tail in (0, 1 << 20):
+    tails = (0, 64, 4096, 1 << 20)
+    for tail in tails:
         for G, rho in ((GB, cfg["rho"][0]), (GF, cfg["rho"][1])):
             cmg.cmg_level_set_schedule(G, tail, tail)
             cmg.cmg_level_set_density(G, rho, 1.0)
             cmg.cmg_level_set_phi(G, np.zeros((cmg.cmg_level_n_octs(G), 8)))
             rc, st = cmg.cmg_level_solve(G, tol=1e-10, fixed_cycles=4, precision=precision)
             out[(tail, G is GB)] = cmg.cmg_level_get_phi(G)
-    for base in (True, False):
-        assert relerr(out[(1 << 20, base)], out[(0, base)]) <= 1e-13
+    for tail in tails[1:]:
+        for base in (True, False):
+            assert relerr(out[(tail, base)], out[(0, base)]) <= 1e-13, (tail, base)
 
 
 def _cube(level, lo, hi):
