@@ -161,10 +161,12 @@ int cmg_level_solve(cmg_level *lvl, const cmg_solve_params *params, cmg_solve_st
 
 /* Execution schedule of the V-cycle (no effect on the arithmetic): MG levels
  * with at most tail_octs_fp64 (FP64 cycles) / tail_octs_fp32 (FP32 inner
- * cycles) octs, together with every coarser level, run in one thread-block-
- * cluster launch instead of one launch per operation; 0 disables (the
- * default: on GB300 a cluster pass over a small level is as slow as a launch).
- * Negative values leave the current setting. */
+ * cycles) octs, together with every coarser level, run in one launch instead
+ * of one launch per operation -- in a single CTA when the first of them has
+ * at most 64 (FP64) / 4096 (FP32) octs, else in one thread-block cluster.
+ * Defaults 64 / 512 (measured on GB300: a cluster pass over a small level is
+ * as slow as a launch, and one SM's FP64 rate only pays for tiny levels);
+ * 0 disables.  Negative values leave the current setting. */
 int cmg_level_set_schedule(cmg_level *lvl, int64_t tail_octs_fp64, int64_t tail_octs_fp32);
 
 /* ---- multigrid hierarchy introspection and single steps (for tests) ----

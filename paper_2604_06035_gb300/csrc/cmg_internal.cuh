@@ -266,9 +266,9 @@ struct cmg_level {
   std::vector<void *> graphs;  // instantiated solve graphs, keyed by parameters
   bool has32 = false;
   // schedule: MG levels with at most this many octs (and all coarser ones) run
-  // in one cluster "tail" launch; 0 = one launch per operation everywhere
-  int64_t tail_octs_fp64 = 0;
-  int64_t tail_octs_fp32 = 0;
+  // in one "tail" launch (tail.cu); 0 = one launch per operation everywhere
+  int64_t tail_octs_fp64 = 64;
+  int64_t tail_octs_fp32 = 512;
   // FFT solve of a full periodic level (fft.cu): dense complex work array,
   // oct-coordinate -> oct-index map, twiddles (lazy)
   float2 *fft_buf = nullptr;
