@@ -848,3 +848,110 @@ int or_level_solve_mixed(or_level *L, const or_params *p, int inner_cycles, or_s
   }
   return p->fixed_cycles > 0 ? OR_OK : OR_ERR_NOT_CONVERGED;
 }
+
+/* ------------------------------- MG-preconditioned CG (App. D.2 reading) */
+
+static double dot8(const double *a, const double *b, int64_t n) {
+  double s = 0.0;
+  for (int64_t t = 0; t < n; t++) s += a[t] * b[t];
+  return s;
+}
+
+/* q = L_h v with zero values across the coarse-fine boundary (the operator
+ * acting on corrections): the residual of v for a zero source, negated. */
+static void apply_L0(or_level *L, const double *v, double *q, const double *zero) {
+  mglev *g = &L->mg[0];
+  double *f_save = g->f;
+  memcpy(g->phi, v, sizeof(double) * 8 * g->n);
+  g->f = (double *)zero;
+  or_residual(L, 0, 0);
+  g->f = f_save;
+  for (int64_t t = 0; t < 8 * g->n; t++) q[t] = -g->r[t];
+}
+
+/* z = one V-cycle from zero on L z = r, homogeneous coarse-fine boundary
+ * values; zero mean on a periodic level (the operator's null space). */
+static void precondition(or_level *L, const or_params *p, const double *r, double *z) {
+  mglev *g = &L->mg[0];
+  double *f_save = g->f;
+  g->f = (double *)r;
+  memset(g->phi, 0, sizeof(double) * 8 * g->n);
+  vcycle(L, 0, p, 0);
+  g->f = f_save;
+  memcpy(z, g->phi, sizeof(double) * 8 * g->n);
+  if (L->periodic_full) subtract_mean(z, 8 * g->n);
+}
+
+int or_level_solve_pcg(or_level *L, const or_params *p, or_stats *st) {
+  int rc = check_solvable(L, p);
+  if (rc != OR_OK) return rc;
+  memset(st, 0, sizeof(*st));
+  or_level_compute_ghosts(L);
+  mglev *g = &L->mg[0];
+  const int64_t N = 8 * g->n;
+  double n0 = zero_guess_norm2(L);
+  st->norm0 = sqrt(n0);
+  if (n0 == 0.0) {
+    memset(g->phi, 0, sizeof(double) * N);
+    return OR_OK;
+  }
+  const int64_t m = N ? N : 1;
+  double *x = (double *)malloc(sizeof(double) * m), *r = (double *)malloc(sizeof(double) * m);
+  double *rn = (double *)malloc(sizeof(double) * m), *z = (double *)malloc(sizeof(double) * m);
+  double *d = (double *)malloc(sizeof(double) * m), *q = (double *)malloc(sizeof(double) * m);
+  double *zero = (double *)calloc(m, sizeof(double));
+  memcpy(x, g->phi, sizeof(double) * N);
+  double nr = or_residual(L, 0, 1); /* true residual of the initial guess */
+  memcpy(r, g->r, sizeof(double) * N);
+  double rel = sqrt(nr / n0);
+  st->rel_initial = rel;
+  st->rel_final = rel;
+  int target = p->fixed_cycles > 0 ? p->fixed_cycles : p->max_cycles;
+  rc = p->fixed_cycles > 0 ? OR_OK : OR_ERR_NOT_CONVERGED;
+  if (p->fixed_cycles == 0 && rel <= p->tol) {
+    rc = OR_OK;
+    target = 0;
+  }
+  if (target > 0) {
+    precondition(L, p, r, z);
+    memcpy(d, z, sizeof(double) * N);
+    double rz = dot8(r, z, N);
+    for (int it = 1; it <= target; it++) {
+      apply_L0(L, d, q, zero);
+      double alpha = rz / dot8(d, q, N);
+      for (int64_t t = 0; t < N; t++) {
+        x[t] += alpha * d[t];
+        rn[t] = r[t] - alpha * q[t];
+      }
+      rel = sqrt(dot8(rn, rn, N) / n0);
+      st->cycles = it;
+      st->rel_history[it - 1] = rel;
+      st->rel_final = rel;
+      if (!isfinite(rel) || rel > 1e3 * (st->rel_initial > 1.0 ? st->rel_initial : 1.0)) {
+        rc = OR_ERR_DIVERGED;
+        break;
+      }
+      if (p->fixed_cycles == 0 && rel <= p->tol) {
+        rc = OR_OK;
+        break;
+      }
+      precondition(L, p, rn, z);
+      /* flexible (Polak-Ribiere) beta: (z_new, r_new - r_old) / (z_old, r_old) */
+      double rz_new = dot8(rn, z, N);
+      double beta = (rz_new - dot8(r, z, N)) / rz;
+      for (int64_t t = 0; t < N; t++) d[t] = z[t] + beta * d[t];
+      rz = rz_new;
+      memcpy(r, rn, sizeof(double) * N);
+    }
+  }
+  memcpy(g->phi, x, sizeof(double) * N);
+  if (L->periodic_full) subtract_mean(g->phi, N);
+  free(x);
+  free(r);
+  free(rn);
+  free(z);
+  free(d);
+  free(q);
+  free(zero);
+  return rc;
+}

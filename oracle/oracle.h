@@ -119,6 +119,15 @@ int or_level_solve(or_level *L, const or_params *p, or_stats *st);
 /* Mixed precision reference: FP64 residual and accumulation, FP32 inner V-cycle
  * on r/||r|| (FP64 coarsest solve).  inner_cycles V-cycles per outer step. */
 int or_level_solve_mixed(or_level *L, const or_params *p, int inner_cycles, or_stats *st);
+/* Multigrid-preconditioned conjugate gradients (App. D.2: MG as the CG
+ * preconditioner).  Flexible (Polak-Ribiere) beta, since a V-cycle with red
+ * first in both smoothing legs is not exactly symmetric; preconditioner = one
+ * V-cycle from zero on the residual with homogeneous coarse-fine values;
+ * operator applied with homogeneous values after the initial (true)
+ * residual; zero-mean preconditioned vectors on a periodic level.  cycles =
+ * CG iterations (one V-cycle and one operator application each); the
+ * relative residual is the CG recurrence's. */
+int or_level_solve_pcg(or_level *L, const or_params *p, or_stats *st);
 
 #ifdef __cplusplus
 }

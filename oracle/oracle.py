@@ -74,6 +74,7 @@ def lib():
             "or_coarse_solve": (None, [_P, C.c_int]),
             "or_level_solve": (C.c_int, [_P, C.POINTER(OrParams), C.POINTER(OrStats)]),
             "or_level_solve_mixed": (C.c_int, [_P, C.POINTER(OrParams), C.c_int, C.POINTER(OrStats)]),
+            "or_level_solve_pcg": (C.c_int, [_P, C.POINTER(OrParams), C.POINTER(OrStats)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -268,6 +269,21 @@ class Level:
         if rc != OR_OK and raise_on_error:
             raise OracleError(rc, "or_level_solve_mixed")
         return rc, _stats_dict(st)
+
+
+def _solve_pcg(self, tol=1e-10, max_cycles=100, n_pre=2, n_post=2, coarse_sweeps=4, fixed_cycles=0,
+               raise_on_error=True):
+    """Multigrid-preconditioned (flexible) conjugate gradients: cycles = CG
+    iterations, one V-cycle preconditioner application each."""
+    p = params(tol, max_cycles, n_pre, n_post, coarse_sweeps, fixed_cycles)
+    st = OrStats()
+    rc = lib().or_level_solve_pcg(self._h, C.byref(p), C.byref(st))
+    if rc != OR_OK and raise_on_error:
+        raise OracleError(rc, "or_level_solve_pcg")
+    return rc, _stats_dict(st)
+
+
+Level.solve_pcg = _solve_pcg
 
 
 def _stats_dict(st):
