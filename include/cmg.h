@@ -67,6 +67,10 @@ typedef struct {
   int fixed_cycles;  /* > 0: run exactly this many cycles and ignore tol */
   int precision;     /* cmg_precision */
   int inner_cycles;  /* MIXED: FP32 V-cycles per FP64 refinement step (>= 1) */
+  int krylov;        /* 0: stationary V-cycle iteration; 1: conjugate gradients
+                        preconditioned by one V-cycle per iteration (App. D.2
+                        names multigrid as the CG preconditioner), FP64 only;
+                        cycles then counts CG iterations.  Batches: 0 only. */
 } cmg_solve_params;
 
 typedef struct {

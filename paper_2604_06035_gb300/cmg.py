@@ -40,7 +40,7 @@ CMG_OP_SWEEP, CMG_OP_RESIDUAL, CMG_OP_RESTRICT, CMG_OP_PROLONG, CMG_OP_COARSE, C
 class cmg_solve_params(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_cycles", C.c_int), ("n_pre", C.c_int), ("n_post", C.c_int),
                 ("coarse_sweeps", C.c_int), ("fixed_cycles", C.c_int), ("precision", C.c_int),
-                ("inner_cycles", C.c_int)]
+                ("inner_cycles", C.c_int), ("krylov", C.c_int)]
 
 
 class cmg_solve_stats(C.Structure):
@@ -477,8 +477,9 @@ def cmg_level_set_phi(lvl, phi):
 
 
 def solve_params(tol=1e-10, max_cycles=100, n_pre=2, n_post=2, coarse_sweeps=4, fixed_cycles=0,
-                 precision=CMG_PREC_FP64, inner_cycles=1):
-    return cmg_solve_params(tol, max_cycles, n_pre, n_post, coarse_sweeps, fixed_cycles, precision, inner_cycles)
+                 precision=CMG_PREC_FP64, inner_cycles=1, krylov=0):
+    return cmg_solve_params(tol, max_cycles, n_pre, n_post, coarse_sweeps, fixed_cycles, precision, inner_cycles,
+                            krylov)
 
 
 def _stats(st):

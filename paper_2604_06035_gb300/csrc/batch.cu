@@ -493,7 +493,7 @@ int64_t barriers_per_cycle(const cmg_batch *b, bool mixed) {
 
 int batch_solve(cmg_batch *b, const cmg_solve_params *p, cmg_batch_stats *st) {
   if (!p || !(p->tol >= 0.0) || p->max_cycles < 0 || p->fixed_cycles < 0 ||
-      (p->precision != CMG_PREC_FP64 && p->precision != CMG_PREC_MIXED))
+      (p->precision != CMG_PREC_FP64 && p->precision != CMG_PREC_MIXED) || p->krylov != 0)
     throw Error(CMG_ERR_INVALID_ARG, "invalid solve parameters");
   cmg_level *L = b->lvl;
   cmg_ctx *ctx = L->ctx;

@@ -274,6 +274,7 @@ struct cmg_level {
   float2 *fft_buf = nullptr;
   int32_t *fft_map = nullptr;
   float2 *fft_tw = nullptr;
+  double *pcg = nullptr;  // CG vectors, partial sums and scalars (pcg.cu, lazy)
   cmg::DeviceBuffers mem;
 };
 
@@ -351,6 +352,9 @@ void unpack_field(cmg_level *L, int m, int field, int prec, void *out);
 void fill_ghosts(cmg_level *L);
 void get_ghosts(cmg_level *L, double *out);
 void ensure_fp32(cmg_level *L);
+// pcg.cu (and the V-cycle it preconditions with, solve.cu)
+void vcycle64_from_zero(cmg_level *L, const cmg_solve_params *p, int64_t *updates);
+void pcg_solve(cmg_level *L, const cmg_solve_params *p, cmg_solve_stats &S);
 // fft.cu
 bool fft_supported(const cmg_level *L);
 void fft_prepare(cmg_level *L);

@@ -231,6 +231,7 @@ void fill_stats(cmg_level *L, cmg_solve_stats &S, int64_t updates_per_cycle) {
 bool same_params(const cmg_solve_params &a, const cmg_solve_params &b) {
   return a.tol == b.tol && a.max_cycles == b.max_cycles && a.n_pre == b.n_pre && a.n_post == b.n_post &&
          a.coarse_sweeps == b.coarse_sweeps && a.fixed_cycles == b.fixed_cycles && a.precision == b.precision &&
+         a.krylov == b.krylov &&
          a.inner_cycles == b.inner_cycles;
 }
 
@@ -326,8 +327,10 @@ int solve(cmg_level *L, const cmg_solve_params *p, cmg_solve_stats *st) {
   if (!p || p->n_pre < 0 || p->n_post < 0 || p->coarse_sweeps < 0 || p->max_cycles < 0 || p->max_cycles > 256 ||
       p->fixed_cycles < 0 || p->fixed_cycles > 256 || !(p->tol >= 0.0) ||
       (p->precision != CMG_PREC_FP64 && p->precision != CMG_PREC_MIXED && p->precision != CMG_PREC_FFT) ||
-      (p->precision == CMG_PREC_MIXED && p->inner_cycles < 1))
+      (p->precision == CMG_PREC_MIXED && p->inner_cycles < 1) || (p->krylov != 0 && p->krylov != 1))
     throw Error(CMG_ERR_INVALID_ARG, "invalid solve parameters");
+  if (p->krylov == 1 && p->precision != CMG_PREC_FP64)
+    throw Error(CMG_ERR_INVALID_ARG, "the CG outer iteration runs in FP64 only");
   if (L->periodic_full && L->nx != 1)
     throw Error(CMG_ERR_INVALID_ARG, "periodic base levels need n_x = 1 (exact 2^3 coarsest solve)");
   if (p->precision == CMG_PREC_MIXED && L->mg.size() < 2)
@@ -347,6 +350,10 @@ int solve(cmg_level *L, const cmg_solve_params *p, cmg_solve_stats *st) {
   if (L->n == 0) {
     S.status = CMG_OK;
     return CMG_OK;
+  }
+  if (p->krylov == 1) {
+    pcg_solve(L, p, S);
+    return S.status;
   }
   CMG_CUDA(cudaEventRecord(ctx->ev0, ctx->stream));
   int64_t updates_per_cycle = 0;
