@@ -313,6 +313,12 @@ CachedGraph *build_graph(cmg_level *L, const cmg_solve_params *p) {
 
 }  // namespace
 
+// One FP64 V-cycle from zero on the level's right-hand side (the CG
+// preconditioner, pcg.cu).
+void vcycle64_from_zero(cmg_level *L, const cmg_solve_params *p, int64_t *updates) {
+  vcycle<double>(L, 0, p, true, updates);
+}
+
 void destroy_graphs(cmg_level *L) {
   for (void *v : L->graphs) {
     auto *cg = static_cast<CachedGraph *>(v);
