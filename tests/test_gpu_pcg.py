@@ -4,9 +4,10 @@ oracle's PCG on the same inputs.
 Both run the same flexible CG with one V-cycle per iteration as the
 preconditioner; only the order of the floating-point reductions differs,
 which perturbs alpha and beta at the 1e-16 level.  So iteration histories
-agree to 1e-9 relative, phi after a fixed number of iterations to 1e-11 and
-converged phi to the FP64 bar (1e-12 relative, plus the 1e-13 stopping
-residual's own spread)."""
+agree to 1e-9 relative above an absolute floor of 1e-15 (a relative residual
+near 1e-13 carries the reductions' rounding, ~1e-16 of the initial norm),
+phi after a fixed number of iterations to 1e-11 and converged phi to the
+FP64 bar (1e-12 relative, plus the stopping residual's own spread)."""
 import numpy as np
 import pytest
 
@@ -48,7 +49,7 @@ def test_pcg_periodic_matches_oracle_and_exact(cmg, ctx):
     rc, st = cmg.cmg_level_solve(G, tol=1e-12, krylov=1)
     ro, so = R.solve_pcg(tol=1e-12)
     assert st["cycles"] == so["cycles"]
-    np.testing.assert_allclose(st["rel_history"], so["rel_history"], rtol=1e-9)
+    np.testing.assert_allclose(st["rel_history"], so["rel_history"], rtol=1e-9, atol=1e-15)
     phi = cmg.cmg_level_get_phi(G)
     assert relerr(phi, R.get_phi()) <= 1e-12
     f = inputs.octs_to_dense(cfg["rho"][0] - 1.0, coords, 32)
@@ -72,7 +73,7 @@ def test_pcg_refined_level_matches_oracle(cmg, ctx, base):
     # a fixed number of iterations
     rc, st = cmg.cmg_level_solve(GF, fixed_cycles=3, krylov=1)
     ro, so = RF.solve_pcg(fixed_cycles=3)
-    np.testing.assert_allclose(st["rel_history"], so["rel_history"], rtol=1e-9)
+    np.testing.assert_allclose(st["rel_history"], so["rel_history"], rtol=1e-9, atol=1e-15)
     assert relerr(cmg.cmg_level_get_phi(GF), RF.get_phi()) <= 1e-11
     # converged, from zero on both sides
     z = np.zeros((RF.n, 8))
