@@ -344,6 +344,28 @@ def bench_fft(cmg, ctx, dev, B, rho_b, args, peaks):
     return res
 
 
+def bench_pcg(cmg, ctx, dev, levels, args):
+    """Time to rel. residual tol of the two-level workload's levels from
+    phi = 0: the stationary V-cycle iteration (one CUDA graph) against
+    V-cycle-preconditioned CG (one host synchronisation per iteration)."""
+    import torch
+    out = {}
+    for name, L, rho in levels:
+        z = torch.zeros_like(rho)
+        cmg.cmg_level_set_density(L, rho, 1.0)
+        r = {}
+        for kind, kr in (("vcycle", 0), ("pcg", 1)):
+            ms = []
+            for _ in range(6):
+                cmg.cmg_level_set_phi(L, z)
+                rc, st = cmg.cmg_level_solve(L, tol=args.tol, krylov=kr)
+                ms.append(st["ms"])
+            r[kind] = {"ms_to_tol": statistics.median(ms[1:]), "iterations": st["cycles"],
+                       "rel_final": st["rel_final"]}
+        out[name] = r
+    return out
+
+
 def bench_forward(cmg, ctx, dev, peaks, D=64, batches=(1, 8), reps=20, paths=("tcgen05", "mma_sync")):
     """The U-Net forward alone on random inputs (untrained He-normal weights):
     device time per call and the convolutions' tensor-core rate."""
@@ -690,6 +712,7 @@ def run_ours(args, rank, local, world):
         out["batched"] = bench_batched(cmg, ctx, dev, stream, args)
         out["smoother_512"] = bench_smoother(cmg, ctx, dev, peaks)
         out["fft"] = bench_fft(cmg, ctx, dev, B, rho[0], args, peaks)
+        out["pcg"] = bench_pcg(cmg, ctx, dev, (("base", B, rho[0]), ("fine", F, rho[1])), args)
         if not args.no_learned:
             out["learned"] = bench_learned(cmg, ctx, dev, args, peaks)
         if rank == 0 and world == 1:
