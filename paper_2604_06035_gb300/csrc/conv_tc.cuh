@@ -181,6 +181,20 @@ struct ConvGeom {
   }
 };
 
+// Optional work of a forward convolution's epilogue (nullptr = off):
+//   pool  the 2x2x2 mean of the (bf16-rounded) outputs on the D/2 grid,
+//         N <= 32 and ZB even (both z slices of a pair are in the thread,
+//         the x / y partners are lanes ^1 / ^8 of the warp);
+//   hw    the linear head (N = 16): delta = hb + sum_c out_c hw_c,
+//         pred = base + norm[3 sample + 2] delta (float fields [B][D^3]);
+//         with store_out = 0 the activations themselves are not written.
+struct ConvEpi {
+  __nv_bfloat16 *pool = nullptr;
+  const float *hw = nullptr, *base = nullptr, *norm = nullptr;
+  float *delta = nullptr, *pred = nullptr;
+  int store_out = 1;
+};
+
 // Barriers:
 //   full[s]     halo of stage s landed (128 producer arrivals)
 //   empty[s]    MMAs that read stage s done (tcgen05.commit of its issuer)
@@ -200,7 +214,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __nv_bfloat16
                                                             const __nv_bfloat16 *__restrict__ wimg,
                                                             const float *__restrict__ bias,
                                                             __nv_bfloat16 *__restrict__ out, int D, int total_bricks,
-                                                            int *__restrict__ err) {
+                                                            int *__restrict__ err, const ConvEpi ep) {
   using G = ConvGeom<N, ZB>;
   constexpr int SIGN = FWD ? 1 : -1;
   constexpr bool STACK = G::kStack;
@@ -342,6 +356,74 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __nv_bfloat16
       // the ZB accumulators are ZB * N consecutive columns; 32 per wait
       const uint32_t acc0 = set + (STACK ? 2 * N : 0);
       const int64_t vbase = (int64_t)sample * D * D * D + (int64_t)y * D + x;
+      if constexpr (FWD && N <= 32) {
+        if (ep.pool != nullptr || ep.hw != nullptr) {
+          // per z slice: all N columns, bias + ReLU + bf16 rounding, then
+          // the optional pooling (pairs of slices) and head
+          float keep[N];
+          const int Dh = D >> 1;
+#pragma unroll 1
+          for (int zz = 0; zz < ZB; ++zz) {
+            float v[N];
+#pragma unroll
+            for (int c0 = 0; c0 < N; c0 += 16) tmem_ld16_nowait(acc0 + zz * N + c0, v + c0);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int z = bz * ZB + zz;
+            const int64_t vox = vbase + (int64_t)z * D * D;
+#pragma unroll
+            for (int c0 = 0; c0 < N; c0 += 16) {
+              __align__(16) __nv_bfloat162 o[8];
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                o[q] = __floats2bfloat162_rn(fmaxf(v[c0 + 2 * q] + __ldg(bias + c0 + 2 * q), 0.f),
+                                             fmaxf(v[c0 + 2 * q + 1] + __ldg(bias + c0 + 2 * q + 1), 0.f));
+                v[c0 + 2 * q] = __low2float(o[q]);
+                v[c0 + 2 * q + 1] = __high2float(o[q]);
+              }
+              if (ep.store_out) {
+                __nv_bfloat16 *dst = out + vox * N + c0;
+                reinterpret_cast<uint4 *>(dst)[0] = reinterpret_cast<const uint4 *>(o)[0];
+                reinterpret_cast<uint4 *>(dst)[1] = reinterpret_cast<const uint4 *>(o)[1];
+              }
+            }
+            if (N == 16 && ep.hw != nullptr) {
+              float dlt = __ldg(ep.hw + 16);  // the head's bias
+#pragma unroll
+              for (int c = 0; c < 16; ++c) dlt = fmaf(v[c], __ldg(ep.hw + c), dlt);
+              ep.delta[vox] = dlt;
+              if (ep.pred) ep.pred[vox] = ep.base[vox] + ep.norm[3 * sample + 2] * dlt;
+            }
+            if (ep.pool != nullptr) {
+              if ((zz & 1) == 0) {
+#pragma unroll
+                for (int c = 0; c < N; ++c) keep[c] = v[c];
+              } else {
+                const bool writer = (lane & 1) == 0 && (lane & 8) == 0;
+                __nv_bfloat16 *pdst =
+                    ep.pool + (((int64_t)sample * Dh + (z >> 1)) * Dh * Dh + (int64_t)(y >> 1) * Dh + (x >> 1)) * N;
+#pragma unroll
+                for (int c0 = 0; c0 < N; c0 += 16) {
+                  __align__(16) __nv_bfloat162 o[8];
+#pragma unroll
+                  for (int q = 0; q < 8; ++q) {
+                    float a = keep[c0 + 2 * q] + v[c0 + 2 * q], b2 = keep[c0 + 2 * q + 1] + v[c0 + 2 * q + 1];
+                    a += __shfl_xor_sync(0xffffffffu, a, 1);
+                    b2 += __shfl_xor_sync(0xffffffffu, b2, 1);
+                    a += __shfl_xor_sync(0xffffffffu, a, 8);
+                    b2 += __shfl_xor_sync(0xffffffffu, b2, 8);
+                    o[q] = __floats2bfloat162_rn(a * 0.125f, b2 * 0.125f);
+                  }
+                  if (writer) {
+                    reinterpret_cast<uint4 *>(pdst + c0)[0] = reinterpret_cast<const uint4 *>(o)[0];
+                    reinterpret_cast<uint4 *>(pdst + c0)[1] = reinterpret_cast<const uint4 *>(o)[1];
+                  }
+                }
+              }
+            }
+          }
+          goto epilogue_done;
+        }
+      }
 #pragma unroll 1
       for (int col0 = 0; col0 < ZB * N; col0 += 32) {
         const int ng = (ZB * N - col0) >= 32 ? 2 : 1;  // 16-column groups in this chunk
@@ -368,6 +450,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __nv_bfloat16
           reinterpret_cast<uint4 *>(dst)[1] = reinterpret_cast<const uint4 *>(o)[1];
         }
       }
+    epilogue_done:
       if (STACK) {
         // zero the whole set (scratch slices included) for its next brick
         for (int c0 = 0; c0 < G::kAccCols; c0 += 16) tmem_st16_zero(set + c0);

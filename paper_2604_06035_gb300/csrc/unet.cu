@@ -530,7 +530,7 @@ using bf16 = __nv_bfloat16;
 
 template <int N, int ZB, bool FWD>
 void conv_tc_launch(cmg_unet *U, const bf16 *in, int K, const bf16 *skip, int Cb, const bf16 *WI, const float *bias,
-                    bf16 *out, int D, int B) {
+                    bf16 *out, int D, int B, const tc::ConvEpi &ep) {
   using G = tc::ConvGeom<N, ZB>;
   static int attr_dev = -1;
   if (attr_dev != U->ctx->device) {
@@ -542,7 +542,7 @@ void conv_tc_launch(cmg_unet *U, const bf16 *in, int K, const bf16 *skip, int Cb
   const int grid = std::min(total, U->ctx->num_sms);
   LaunchScope ls(U->ctx, FWD ? K_CONV_FWD : K_CONV_DGRAD, 0.0, 2.0 * 27 * K * N * (double)D * D * D * B);
   tc::k_conv_tc<N, ZB, FWD><<<grid, tc::kConvThreads, G::smem_bytes(K), U->ctx->stream>>>(in, K, skip, Cb, WI, bias, out,
-                                                                                     D, total, U->d_err);
+                                                                                     D, total, U->d_err, ep);
   CMG_CUDA(cudaGetLastError());
 }
 
@@ -566,19 +566,24 @@ bool tc_eligible(const cmg_unet *U, int N, int D) {
 }
 
 // Deep bricks (ZB = 8 for N = 16, 4 for N = 32, 2 above) when they still
-// give every SM a brick, else one-slice bricks.
-void conv_tc(cmg_unet *U, const bf16 *in, int K, const bf16 *skip, int Cb, const bf16 *WI, const float *bias,
-             bf16 *out, int N, int D, int B, bool fwd) {
+// give every SM a brick, else one-slice bricks.  The epilogue extras need
+// N <= 32 (head: N = 16), and the pooling also needs the deep (even) ZB:
+// returns whether ep.pool was done (else the caller pools separately).
+bool conv_tc(cmg_unet *U, const bf16 *in, int K, const bf16 *skip, int Cb, const bf16 *WI, const float *bias,
+             bf16 *out, int N, int D, int B, bool fwd, tc::ConvEpi ep = tc::ConvEpi()) {
   const int zb = N == 16 ? 8 : N == 32 ? 4 : 2;
   const bool deep = (D / 8) * (D / 16) * (D / zb) * B >= U->ctx->num_sms;
+  const bool pooled = ep.pool != nullptr && deep && N <= 32;
+  tc::ConvEpi e = ep;
+  if (!pooled) e.pool = nullptr;
 #define CMG_CONV_TC(NN, ZB)                                                                           \
   case NN:                                                                                            \
     if (deep) {                                                                                       \
-      if (fwd) conv_tc_launch<NN, ZB, true>(U, in, K, skip, Cb, WI, bias, out, D, B);                 \
-      else conv_tc_launch<NN, ZB, false>(U, in, K, nullptr, 0, WI, nullptr, out, D, B);               \
+      if (fwd) conv_tc_launch<NN, ZB, true>(U, in, K, skip, Cb, WI, bias, out, D, B, e);              \
+      else conv_tc_launch<NN, ZB, false>(U, in, K, nullptr, 0, WI, nullptr, out, D, B, e);            \
     } else {                                                                                          \
-      if (fwd) conv_tc_launch<NN, 1, true>(U, in, K, skip, Cb, WI, bias, out, D, B);                  \
-      else conv_tc_launch<NN, 1, false>(U, in, K, nullptr, 0, WI, nullptr, out, D, B);                \
+      if (fwd) conv_tc_launch<NN, 1, true>(U, in, K, skip, Cb, WI, bias, out, D, B, e);               \
+      else conv_tc_launch<NN, 1, false>(U, in, K, nullptr, 0, WI, nullptr, out, D, B, e);             \
     }                                                                                                 \
     break;
   switch (N) {
@@ -590,6 +595,7 @@ void conv_tc(cmg_unet *U, const bf16 *in, int K, const bf16 *skip, int Cb, const
     default: throw Error(CMG_ERR_INVALID_ARG, "unsupported channel count");
   }
 #undef CMG_CONV_TC
+  return pooled;
 }
 
 // Convolution of layer l: forward (in = activations, N = cout) or input
@@ -705,12 +711,25 @@ void forward(cmg_unet *U, int B, float *phi_pred, bool training) {
     const LayerSpec &L = kLayers[l];
     conv(U, l, in, L.cin, bias_of(U, l), out, L.cout, dim_of(U, L.lvl), B, true);
   };
+  // encoder convolution + 2x2x2 pooling (fused into the tcgen05 epilogue
+  // where the bricks allow it)
+  auto layer_pool = [&](int l, const bf16 *in, bf16 *out, bf16 *pooled) {
+    const LayerSpec &L = kLayers[l];
+    const int D = dim_of(U, L.lvl);
+    bool done = false;
+    if (tc_eligible(U, L.cout, D)) {
+      tc::ConvEpi ep;
+      ep.pool = pooled;
+      done = conv_tc(U, in, L.cin, nullptr, 0, U->WI[l], bias_of(U, l), out, L.cout, D, B, true, ep);
+    } else {
+      layer(l, in, out);
+    }
+    if (!done) k_pool<<<gsz(B * (int64_t)(D / 2) * (D / 2) * (D / 2) * L.cout), 256, 0, s>>>(out, D, L.cout, B, pooled);
+  };
   layer(0, U->x, U->a[0]);
-  layer(1, U->a[0], U->a[1]);  // s0
-  k_pool<<<gsz(B * vox(U, 1) * 16), 256, 0, s>>>(U->a[1], D0, 16, B, U->p0);
+  layer_pool(1, U->a[0], U->a[1], U->p0);  // s0
   layer(2, U->p0, U->a[2]);
-  layer(3, U->a[2], U->a[3]);  // s1
-  k_pool<<<gsz(B * vox(U, 2) * 32), 256, 0, s>>>(U->a[3], D1, 32, B, U->p1);
+  layer_pool(3, U->a[2], U->a[3], U->p1);  // s1
   layer(4, U->p1, U->a[4]);
   layer(5, U->a[4], U->a[5]);
   // decoder convolutions: in inference the tcgen05 kernels read the
@@ -729,9 +748,21 @@ void forward(cmg_unet *U, int B, float *phi_pred, bool training) {
   up_layer(6, U->a[5], 64, U->a[3], 32, U->c1, U->a[6]);
   layer(7, U->a[6], U->a[7]);
   up_layer(8, U->a[7], 32, U->a[1], 16, U->c0, U->a[8]);
-  layer(9, U->a[8], U->a[9]);
   const float *hw = U->params + layer_offset(10);
-  k_head<<<gsz(B * V0), 256, 0, s>>>(U->a[9], hw, hw + 16, U->in_base, U->norm, V0, B, U->delta, phi_pred);
+  if (!training && tc_eligible(U, 16, D0)) {
+    // last convolution + head in one kernel; its activations are not kept
+    tc::ConvEpi ep;
+    ep.hw = hw;
+    ep.base = U->in_base;
+    ep.norm = U->norm;
+    ep.delta = U->delta;
+    ep.pred = phi_pred;
+    ep.store_out = 0;
+    conv_tc(U, U->a[8], 16, nullptr, 0, U->WI[9], bias_of(U, 9), U->a[9], 16, D0, B, true, ep);
+  } else {
+    layer(9, U->a[8], U->a[9]);
+    k_head<<<gsz(B * V0), 256, 0, s>>>(U->a[9], hw, hw + 16, U->in_base, U->norm, V0, B, U->delta, phi_pred);
+  }
   CMG_CUDA(cudaGetLastError());
   (void)D2;
 }

@@ -72,6 +72,27 @@ def test_forward_matches_reference(cmg, ctx, D):
     assert np.array_equal(cmg.cmg_unet_get_params(net), p)
 
 
+def test_forward_fused_epilogues_batch4_64(cmg, ctx):
+    """8 x 8 x 16 deep bricks at 64^3 with a batch of 4: the pooling of both
+    encoder levels and the head run inside the tcgen05 epilogues; every
+    sample against the reference network."""
+    D, B = 64, 4
+    net = cmg.cmg_unet_create(ctx, D, B)
+    p = _params(31)
+    cmg.cmg_unet_set_params(net, p)
+    samples = [_sample(D, 40 + b) for b in range(B)]
+    rho = np.stack([smp[0] for smp in samples])
+    phi = np.stack([smp[1] for smp in samples])
+    base = (phi * 0.5 + 0.25).astype(np.float32)
+    pred, delta = cmg.cmg_unet_forward(net, rho, phi, base=base, delta=True)
+    p64 = p.astype(np.float64)
+    for b in range(B):
+        ref_d, ref_pred, _ = U.forward(p64, rho[b].astype(np.float64), phi[b].astype(np.float64),
+                                       base[b].astype(np.float64), bf=True)
+        assert _rel(delta[b], ref_d) <= 1e-2, b
+        assert _rel(pred[b] - base[b], ref_pred - base[b]) <= 1e-2, b
+
+
 def _layer_slices():
     out, o = [], 0
     for name, ci, co, _ in U.LAYERS:
