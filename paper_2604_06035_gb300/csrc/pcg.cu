@@ -12,8 +12,10 @@
 // periodic level z is projected to zero mean (the operator's null space).
 // Everything is FP64 and in the solver's pre-scaled units (d = -h^2 r / 6;
 // the iteration is invariant to that scale).  Dot products are per-block
-// partial sums reduced in a fixed order (deterministic).  One host
-// synchronisation per iteration reads the residual norm for the stop test.
+// partial sums reduced in a fixed order (deterministic), alpha and beta are
+// formed on the device, and the iteration runs as the set-up / body /
+// wrap-up segments of the level solve's CUDA graph (solve.cu): the residual
+// norm goes to the same control block as the stationary iteration's.
 #include <cmath>
 
 #include "cmg_internal.cuh"
@@ -164,112 +166,133 @@ __global__ void k_pcg_reduce(const double *__restrict__ part, int np, double *__
 }
 
 // scalars: sc[0] (z, r), sc[1] (z, ro), sc[2] previous (z, r), sc[3] beta,
-// sc[4] (p, q), sc[5] alpha, sc[6] (r, r)
-__global__ void k_pcg_beta(double *sc, int first) {
-  sc[3] = first ? 0.0 : (sc[0] - sc[1]) / sc[2];
+// sc[4] (p, q), sc[5] alpha, sc[6] (r, r), sc[7] first-iteration flag
+__global__ void k_pcg_beta(double *sc) {
+  sc[3] = sc[7] != 0.0 ? 0.0 : (sc[0] - sc[1]) / sc[2];
   sc[2] = sc[0];
+  sc[7] = 0.0;
 }
 __global__ void k_pcg_alpha(double *sc) { sc[5] = sc[2] / sc[4]; }
+// the solve control reads ||r||^2 in source units from scal[2]
+__global__ void k_pcg_norm_out(double *sc, double d2f, double *scal2) {
+  *scal2 = sc[6] * d2f;
+}
+__global__ void k_pcg_first(double *sc) { sc[7] = 1.0; }
+
+struct PcgView {
+  double *x, *r, *ro, *pd, *q, *gsave, *part, *sc;
+  int64_t n, ps, nv;
+  unsigned nb;
+};
+
+PcgView view(cmg_level *L) {
+  MgLev &g = L->mg[0];
+  PcgView v;
+  v.n = g.n;
+  v.ps = g.n_alloc * 4;
+  v.nv = 8 * g.n_alloc;
+  v.nb = blocks_for(g.n, kPcgThreads);
+  v.x = L->pcg;
+  v.r = v.x + v.nv;
+  v.ro = v.r + v.nv;
+  v.pd = v.ro + v.nv;
+  v.q = v.pd + v.nv;
+  v.gsave = v.q + v.nv;
+  v.part = v.gsave + v.nv;
+  v.sc = v.part + 2 * v.nb;
+  return v;
+}
+
+double d2f_of(const cmg_level *L) {
+  const double h = L->mg[0].h;
+  return 36.0 / (h * h * h * h);  // squared pre-scaled norms -> source units
+}
 
 }  // namespace
 
-void pcg_solve(cmg_level *L, const cmg_solve_params *p, cmg_solve_stats &S) {
+void pcg_prepare(cmg_level *L) {
+  if (L->pcg) return;
   MgLev &g = L->mg[0];
-  cmg_ctx *ctx = L->ctx;
-  cudaStream_t s = ctx->stream;
-  const int64_t n = g.n, ps = g.n_alloc * 4, nv = 8 * g.n_alloc;
-  const unsigned nb = blocks_for(n, kPcgThreads);
-  if (!L->pcg) {
-    // x, r, ro, p, q, saved right-hand side; partials; scalars
-    L->pcg = L->mem.alloc<double>(6 * nv + 2 * (int64_t)nb + 16, true, s);
-  }
-  double *x = L->pcg, *r = x + nv, *ro = r + nv, *pd = ro + nv, *q = pd + nv, *gsave = q + nv;
-  double *part = gsave + nv, *sc = part + 2 * nb;
-  const double h = g.h, d2f = 36.0 / (h * h * h * h);  // squared d-unit norms -> source units
-  CMG_CUDA(cudaEventRecord(ctx->ev0, s));
+  const int64_t nv = 8 * g.n_alloc;
+  const unsigned nb = blocks_for(g.n, kPcgThreads);
+  // x, r, ro, p, q, saved right-hand side; partials; scalars
+  L->pcg = L->mem.alloc<double>(6 * nv + 2 * (int64_t)nb + 16, true, L->ctx->stream);
+  CMG_CUDA(cudaStreamSynchronize(L->ctx->stream));
+}
+
+// Set-up (inside the solve graph): ghosts, ||f - L 0||^2 into scal[0], the
+// true residual r0 (also the first right-hand side of the preconditioner)
+// with ||r0||^2 into scal[2], x = phi, p = 0, ghost octs of phi cleared.
+void pcg_pre(cmg_level *L) {
+  MgLev &g = L->mg[0];
+  cudaStream_t s = L->ctx->stream;
+  const PcgView v = view(L);
   fill_ghosts(L);
-  zero_phi_norm(L, L->scal + 0);  // ||f - L 0||^2 (source units) and its root
-  CMG_CUDA(cudaMemcpyAsync(gsave, g.g, sizeof(double) * 8 * n, cudaMemcpyDeviceToDevice, s));
-  CMG_CUDA(cudaMemcpyAsync(x, g.phi, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
-  CMG_CUDA(cudaMemsetAsync(pd, 0, sizeof(double) * nv, s));
+  zero_phi_norm(L, L->scal + 0);
+  CMG_CUDA(cudaMemcpyAsync(v.gsave, g.g, sizeof(double) * 8 * v.n, cudaMemcpyDeviceToDevice, s));
+  CMG_CUDA(cudaMemcpyAsync(v.x, g.phi, sizeof(double) * v.nv, cudaMemcpyDeviceToDevice, s));
+  CMG_CUDA(cudaMemsetAsync(v.pd, 0, sizeof(double) * v.nv, s));
   {
-    LaunchScope ls(ctx, K_RESID64, 8.0 * n * 24.0, 8.0 * n * 9.0);
-    k_pcg_resid<<<nb, kPcgThreads, 0, s>>>(g.nbr, g.phi, g.g, n, ps, r, g.g, part);
+    LaunchScope ls(L->ctx, K_RESID64, 8.0 * v.n * 24.0, 8.0 * v.n * 9.0);
+    k_pcg_resid<<<v.nb, kPcgThreads, 0, s>>>(g.nbr, g.phi, g.g, v.n, v.ps, v.r, g.g, v.part);
   }
-  k_pcg_reduce<<<1, 1024, 0, s>>>(part, (int)nb, sc + 6);
+  {
+    LaunchScope ls(L->ctx, K_REDUCE, 8.0 * v.nb, v.nb);
+    k_pcg_reduce<<<1, 1024, 0, s>>>(v.part, (int)v.nb, v.sc + 6);
+  }
+  k_pcg_norm_out<<<1, 1, 0, s>>>(v.sc, d2f_of(L), L->scal + 2);
+  k_pcg_first<<<1, 1, 0, s>>>(v.sc);
   // corrections see zero coarse-fine values: clear the ghost octs of phi
-  if (g.n_alloc > n) {
-    CMG_CUDA(cudaMemsetAsync(g.phi + 4 * n, 0, sizeof(double) * 4 * (g.n_alloc - n), s));
-    CMG_CUDA(cudaMemsetAsync(g.phi + ps + 4 * n, 0, sizeof(double) * 4 * (g.n_alloc - n), s));
+  if (g.n_alloc > v.n) {
+    CMG_CUDA(cudaMemsetAsync(g.phi + 4 * v.n, 0, sizeof(double) * 4 * (g.n_alloc - v.n), s));
+    CMG_CUDA(cudaMemsetAsync(g.phi + v.ps + 4 * v.n, 0, sizeof(double) * 4 * (g.n_alloc - v.n), s));
   }
   CMG_CUDA(cudaGetLastError());
-  double *h_pin = ctx->h_dpinned;
-  CMG_CUDA(cudaMemcpyAsync(h_pin, L->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
-  CMG_CUDA(cudaMemcpyAsync(h_pin + 1, sc + 6, sizeof(double), cudaMemcpyDeviceToHost, s));
-  CMG_CUDA(cudaStreamSynchronize(s));
-  const double n0 = h_pin[0];
-  S.norm0 = std::sqrt(n0);
-  S.status = CMG_OK;
-  int cycles = 0;
-  int64_t updates = 0, upc = 0;
-  if (n0 > 0.0) {
-    double rel = std::sqrt(h_pin[1] * d2f / n0);
-    S.rel_initial = rel;
-    S.rel_final = rel;
-    const int target = p->fixed_cycles > 0 ? p->fixed_cycles : p->max_cycles;
-    if (!(p->fixed_cycles == 0 && rel <= p->tol)) {
-      S.status = p->fixed_cycles > 0 ? CMG_OK : CMG_ERR_NOT_CONVERGED;
-      for (int it = 1; it <= target; ++it) {
-        upc = 0;
-        vcycle64_from_zero(L, p, &upc);  // z = M r in phi
-        updates += upc;
-        if (L->periodic_full) subtract_mean(L);
-        k_pcg_dots<<<nb, kPcgThreads, 0, s>>>(g.phi, r, ro, n, ps, part);
-        k_pcg_reduce<<<1, 1024, 0, s>>>(part, (int)nb, sc + 0);
-        k_pcg_reduce<<<1, 1024, 0, s>>>(part + nb, (int)nb, sc + 1);
-        k_pcg_beta<<<1, 1, 0, s>>>(sc, it == 1);
-        k_pcg_dir<<<nb, kPcgThreads, 0, s>>>(g.phi, pd, n, ps, sc + 3);
-        {
-          LaunchScope ls(ctx, K_RESID64, 8.0 * n * 16.0, 8.0 * n * 9.0);
-          k_pcg_apply<<<nb, kPcgThreads, 0, s>>>(g.nbr, pd, n, ps, q, part);
-        }
-        k_pcg_reduce<<<1, 1024, 0, s>>>(part, (int)nb, sc + 4);
-        k_pcg_alpha<<<1, 1, 0, s>>>(sc);
-        k_pcg_step<<<nb, kPcgThreads, 0, s>>>(x, pd, r, ro, q, g.g, n, ps, sc + 5, part);
-        k_pcg_reduce<<<1, 1024, 0, s>>>(part, (int)nb, sc + 6);
-        CMG_CUDA(cudaGetLastError());
-        CMG_CUDA(cudaMemcpyAsync(h_pin, sc + 6, sizeof(double), cudaMemcpyDeviceToHost, s));
-        CMG_CUDA(cudaStreamSynchronize(s));
-        rel = std::sqrt(h_pin[0] * d2f / n0);
-        cycles = it;
-        if (it <= 256) S.rel_history[it - 1] = rel;
-        S.rel_final = rel;
-        if (!std::isfinite(rel) || rel > 1e3 * std::max(S.rel_initial, 1.0)) {
-          S.status = CMG_ERR_DIVERGED;
-          break;
-        }
-        if (p->fixed_cycles == 0 && rel <= p->tol) {
-          S.status = CMG_OK;
-          break;
-        }
-      }
-    }
-    CMG_CUDA(cudaMemcpyAsync(g.phi, x, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
-    if (L->periodic_full) subtract_mean(L);
-  } else {
-    CMG_CUDA(cudaMemsetAsync(g.phi, 0, sizeof(double) * 4 * n, s));
-    CMG_CUDA(cudaMemsetAsync(g.phi + ps, 0, sizeof(double) * 4 * n, s));
-    S.rel_initial = S.rel_final = 0.0;
+}
+
+// One CG iteration: z = M r (V-cycle), beta, p, q = L0 p, alpha, x and r
+// updates; ||r||^2 into scal[2] for the control's check.
+void pcg_body(cmg_level *L, const cmg_solve_params *p, int64_t *updates) {
+  MgLev &g = L->mg[0];
+  cudaStream_t s = L->ctx->stream;
+  const PcgView v = view(L);
+  int64_t upc = 0;
+  vcycle64_from_zero(L, p, &upc);  // z = M r in phi
+  *updates += upc;
+  if (L->periodic_full) subtract_mean(L);
+  {
+    LaunchScope ls(L->ctx, K_REDUCE, 8.0 * v.n * 24.0, 8.0 * v.n * 4.0);
+    k_pcg_dots<<<v.nb, kPcgThreads, 0, s>>>(g.phi, v.r, v.ro, v.n, v.ps, v.part);
   }
-  CMG_CUDA(cudaMemcpyAsync(g.g, gsave, sizeof(double) * 8 * n, cudaMemcpyDeviceToDevice, s));
-  fill_ghosts(L);
-  CMG_CUDA(cudaEventRecord(ctx->ev1, s));
-  CMG_CUDA(cudaEventSynchronize(ctx->ev1));
-  float ms = 0.f;
-  CMG_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
-  S.ms = ms;
-  S.cycles = cycles;
-  S.cell_updates = updates;
+  k_pcg_reduce<<<1, 1024, 0, s>>>(v.part, (int)v.nb, v.sc + 0);
+  k_pcg_reduce<<<1, 1024, 0, s>>>(v.part + v.nb, (int)v.nb, v.sc + 1);
+  k_pcg_beta<<<1, 1, 0, s>>>(v.sc);
+  {
+    LaunchScope ls(L->ctx, K_CONVERT, 8.0 * v.n * 24.0, 8.0 * v.n * 2.0);
+    k_pcg_dir<<<v.nb, kPcgThreads, 0, s>>>(g.phi, v.pd, v.n, v.ps, v.sc + 3);
+  }
+  {
+    LaunchScope ls(L->ctx, K_RESID64, 8.0 * v.n * 16.0, 8.0 * v.n * 9.0);
+    k_pcg_apply<<<v.nb, kPcgThreads, 0, s>>>(g.nbr, v.pd, v.n, v.ps, v.q, v.part);
+  }
+  k_pcg_reduce<<<1, 1024, 0, s>>>(v.part, (int)v.nb, v.sc + 4);
+  k_pcg_alpha<<<1, 1, 0, s>>>(v.sc);
+  {
+    LaunchScope ls(L->ctx, K_CONVERT, 8.0 * v.n * 56.0, 8.0 * v.n * 6.0);
+    k_pcg_step<<<v.nb, kPcgThreads, 0, s>>>(v.x, v.pd, v.r, v.ro, v.q, g.g, v.n, v.ps, v.sc + 5, v.part);
+  }
+  k_pcg_reduce<<<1, 1024, 0, s>>>(v.part, (int)v.nb, v.sc + 6);
+  k_pcg_norm_out<<<1, 1, 0, s>>>(v.sc, d2f_of(L), L->scal + 2);
+  CMG_CUDA(cudaGetLastError());
+}
+
+// Wrap-up: phi = x, the source restored, the ghosts refilled.
+void pcg_post(cmg_level *L) {
+  MgLev &g = L->mg[0];
+  cudaStream_t s = L->ctx->stream;
+  const PcgView v = view(L);
+  CMG_CUDA(cudaMemcpyAsync(g.phi, v.x, sizeof(double) * v.nv, cudaMemcpyDeviceToDevice, s));
+  CMG_CUDA(cudaMemcpyAsync(g.g, v.gsave, sizeof(double) * 8 * v.n, cudaMemcpyDeviceToDevice, s));
 }
 
 }  // namespace cmg

@@ -155,6 +155,13 @@ SolveCtrl *ctrl_dev(cmg_level *L) { return reinterpret_cast<SolveCtrl *>(L->ctrl
 void segment_pre(cmg_level *L, const cmg_solve_params *p, cudaGraphConditionalHandle h, int use_handle) {
   cudaStream_t s = L->ctx->stream;
   double *scal = L->scal;
+  if (p->krylov == 1) {
+    pcg_pre(L);
+    LaunchScope ls(L->ctx, K_REDUCE, 64.0, 0.0);
+    k_ctrl_init<<<1, 1, 0, s>>>(ctrl_dev(L), scal, p->tol, p->fixed_cycles, p->max_cycles, h, use_handle);
+    CMG_CUDA(cudaGetLastError());
+    return;
+  }
   fill_ghosts(L);
   zero_phi_norm(L, scal + 0);
   if (p->precision != CMG_PREC_FP64) {
@@ -177,7 +184,9 @@ void segment_body(cmg_level *L, const cmg_solve_params *p, cudaGraphConditionalH
                   int64_t *updates) {
   cudaStream_t s = L->ctx->stream;
   double *scal = L->scal;
-  if (p->precision == CMG_PREC_FP64) {
+  if (p->krylov == 1) {
+    pcg_body(L, p, updates);
+  } else if (p->precision == CMG_PREC_FP64) {
     vcycle<double>(L, 0, p, false, updates);
     resid_restrict<double>(L, 0, false, true, false, scal + 2);
   } else {
@@ -203,8 +212,9 @@ void segment_body(cmg_level *L, const cmg_solve_params *p, cudaGraphConditionalH
   CMG_CUDA(cudaGetLastError());
 }
 
-void segment_post(cmg_level *L) {
+void segment_post(cmg_level *L, const cmg_solve_params *p) {
   MgLev &g = L->mg[0];
+  if (p->krylov == 1) pcg_post(L);
   {
     LaunchScope ls(L->ctx, K_CONVERT, 0.0, 0.0);
     k_zero_if<<<blocks_for(8 * g.n), kThreads, 0, L->ctx->stream>>>(ctrl_dev(L), g.phi, g.n, g.n_alloc);
@@ -283,7 +293,7 @@ CachedGraph *build_graph(cmg_level *L, const cmg_solve_params *p) {
     CMG_CUDA(cudaStreamEndCapture(ctx->stream, &body_out));
     ctx->stream = main_cap;
     ctx->captured = 0;
-    segment_post(L);
+    segment_post(L, p);
     copy_ctrl_to_host(L);
     cg->launches_post = ctx->captured;
     cudaGraph_t out = nullptr;
@@ -349,6 +359,7 @@ int solve(cmg_level *L, const cmg_solve_params *p, cmg_solve_stats *st) {
   cmg_ctx *ctx = L->ctx;
   if (p->precision != CMG_PREC_FP64) ensure_fp32(L);
   if (p->precision == CMG_PREC_FFT) fft_prepare(L);
+  if (p->krylov == 1) pcg_prepare(L);
   if (!L->ctrl) {
     L->ctrl = L->mem.alloc<uint8_t>(sizeof(SolveCtrl), true, ctx->stream);
     CMG_CUDA(cudaMallocHost(&L->h_ctrl, sizeof(SolveCtrl)));
@@ -356,10 +367,6 @@ int solve(cmg_level *L, const cmg_solve_params *p, cmg_solve_stats *st) {
   if (L->n == 0) {
     S.status = CMG_OK;
     return CMG_OK;
-  }
-  if (p->krylov == 1) {
-    pcg_solve(L, p, S);
-    return S.status;
   }
   CMG_CUDA(cudaEventRecord(ctx->ev0, ctx->stream));
   int64_t updates_per_cycle = 0;
@@ -392,7 +399,7 @@ int solve(cmg_level *L, const cmg_solve_params *p, cmg_solve_stats *st) {
       copy_ctrl_to_host(L);
       CMG_CUDA(cudaStreamSynchronize(ctx->stream));
     }
-    segment_post(L);
+    segment_post(L, p);
     copy_ctrl_to_host(L);
     CMG_CUDA(cudaEventRecord(ctx->ev1, ctx->stream));
     CMG_CUDA(cudaEventSynchronize(ctx->ev1));
