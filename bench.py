@@ -47,7 +47,7 @@ def parse():
                     help="trajectories of 8 steps for the learned warm start (1/16 held out)")
     ap.add_argument("--train-seconds", type=float, default=60.0, help="U-Net training budget")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start block")
-    ap.add_argument("--block", choices=["smoother", "learned", "forward", "fft"], default=None,
+    ap.add_argument("--block", choices=["smoother", "learned", "forward", "fft", "pcg"], default=None,
                     help="run one sub-benchmark alone and print its JSON (profiling runs)")
     ap.add_argument("--smoother-level", type=int, default=9, help="level of the full periodic grid (9 = 512^3)")
     ap.add_argument("--fwd-batches", default="1,8", help="batch sizes of --block forward")
@@ -346,8 +346,8 @@ def bench_fft(cmg, ctx, dev, B, rho_b, args, peaks):
 
 def bench_pcg(cmg, ctx, dev, levels, args):
     """Time to rel. residual tol of the two-level workload's levels from
-    phi = 0: the stationary V-cycle iteration (one CUDA graph) against
-    V-cycle-preconditioned CG (one host synchronisation per iteration)."""
+    phi = 0: the stationary V-cycle iteration against V-cycle-preconditioned
+    CG, each one CUDA graph with the stop test on the device."""
     import torch
     out = {}
     for name, L, rho in levels:
@@ -362,6 +362,14 @@ def bench_pcg(cmg, ctx, dev, levels, args):
                 ms.append(st["ms"])
             r[kind] = {"ms_to_tol": statistics.median(ms[1:]), "iterations": st["cycles"],
                        "rel_final": st["rel_final"]}
+            # the same solve launch by launch, for the per-kernel-family split
+            cmg.cmg_level_set_phi(L, z)
+            cmg.cmg_ctx_reset_profile(ctx)
+            cmg.cmg_ctx_set_profiling(ctx, True)
+            cmg.cmg_level_solve(L, tol=args.tol, krylov=kr)
+            cmg.cmg_ctx_set_profiling(ctx, False)
+            r[kind]["kernel_ms"] = {k: round(v["ms"], 4) for k, v in cmg.cmg_ctx_get_profile(ctx).items()
+                                    if v["launches"]}
         out[name] = r
     return out
 
@@ -746,6 +754,16 @@ def run_block(args):
         cfg = inputs.two_level_amr(base_level=7, seed=2)
         B = cmg.cmg_level_build(ctx, 7, cmg.cmg_morton_encode(ctx, torch.from_numpy(cfg["coords"][0]).to(dev)))
         out = bench_fft(cmg, ctx, dev, B, torch.from_numpy(cfg["rho"][0]).to(dev), args, peaks)
+        cmg.cmg_level_destroy(B)
+    elif args.block == "pcg":
+        from paper_2604_06035_gb300 import inputs
+        cfg = inputs.two_level_amr(base_level=7, seed=2)
+        cs = [torch.from_numpy(c).to(dev) for c in cfg["coords"]]
+        rs = [torch.from_numpy(r).to(dev) for r in cfg["rho"]]
+        B = cmg.cmg_level_build(ctx, 7, cmg.cmg_morton_encode(ctx, cs[0]))
+        F = cmg.cmg_level_build(ctx, 8, cmg.cmg_morton_encode(ctx, cs[1]), parent=B)
+        out = bench_pcg(cmg, ctx, dev, (("base", B, rs[0]), ("fine", F, rs[1])), args)
+        cmg.cmg_level_destroy(F)
         cmg.cmg_level_destroy(B)
     elif args.block == "forward":
         out = bench_forward(cmg, ctx, dev, peaks, batches=[int(b) for b in args.fwd_batches.split(",")],

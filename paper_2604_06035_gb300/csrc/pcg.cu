@@ -6,12 +6,15 @@
 //   r0 = f - L phi0 (true residual, Dirichlet ghosts); z = M r; p = z (first)
 //   loop: q = L0 p; alpha = (r, z) / (p, q); phi += alpha p; r' = r - alpha q;
 //         stop on ||r'||; z' = M r'; beta = (z', r' - r) / (z, r); p = z' + beta p
+// (r' - r = -alpha q, so the numerator is formed as -alpha (z', q) and the old
+// residual is never stored)
 // M = one V-cycle from zero with homogeneous coarse-fine values (the level's
 // own V-cycle, reading its right-hand side array, which holds r during the
 // iteration); L0 = the operator with homogeneous coarse-fine values.  On a
 // periodic level z is projected to zero mean (the operator's null space).
 // Everything is FP64 and in the solver's pre-scaled units (d = -h^2 r / 6;
-// the iteration is invariant to that scale).  Dot products are per-block
+// the iteration is invariant to that scale); r lives in the level's
+// right-hand side array, saved at set-up and restored at wrap-up.  Dot products are per-block
 // partial sums reduced in a fixed order (deterministic), alpha and beta are
 // formed on the device, and the iteration runs as the set-up / body /
 // wrap-up segments of the level solve's CUDA graph (solve.cu): the residual
@@ -57,11 +60,10 @@ __device__ __forceinline__ void block_partial(double v, double *part) {
 }
 
 // r = g + nbsum(phi) / 6 - phi (phi's ghost octs hold the Dirichlet values),
-// written to r (plane stride ps) and to the right-hand side gtop (plane
-// stride 4 n); partial sums of r^2
-__global__ void k_pcg_resid(const int32_t *__restrict__ nbr, const double *__restrict__ phi,
-                            const double *__restrict__ g, int64_t n, int64_t ps, double *__restrict__ r,
-                            double *__restrict__ gtop, double *__restrict__ part) {
+// in place in the right-hand side array g (plane stride 4 n), which holds r
+// for the rest of the iteration; partial sums of r^2
+__global__ void k_pcg_resid(const int32_t *__restrict__ nbr, const double *__restrict__ phi, double *__restrict__ g,
+                            int64_t n, int64_t ps, double *__restrict__ part) {
   double acc = 0.0;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) {
@@ -69,56 +71,76 @@ __global__ void k_pcg_resid(const int32_t *__restrict__ nbr, const double *__res
     for (int c = 0; c < 8; ++c) {
       const int64_t gi = (int64_t)cell_parity(c) * (n * 4) + i * 4 + (c >> 1);
       const double v = fma(nbsum(phi, nbr, n, i, c, ps), 1.0 / 6.0, g[gi]) - phi[at(i, c, ps)];
-      r[at(i, c, ps)] = v;
-      gtop[gi] = v;
+      g[gi] = v;
       acc += v * v;
     }
   }
   block_partial(acc, part);
 }
 
-// q = p - nbsum(p) / 6 (p is zero on the ghost and zero octs); partial (p, q)
-__global__ void k_pcg_apply(const int32_t *__restrict__ nbr, const double *__restrict__ p, int64_t n, int64_t ps,
-                            double *__restrict__ q, double *__restrict__ part) {
+// The two direction buffers alternate: sc[8] names the one written this
+// iteration.
+__device__ __forceinline__ int cur_dir(const double *sc) { return sc[8] != 0.0 ? 1 : 0; }
+
+// p = z + beta p_old (into the other direction buffer) and q = p - nbsum(p) / 6,
+// the neighbours' p formed on the fly from z and p_old exactly as their owners
+// form it (z and p_old are zero on the ghost and zero octs); partial (p, q)
+__global__ void k_pcg_dir_apply(const int32_t *__restrict__ nbr, const double *__restrict__ z, double *P0,
+                                double *P1, int64_t n, int64_t ps, const double *__restrict__ sc,
+                                double *__restrict__ q, double *__restrict__ part) {
   double acc = 0.0;
+  const double b = sc[3];
+  const int cur = cur_dir(sc);
+  double *__restrict__ pn = cur ? P1 : P0;
+  const double *__restrict__ po = cur ? P0 : P1;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) {
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-      const double pv = p[at(i, c, ps)];
-      const double v = pv - nbsum(p, nbr, n, i, c, ps) * (1.0 / 6.0);
-      q[at(i, c, ps)] = v;
+      const int64_t k = at(i, c, ps);
+      const double pv = fma(b, po[k], z[k]);
+      double s = 0.0;
+#pragma unroll
+      for (int d = 0; d < 6; ++d) {
+        const int a = d >> 1, side = d & 1, c2 = c ^ (1 << a);
+        const int64_t o = (((c >> a) & 1) != side) ? i : (int64_t)nbr[(int64_t)d * n + i];
+        const int64_t k2 = at(o, c2, ps);
+        s += fma(b, po[k2], z[k2]);
+      }
+      const double v = pv - s * (1.0 / 6.0);
+      pn[k] = pv;
+      q[k] = v;
       acc += pv * v;
     }
   }
   block_partial(acc, part);
 }
 
-// x += alpha p; ro = r; r -= alpha q; gtop = r; partial (r, r)
-__global__ void k_pcg_step(double *__restrict__ x, const double *__restrict__ p, double *__restrict__ r,
-                           double *__restrict__ ro, const double *__restrict__ q, double *__restrict__ gtop, int64_t n,
-                           int64_t ps, const double *__restrict__ alpha, double *__restrict__ part) {
+// x += alpha p; r -= alpha q (r in the right-hand side array); partial (r, r)
+__global__ void k_pcg_step(double *__restrict__ x, const double *P0, const double *P1, double *__restrict__ r,
+                           const double *__restrict__ q, int64_t n, int64_t ps, const double *__restrict__ sc,
+                           double *__restrict__ part) {
   double acc = 0.0;
-  const double a = *alpha;
+  const double a = sc[5];
+  const double *__restrict__ p = cur_dir(sc) ? P1 : P0;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) {
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int64_t k = at(i, c, ps);
+      const int64_t gi = (int64_t)cell_parity(c) * (n * 4) + i * 4 + (c >> 1);
       x[k] += a * p[k];
-      const double rv = r[k];
-      ro[k] = rv;
-      const double nv = rv - a * q[k];
-      r[k] = nv;
-      gtop[(int64_t)cell_parity(c) * (n * 4) + i * 4 + (c >> 1)] = nv;
+      const double nv = r[gi] - a * q[k];
+      r[gi] = nv;
       acc += nv * nv;
     }
   }
   block_partial(acc, part);
 }
 
-// partial (z, r) into part[b], (z, ro) into part[nb + b]
-__global__ void k_pcg_dots(const double *__restrict__ z, const double *__restrict__ r, const double *__restrict__ ro,
+// partial (z, r) into part[b], (z, q) into part[nb + b]; q is the previous
+// iteration's L0 p, so that r' - r = -alpha q
+__global__ void k_pcg_dots(const double *__restrict__ z, const double *__restrict__ r, const double *__restrict__ q,
                            int64_t n, int64_t ps, double *__restrict__ part) {
   double a = 0.0, b = 0.0;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -126,8 +148,9 @@ __global__ void k_pcg_dots(const double *__restrict__ z, const double *__restric
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int64_t k = at(i, c, ps);
-      a += z[k] * r[k];
-      b += z[k] * ro[k];
+      const double zv = z[k];
+      a += zv * r[(int64_t)cell_parity(c) * (n * 4) + i * 4 + (c >> 1)];
+      b += zv * q[k];
     }
   }
   block_partial(a, part);
@@ -135,23 +158,10 @@ __global__ void k_pcg_dots(const double *__restrict__ z, const double *__restric
   block_partial(b, part + gridDim.x);
 }
 
-// p = z + beta p
-__global__ void k_pcg_dir(const double *__restrict__ z, double *__restrict__ p, int64_t n, int64_t ps,
-                          const double *__restrict__ beta) {
-  const double b = *beta;
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) {
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int64_t k = at(i, c, ps);
-      p[k] = z[k] + b * p[k];
-    }
-  }
-}
-
-// out = sum of part[0..np) in a fixed order (one block)
-__global__ void k_pcg_reduce(const double *__restrict__ part, int np, double *__restrict__ out) {
+// sum of part[0..np) in a fixed order, on all threads of a one-block launch
+__device__ double block_sum(const double *__restrict__ part, int np) {
   __shared__ double ws[32];
+  __shared__ double total;
   double v = 0.0;
   for (int t = threadIdx.x; t < np; t += blockDim.x) v += part[t];
 #pragma unroll
@@ -161,26 +171,52 @@ __global__ void k_pcg_reduce(const double *__restrict__ part, int np, double *__
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += ws[w];
-    *out = s;
+    total = s;
+  }
+  __syncthreads();
+  const double r = total;
+  __syncthreads();
+  return r;
+}
+
+// Scalars: sc[0] (z, r), sc[1] (z, q), sc[2] (z, r) of the last beta, sc[3]
+// beta, sc[4] (p, q), sc[5] alpha, sc[6] (r, r), sc[7] first-iteration flag,
+// sc[8] current direction buffer.  The reductions finish into them:
+enum { FIN_BETA, FIN_ALPHA, FIN_NORM, FIN_NORM_FIRST };
+
+// beta = (z', r' - r) / (z, r) = -alpha (z', q) / (z, r) (Polak-Ribiere; 0 on
+// the first iteration); alpha = (z, r) / (p, q); ||r||^2 to the solve control
+// in source units (and, at set-up, the first-iteration flag)
+template <int MODE>
+__global__ void k_pcg_fin(const double *__restrict__ part, int np, double *sc, double d2f, double *scal2) {
+  const double a = block_sum(part, np);
+  if (MODE == FIN_BETA) {
+    const double b = block_sum(part + np, np);
+    if (threadIdx.x == 0) {
+      sc[0] = a;
+      sc[1] = b;
+      sc[3] = sc[7] != 0.0 ? 0.0 : -sc[5] * b / sc[2];
+      sc[2] = a;
+      sc[7] = 0.0;
+      sc[8] = sc[8] != 0.0 ? 0.0 : 1.0;
+    }
+  } else if (threadIdx.x == 0) {
+    if (MODE == FIN_ALPHA) {
+      sc[4] = a;
+      sc[5] = sc[2] / a;
+    } else {
+      sc[6] = a;
+      *scal2 = a * d2f;
+      if (MODE == FIN_NORM_FIRST) {
+        sc[7] = 1.0;
+        sc[8] = 0.0;
+      }
+    }
   }
 }
 
-// scalars: sc[0] (z, r), sc[1] (z, ro), sc[2] previous (z, r), sc[3] beta,
-// sc[4] (p, q), sc[5] alpha, sc[6] (r, r), sc[7] first-iteration flag
-__global__ void k_pcg_beta(double *sc) {
-  sc[3] = sc[7] != 0.0 ? 0.0 : (sc[0] - sc[1]) / sc[2];
-  sc[2] = sc[0];
-  sc[7] = 0.0;
-}
-__global__ void k_pcg_alpha(double *sc) { sc[5] = sc[2] / sc[4]; }
-// the solve control reads ||r||^2 in source units from scal[2]
-__global__ void k_pcg_norm_out(double *sc, double d2f, double *scal2) {
-  *scal2 = sc[6] * d2f;
-}
-__global__ void k_pcg_first(double *sc) { sc[7] = 1.0; }
-
 struct PcgView {
-  double *x, *r, *ro, *pd, *q, *gsave, *part, *sc;
+  double *x, *p0, *p1, *q, *gsave, *part, *sc;
   int64_t n, ps, nv;
   unsigned nb;
 };
@@ -193,10 +229,9 @@ PcgView view(cmg_level *L) {
   v.nv = 8 * g.n_alloc;
   v.nb = blocks_for(g.n, kPcgThreads);
   v.x = L->pcg;
-  v.r = v.x + v.nv;
-  v.ro = v.r + v.nv;
-  v.pd = v.ro + v.nv;
-  v.q = v.pd + v.nv;
+  v.p0 = v.x + v.nv;
+  v.p1 = v.p0 + v.nv;
+  v.q = v.p1 + v.nv;
   v.gsave = v.q + v.nv;
   v.part = v.gsave + v.nv;
   v.sc = v.part + 2 * v.nb;
@@ -208,6 +243,8 @@ double d2f_of(const cmg_level *L) {
   return 36.0 / (h * h * h * h);  // squared pre-scaled norms -> source units
 }
 
+constexpr int kFinThreads = 1024;
+
 }  // namespace
 
 void pcg_prepare(cmg_level *L) {
@@ -215,14 +252,16 @@ void pcg_prepare(cmg_level *L) {
   MgLev &g = L->mg[0];
   const int64_t nv = 8 * g.n_alloc;
   const unsigned nb = blocks_for(g.n, kPcgThreads);
-  // x, r, ro, p, q, saved right-hand side; partials; scalars
-  L->pcg = L->mem.alloc<double>(6 * nv + 2 * (int64_t)nb + 16, true, L->ctx->stream);
+  // x, two direction buffers, q, saved right-hand side; partials; scalars
+  // (zeroed, so that q and both directions start finite)
+  L->pcg = L->mem.alloc<double>(5 * nv + 2 * (int64_t)nb + 16, true, L->ctx->stream);
   CMG_CUDA(cudaStreamSynchronize(L->ctx->stream));
 }
 
 // Set-up (inside the solve graph): ghosts, ||f - L 0||^2 into scal[0], the
-// true residual r0 (also the first right-hand side of the preconditioner)
-// with ||r0||^2 into scal[2], x = phi, p = 0, ghost octs of phi cleared.
+// true residual r0 in place of the right-hand side (the first right-hand side
+// of the preconditioner) with ||r0||^2 into scal[2], x = phi, p = 0, ghost
+// octs of phi cleared.
 void pcg_pre(cmg_level *L) {
   MgLev &g = L->mg[0];
   cudaStream_t s = L->ctx->stream;
@@ -231,17 +270,15 @@ void pcg_pre(cmg_level *L) {
   zero_phi_norm(L, L->scal + 0);
   CMG_CUDA(cudaMemcpyAsync(v.gsave, g.g, sizeof(double) * 8 * v.n, cudaMemcpyDeviceToDevice, s));
   CMG_CUDA(cudaMemcpyAsync(v.x, g.phi, sizeof(double) * v.nv, cudaMemcpyDeviceToDevice, s));
-  CMG_CUDA(cudaMemsetAsync(v.pd, 0, sizeof(double) * v.nv, s));
+  CMG_CUDA(cudaMemsetAsync(v.p0, 0, sizeof(double) * 2 * v.nv, s));
   {
     LaunchScope ls(L->ctx, K_RESID64, 8.0 * v.n * 24.0, 8.0 * v.n * 9.0);
-    k_pcg_resid<<<v.nb, kPcgThreads, 0, s>>>(g.nbr, g.phi, g.g, v.n, v.ps, v.r, g.g, v.part);
+    k_pcg_resid<<<v.nb, kPcgThreads, 0, s>>>(g.nbr, g.phi, g.g, v.n, v.ps, v.part);
   }
   {
     LaunchScope ls(L->ctx, K_REDUCE, 8.0 * v.nb, v.nb);
-    k_pcg_reduce<<<1, 1024, 0, s>>>(v.part, (int)v.nb, v.sc + 6);
+    k_pcg_fin<FIN_NORM_FIRST><<<1, kFinThreads, 0, s>>>(v.part, (int)v.nb, v.sc, d2f_of(L), L->scal + 2);
   }
-  k_pcg_norm_out<<<1, 1, 0, s>>>(v.sc, d2f_of(L), L->scal + 2);
-  k_pcg_first<<<1, 1, 0, s>>>(v.sc);
   // corrections see zero coarse-fine values: clear the ghost octs of phi
   if (g.n_alloc > v.n) {
     CMG_CUDA(cudaMemsetAsync(g.phi + 4 * v.n, 0, sizeof(double) * 4 * (g.n_alloc - v.n), s));
@@ -250,7 +287,7 @@ void pcg_pre(cmg_level *L) {
   CMG_CUDA(cudaGetLastError());
 }
 
-// One CG iteration: z = M r (V-cycle), beta, p, q = L0 p, alpha, x and r
+// One CG iteration: z = M r (V-cycle), beta, p and q = L0 p, alpha, x and r
 // updates; ||r||^2 into scal[2] for the control's check.
 void pcg_body(cmg_level *L, const cmg_solve_params *p, int64_t *updates) {
   MgLev &g = L->mg[0];
@@ -262,27 +299,28 @@ void pcg_body(cmg_level *L, const cmg_solve_params *p, int64_t *updates) {
   if (L->periodic_full) subtract_mean(L);
   {
     LaunchScope ls(L->ctx, K_REDUCE, 8.0 * v.n * 24.0, 8.0 * v.n * 4.0);
-    k_pcg_dots<<<v.nb, kPcgThreads, 0, s>>>(g.phi, v.r, v.ro, v.n, v.ps, v.part);
-  }
-  k_pcg_reduce<<<1, 1024, 0, s>>>(v.part, (int)v.nb, v.sc + 0);
-  k_pcg_reduce<<<1, 1024, 0, s>>>(v.part + v.nb, (int)v.nb, v.sc + 1);
-  k_pcg_beta<<<1, 1, 0, s>>>(v.sc);
-  {
-    LaunchScope ls(L->ctx, K_CONVERT, 8.0 * v.n * 24.0, 8.0 * v.n * 2.0);
-    k_pcg_dir<<<v.nb, kPcgThreads, 0, s>>>(g.phi, v.pd, v.n, v.ps, v.sc + 3);
+    k_pcg_dots<<<v.nb, kPcgThreads, 0, s>>>(g.phi, g.g, v.q, v.n, v.ps, v.part);
   }
   {
-    LaunchScope ls(L->ctx, K_RESID64, 8.0 * v.n * 16.0, 8.0 * v.n * 9.0);
-    k_pcg_apply<<<v.nb, kPcgThreads, 0, s>>>(g.nbr, v.pd, v.n, v.ps, v.q, v.part);
+    LaunchScope ls(L->ctx, K_REDUCE, 16.0 * v.nb, 2.0 * v.nb);
+    k_pcg_fin<FIN_BETA><<<1, kFinThreads, 0, s>>>(v.part, (int)v.nb, v.sc, 0.0, nullptr);
   }
-  k_pcg_reduce<<<1, 1024, 0, s>>>(v.part, (int)v.nb, v.sc + 4);
-  k_pcg_alpha<<<1, 1, 0, s>>>(v.sc);
   {
-    LaunchScope ls(L->ctx, K_CONVERT, 8.0 * v.n * 56.0, 8.0 * v.n * 6.0);
-    k_pcg_step<<<v.nb, kPcgThreads, 0, s>>>(v.x, v.pd, v.r, v.ro, v.q, g.g, v.n, v.ps, v.sc + 5, v.part);
+    LaunchScope ls(L->ctx, K_RESID64, 8.0 * v.n * 32.0 + 24.0 * v.n, 8.0 * v.n * 11.0);
+    k_pcg_dir_apply<<<v.nb, kPcgThreads, 0, s>>>(g.nbr, g.phi, v.p0, v.p1, v.n, v.ps, v.sc, v.q, v.part);
   }
-  k_pcg_reduce<<<1, 1024, 0, s>>>(v.part, (int)v.nb, v.sc + 6);
-  k_pcg_norm_out<<<1, 1, 0, s>>>(v.sc, d2f_of(L), L->scal + 2);
+  {
+    LaunchScope ls(L->ctx, K_REDUCE, 8.0 * v.nb, v.nb);
+    k_pcg_fin<FIN_ALPHA><<<1, kFinThreads, 0, s>>>(v.part, (int)v.nb, v.sc, 0.0, nullptr);
+  }
+  {
+    LaunchScope ls(L->ctx, K_CONVERT, 8.0 * v.n * 48.0, 8.0 * v.n * 6.0);
+    k_pcg_step<<<v.nb, kPcgThreads, 0, s>>>(v.x, v.p0, v.p1, g.g, v.q, v.n, v.ps, v.sc, v.part);
+  }
+  {
+    LaunchScope ls(L->ctx, K_REDUCE, 8.0 * v.nb, v.nb);
+    k_pcg_fin<FIN_NORM><<<1, kFinThreads, 0, s>>>(v.part, (int)v.nb, v.sc, d2f_of(L), L->scal + 2);
+  }
   CMG_CUDA(cudaGetLastError());
 }
 
