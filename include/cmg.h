@@ -167,11 +167,20 @@ int cmg_level_solve(cmg_level *lvl, const cmg_solve_params *params, cmg_solve_st
  * with at most tail_octs_fp64 (FP64 cycles) / tail_octs_fp32 (FP32 inner
  * cycles) octs, together with every coarser level, run in one launch instead
  * of one launch per operation -- in a single CTA when the first of them has
- * at most 64 (FP64) / 4096 (FP32) octs, else in one thread-block cluster.
- * Defaults 64 / 512 (measured on GB300: a cluster pass over a small level is
- * as slow as a launch, and one SM's FP64 rate only pays for tiny levels);
- * 0 disables.  Negative values leave the current setting. */
+ * at most 64 (FP64) / 4096 (FP32) octs, else in one cooperative launch of one
+ * CTA per SM with grid barriers (the levels within the single-CTA limit then
+ * run on its first CTA).  Defaults 64 / 512 (measured on GB300: a grid-wide
+ * pass over a small level costs as much as a launch, and one SM's FP64 rate
+ * only pays for tiny levels); 0 disables.  Negative values leave the current
+ * setting. */
 int cmg_level_set_schedule(cmg_level *lvl, int64_t tail_octs_fp64, int64_t tail_octs_fp32);
+
+/* SM clock cycles one wait at a grid barrier of the tail kernel may last
+ * (default 2^30, about half a second).  A wait that runs out records
+ * CMG_ERR_TIMEOUT, every later barrier of that launch stops waiting, and the
+ * solve returns CMG_ERR_TIMEOUT with the context still usable (0 makes
+ * every wait give up at once: for tests).  CMG_ERR_INVALID_ARG if negative. */
+int cmg_level_set_spin_budget(cmg_level *lvl, int64_t cycles);
 
 /* ---- multigrid hierarchy introspection and single steps (for tests) ----
  * m = 0 is the level itself; m + 1 is the coarsening of m (octs = the parents

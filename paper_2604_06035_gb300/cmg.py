@@ -100,6 +100,7 @@ _SIGS = {
     "cmg_level_get_ghosts": (_I, [_P, _P, _I]),
     "cmg_level_solve": (_I, [_P, C.POINTER(cmg_solve_params), C.POINTER(cmg_solve_stats)]),
     "cmg_level_set_schedule": (_I, [_P, _I64, _I64]),
+    "cmg_level_set_spin_budget": (_I, [_P, _I64]),
     "cmg_level_mg_depth": (_I, [_P, C.POINTER(_I)]),
     "cmg_level_mg_info": (_I, [_P, _I, C.POINTER(_I64), C.POINTER(_I)]),
     "cmg_level_mg_keys": (_I, [_P, _I, _P, _I]),
@@ -500,6 +501,10 @@ def cmg_level_solve(lvl, params=None, raise_on_error=True, **kw):
 
 def cmg_level_set_schedule(lvl, tail_octs_fp64=-1, tail_octs_fp32=-1):
     _check(lib().cmg_level_set_schedule(lvl.h, int(tail_octs_fp64), int(tail_octs_fp32)), "cmg_level_set_schedule")
+
+
+def cmg_level_set_spin_budget(lvl, cycles):
+    _check(lib().cmg_level_set_spin_budget(lvl.h, int(cycles)), "cmg_level_set_spin_budget")
 
 
 def cmg_level_mg_depth(lvl):

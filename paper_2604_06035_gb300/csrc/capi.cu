@@ -394,6 +394,18 @@ int cmg_level_set_schedule(cmg_level *lvl, int64_t tail_octs_fp64, int64_t tail_
   });
 }
 
+int cmg_level_set_spin_budget(cmg_level *lvl, int64_t cycles) {
+  return guard([&] {
+    need(lvl != nullptr, "NULL level");
+    need(cycles >= 0, "negative spin budget");
+    DeviceScope ds(lvl->device);
+    CMG_CUDA(cudaStreamSynchronize(lvl->stream));
+    lvl->tail_spin_budget = cycles;
+    cmg::destroy_graphs(lvl);  // recorded graphs hold the old budget
+    return CMG_OK;
+  });
+}
+
 int cmg_batch_create(cmg_level *lvl, const int64_t *offsets, int n_patches, cmg_batch **out) {
   return guard([&] {
     need(out != nullptr, "out is NULL");

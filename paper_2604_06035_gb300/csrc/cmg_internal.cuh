@@ -269,6 +269,7 @@ struct cmg_level {
   // in one "tail" launch (tail.cu); 0 = one launch per operation everywhere
   int64_t tail_octs_fp64 = 64;
   int64_t tail_octs_fp32 = 512;
+  int64_t tail_spin_budget = 1ll << 30;  // SM clock cycles a grid-tail barrier wait may last
   // FFT solve of a full periodic level (fft.cu): dense complex work array,
   // oct-coordinate -> oct-index map, twiddles (lazy)
   float2 *fft_buf = nullptr;
@@ -380,6 +381,10 @@ void finalize_norm(cmg_level *L, int n_partials, double scale, double *out);
 // tail.cu
 template <typename T>
 void tail_vcycle(cmg_level *L, int m0, const cmg_solve_params *p, const bool *zero_coarse);
+// the solve's sticky device error word and the tail kernel's grid-barrier
+// words (control block of the level's solve)
+int *solve_err_word(cmg_level *L);
+unsigned *solve_bar_words(cmg_level *L);
 
 // batch.cu
 void batch_create(cmg_level *L, const int64_t *offsets, int n_patches, cmg_batch **out);

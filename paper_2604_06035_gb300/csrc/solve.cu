@@ -18,6 +18,8 @@ namespace cmg {
 struct SolveCtrl {
   double n0sq, rel_initial, rel_final, blowup;
   int cycles, status, zero, go;
+  int err;           // sticky device error of this solve (a grid-barrier timeout)
+  unsigned bar[2];   // grid barrier of the tail kernel: arrivals, generation
   double hist[256];
 };
 
@@ -37,7 +39,10 @@ __device__ void decide(SolveCtrl *c, double tol, int fixed, int maxc, cudaGraphC
                        int use_handle) {
   int go;
   const double rel = c->rel_final;
-  if (!(rel == rel) || rel > c->blowup || isinf(rel)) {
+  if (c->err != 0) {
+    c->status = c->err;
+    go = 0;
+  } else if (!(rel == rel) || rel > c->blowup || isinf(rel)) {
     c->status = CMG_ERR_DIVERGED;
     go = 0;
   } else if (fixed > 0) {
@@ -60,6 +65,8 @@ __global__ void k_ctrl_init(SolveCtrl *c, const double *scal, double tol, int fi
   const double n0sq = scal[0];
   c->n0sq = n0sq;
   c->cycles = 0;
+  c->err = 0;
+  c->bar[0] = c->bar[1] = 0u;
   if (n0sq == 0.0) {
     c->zero = 1;
     c->status = CMG_OK;
@@ -325,6 +332,9 @@ CachedGraph *build_graph(cmg_level *L, const cmg_solve_params *p) {
 
 // One FP64 V-cycle from zero on the level's right-hand side (the CG
 // preconditioner, pcg.cu).
+int *solve_err_word(cmg_level *L) { return &reinterpret_cast<SolveCtrl *>(L->ctrl)->err; }
+unsigned *solve_bar_words(cmg_level *L) { return reinterpret_cast<SolveCtrl *>(L->ctrl)->bar; }
+
 void vcycle64_from_zero(cmg_level *L, const cmg_solve_params *p, int64_t *updates) {
   vcycle<double>(L, 0, p, true, updates);
 }

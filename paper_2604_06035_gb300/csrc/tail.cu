@@ -1,22 +1,23 @@
 // tail.cu -- the small multigrid levels of a V-cycle in one launch.
 //
-// Below a few thousand octs a level's work no longer fills the GPU and each
-// operation would cost a full kernel launch.  The tail kernel runs, in one
-// thread-block cluster (16 CTAs on GB300 when the non-portable size is
-// available, else 8), every operation of the V-cycle from MG level m0 down to
-// the coarsest and back up: pre-smoothing, residual + restriction, the
-// coarsest solve (exact 2^3 transform or red-black sweeps), prolongation and
-// post-smoothing.  Operations are separated by hardware cluster barriers
-// (barrier.cluster arrive.release / wait.acquire); data written by one CTA is
-// read by the others through L2 (ld.global.cg).  The arithmetic is the same
-// per-oct code as the one-launch-per-operation path (oct_ops.cuh), so the two
-// paths give the same results.
-#include <cooperative_groups.h>
-
+// Below a few ten thousand octs a level's work no longer fills the GPU and
+// each operation would cost a full kernel launch.  The tail kernel runs every
+// operation of the V-cycle from MG level m0 down to the coarsest and back up:
+// pre-smoothing, residual + restriction, the coarsest solve (exact 2^3
+// transform or red-black sweeps), prolongation and post-smoothing.
+//   * Grid tail: one cooperative launch of one CTA per SM.  A level's octs
+//     are split into one contiguous chunk per CTA; operations are separated
+//     by a grid barrier (a generation word in the solve's control block,
+//     bounded waits that record CMG_ERR_TIMEOUT); loads go through L2
+//     (ld.global.cg), since another CTA may have written the data.  Levels
+//     small enough for one SM run inside the same launch on CTA 0 alone,
+//     with block barriers, while the others wait at the next grid barrier.
+//   * Single-CTA tail: when even the first tail level fits one SM, one CTA of
+//     1024 threads with block barriers and L1 loads.
+// The arithmetic is the same per-oct code as the one-launch-per-operation
+// path (oct_ops.cuh), so every schedule gives the same results.
 #include "cmg_internal.cuh"
 #include "oct_ops.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace cmg {
 
@@ -40,18 +41,44 @@ struct TailLevel {
 
 struct TailPlan {
   int m0, last, n_pre, n_post, coarse_sweeps, exact, mixed;
+  int split;  // grid tail: first level run by CTA 0 alone (last + 1: none)
   double h_last;
+  int *err;       // sticky error word of the solve (grid-barrier timeout)
+  unsigned *bar;  // grid barrier: [0] arrivals, [1] generation
+  long long spin_budget;
   TailLevel lv[kMaxTail];
 };
 
-// CG: loads through L2 only (another CTA of the cluster may have written the
-// data); a single-CTA tail reads through L1.
-template <typename T, bool MASK, bool CG>
-__device__ void pass(const TailLevel &L, int P, bool zero, int64_t tid, int64_t nthr) {
+// The octs (or values) [0, n) a thread handles: a, a + s, ... below e.
+struct Span {
+  int64_t a, e, s;
+};
+// every thread of one CTA strides over the whole range
+struct FlatMap {
+  int64_t tid, nthr;
+  __device__ Span span(int64_t n) const { return {tid, n, nthr}; }
+  __device__ bool leader() const { return tid == 0; }
+};
+// one contiguous chunk per CTA, the CTA's threads striding over it
+struct ChunkMap {
+  int64_t b, nb, t, nt;
+  __device__ Span span(int64_t n) const {
+    const int64_t c = (n + nb - 1) / nb;
+    const int64_t a = b * c;
+    return {a + t, a + c < n ? a + c : n, nt};
+  }
+  __device__ bool leader() const { return b == 0 && t == 0; }
+};
+
+// CG: loads through L2 only (another CTA may have written the data); a
+// single-CTA tail reads through L1.
+template <typename T, bool MASK, bool CG, class Map>
+__device__ void pass(const TailLevel &L, int P, bool zero, const Map &map) {
   T *phi = static_cast<T *>(L.phi);
   const T *g = static_cast<const T *>(L.g);
   const int64_t st = L.n_alloc * 4;
-  for (int64_t i = tid; i < L.n; i += nthr) {
+  const Span sp = map.span(L.n);
+  for (int64_t i = sp.a; i < sp.e; i += sp.s) {
     if (P == 0) {
       if (zero)
         dev::sweep_oct<T, 0, true, MASK, CG>(i, L.nbr, phi + st, phi, g, L.active, L.n);
@@ -63,128 +90,179 @@ __device__ void pass(const TailLevel &L, int P, bool zero, int64_t tid, int64_t 
   }
 }
 
-template <typename T, bool CG>
-__device__ void colour_pass(const TailLevel &L, int P, bool zero, int64_t tid, int64_t nthr) {
+template <typename T, bool CG, class Map>
+__device__ void colour_pass(const TailLevel &L, int P, bool zero, const Map &map) {
   if (L.all_active)
-    pass<T, false, CG>(L, P, zero, tid, nthr);
+    pass<T, false, CG>(L, P, zero, map);
   else
-    pass<T, true, CG>(L, P, zero, tid, nthr);
+    pass<T, true, CG>(L, P, zero, map);
 }
 
-template <typename T, bool CG, class Sync>
-__device__ void sweeps(const TailLevel &L, int n_sweeps, bool zero_first, int64_t tid, int64_t nthr, Sync &sync) {
+template <typename T, bool CG, class Map, class Sync>
+__device__ void sweeps(const TailLevel &L, int n_sweeps, bool zero_first, const Map &map, Sync &sync) {
   for (int k = 0; k < n_sweeps; ++k) {
-    colour_pass<T, CG>(L, 0, zero_first && k == 0, tid, nthr);
+    colour_pass<T, CG>(L, 0, zero_first && k == 0, map);
     sync();
-    colour_pass<T, CG>(L, 1, false, tid, nthr);
+    colour_pass<T, CG>(L, 1, false, map);
     sync();
   }
 }
 
-// The V-cycle from MG level plan.m0 down to the coarsest and back up, by
-// nthr threads (thread tid), operations separated by sync().
-template <typename T, bool CG, class Sync>
-__device__ void tail_body(const TailPlan &plan, int64_t tid, int64_t nthr, Sync &sync) {
-  // descend: pre-smoothing, residual + restriction
-  for (int m = plan.m0; m < plan.last; ++m) {
+// Down leg over levels [m_from, m_to): pre-smoothing of m, residual of m
+// restricted to the right-hand side of m + 1.
+template <typename T, bool CG, class Map, class Sync>
+__device__ void descend(const TailPlan &plan, int m_from, int m_to, const Map &map, Sync &sync) {
+  for (int m = m_from; m < m_to; ++m) {
     const TailLevel &L = plan.lv[m];
     const TailLevel &C = plan.lv[m + 1];
-    sweeps<T, CG>(L, plan.n_pre, true, tid, nthr, sync);
+    sweeps<T, CG>(L, plan.n_pre, true, map, sync);
     const T *phi = static_cast<const T *>(L.phi);
     const T *g = static_cast<const T *>(L.g);
-    for (int64_t i = tid; i < L.n; i += nthr)
+    const Span sp = map.span(L.n);
+    for (int64_t i = sp.a; i < sp.e; i += sp.s)
       dev::resid_oct<T, false, true, false, false, false, CG>(
           i, L.nbr, phi, g, L.all_active ? nullptr : L.active, L.n, L.n_alloc, L.father, static_cast<T *>(C.g),
           static_cast<T *>(C.phi), C.n, C.n_alloc, L.zero_coarse, nullptr, 0.0, nullptr, 0.0);
     sync();
   }
-  // coarsest level
-  {
-    const TailLevel &L = plan.lv[plan.last];
-    if (plan.exact) {
-      if (tid == 0) dev::wht_solve<T, T, CG>(static_cast<const T *>(L.g), static_cast<T *>(L.phi), L.n_alloc,
-                                             plan.h_last);
-      sync();
-    } else if (!plan.mixed) {
-      sweeps<T, CG>(L, plan.coarse_sweeps, plan.last > 0, tid, nthr, sync);
-    } else {
-      // mixed precision: the coarsest level is solved in FP64
-      TailLevel L64 = L;
-      L64.phi = L.phi64;
-      L64.g = L.g64;
-      const float *g32 = static_cast<const float *>(L.g);
-      for (int64_t t = tid; t < 8 * L.n; t += nthr) L.g64[t] = (double)(CG ? __ldcg(g32 + t) : g32[t]);
-      sync();
-      sweeps<double, CG>(L64, plan.coarse_sweeps, true, tid, nthr, sync);
-      float *p32 = static_cast<float *>(L.phi);
-      for (int64_t t = tid; t < 8 * L.n_alloc; t += nthr) p32[t] = (float)(CG ? __ldcg(L.phi64 + t) : L.phi64[t]);
-      sync();
-    }
+}
+
+// The coarsest level: exact 2^3 transform or red-black sweeps (in FP64 in a
+// mixed-precision solve).
+template <typename T, bool CG, class Map, class Sync>
+__device__ void coarsest(const TailPlan &plan, const Map &map, Sync &sync) {
+  const TailLevel &L = plan.lv[plan.last];
+  if (plan.exact) {
+    if (map.leader()) dev::wht_solve<T, T, CG>(static_cast<const T *>(L.g), static_cast<T *>(L.phi), L.n_alloc,
+                                               plan.h_last);
+    sync();
+  } else if (!plan.mixed) {
+    sweeps<T, CG>(L, plan.coarse_sweeps, plan.last > 0, map, sync);
+  } else {
+    TailLevel L64 = L;
+    L64.phi = L.phi64;
+    L64.g = L.g64;
+    const float *g32 = static_cast<const float *>(L.g);
+    const Span sg = map.span(8 * L.n);
+    for (int64_t t = sg.a; t < sg.e; t += sg.s) L.g64[t] = (double)(CG ? __ldcg(g32 + t) : g32[t]);
+    sync();
+    sweeps<double, CG>(L64, plan.coarse_sweeps, true, map, sync);
+    float *p32 = static_cast<float *>(L.phi);
+    const Span sq = map.span(8 * L.n_alloc);
+    for (int64_t t = sq.a; t < sq.e; t += sq.s) p32[t] = (float)(CG ? __ldcg(L.phi64 + t) : L.phi64[t]);
+    sync();
   }
-  // ascend: prolongation + correction, post-smoothing
-  for (int m = plan.last - 1; m >= plan.m0; --m) {
+}
+
+// Up leg from level m_from down to m_to: prolongation of m + 1 added to m,
+// post-smoothing of m.
+template <typename T, bool CG, class Map, class Sync>
+__device__ void ascend(const TailPlan &plan, int m_from, int m_to, const Map &map, Sync &sync) {
+  for (int m = m_from; m >= m_to; --m) {
     const TailLevel &L = plan.lv[m];
     const TailLevel &C = plan.lv[m + 1];
     T *phi = static_cast<T *>(L.phi);
     const T *cphi = static_cast<const T *>(C.phi);
-    for (int64_t i = tid; i < L.n; i += nthr) {
+    const Span sp = map.span(L.n);
+    for (int64_t i = sp.a; i < sp.e; i += sp.s) {
       if (L.all_active)
         dev::prolong_oct<T, false, CG>(i, L.keys, L.blk, L.n, L.n_alloc, phi, L.active, cphi, C.n_alloc);
       else
         dev::prolong_oct<T, true, CG>(i, L.keys, L.blk, L.n, L.n_alloc, phi, L.active, cphi, C.n_alloc);
     }
     sync();
-    sweeps<T, CG>(L, plan.n_post, false, tid, nthr, sync);
+    sweeps<T, CG>(L, plan.n_post, false, map, sync);
   }
 }
 
-struct ClusterSync {
-  cg::cluster_group cl;
-  __device__ void operator()() { cl.sync(); }
-};
+// The V-cycle from MG level m0 down to the coarsest and back up.
+template <typename T, bool CG, class Map, class Sync>
+__device__ void tail_body(const TailPlan &plan, int m0, const Map &map, Sync &sync) {
+  descend<T, CG>(plan, m0, plan.last, map, sync);
+  coarsest<T, CG>(plan, map, sync);
+  ascend<T, CG>(plan, plan.last - 1, m0, map, sync);
+}
+
 struct BlockSync {
   __device__ void operator()() { __syncthreads(); }
 };
 
-template <typename T>
-__global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ TailPlan plan) {
-  ClusterSync sync{cg::this_cluster()};
-  const int64_t nthr = (int64_t)sync.cl.num_threads();
-  const int64_t tid = (int64_t)sync.cl.block_rank() * blockDim.x + threadIdx.x;
-  tail_body<T, true>(plan, tid, nthr, sync);
-}
-
-// The same V-cycle tail in one CTA: block barriers, loads through L1.  For
-// levels so small that a launch costs more than their arithmetic on one SM.
-constexpr int kTail1Threads = 1024;
-template <typename T>
-__global__ void __launch_bounds__(kTail1Threads) k_tail1(const __grid_constant__ TailPlan plan) {
-  BlockSync sync;
-  tail_body<T, false>(plan, threadIdx.x, blockDim.x, sync);
-}
-
-template <typename T>
-int tail_cluster_size() {
-  static int size = 0;
-  if (size) return size;
-  int s = 8;
-  if (cudaFuncSetAttribute(k_tail<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(16);
-    cfg.blockDim = dim3(kTailThreads);
-    cudaLaunchAttribute attr;
-    attr.id = cudaLaunchAttributeClusterDimension;
-    attr.val.clusterDim.x = 16;
-    attr.val.clusterDim.y = 1;
-    attr.val.clusterDim.z = 1;
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
-    int clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&clusters, k_tail<T>, &cfg) == cudaSuccess && clusters > 0) s = 16;
+// Grid-wide barrier of a cooperative launch.  Waiting CTAs spin on the
+// generation word with __nanosleep and give up after spin_budget SM clock
+// cycles, recording CMG_ERR_TIMEOUT; once the error word is set no barrier
+// waits any more, so a failed launch always ends (with its results void).
+struct GridSync {
+  unsigned *bar;
+  int *err;
+  long long budget;
+  __device__ void operator()() {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      volatile unsigned *gen = bar + 1;
+      volatile int *e = err;
+      const unsigned g0 = *gen;
+      __threadfence();
+      if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+        atomicExch(bar, 0u);
+        __threadfence();
+        atomicAdd(bar + 1, 1u);
+      } else {
+        const long long t0 = clock64();
+        while (*gen == g0 && *e == 0) {
+          if (clock64() - t0 > budget) {
+            atomicCAS(err, 0, (int)CMG_ERR_TIMEOUT);
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      __threadfence();
+    }
+    __syncthreads();
   }
-  cudaGetLastError();
-  size = s;
-  return size;
+};
+
+constexpr int kTailThreads1 = 1024;
+
+// Grid tail: levels [m0, split) on all CTAs, [split, last] on CTA 0.
+template <typename T>
+__global__ void __launch_bounds__(kTailThreads) k_tailg(const __grid_constant__ TailPlan plan) {
+  GridSync gs{plan.bar, plan.err, plan.spin_budget};
+  const ChunkMap map{(int64_t)blockIdx.x, (int64_t)gridDim.x, (int64_t)threadIdx.x, (int64_t)blockDim.x};
+  const int split = plan.split;
+  if (split <= plan.last) {
+    descend<T, true>(plan, plan.m0, split, map, gs);
+    if (blockIdx.x == 0) {
+      BlockSync bs;
+      const FlatMap fm{(int64_t)threadIdx.x, (int64_t)blockDim.x};
+      tail_body<T, true>(plan, split, fm, bs);
+    }
+    gs();
+    ascend<T, true>(plan, split - 1, plan.m0, map, gs);
+  } else {
+    tail_body<T, true>(plan, plan.m0, map, gs);
+  }
+}
+
+// The whole tail in one CTA: block barriers, loads through L1.  For levels
+// so small that a launch costs more than their arithmetic on one SM.
+template <typename T>
+__global__ void __launch_bounds__(kTailThreads1) k_tail1(const __grid_constant__ TailPlan plan) {
+  BlockSync sync;
+  const FlatMap fm{(int64_t)threadIdx.x, (int64_t)blockDim.x};
+  tail_body<T, false>(plan, plan.m0, fm, sync);
+}
+
+template <typename T>
+int tailg_grid(const cmg_ctx *ctx) {
+  static int per_sm = -1;
+  if (per_sm < 0) {
+    int b = 0;
+    CMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tailg<T>, kTailThreads, 0));
+    per_sm = b;
+  }
+  if (per_sm < 1) throw Error(CMG_ERR_CUDA, "the grid tail kernel does not fit on an SM");
+  return ctx->num_sms;  // one CTA per SM: co-resident, as the cooperative launch requires
 }
 
 }  // namespace
@@ -231,24 +309,31 @@ void tail_vcycle(cmg_level *L, int m0, const cmg_solve_params *p, const bool *ze
   for (int m = m0; m <= last; ++m) cells += 8.0 * L->mg[m].n;
   LaunchScope ls(L->ctx, K_COARSE, cells * (p->n_pre + p->n_post + 2) * 3.0 * sizeof(T),
                  cells * (p->n_pre + p->n_post) * 7.0);
-  if (L->mg[m0].n <= tail1_max_octs<T>()) {
-    k_tail1<T><<<1, kTail1Threads, 0, L->ctx->stream>>>(plan);
+  const int64_t one = tail1_max_octs<T>();
+  if (L->mg[m0].n <= one) {
+    k_tail1<T><<<1, kTailThreads1, 0, L->ctx->stream>>>(plan);
     CMG_CUDA(cudaGetLastError());
     return;
   }
-  const int cs = tail_cluster_size<T>();
+  plan.split = last + 1;
+  for (int m = m0 + 1; m <= last; ++m)
+    if (L->mg[m].n <= one) {
+      plan.split = m;
+      break;
+    }
+  plan.err = solve_err_word(L);
+  plan.bar = solve_bar_words(L);
+  plan.spin_budget = L->tail_spin_budget;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(cs);
+  cfg.gridDim = dim3(tailg_grid<T>(L->ctx));
   cfg.blockDim = dim3(kTailThreads);
   cfg.stream = L->ctx->stream;
   cudaLaunchAttribute attr;
-  attr.id = cudaLaunchAttributeClusterDimension;
-  attr.val.clusterDim.x = cs;
-  attr.val.clusterDim.y = 1;
-  attr.val.clusterDim.z = 1;
+  attr.id = cudaLaunchAttributeCooperative;
+  attr.val.cooperative = 1;
   cfg.attrs = &attr;
   cfg.numAttrs = 1;
-  CMG_CUDA(cudaLaunchKernelEx(&cfg, k_tail<T>, plan));
+  CMG_CUDA(cudaLaunchKernelEx(&cfg, k_tailg<T>, plan));
 }
 
 template void tail_vcycle<double>(cmg_level *, int, const cmg_solve_params *, const bool *);

@@ -365,14 +365,15 @@ def test_device_arrays_match_host_arrays(cmg, ctx):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_tail_schedule_matches_per_operation_launches(cmg, ctx, precision):
-    """The tail kernels (one CTA for the smallest levels, a cluster above) run
-    the same per-oct arithmetic as the one-launch-per-operation path: the
-    schedule must not change phi.  Tails from 64 octs (one CTA in FP64 and
-    FP32), 4096 (cluster in FP64, one CTA in FP32) and the whole hierarchy
-    (cluster)."""
+    """The tail kernels (one CTA for the smallest levels, a cooperative grid
+    launch above) run the same per-oct arithmetic as the
+    one-launch-per-operation path: the schedule must not change phi.  Tails
+    from 64 octs (one CTA in FP64 and FP32), 512 (grid in FP64 with the levels
+    of at most 64 octs on CTA 0; one CTA in FP32), 4096 (grid in FP64, one CTA
+    in FP32) and the whole hierarchy below the level itself (grid)."""
     cfg, GB, GF, RB, RF = _two_level(cmg, ctx, 6)
     out = {}
-    tails = (0, 64, 4096, 1 << 20)
+    tails = (0, 64, 512, 4096, 1 << 20)
     for tail in tails:
         for G, rho in ((GB, cfg["rho"][0]), (GF, cfg["rho"][1])):
             cmg.cmg_level_set_schedule(G, tail, tail)
@@ -383,6 +384,27 @@ def test_tail_schedule_matches_per_operation_launches(cmg, ctx, precision):
     for tail in tails[1:]:
         for base in (True, False):
             assert relerr(out[(tail, base)], out[(0, base)]) <= 1e-13, (tail, base)
+
+
+def test_grid_tail_barrier_timeout_returns_status(cmg, ctx):
+    """A grid-tail barrier wait that runs out of spin budget ends the launch
+    and the solve with CMG_ERR_TIMEOUT; the context stays usable and the next
+    solve with the default budget converges."""
+    cfg, GB, GF, RB, RF = _two_level(cmg, ctx, 6)
+    cmg.cmg_level_set_schedule(GB, 1 << 20, 1 << 20)
+    cmg.cmg_level_set_density(GB, cfg["rho"][0], 1.0)
+    z = np.zeros((cmg.cmg_level_n_octs(GB), 8))
+    cmg.cmg_level_set_spin_budget(GB, 0)
+    cmg.cmg_level_set_phi(GB, z)
+    rc, st = cmg.cmg_level_solve(GB, tol=1e-10, raise_on_error=False)
+    assert rc == cmg.CMG_ERR_TIMEOUT
+    cmg.cmg_level_set_spin_budget(GB, 1 << 30)
+    cmg.cmg_level_set_phi(GB, z)
+    rc, st = cmg.cmg_level_solve(GB, tol=1e-10)
+    assert rc == cmg.CMG_OK and st["rel_final"] <= 1e-10
+    with pytest.raises(cmg.CmgError) as e:
+        cmg.cmg_level_set_spin_budget(GB, -1)
+    assert e.value.code == cmg.CMG_ERR_INVALID_ARG
 
 
 def _cube(level, lo, hi):
