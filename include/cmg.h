@@ -66,7 +66,8 @@ typedef struct {
   int coarse_sweeps; /* sweeps on a non-periodic coarsest level */
   int fixed_cycles;  /* > 0: run exactly this many cycles and ignore tol */
   int precision;     /* cmg_precision */
-  int inner_cycles;  /* MIXED: FP32 V-cycles per FP64 refinement step (>= 1) */
+  int inner_cycles;  /* MIXED: FP32 V-cycles per FP64 refinement step (>= 1; 2 is
+                        the fastest to 1e-10 on the two-level 128^3 workload) */
   int krylov;        /* 0: stationary V-cycle iteration; 1: conjugate gradients
                         preconditioned by one V-cycle per iteration (App. D.2
                         names multigrid as the CG preconditioner), FP64 only;
@@ -166,13 +167,13 @@ int cmg_level_solve(cmg_level *lvl, const cmg_solve_params *params, cmg_solve_st
 /* Execution schedule of the V-cycle (no effect on the arithmetic): MG levels
  * with at most tail_octs_fp64 (FP64 cycles) / tail_octs_fp32 (FP32 inner
  * cycles) octs, together with every coarser level, run in one launch instead
- * of one launch per operation -- in a single CTA when the first of them has
- * at most 64 (FP64) / 4096 (FP32) octs, else in one cooperative launch of one
- * CTA per SM with grid barriers (the levels within the single-CTA limit then
- * run on its first CTA).  Defaults 64 / 512 (measured on GB300: a grid-wide
- * pass over a small level costs as much as a launch, and one SM's FP64 rate
- * only pays for tiny levels); 0 disables.  Negative values leave the current
- * setting. */
+ * of one launch per operation -- in a single CTA when they all fit one SM (at
+ * most 64 octs in FP64, 512 in FP32, and a coarsest level swept in FP64 of at
+ * most 64), else in one cooperative launch of one CTA per SM with grid
+ * barriers, whose first CTA alone takes the levels that fit one SM.  Defaults
+ * 32768 / 512 (measured on GB300, two-level 128^3 workload: FP64 levels from
+ * 64^3 down are cheaper under grid barriers than as separate launches, FP32
+ * ones are not); 0 disables.  Negative values leave the current setting. */
 int cmg_level_set_schedule(cmg_level *lvl, int64_t tail_octs_fp64, int64_t tail_octs_fp32);
 
 /* SM clock cycles one wait at a grid barrier of the tail kernel may last

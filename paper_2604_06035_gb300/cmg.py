@@ -478,7 +478,7 @@ def cmg_level_set_phi(lvl, phi):
 
 
 def solve_params(tol=1e-10, max_cycles=100, n_pre=2, n_post=2, coarse_sweeps=4, fixed_cycles=0,
-                 precision=CMG_PREC_FP64, inner_cycles=1, krylov=0):
+                 precision=CMG_PREC_FP64, inner_cycles=2, krylov=0):
     return cmg_solve_params(tol, max_cycles, n_pre, n_post, coarse_sweeps, fixed_cycles, precision, inner_cycles,
                             krylov)
 

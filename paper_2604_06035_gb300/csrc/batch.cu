@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "cmg_internal.cuh"
+#include "gridsync.cuh"
 #include "oct_ops.cuh"
 
 namespace cmg {
@@ -54,42 +55,17 @@ struct BatchPlan {
   int32_t *conv_at;
   // control: [0] status, [1] cycles, [2..3] unconverged counters, [4] barriers, [5] n_converged
   int *ctrl;
-  unsigned *bar;  // [0] arrivals, [1] generation
+  unsigned *bar;  // grid barrier word
 };
 
-// Grid-wide barrier for a cooperative launch.  Waiting blocks spin on the
-// generation word with __nanosleep and give up after spin_budget SM clock
-// cycles, recording CMG_ERR_TIMEOUT; every block then leaves at its next
-// barrier, so a failed launch always ends.
+// Grid-wide barrier (gridsync.cuh): waits give up after spin_budget SM clock
+// cycles with CMG_ERR_TIMEOUT in the status word, and every block then leaves
+// at its next barrier, so a failed launch always ends.  CTA 0 counts the
+// barriers passed.
 __device__ bool grid_sync(const BatchPlan &P) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ok = 1;
-    volatile unsigned *gen = P.bar + 1;
-    const unsigned g0 = *gen;
-    __threadfence();
-    if (atomicAdd(P.bar, 1u) == gridDim.x - 1) {
-      atomicExch(P.bar, 0u);
-      __threadfence();
-      atomicAdd(P.bar + 1, 1u);
-      atomicAdd(P.ctrl + 4, 1);
-    } else {
-      const long long t0 = clock64();
-      while (*gen == g0) {
-        if (clock64() - t0 > P.spin_budget) {
-          atomicCAS(P.ctrl, 0, CMG_ERR_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    if (*(volatile int *)P.ctrl == CMG_ERR_TIMEOUT) ok = 0;
-    __threadfence();
-  }
-  __syncthreads();
-  return ok != 0;
+  if (!dev::grid_barrier(P.bar, P.ctrl, P.spin_budget)) return false;
+  if (blockIdx.x == 0 && threadIdx.x == 0) P.ctrl[4] += 1;
+  return true;
 }
 
 // Sum v over the lanes of the warp that share patch p (p < 0: no value).

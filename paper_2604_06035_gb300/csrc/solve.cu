@@ -19,7 +19,7 @@ struct SolveCtrl {
   double n0sq, rel_initial, rel_final, blowup;
   int cycles, status, zero, go;
   int err;           // sticky device error of this solve (a grid-barrier timeout)
-  unsigned bar[2];   // grid barrier of the tail kernel: arrivals, generation
+  unsigned bar[2];   // grid barrier word of the tail kernel (bar[0]), spare
   double hist[256];
 };
 

@@ -7,8 +7,8 @@
 // transform or red-black sweeps), prolongation and post-smoothing.
 //   * Grid tail: one cooperative launch of one CTA per SM.  A level's octs
 //     are split into one contiguous chunk per CTA; operations are separated
-//     by a grid barrier (a generation word in the solve's control block,
-//     bounded waits that record CMG_ERR_TIMEOUT); loads go through L2
+//     by a grid barrier (a word in the solve's control block, bounded waits
+//     that record CMG_ERR_TIMEOUT); loads go through L2
 //     (ld.global.cg), since another CTA may have written the data.  Levels
 //     small enough for one SM run inside the same launch on CTA 0 alone,
 //     with block barriers, while the others wait at the next grid barrier.
@@ -17,6 +17,7 @@
 // The arithmetic is the same per-oct code as the one-launch-per-operation
 // path (oct_ops.cuh), so every schedule gives the same results.
 #include "cmg_internal.cuh"
+#include "gridsync.cuh"
 #include "oct_ops.cuh"
 
 namespace cmg {
@@ -44,7 +45,7 @@ struct TailPlan {
   int split;  // grid tail: first level run by CTA 0 alone (last + 1: none)
   double h_last;
   int *err;       // sticky error word of the solve (grid-barrier timeout)
-  unsigned *bar;  // grid barrier: [0] arrivals, [1] generation
+  unsigned *bar;  // grid barrier word
   long long spin_budget;
   TailLevel lv[kMaxTail];
 };
@@ -187,39 +188,14 @@ struct BlockSync {
   __device__ void operator()() { __syncthreads(); }
 };
 
-// Grid-wide barrier of a cooperative launch.  Waiting CTAs spin on the
-// generation word with __nanosleep and give up after spin_budget SM clock
-// cycles, recording CMG_ERR_TIMEOUT; once the error word is set no barrier
-// waits any more, so a failed launch always ends (with its results void).
+// Grid-wide barrier of a cooperative launch (gridsync.cuh); after a wait
+// gives up (CMG_ERR_TIMEOUT in the solve's error word) no barrier waits any
+// more, so the launch ends with its results void.
 struct GridSync {
   unsigned *bar;
   int *err;
   long long budget;
-  __device__ void operator()() {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      volatile unsigned *gen = bar + 1;
-      volatile int *e = err;
-      const unsigned g0 = *gen;
-      __threadfence();
-      if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-        atomicExch(bar, 0u);
-        __threadfence();
-        atomicAdd(bar + 1, 1u);
-      } else {
-        const long long t0 = clock64();
-        while (*gen == g0 && *e == 0) {
-          if (clock64() - t0 > budget) {
-            atomicCAS(err, 0, (int)CMG_ERR_TIMEOUT);
-            break;
-          }
-          __nanosleep(32);
-        }
-      }
-      __threadfence();
-    }
-    __syncthreads();
-  }
+  __device__ void operator()() { dev::grid_barrier(bar, err, budget); }
 };
 
 constexpr int kTailThreads1 = 1024;
@@ -233,9 +209,12 @@ __global__ void __launch_bounds__(kTailThreads) k_tailg(const __grid_constant__ 
   if (split <= plan.last) {
     descend<T, true>(plan, plan.m0, split, map, gs);
     if (blockIdx.x == 0) {
+      // L1 loads are safe here: every level from split down is its own
+      // allocation that CTA 0 has not read earlier in this launch (L1 starts
+      // each launch empty), and below split only CTA 0 writes
       BlockSync bs;
       const FlatMap fm{(int64_t)threadIdx.x, (int64_t)blockDim.x};
-      tail_body<T, true>(plan, split, fm, bs);
+      tail_body<T, false>(plan, split, fm, bs);
     }
     gs();
     ascend<T, true>(plan, split - 1, plan.m0, map, gs);
@@ -267,12 +246,21 @@ int tailg_grid(const cmg_ctx *ctx) {
 
 }  // namespace
 
-// Largest first tail level run by one CTA: one SM does ~2 FP64 FMAs per
-// clock but ~64 FP32 ones, so the single-CTA tail pays for far larger FP32
-// levels than FP64 ones.
+// Largest level one CTA runs: one SM does ~2 FP64 FMAs per clock but ~128
+// FP32 ones, so a single SM pays for far larger FP32 levels than FP64 ones.
+// The coarsest level of a mixed-precision solve is swept in FP64.
 template <typename T>
-int64_t tail1_max_octs() {
-  return sizeof(T) == 8 ? 64 : 4096;
+int64_t one_cta_octs() {
+  return sizeof(T) == 8 ? 64 : 512;
+}
+
+// Whether levels m .. last fit one CTA.
+template <typename T>
+bool one_cta(const cmg_level *L, int m) {
+  const int last = (int)L->mg.size() - 1;
+  if (L->mg[m].n > one_cta_octs<T>()) return false;
+  if (sizeof(T) == 4 && !L->exact_coarse && L->mg[last].n > one_cta_octs<double>()) return false;
+  return true;
 }
 
 template <typename T>
@@ -309,15 +297,15 @@ void tail_vcycle(cmg_level *L, int m0, const cmg_solve_params *p, const bool *ze
   for (int m = m0; m <= last; ++m) cells += 8.0 * L->mg[m].n;
   LaunchScope ls(L->ctx, K_COARSE, cells * (p->n_pre + p->n_post + 2) * 3.0 * sizeof(T),
                  cells * (p->n_pre + p->n_post) * 7.0);
-  const int64_t one = tail1_max_octs<T>();
-  if (L->mg[m0].n <= one) {
+  if (one_cta<T>(L, m0)) {
     k_tail1<T><<<1, kTailThreads1, 0, L->ctx->stream>>>(plan);
     CMG_CUDA(cudaGetLastError());
     return;
   }
+  // grid tail; CTA 0 alone takes the levels from the first that fits it
   plan.split = last + 1;
   for (int m = m0 + 1; m <= last; ++m)
-    if (L->mg[m].n <= one) {
+    if (one_cta<T>(L, m)) {
       plan.split = m;
       break;
     }

@@ -314,19 +314,21 @@ def test_two_level_full_size_128(cmg, ctx):
         assert np.sqrt(n2) <= 1.0001e-10 * st["norm0"]
 
 
-def test_mixed_precision_matches_fp64(cmg, ctx):
-    """FP32 V-cycles inside FP64 refinement reach the FP64 solution: at the
-    stopping residual 1e-11 phi agrees with the oracle converged to 1e-13 to
-    1e-10 relative, and refinement keeps going below FP32 round-off."""
+@pytest.mark.parametrize("inner", [1, 2, 3])
+def test_mixed_precision_matches_fp64(cmg, ctx, inner):
+    """FP32 V-cycles (1 to 3 per refinement step) inside FP64 refinement reach
+    the FP64 solution: at the stopping residual 1e-11 phi agrees with the
+    oracle converged to 1e-13 to 1e-10 relative, and refinement keeps going
+    below FP32 round-off."""
     cfg, GB, GF, RB, RF = _two_level(cmg, ctx, 6)
     for G, R, rho in ((GB, RB, cfg["rho"][0]), (GF, RF, cfg["rho"][1])):
         cmg.cmg_level_set_density(G, rho, 1.0)
         R.set_density(rho, 1.0)
         R.solve(tol=1e-13)
-        rc, st = cmg.cmg_level_solve(G, tol=1e-11, precision=cmg.CMG_PREC_MIXED)
+        rc, st = cmg.cmg_level_solve(G, tol=1e-11, precision=cmg.CMG_PREC_MIXED, inner_cycles=inner)
         assert st["rel_final"] <= 1e-11
         assert relerr(cmg.cmg_level_get_phi(G), R.get_phi()) <= RTOL_MIXED
-        rc, st = cmg.cmg_level_solve(G, tol=1e-13, precision=cmg.CMG_PREC_MIXED)
+        rc, st = cmg.cmg_level_solve(G, tol=1e-13, precision=cmg.CMG_PREC_MIXED, inner_cycles=inner)
         assert st["rel_final"] <= 1e-13
         # the parent phi the fine level sees is the GPU's own mixed solution
         if G is GB:
