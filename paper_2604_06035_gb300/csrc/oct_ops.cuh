@@ -97,7 +97,9 @@ __device__ __forceinline__ void sweep_oct(int64_t i, const int32_t *__restrict__
 }
 
 // Residual of oct i: d = fma(s, 1/6, g) - phi per cell, r = (-6 / h^2) d.
-// Returns the sum of d^2 over the oct (NORM).  RESTRICT: a fully active oct
+// Returns the sum of d^2 over the oct (NORM; accumulated in FP64 for FP64
+// data, in FP32 within the oct for FP32 data, whose FP64 conversions would
+// otherwise bind the kernel to GB300's FP64 pipe).  RESTRICT: a fully active oct
 // writes its father cell g_c = 0.5 * sum_8 d (= -h_c^2/6 * mean_8 r) and, if
 // zero_cphi, zeroes the father's phi.  EMIT: g32 = (float)(d * inv_s).
 // ROUT: r oct-major.  ZPHI: phi taken as zero on real octs.
@@ -124,6 +126,7 @@ __device__ __forceinline__ double resid_oct(int64_t i, const int32_t *__restrict
   const unsigned m = active ? __ldg(active + i) : 0xFFu;
   T rsum = T(0);
   double acc = 0.0;
+  T tacc = T(0);  // FP32 data: the oct's squares summed in FP32, one conversion
 #pragma unroll
   for (int p = 0; p < 2; ++p) {
 #pragma unroll
@@ -144,12 +147,18 @@ __device__ __forceinline__ double resid_oct(int64_t i, const int32_t *__restrict
       }
       T dv = fma_t(s, inv6, gv[p][q]) - pl[p][q];
       if (!((m >> c) & 1)) dv = T(0);
-      if (NORM) acc = fma((double)dv, (double)dv, acc);
+      if (NORM) {
+        if constexpr (sizeof(T) == 8)
+          acc = fma((double)dv, (double)dv, acc);
+        else
+          tacc = fma_t(dv, dv, tacc);
+      }
       if (RESTRICT) rsum += dv;
       if (EMIT) g32[(p * n + i) * 4 + q] = (float)((double)dv * inv_s);
       if (ROUT) rout[i * 8 + c] = rscale * (double)dv;
     }
   }
+  if (NORM && sizeof(T) == 4) acc = (double)tacc;
   if (RESTRICT) {
     const int32_t fa = __ldg(father + i);
     if (fa >= 0) {

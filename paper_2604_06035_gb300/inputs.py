@@ -78,45 +78,66 @@ def lognormal(n, sigma, seed):
 
 # -------------------------------------------------------------- refinement
 
-def dilate_periodic(flags):
-    """One-cell dilation over the 6 face neighbours on a periodic dense grid.
-    (A 26-neighbour dilation of the k^-2 lognormal flags refines ~23 % of the
-    volume at sigma = 1.5; the face dilation gives ~9 %, inside the 5-10 %
-    band the two-level workload is specified with.)"""
-    out = flags.copy()
-    for axis in range(3):
-        for s in (-1, 1):
-            out |= np.roll(flags, s, axis=axis)
-    return out
+def _cell_index(cells, size):
+    """Sorted linear keys of a level's cells (periodic box of size^3 cells) and a
+    lookup q [k, 3] -> position in `cells` or -1."""
+    lin = lambda c: ((c[:, 0] % size) * size + (c[:, 1] % size)) * size + (c[:, 2] % size)
+    keys = lin(cells)
+    order = np.argsort(keys, kind="stable")
+    sk = keys[order]
+
+    def find(q):
+        k = lin(q)
+        pos = np.minimum(np.searchsorted(sk, k), len(sk) - 1)
+        return np.where(sk[pos] == k, order[pos], -1)
+    return find
 
 
 def refine_cells(level, coords, rho_octs, threshold):
-    """Cells of a level to refine: rho > threshold, dilated by one cell (face
-    neighbours) among existing cells, keeping only cells whose 26 neighbours
-    all exist (so that the new octs' coarse-fine ghost stencils exist).
+    """Cells of a level to refine: rho > threshold, dilated by one cell over the
+    6 face neighbours among existing cells (periodic), keeping only cells whose
+    26 neighbours all exist (so that the new octs' coarse-fine ghost stencils
+    exist).  A 26-neighbour dilation of the k^-2 lognormal flags refines ~23 %
+    of the volume at sigma = 1.5; the face dilation gives ~9 %, inside the
+    5-10 % band the two-level workload is specified with.
 
     coords: oct coords [n, 3] of the level, rho_octs [n, 8].  Returns the global
     cell coordinates [m, 3] (uint32) in oct-major order of the level, i.e. the
-    oct coordinates of the new octs one level down."""
+    oct coordinates of the new octs one level down, and their positions in the
+    level's flattened [n * 8] cell order.  Sparse: lookups in the sorted cell
+    keys, so that deep levels need no dense volume."""
     off = child_offsets()
     cells = (2 * coords[:, None, :].astype(np.int64) + off[None, :, :]).reshape(-1, 3)
-    flag = (rho_octs.reshape(-1) > threshold)
-    size = 1 << level  # dense bookkeeping on the whole periodic level
-    exist = np.zeros((size,) * 3, dtype=bool)
-    exist[cells[:, 0], cells[:, 1], cells[:, 2]] = True
-    fl = np.zeros_like(exist)
-    fl[cells[flag, 0], cells[flag, 1], cells[flag, 2]] = True
-    fl = dilate_periodic(fl) & exist
-    # keep cells whose full 26-neighbourhood exists
-    ok = exist.copy()
-    for dx in (-1, 0, 1):
-        for dy in (-1, 0, 1):
-            for dz in (-1, 0, 1):
-                if dx or dy or dz:
-                    ok &= np.roll(exist, (-dx, -dy, -dz), axis=(0, 1, 2))
-    fl &= ok
-    keep = fl[cells[:, 0], cells[:, 1], cells[:, 2]]
-    return cells[keep].astype(np.uint32)
+    size = 1 << level
+    find = _cell_index(cells, size)
+    flag = rho_octs.reshape(-1) > threshold
+    fl = flag.copy()
+    fc = cells[flag]
+    for axis in range(3):
+        for s in (-1, 1):
+            q = fc.copy()
+            q[:, axis] += s
+            j = find(q)
+            fl[j[j >= 0]] = True
+    cand = np.nonzero(fl)[0]
+    cc = cells[cand]
+    # a cell exists iff its oct does: a dense oct-occupancy grid ((size/2)^3
+    # bytes) answers the 26 neighbour tests
+    half = size >> 1
+    occ = np.zeros(half ** 3, dtype=bool)
+    co = coords.astype(np.int64)
+    occ[(co[:, 0] * half + co[:, 1]) * half + co[:, 2]] = True
+    # oct coordinate of the neighbour cell along each axis for offsets -1, 0, 1
+    ax = [[((cc[:, a] + d) & (size - 1)) >> 1 for d in (-1, 0, 1)] for a in range(3)]
+    ok = np.ones(len(cand), dtype=bool)
+    for i in range(3):
+        for j in range(3):
+            xy = (ax[0][i] * half + ax[1][j]) * half
+            for k in range(3):
+                if (i, j, k) != (1, 1, 1):
+                    ok &= occ[xy + ax[2][k]]
+    idx = cand[ok]
+    return cells[idx].astype(np.uint32), idx
 
 
 def child_density(rho_parent_cells, seed, level, sigma_inc=0.5):
@@ -151,16 +172,10 @@ def amr_lognormal(base_level, n_refine, sigma, seed, threshold=8.0, sigma_inc=0.
     rho_bar = 1.0
     for r in range(n_refine):
         lev = base_level + r
-        cells = refine_cells(lev, all_coords[-1], all_rho[-1], threshold * rho_bar)
+        cells, idx = refine_cells(lev, all_coords[-1], all_rho[-1], threshold * rho_bar)
         if len(cells) == 0:
             break
-        # density of each refined (parent) cell, in the order of `cells`
-        off = child_offsets()
-        pc = all_coords[-1]
-        X = (2 * pc[:, None, :].astype(np.int64) + off[None, :, :]).reshape(-1, 3)
-        dense = np.zeros((1 << lev,) * 3)
-        dense[X[:, 0], X[:, 1], X[:, 2]] = all_rho[-1].reshape(-1)
-        parent_rho = dense[cells[:, 0], cells[:, 1], cells[:, 2]]
+        parent_rho = all_rho[-1].reshape(-1)[idx]  # density of each refined (parent) cell
         levels.append(lev + 1)
         all_coords.append(cells)
         all_rho.append(child_density(parent_rho, seed, lev + 1, sigma_inc))

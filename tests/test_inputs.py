@@ -46,3 +46,44 @@ def test_batched_patches_structure():
         for d in np.array(np.meshgrid([-1, 0, 1], [-1, 0, 1], [-1, 0, 1])).reshape(3, -1).T:
             assert tuple((x >> 1) + d) in par
     assert b["rho"].shape == (len(c), 8) and np.all(b["rho"] > 0)
+
+
+def _refine_dense(level, coords, rho_octs, threshold):
+    """Brute-force reading of the refinement rule on a dense periodic volume:
+    flagged cells, face-dilated among existing cells, kept where all 26
+    neighbours exist."""
+    off = inputs.child_offsets()
+    cells = (2 * coords[:, None, :].astype(np.int64) + off[None, :, :]).reshape(-1, 3)
+    size = 1 << level
+    exist = np.zeros((size,) * 3, dtype=bool)
+    exist[tuple(cells.T)] = True
+    flag = np.zeros_like(exist)
+    sel = rho_octs.reshape(-1) > threshold
+    flag[tuple(cells[sel].T)] = True
+    dil = flag.copy()
+    for axis in range(3):
+        for s in (-1, 1):
+            dil |= np.roll(flag, s, axis=axis)
+    dil &= exist
+    ok = exist.copy()
+    for d in np.array(np.meshgrid([-1, 0, 1], [-1, 0, 1], [-1, 0, 1])).reshape(3, -1).T:
+        if d.any():
+            ok &= np.roll(exist, tuple(-d), axis=(0, 1, 2))
+    keep = (dil & ok)[tuple(cells.T)]
+    return cells[keep].astype(np.uint32), np.nonzero(keep)[0]
+
+
+def test_sparse_refinement_matches_dense_rule():
+    """The sparse refinement (sorted-key lookups, oct occupancy) selects the
+    same cells, in the same order, as the rule applied on dense volumes, down
+    a three-level sigma = 2 hierarchy."""
+    cfg = inputs.amr_lognormal(5, 3, 2.0, 3)
+    assert len(cfg["levels"]) == 4
+    for m in range(3):
+        lev, c, r = cfg["levels"][m], cfg["coords"][m], cfg["rho"][m]
+        got, gi = inputs.refine_cells(lev, c, r, 8.0)
+        want, wi = _refine_dense(lev, c, r, 8.0)
+        assert np.array_equal(got, want) and np.array_equal(gi, wi)
+        assert np.array_equal(got, cfg["coords"][m + 1])
+        # children conserve the parent cell's mass
+        assert np.allclose(cfg["rho"][m + 1].mean(axis=1), r.reshape(-1)[gi], rtol=1e-12)
