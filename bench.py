@@ -47,7 +47,8 @@ def parse():
                     help="trajectories of 8 steps for the learned warm start (1/16 held out)")
     ap.add_argument("--train-seconds", type=float, default=60.0, help="U-Net training budget")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start block")
-    ap.add_argument("--block", choices=["smoother", "learned", "forward", "fft", "pcg"], default=None,
+    ap.add_argument("--no-amr3", action="store_true", help="skip the 256^3 + 3-level mixed-precision block")
+    ap.add_argument("--block", choices=["smoother", "learned", "forward", "fft", "pcg", "amr3"], default=None,
                     help="run one sub-benchmark alone and print its JSON (profiling runs)")
     ap.add_argument("--smoother-level", type=int, default=9, help="level of the full periodic grid (9 = 512^3)")
     ap.add_argument("--fwd-batches", default="1,8", help="batch sizes of --block forward")
@@ -374,6 +375,72 @@ def bench_pcg(cmg, ctx, dev, levels, args):
     return out
 
 
+def bench_amr3(cmg, ctx, dev, args):
+    """The 256^3 mixed-precision workload: periodic lognormal base (sigma 2)
+    plus three levels refined where rho > 8 rho_bar, solved level by level
+    (each after its parent, whose phi gives the coarse-fine values) from phi = 0
+    to rel. residual tol: FP64 V-cycles, FP32 V-cycles inside FP64 refinement,
+    and the FFT solve of the base under mixed fine levels; phi of the mixed
+    chain against the FP64 one."""
+    import torch
+    from paper_2604_06035_gb300 import inputs
+    t0 = time.perf_counter()
+    cfg = inputs.mixed_amr()
+    gen_s = time.perf_counter() - t0
+    levels, parent = [], None
+    for lev, c, r in zip(cfg["levels"], cfg["coords"], cfg["rho"]):
+        L = cmg.cmg_level_build(ctx, lev, cmg.cmg_morton_encode(ctx, torch.from_numpy(c).to(dev)), parent=parent)
+        rho = torch.from_numpy(r).to(dev)
+        cmg.cmg_level_set_density(L, rho, cfg["rho_bar"])
+        levels.append((lev, L, rho))
+        parent = L
+    out = {"workload": "256^3 periodic lognormal base (sigma 2, k^-2) + 3 levels refined at rho > 8 rho_bar",
+           "levels": cfg["levels"], "octs": [len(c) for c in cfg["coords"]],
+           "cells": int(sum(8 * len(c) for c in cfg["coords"])), "generate_s": gen_s, "tol": args.tol}
+
+    def chain(precs, reps=5):
+        per = [[] for _ in levels]
+        stats = [None] * len(levels)
+        for _ in range(reps):
+            for k, (lev, L, rho) in enumerate(levels):
+                cmg.cmg_level_set_phi(L, torch.zeros_like(rho))
+                rc, st = cmg.cmg_level_solve(L, tol=args.tol, precision=precs[k])
+                per[k].append(st["ms"])
+                stats[k] = st
+        ms = [statistics.median(p[1:]) for p in per]
+        upd = sum(st["cell_updates"] for st in stats)
+        return {"ms_to_tol_per_level": ms, "ms_total": sum(ms),
+                "iterations": [st["cycles"] for st in stats], "rel_final": [st["rel_final"] for st in stats],
+                "Mcell_updates_per_s": upd / (sum(ms) / 1e3) / 1e6}
+
+    F64, MIX, FFT = cmg.CMG_PREC_FP64, cmg.CMG_PREC_MIXED, cmg.CMG_PREC_FFT
+    out["fp64"] = chain([F64] * len(levels))
+    phi64 = [cmg.cmg_level_get_phi(L, device=True).clone() for _, L, _ in levels]
+    out["mixed"] = chain([MIX] * len(levels))
+    err = []
+    for (lev, L, rho), p64 in zip(levels, phi64):
+        p = cmg.cmg_level_get_phi(L, device=True)
+        err.append(float((p - p64).abs().max() / p64.abs().max()))
+    out["mixed"]["phi_rel_err_vs_fp64"] = err
+    # the precision effect alone: both chains refined to 1e-12 (untimed)
+    tight = []
+    for precs in ([F64] * len(levels), [MIX] * len(levels)):
+        got = []
+        for k, (lev, L, rho) in enumerate(levels):
+            cmg.cmg_level_set_phi(L, torch.zeros_like(rho))
+            cmg.cmg_level_solve(L, tol=1e-12, precision=precs[k])
+            got.append(cmg.cmg_level_get_phi(L, device=True).clone())
+        tight.append(got)
+    out["mixed"]["phi_rel_err_vs_fp64_both_at_1e-12"] = [
+        float((b - a).abs().max() / a.abs().max()) for a, b in zip(*tight)]
+    out["fft_base_mixed_fine"] = chain([FFT] + [MIX] * (len(levels) - 1))
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_total"] / out["mixed"]["ms_total"]
+    out["speedup_fft_mixed_vs_fp64"] = out["fp64"]["ms_total"] / out["fft_base_mixed_fine"]["ms_total"]
+    for _, L, _ in reversed(levels):
+        cmg.cmg_level_destroy(L)
+    return out
+
+
 def bench_forward(cmg, ctx, dev, peaks, D=64, batches=(1, 8), reps=20, paths=("tcgen05", "mma_sync")):
     """The U-Net forward alone on random inputs (untrained He-normal weights):
     device time per call and the convolutions' tensor-core rate."""
@@ -619,9 +686,15 @@ def run_ours(args, rank, local, world):
     hbm, hbm_src = peaks["hbm"], peaks["hbm_src"]
     fp64 = dname.endswith("fp64")
     if fp64:
+        # the sweep issues 6 FP64-pipe instructions (5 DADD + 1 DFMA = 7 flop)
+        # per cell update against 2 per SM per clock: 7/12 of the nominal
+        # flop rate is the pipe's ceiling for this instruction mix
+        pipe_ops = achieved_tflops * 1e12 * 6.0 / 7.0
         roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved_tflops / FP64_PEAK_TFLOPS, "kernel": dname,
                     "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (FMA = 2)",
+                    "fp64_pipe_frac": pipe_ops / (FP64_PEAK_TFLOPS * 1e12 / 2.0),
+                    "fp64_pipe_note": "6 FP64 instructions per cell update vs 2 per SM per clock (nominal)",
                     "hbm_equivalent_gbs": achieved_gbs, "hbm_frac_of_%s" % hbm_src: achieved_gbs / hbm}
     else:
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
@@ -721,6 +794,8 @@ def run_ours(args, rank, local, world):
         out["smoother_512"] = bench_smoother(cmg, ctx, dev, peaks)
         out["fft"] = bench_fft(cmg, ctx, dev, B, rho[0], args, peaks)
         out["pcg"] = bench_pcg(cmg, ctx, dev, (("base", B, rho[0]), ("fine", F, rho[1])), args)
+        if not args.no_amr3:
+            out["amr3_256"] = bench_amr3(cmg, ctx, dev, args)
         if not args.no_learned:
             out["learned"] = bench_learned(cmg, ctx, dev, args, peaks)
         if rank == 0 and world == 1:
@@ -755,6 +830,8 @@ def run_block(args):
         B = cmg.cmg_level_build(ctx, 7, cmg.cmg_morton_encode(ctx, torch.from_numpy(cfg["coords"][0]).to(dev)))
         out = bench_fft(cmg, ctx, dev, B, torch.from_numpy(cfg["rho"][0]).to(dev), args, peaks)
         cmg.cmg_level_destroy(B)
+    elif args.block == "amr3":
+        out = bench_amr3(cmg, ctx, dev, args)
     elif args.block == "pcg":
         from paper_2604_06035_gb300 import inputs
         cfg = inputs.two_level_amr(base_level=7, seed=2)
