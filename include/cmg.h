@@ -121,6 +121,14 @@ int cmg_ctx_launch_count(cmg_ctx *ctx, int64_t *launches);
 int cmg_morton_encode(cmg_ctx *ctx, const uint32_t *ijk, int64_t n, uint64_t *keys, cmg_mem mem);
 int cmg_morton_decode(cmg_ctx *ctx, const uint64_t *keys, int64_t n, uint32_t *ijk, cmg_mem mem);
 
+/* 128-bit Morton keys (Sec. 4.2: B = 42 bits per coordinate, levels up to 43
+ * with n_x = 1): ijk is [n][3] uint64, keys is [n][2] uint64 = (bits 0..63,
+ * bits 64..127) of each key; bit b of i, j, k goes to key bit 3b, 3b+1, 3b+2
+ * as in the 64-bit key, which a 128-bit key of coordinates below 2^21 equals
+ * in its low word.  Coordinates >= 2^42 give CMG_ERR_KEY_OUT_OF_RANGE. */
+int cmg_morton_encode128(cmg_ctx *ctx, const uint64_t *ijk, int64_t n, uint64_t *keys, cmg_mem mem);
+int cmg_morton_decode128(cmg_ctx *ctx, const uint64_t *keys, int64_t n, uint64_t *ijk, cmg_mem mem);
+
 /* Build level `level` (>= 1) from n_octs Morton keys (Sec. 4.2; App. B):
  * per-level open-addressing hash table (hash of App. B Eq. (hash_func),
  * linear probing, power-of-two capacity with fill <= 0.7), the neighbour
@@ -133,6 +141,15 @@ int cmg_morton_decode(cmg_ctx *ctx, const uint64_t *keys, int64_t n, uint32_t *i
  * Errors: DUPLICATE_KEY, KEY_OUT_OF_RANGE, MISSING_PARENT, INVALID_ARG, OOM. */
 int cmg_level_build(cmg_ctx *ctx, int level, int nx, int periodic_mask, const uint64_t *keys,
                     int64_t n_octs, cmg_mem mem, cmg_level *parent, cmg_level **out);
+/* The same with 128-bit keys ([n_octs][2] uint64, see cmg_morton_encode128)
+ * for levels up to 43: the hash reduces a key to 64 bits by the XOR of its
+ * halves before Eq. (hash_func) (App. B).  The parent must be a 128-bit level
+ * too (INVALID_ARG otherwise; likewise for the 64-bit call); everything else
+ * (solve, fields, batches) is the same for both widths. */
+int cmg_level_build128(cmg_ctx *ctx, int level, int nx, int periodic_mask, const uint64_t *keys,
+                       int64_t n_octs, cmg_mem mem, cmg_level *parent, cmg_level **out);
+/* 64 or 128. */
+int cmg_level_key_bits(const cmg_level *lvl, int *bits);
 int cmg_level_destroy(cmg_level *lvl);
 int cmg_level_n_octs(const cmg_level *lvl, int64_t *n_octs);
 /* Hash capacity (power of two) of the level's table. */
@@ -140,6 +157,9 @@ int cmg_level_hash_capacity(const cmg_level *lvl, int64_t *capacity);
 
 /* Hash lookup (App. B): idx[t] = oct index of key q[t], or -1. */
 int cmg_level_lookup(cmg_level *lvl, const uint64_t *q, int64_t n, int32_t *idx, cmg_mem mem);
+/* The same for a 128-bit level; q is [n][2] uint64.  Each call rejects a
+ * level of the other width with INVALID_ARG. */
+int cmg_level_lookup128(cmg_level *lvl, const uint64_t *q, int64_t n, int32_t *idx, cmg_mem mem);
 /* Neighbour cache, [n][7] int32: column 0 = the oct itself, 1..6 = the
  * same-level neighbour in -x,+x,-y,+y,-z,+z or -1 (App. D.1). */
 int cmg_level_get_neighbors(cmg_level *lvl, int32_t *out, cmg_mem mem);
@@ -190,6 +210,8 @@ int cmg_level_set_spin_budget(cmg_level *lvl, int64_t cycles);
 int cmg_level_mg_depth(const cmg_level *lvl, int *depth);
 int cmg_level_mg_info(const cmg_level *lvl, int m, int64_t *n_octs, int *amr_level);
 int cmg_level_mg_keys(cmg_level *lvl, int m, uint64_t *out, cmg_mem mem);
+/* Keys of MG level m of a 128-bit level, [n][2] uint64. */
+int cmg_level_mg_keys128(cmg_level *lvl, int m, uint64_t *out, cmg_mem mem);
 int cmg_level_mg_active(cmg_level *lvl, int m, uint8_t *out /* [n][8] 0/1 */, cmg_mem mem);
 
 typedef enum { CMG_FIELD_PHI = 0, CMG_FIELD_F = 1 } cmg_field;

@@ -14,8 +14,14 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define EMPTY_KEY UINT64_MAX
-#define MORTON_BITS 21
+#define MORTON_BITS 21      /* 64-bit keys (Sec. 4.2) */
+#define MORTON_BITS_WIDE 42 /* 128-bit keys (Sec. 4.2) */
+
+/* Every level keeps its keys as 128-bit integers: a 64-bit key (B = 21) is the
+ * same integer with its upper half zero, and its hash (the XOR fold of the two
+ * halves, App. B) is the key itself. */
+typedef unsigned __int128 okey;
+#define EMPTY_KEY (~(okey)0)
 
 /* ------------------------------------------------------------------ keys */
 
@@ -52,6 +58,57 @@ void or_decode_many(const uint64_t *keys, int64_t n, uint32_t *ijk) {
   for (int64_t t = 0; t < n; t++) or_morton_decode(keys[t], &ijk[3 * t], &ijk[3 * t + 1], &ijk[3 * t + 2]);
 }
 
+/* App. A Alg. 1 with B = 42 on 128-bit keys. */
+static okey key_encode(uint64_t i, uint64_t j, uint64_t k) {
+  okey m = 0;
+  /* bits above the highest set coordinate bit contribute nothing */
+  for (int b = 0; b < MORTON_BITS_WIDE && ((i | j | k) >> b) != 0; b++) {
+    m |= (okey)((i >> b) & 1u) << (3 * b);
+    m |= (okey)((j >> b) & 1u) << (3 * b + 1);
+    m |= (okey)((k >> b) & 1u) << (3 * b + 2);
+  }
+  return m;
+}
+
+static void key_decode(okey m, uint64_t c[3]) {
+  c[0] = c[1] = c[2] = 0;
+  for (int b = 0; b < MORTON_BITS_WIDE && (m >> (3 * b)) != 0; b++) {
+    c[0] |= (uint64_t)((m >> (3 * b)) & 1u) << b;
+    c[1] |= (uint64_t)((m >> (3 * b + 1)) & 1u) << b;
+    c[2] |= (uint64_t)((m >> (3 * b + 2)) & 1u) << b;
+  }
+}
+
+static okey key_from_words(const uint64_t *w) { return ((okey)w[1] << 64) | (okey)w[0]; }
+static void key_to_words(okey k, uint64_t *w) {
+  w[0] = (uint64_t)k;
+  w[1] = (uint64_t)(k >> 64);
+}
+
+void or_encode128_many(const uint64_t *ijk, int64_t n, uint64_t *out) {
+  for (int64_t t = 0; t < n; t++) key_to_words(key_encode(ijk[3 * t], ijk[3 * t + 1], ijk[3 * t + 2]), out + 2 * t);
+}
+
+void or_decode128_many(const uint64_t *keys, int64_t n, uint64_t *ijk) {
+  for (int64_t t = 0; t < n; t++) key_decode(key_from_words(keys + 2 * t), ijk + 3 * t);
+}
+
+/* App. A Alg. 2 on keys of either width: returns 0 for "no neighbour". */
+static int key_neighbor(okey m, int d, uint64_t n_per_dim, int periodic_mask, okey *out) {
+  uint64_t c[3];
+  key_decode(m, c);
+  int axis = d / 2;
+  int64_t v = (int64_t)c[axis] + ((d & 1) ? 1 : -1);
+  if ((periodic_mask >> axis) & 1) {
+    v = ((v % (int64_t)n_per_dim) + (int64_t)n_per_dim) % (int64_t)n_per_dim;
+  } else if (v < 0 || v >= (int64_t)n_per_dim) {
+    return 0;
+  }
+  c[axis] = (uint64_t)v;
+  *out = key_encode(c[0], c[1], c[2]);
+  return 1;
+}
+
 /* App. A Alg. 2: decode, step one cell along the axis of direction d, wrap
  * periodically (mod n_d) or report "no neighbour" (-1), re-encode. */
 int64_t or_neighbor_key(uint64_t m, int d, uint32_t n_per_dim, int periodic_mask) {
@@ -76,6 +133,10 @@ uint64_t or_hash_fn(uint64_t h) {
   return t ^ (t >> 13);
 }
 
+/* App. B: a key is reduced to 64 bits before Eq. (hash_func) -- the XOR of its
+ * upper and lower halves (128-bit keys), the key itself (64-bit keys). */
+static uint64_t key_hash(okey k) { return or_hash_fn((uint64_t)k ^ (uint64_t)(k >> 64)); }
+
 /* Smallest power of two with fill n/cap <= 0.7 (App. B). */
 int64_t or_hash_capacity_for(int64_t n) {
   int64_t cap = 1;
@@ -87,13 +148,13 @@ int64_t or_hash_capacity_for(int64_t n) {
 
 typedef struct {
   int64_t cap;
-  uint64_t *key;
+  okey *key;
   int32_t *val;
 } hashtab;
 
 static int ht_init(hashtab *h, int64_t n) {
   h->cap = or_hash_capacity_for(n);
-  h->key = (uint64_t *)malloc(sizeof(uint64_t) * h->cap);
+  h->key = (okey *)malloc(sizeof(okey) * h->cap);
   h->val = (int32_t *)malloc(sizeof(int32_t) * h->cap);
   if (!h->key || !h->val) return OR_ERR_OOM;
   for (int64_t s = 0; s < h->cap; s++) {
@@ -111,9 +172,9 @@ static void ht_free(hashtab *h) {
 }
 
 /* Linear probing from slot h(M) & (cap-1) (App. B). */
-static int ht_insert(hashtab *h, uint64_t k, int32_t v) {
+static int ht_insert(hashtab *h, okey k, int32_t v) {
   uint64_t mask = (uint64_t)h->cap - 1;
-  uint64_t s = or_hash_fn(k) & mask;
+  uint64_t s = key_hash(k) & mask;
   for (;;) {
     if (h->key[s] == EMPTY_KEY) {
       h->key[s] = k;
@@ -125,9 +186,9 @@ static int ht_insert(hashtab *h, uint64_t k, int32_t v) {
   }
 }
 
-static int32_t ht_find(const hashtab *h, uint64_t k) {
+static int32_t ht_find(const hashtab *h, okey k) {
   uint64_t mask = (uint64_t)h->cap - 1;
-  uint64_t s = or_hash_fn(k) & mask;
+  uint64_t s = key_hash(k) & mask;
   for (;;) {
     if (h->key[s] == EMPTY_KEY) return -1;
     if (h->key[s] == k) return h->val[s];
@@ -140,7 +201,7 @@ static int32_t ht_find(const hashtab *h, uint64_t k) {
 typedef struct {
   int lev;
   int64_t n;
-  uint64_t *key;
+  okey *key;
   hashtab ht;
   int32_t *nbr;    /* [n][7]: j = 0 self, 1..6 = -x,+x,-y,+y,-z,+z */
   uint8_t *active; /* [n][8] */
@@ -160,20 +221,20 @@ struct or_level {
   int periodic_full;
 };
 
-static uint32_t octs_per_dim(int lev, int nx) { return (uint32_t)((uint64_t)nx << (lev - 1)); }
+static uint64_t octs_per_dim(int lev, int nx) { return (uint64_t)nx << (lev - 1); }
 static uint64_t cells_per_dim(int lev, int nx) { return (uint64_t)nx << lev; }
 static double cell_h(int lev, int nx) { return ldexp(1.0, -lev) / (double)nx; }
 
 static int parity(int c) { return ((c & 1) + ((c >> 1) & 1) + ((c >> 2) & 1)) & 1; }
 
-static int build_nbr(mglev *g, uint32_t npd, int pmask) {
+static int build_nbr(mglev *g, uint64_t npd, int pmask) {
   g->nbr = (int32_t *)malloc(sizeof(int32_t) * 7 * (g->n ? g->n : 1));
   if (!g->nbr) return OR_ERR_OOM;
   for (int64_t i = 0; i < g->n; i++) {
     g->nbr[7 * i] = (int32_t)i;
     for (int d = 0; d < 6; d++) {
-      int64_t nk = or_neighbor_key(g->key[i], d, npd, pmask);
-      g->nbr[7 * i + 1 + d] = nk < 0 ? -1 : ht_find(&g->ht, (uint64_t)nk);
+      okey nk;
+      g->nbr[7 * i + 1 + d] = key_neighbor(g->key[i], d, npd, pmask, &nk) ? ht_find(&g->ht, nk) : -1;
     }
   }
   return OR_OK;
@@ -207,17 +268,17 @@ static void free_mg(mglev *g) {
 }
 
 /* Global cell coordinates at level lev of child c of the oct with key k. */
-static void cell_coords(uint64_t k, int c, uint64_t X[3]) {
-  uint32_t o[3];
-  or_morton_decode(k, &o[0], &o[1], &o[2]);
-  for (int a = 0; a < 3; a++) X[a] = 2 * (uint64_t)o[a] + ((c >> a) & 1);
+static void cell_coords(okey k, int c, uint64_t X[3]) {
+  uint64_t o[3];
+  key_decode(k, o);
+  for (int a = 0; a < 3; a++) X[a] = 2 * o[a] + ((c >> a) & 1);
 }
 
 /* Look up the cell at global coordinates Y (level lev, possibly outside the
  * box) in MG level g: returns 1 and (oct, child) if its oct exists. */
 static int find_cell(const hashtab *ht, int64_t Y[3], int lev, int nx, int pmask, int32_t *oct, int *child) {
   int64_t ncell = (int64_t)cells_per_dim(lev, nx);
-  uint32_t o[3];
+  uint64_t o[3];
   int ch = 0;
   for (int a = 0; a < 3; a++) {
     int64_t v = Y[a];
@@ -226,10 +287,10 @@ static int find_cell(const hashtab *ht, int64_t Y[3], int lev, int nx, int pmask
     } else if (v < 0 || v >= ncell) {
       return 0;
     }
-    o[a] = (uint32_t)(v >> 1);
+    o[a] = (uint64_t)(v >> 1);
     ch |= (int)(v & 1) << a;
   }
-  int32_t idx = ht_find(ht, or_morton_encode(o[0], o[1], o[2]));
+  int32_t idx = ht_find(ht, key_encode(o[0], o[1], o[2]));
   if (idx < 0) return 0;
   *oct = idx;
   *child = ch;
@@ -273,7 +334,7 @@ static int face_rank(int c, int a) {
 }
 
 /* Position of the ghost cell across face d of cell (k, c) at level lev. */
-static int ghost_position(uint64_t k, int c, int d, int lev, int nx, int pmask, uint64_t G[3]) {
+static int ghost_position(okey k, int c, int d, int lev, int nx, int pmask, uint64_t G[3]) {
   cell_coords(k, c, G);
   int a = d / 2;
   int64_t v = (int64_t)G[a] + ((d & 1) ? 1 : -1);
@@ -287,20 +348,21 @@ static int ghost_position(uint64_t k, int c, int d, int lev, int nx, int pmask, 
   return 1;
 }
 
-int or_level_build(int level, int nx, int pmask, const uint64_t *keys, int64_t n, or_level *parent,
-                   or_level **out) {
+/* Level build on 128-bit keys; bits = 21 or 42 sets the coordinate range. */
+static int level_build(int level, int nx, int pmask, const okey *keys, int64_t n, or_level *parent,
+                       or_level **out, int bits) {
   *out = NULL;
-  if (level < 1 || nx < 1 || n < 0 || pmask < 0 || pmask > 7) return OR_ERR_INVALID_ARG;
-  if ((uint64_t)nx << (level - 1) > (1ull << MORTON_BITS)) return OR_ERR_INVALID_ARG;
+  if (level < 1 || nx < 1 || nx > (1 << 20) || n < 0 || pmask < 0 || pmask > 7) return OR_ERR_INVALID_ARG;
+  if (level > bits + 1 || (uint64_t)nx << (level - 1) > (1ull << bits)) return OR_ERR_INVALID_ARG;
   if (parent && (parent->lev != level - 1 || parent->nx != nx || parent->pmask != pmask))
     return OR_ERR_INVALID_ARG;
-  uint32_t npd = octs_per_dim(level, nx);
+  uint64_t npd = octs_per_dim(level, nx);
   for (int64_t t = 0; t < n; t++) {
-    if (keys[t] >> 63) return OR_ERR_KEY_OUT_OF_RANGE;
-    uint32_t i, j, k;
-    or_morton_decode(keys[t], &i, &j, &k);
-    if (or_morton_encode(i, j, k) != keys[t]) return OR_ERR_KEY_OUT_OF_RANGE;
-    if (i >= npd || j >= npd || k >= npd) return OR_ERR_KEY_OUT_OF_RANGE;
+    if (bits == MORTON_BITS ? (keys[t] >> 63) != 0 : (keys[t] >> 126) != 0) return OR_ERR_KEY_OUT_OF_RANGE;
+    uint64_t c[3];
+    key_decode(keys[t], c);
+    if (key_encode(c[0], c[1], c[2]) != keys[t]) return OR_ERR_KEY_OUT_OF_RANGE;
+    if (c[0] >= npd || c[1] >= npd || c[2] >= npd) return OR_ERR_KEY_OUT_OF_RANGE;
   }
   or_level *L = (or_level *)calloc(1, sizeof(or_level));
   if (!L) return OR_ERR_OOM;
@@ -313,8 +375,8 @@ int or_level_build(int level, int nx, int pmask, const uint64_t *keys, int64_t n
   mglev *g = &L->mg[0];
   g->lev = level;
   g->n = n;
-  g->key = (uint64_t *)malloc(sizeof(uint64_t) * (n ? n : 1));
-  memcpy(g->key, keys, sizeof(uint64_t) * n);
+  g->key = (okey *)malloc(sizeof(okey) * (n ? n : 1));
+  memcpy(g->key, keys, sizeof(okey) * n);
   int st = ht_init(&g->ht, n);
   for (int64_t t = 0; t < n && st == OR_OK; t++) st = ht_insert(&g->ht, keys[t], (int32_t)t);
   if (st == OR_OK) st = build_nbr(g, npd, pmask);
@@ -326,7 +388,7 @@ int or_level_build(int level, int nx, int pmask, const uint64_t *keys, int64_t n
   }
   for (int64_t t = 0; t < 8 * n; t++) g->active[t] = 1;
   L->depth = 1;
-  L->periodic_full = (parent == NULL && pmask == 7 && (uint64_t)n == (uint64_t)npd * npd * npd);
+  L->periodic_full = (parent == NULL && pmask == 7 && npd <= 2048 && (uint64_t)n == npd * npd * npd);
 
   /* morton_nbor_cell (App. B): father cell of every missing neighbour, and a
    * check that every Dirichlet ghost value can be interpolated. */
@@ -338,18 +400,18 @@ int or_level_build(int level, int nx, int pmask, const uint64_t *keys, int64_t n
     for (int64_t i = 0; i < n && st == OR_OK; i++)
       for (int d = 0; d < 6 && st == OR_OK; d++) {
         if (g->nbr[7 * i + 1 + d] >= 0) continue;
-        int64_t nk = or_neighbor_key(keys[i], d, npd, pmask);
-        if (nk < 0) {
+        okey nk;
+        if (!key_neighbor(keys[i], d, npd, pmask, &nk)) {
           st = OR_ERR_MISSING_PARENT;
           break;
         }
-        int32_t p = ht_find(&parent->mg[0].ht, (uint64_t)nk >> 3);
+        int32_t p = ht_find(&parent->mg[0].ht, nk >> 3);
         if (p < 0) {
           st = OR_ERR_MISSING_PARENT;
           break;
         }
         L->father[12 * i + 2 * d] = p;
-        L->father[12 * i + 2 * d + 1] = (int32_t)((uint64_t)nk & 7);
+        L->father[12 * i + 2 * d + 1] = (int32_t)(nk & 7);
         int a = d / 2, side = d & 1;
         for (int c = 0; c < 8; c++) {
           if (((c >> a) & 1) != side) continue;
@@ -374,13 +436,13 @@ int or_level_build(int level, int nx, int pmask, const uint64_t *keys, int64_t n
     if (cur->lev == 1) break;
     hashtab tmp;
     ht_init(&tmp, cur->n);
-    uint64_t *pk = (uint64_t *)malloc(sizeof(uint64_t) * (cur->n ? cur->n : 1));
+    okey *pk = (okey *)malloc(sizeof(okey) * (cur->n ? cur->n : 1));
     int64_t np = 0;
     for (int64_t i = 0; i < cur->n; i++) {
       int full = 1;
       for (int c = 0; c < 8; c++) full &= cur->active[8 * i + c];
       if (!full) continue;
-      uint64_t k = cur->key[i] >> 3;
+      okey k = cur->key[i] >> 3;
       if (ht_find(&tmp, k) < 0) {
         ht_insert(&tmp, k, (int32_t)np);
         pk[np++] = k;
@@ -414,6 +476,26 @@ int or_level_build(int level, int nx, int pmask, const uint64_t *keys, int64_t n
   return OR_OK;
 }
 
+int or_level_build(int level, int nx, int pmask, const uint64_t *keys, int64_t n, or_level *parent,
+                   or_level **out) {
+  okey *k = (okey *)malloc(sizeof(okey) * (n > 0 ? n : 1));
+  if (!k) return OR_ERR_OOM;
+  for (int64_t t = 0; t < n; t++) k[t] = (okey)keys[t];
+  int st = level_build(level, nx, pmask, k, n, parent, out, MORTON_BITS);
+  free(k);
+  return st;
+}
+
+int or_level_build128(int level, int nx, int pmask, const uint64_t *keys, int64_t n, or_level *parent,
+                      or_level **out) {
+  okey *k = (okey *)malloc(sizeof(okey) * (n > 0 ? n : 1));
+  if (!k) return OR_ERR_OOM;
+  for (int64_t t = 0; t < n; t++) k[t] = key_from_words(keys + 2 * t);
+  int st = level_build(level, nx, pmask, k, n, parent, out, MORTON_BITS_WIDE);
+  free(k);
+  return st;
+}
+
 void or_level_free(or_level *L) {
   if (!L) return;
   for (int m = 0; m < L->depth; m++) free_mg(&L->mg[m]);
@@ -426,13 +508,18 @@ void or_level_free(or_level *L) {
 int64_t or_level_n_octs(const or_level *L) { return L->n; }
 int64_t or_level_hash_capacity(const or_level *L) { return L->mg[0].ht.cap; }
 
+/* slot keys as their low 64 bits (a 64-bit level's keys; empty slots all ones) */
 void or_level_hash_dump(const or_level *L, uint64_t *keys, int32_t *vals) {
-  memcpy(keys, L->mg[0].ht.key, sizeof(uint64_t) * L->mg[0].ht.cap);
+  for (int64_t t = 0; t < L->mg[0].ht.cap; t++) keys[t] = (uint64_t)L->mg[0].ht.key[t];
   memcpy(vals, L->mg[0].ht.val, sizeof(int32_t) * L->mg[0].ht.cap);
 }
 
 void or_level_lookup(const or_level *L, const uint64_t *q, int64_t n, int32_t *out) {
-  for (int64_t t = 0; t < n; t++) out[t] = ht_find(&L->mg[0].ht, q[t]);
+  for (int64_t t = 0; t < n; t++) out[t] = ht_find(&L->mg[0].ht, (okey)q[t]);
+}
+
+void or_level_lookup128(const or_level *L, const uint64_t *q, int64_t n, int32_t *out) {
+  for (int64_t t = 0; t < n; t++) out[t] = ht_find(&L->mg[0].ht, key_from_words(q + 2 * t));
 }
 
 void or_level_neighbors(const or_level *L, int32_t *out) {
@@ -485,7 +572,10 @@ int or_level_mg_depth(const or_level *L) { return L->depth; }
 int64_t or_level_mg_n_octs(const or_level *L, int m) { return L->mg[m].n; }
 int or_level_mg_lev(const or_level *L, int m) { return L->mg[m].lev; }
 void or_level_mg_keys(const or_level *L, int m, uint64_t *out) {
-  memcpy(out, L->mg[m].key, sizeof(uint64_t) * L->mg[m].n);
+  for (int64_t t = 0; t < L->mg[m].n; t++) out[t] = (uint64_t)L->mg[m].key[t];
+}
+void or_level_mg_keys128(const or_level *L, int m, uint64_t *out) {
+  for (int64_t t = 0; t < L->mg[m].n; t++) key_to_words(L->mg[m].key[t], out + 2 * t);
 }
 void or_level_mg_active(const or_level *L, int m, uint8_t *out) {
   memcpy(out, L->mg[m].active, 8 * L->mg[m].n);

@@ -48,6 +48,10 @@ uint64_t or_morton_encode(uint32_t i, uint32_t j, uint32_t k);
 void or_morton_decode(uint64_t m, uint32_t *i, uint32_t *j, uint32_t *k);
 void or_encode_many(const uint32_t *ijk, int64_t n, uint64_t *out);
 void or_decode_many(const uint64_t *keys, int64_t n, uint32_t *ijk);
+/* 128-bit keys (Sec. 4.2, B = 42): ijk [n][3] uint64 <-> keys [n][2] uint64
+ * (bits 0..63, bits 64..127). */
+void or_encode128_many(const uint64_t *ijk, int64_t n, uint64_t *out);
+void or_decode128_many(const uint64_t *keys, int64_t n, uint64_t *ijk);
 /* Neighbour key of m in direction d (0..5 = -x,+x,-y,+y,-z,+z) on a grid of
  * n_per_dim octs per axis; periodic wrap on axes whose bit is set in
  * periodic_mask, else -1 when the step leaves [0, n_per_dim). */
@@ -60,12 +64,17 @@ typedef struct or_level or_level;
 
 int or_level_build(int level, int nx, int periodic_mask, const uint64_t *keys,
                    int64_t n, or_level *parent, or_level **out);
+/* The same with 128-bit keys [n][2] (Sec. 4.2, B = 42, levels up to 43); the
+ * hash reduces a key by the XOR of its halves (App. B). */
+int or_level_build128(int level, int nx, int periodic_mask, const uint64_t *keys, int64_t n, or_level *parent,
+                      or_level **out);
 void or_level_free(or_level *L);
 int64_t or_level_n_octs(const or_level *L);
 int64_t or_level_hash_capacity(const or_level *L);
 /* Hash-table contents: slot keys (UINT64_MAX = empty) and values. */
 void or_level_hash_dump(const or_level *L, uint64_t *keys, int32_t *vals);
 void or_level_lookup(const or_level *L, const uint64_t *q, int64_t n, int32_t *out);
+void or_level_lookup128(const or_level *L, const uint64_t *q, int64_t n, int32_t *out);
 void or_level_neighbors(const or_level *L, int32_t *out /* [n][7] */);
 /* Father cell of each missing same-level neighbour: [n][6][2] = (parent oct,
  * octant), (-1,-1) where the neighbour exists or no parent is given. */
@@ -87,6 +96,7 @@ int or_level_mg_depth(const or_level *L);
 int64_t or_level_mg_n_octs(const or_level *L, int m);
 int or_level_mg_lev(const or_level *L, int m);
 void or_level_mg_keys(const or_level *L, int m, uint64_t *out);
+void or_level_mg_keys128(const or_level *L, int m, uint64_t *out);
 void or_level_mg_active(const or_level *L, int m, uint8_t *out /* [n][8] */);
 /* field: 0 = phi, 1 = f, 2 = r */
 void or_level_mg_get(const or_level *L, int m, int field, double *out);

@@ -42,6 +42,11 @@ def lib():
             "or_morton_encode": (C.c_uint64, [C.c_uint32] * 3),
             "or_encode_many": (None, [_P, _I64, _P]),
             "or_decode_many": (None, [_P, _I64, _P]),
+            "or_encode128_many": (None, [_P, _I64, _P]),
+            "or_decode128_many": (None, [_P, _I64, _P]),
+            "or_level_build128": (C.c_int, [C.c_int, C.c_int, C.c_int, _P, _I64, _P, C.POINTER(_P)]),
+            "or_level_lookup128": (None, [_P, _P, _I64, _P]),
+            "or_level_mg_keys128": (None, [_P, C.c_int, _P]),
             "or_neighbor_key": (C.c_int64, [C.c_uint64, C.c_int, C.c_uint32, C.c_int]),
             "or_hash_fn": (C.c_uint64, [C.c_uint64]),
             "or_hash_capacity_for": (C.c_int64, [_I64]),
@@ -102,6 +107,22 @@ def morton_decode(keys):
     return out
 
 
+def morton_encode128(ijk):
+    """128-bit keys (B = 42) of [n, 3] uint64 coordinates: [n, 2] uint64
+    (bits 0..63, bits 64..127)."""
+    ijk = np.ascontiguousarray(ijk, dtype=np.uint64).reshape(-1, 3)
+    out = np.empty((len(ijk), 2), dtype=np.uint64)
+    lib().or_encode128_many(_ptr(ijk), len(ijk), _ptr(out))
+    return out
+
+
+def morton_decode128(keys):
+    keys = np.ascontiguousarray(keys, dtype=np.uint64).reshape(-1, 2)
+    out = np.empty((len(keys), 3), dtype=np.uint64)
+    lib().or_decode128_many(_ptr(keys), len(keys), _ptr(out))
+    return out
+
+
 def neighbor_key(m, d, n_per_dim, periodic_mask=7):
     return lib().or_neighbor_key(int(m), int(d), int(n_per_dim), int(periodic_mask))
 
@@ -128,15 +149,19 @@ class Level:
     """One AMR level of octs (plus its multigrid hierarchy) in the oracle."""
 
     def __init__(self, level, keys, parent=None, nx=1, periodic_mask=7):
-        keys = np.ascontiguousarray(keys, dtype=np.uint64).ravel()
+        """keys: [n] uint64 (64-bit keys) or [n, 2] uint64 (128-bit keys)."""
+        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        self.wide = keys.ndim == 2
+        keys = keys.reshape(-1, 2) if self.wide else keys.ravel()
         self._keys = keys
         self.level = level
         self.parent = parent  # keep alive
         h = C.c_void_p()
-        rc = lib().or_level_build(level, nx, periodic_mask, _ptr(keys), len(keys),
-                                  parent._h if parent is not None else None, C.byref(h))
+        build = lib().or_level_build128 if self.wide else lib().or_level_build
+        rc = build(level, nx, periodic_mask, _ptr(keys), len(keys), parent._h if parent is not None else None,
+                   C.byref(h))
         if rc != OR_OK:
-            raise OracleError(rc, "or_level_build")
+            raise OracleError(rc, "or_level_build128" if self.wide else "or_level_build")
         self._h = h
         self.n = len(keys)
 
@@ -158,6 +183,11 @@ class Level:
         return k, v
 
     def lookup(self, q):
+        if self.wide:
+            q = np.ascontiguousarray(q, dtype=np.uint64).reshape(-1, 2)
+            out = np.empty(len(q), dtype=np.int32)
+            lib().or_level_lookup128(self._h, _ptr(q), len(q), _ptr(out))
+            return out
         q = np.ascontiguousarray(q, dtype=np.uint64).ravel()
         out = np.empty(len(q), dtype=np.int32)
         lib().or_level_lookup(self._h, _ptr(q), len(q), _ptr(out))
@@ -214,6 +244,10 @@ class Level:
         return lib().or_level_mg_lev(self._h, m)
 
     def mg_keys(self, m):
+        if self.wide:
+            out = np.empty((self.mg_n_octs(m), 2), dtype=np.uint64)
+            lib().or_level_mg_keys128(self._h, m, _ptr(out))
+            return out
         out = np.empty(self.mg_n_octs(m), dtype=np.uint64)
         lib().or_level_mg_keys(self._h, m, _ptr(out))
         return out

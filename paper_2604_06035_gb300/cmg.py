@@ -85,6 +85,12 @@ _SIGS = {
     "cmg_ctx_reset_profile": (_I, [_P]),
     "cmg_ctx_launch_count": (_I, [_P, C.POINTER(_I64)]),
     "cmg_morton_encode": (_I, [_P, _P, _I64, _P, _I]),
+    "cmg_morton_encode128": (_I, [_P, _P, _I64, _P, _I]),
+    "cmg_morton_decode128": (_I, [_P, _P, _I64, _P, _I]),
+    "cmg_level_build128": (_I, [_P, _I, _I, _I, _P, _I64, _I, _P, C.POINTER(_P)]),
+    "cmg_level_key_bits": (_I, [_P, C.POINTER(_I)]),
+    "cmg_level_lookup128": (_I, [_P, _P, _I64, _P, _I]),
+    "cmg_level_mg_keys128": (_I, [_P, _I, _P, _I]),
     "cmg_morton_decode": (_I, [_P, _P, _I64, _P, _I]),
     "cmg_level_build": (_I, [_P, _I, _I, _I, _P, _I64, _I, _P, C.POINTER(_P)]),
     "cmg_level_destroy": (_I, [_P]),
@@ -307,6 +313,26 @@ def cmg_morton_decode(ctx, keys, out=None):
     return res
 
 
+def cmg_morton_encode128(ctx, ijk, out=None):
+    """128-bit keys (B = 42) of [n, 3] uint64 coordinates: [n, 2] uint64
+    (low word, high word)."""
+    p, mem, keep = _in(ijk, np.uint64)
+    n = keep.numel() // 3 if _is_torch(keep) else keep.size // 3
+    q, mem2, res = _out((n, 2), np.uint64, device=(mem == CMG_MEM_DEVICE), out=out)
+    _same_mem(mem, mem2, "cmg_morton_encode128")
+    _check(lib().cmg_morton_encode128(ctx, p, n, q, mem), "cmg_morton_encode128")
+    return res
+
+
+def cmg_morton_decode128(ctx, keys, out=None):
+    p, mem, keep = _in(keys, np.uint64)
+    n = keep.numel() // 2 if _is_torch(keep) else keep.size // 2
+    q, mem2, res = _out((n, 3), np.uint64, device=(mem == CMG_MEM_DEVICE), out=out)
+    _same_mem(mem, mem2, "cmg_morton_decode128")
+    _check(lib().cmg_morton_decode128(ctx, p, n, q, mem), "cmg_morton_decode128")
+    return res
+
+
 class LevelHandle:
     """Owns a cmg_level* (destroyed with the object) and keeps its parent alive."""
 
@@ -334,6 +360,22 @@ def cmg_level_build(ctx, level, keys, parent=None, nx=1, periodic_mask=7):
     _check(lib().cmg_level_build(ctx, level, nx, periodic_mask, p, n, mem,
                                  parent.h if parent is not None else None, C.byref(h)), "cmg_level_build")
     return LevelHandle(h, parent, ctx)
+
+
+def cmg_level_build128(ctx, level, keys, parent=None, nx=1, periodic_mask=7):
+    """A level with 128-bit keys ([n, 2] uint64), levels up to 43."""
+    p, mem, keep = _in(keys, np.uint64)
+    n = keep.numel() // 2 if _is_torch(keep) else keep.size // 2
+    h = C.c_void_p()
+    _check(lib().cmg_level_build128(ctx, level, nx, periodic_mask, p, n, mem,
+                                    parent.h if parent is not None else None, C.byref(h)), "cmg_level_build128")
+    return LevelHandle(h, parent, ctx)
+
+
+def cmg_level_key_bits(lvl):
+    v = C.c_int()
+    _check(lib().cmg_level_key_bits(lvl.h, C.byref(v)), "cmg_level_key_bits")
+    return v.value
 
 
 def cmg_level_destroy(lvl):
@@ -441,6 +483,15 @@ def cmg_level_lookup(lvl, q, out=None):
     return res
 
 
+def cmg_level_lookup128(lvl, q, out=None):
+    p, mem, keep = _in(q, np.uint64)
+    n = keep.numel() // 2 if _is_torch(keep) else keep.size // 2
+    o, mem2, res = _out((n,), np.int32, device=(mem == CMG_MEM_DEVICE), out=out)
+    _same_mem(mem, mem2, "cmg_level_lookup128")
+    _check(lib().cmg_level_lookup128(lvl.h, p, n, o, mem), "cmg_level_lookup128")
+    return res
+
+
 def _get(fn, lvl, shape, dtype, device, out):
     o, mem, res = _out(shape, dtype, device=device, out=out)
     _check(getattr(lib(), fn)(lvl.h, o, mem), fn)
@@ -524,6 +575,13 @@ def cmg_level_mg_keys(lvl, m, device=False):
     n, _ = cmg_level_mg_info(lvl, m)
     o, mem, res = _out((n,), np.uint64, device=device)
     _check(lib().cmg_level_mg_keys(lvl.h, m, o, mem), "cmg_level_mg_keys")
+    return res
+
+
+def cmg_level_mg_keys128(lvl, m, device=False):
+    n, _ = cmg_level_mg_info(lvl, m)
+    o, mem, res = _out((n, 2), np.uint64, device=device)
+    _check(lib().cmg_level_mg_keys128(lvl.h, m, o, mem), "cmg_level_mg_keys128")
     return res
 
 

@@ -23,7 +23,7 @@ namespace cmg {
 
 namespace {
 
-constexpr int kBMaxLevels = 24;
+constexpr int kBMaxLevels = 48;
 
 struct BLevel {
   int64_t n, n_alloc;

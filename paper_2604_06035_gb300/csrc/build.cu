@@ -6,6 +6,7 @@
 #include <cmath>
 
 #include "cmg_internal.cuh"
+#include "keys.cuh"
 
 namespace cmg {
 
@@ -42,6 +43,7 @@ template uint32_t *DeviceBuffers::alloc<uint32_t>(int64_t, bool, cudaStream_t);
 template uint8_t *DeviceBuffers::alloc<uint8_t>(int64_t, bool, cudaStream_t);
 template double *DeviceBuffers::alloc<double>(int64_t, bool, cudaStream_t);
 template float *DeviceBuffers::alloc<float>(int64_t, bool, cudaStream_t);
+template Key128 *DeviceBuffers::alloc<Key128>(int64_t, bool, cudaStream_t);
 
 namespace {
 
@@ -65,20 +67,45 @@ __global__ void k_decode(const uint64_t *__restrict__ keys, int64_t n, uint32_t 
   ijk[3 * t + 2] = k;
 }
 
-// Range check (coordinates < npd, key < 2^63) and hash insert (A2).
-__global__ void k_insert_keys(const uint64_t *__restrict__ keys, int64_t n, uint32_t npd, uint64_t *ht_keys,
-                              int32_t *ht_vals, uint64_t mask, int *err) {
+__global__ void k_encode128(const uint64_t *__restrict__ ijk, int64_t n, Key128 *__restrict__ keys, int *err) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= n) return;
-  const uint64_t k = keys[t];
-  uint32_t i, j, kk;
-  morton_decode(k, i, j, kk);
-  if ((k >> 63) || i >= npd || j >= npd || kk >= npd) {
+  const uint64_t i = ijk[3 * t], j = ijk[3 * t + 1], k = ijk[3 * t + 2];
+  if ((i | j | k) >> KeyOps<Key128>::kBits) set_error(err, CMG_ERR_KEY_OUT_OF_RANGE);
+  keys[t] = KeyOps<Key128>::encode(i, j, k);
+}
+
+__global__ void k_decode128(const Key128 *__restrict__ keys, int64_t n, uint64_t *__restrict__ ijk) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  uint64_t c[3];
+  KeyOps<Key128>::decode(keys[t], c);
+  ijk[3 * t] = c[0];
+  ijk[3 * t + 1] = c[1];
+  ijk[3 * t + 2] = c[2];
+}
+
+// low words of 128-bit keys (the octant bits the solver kernels read)
+__global__ void k_low_words(const Key128 *__restrict__ keys, int64_t n, uint64_t *__restrict__ lo) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < n) lo[t] = keys[t].lo;
+}
+
+// Range check (valid key, coordinates < npd) and hash insert (A2).
+template <class K>
+__global__ void k_insert_keys(const K *__restrict__ keys, int64_t n, uint64_t npd, K *ht_keys, int32_t *ht_vals,
+                              uint64_t mask, int *err) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const K k = keys[t];
+  uint64_t c[3];
+  KeyOps<K>::decode(k, c);
+  if (!KeyOps<K>::in_range(k) || c[0] >= npd || c[1] >= npd || c[2] >= npd) {
     set_error(err, CMG_ERR_KEY_OUT_OF_RANGE);
     return;
   }
   bool inserted = false;
-  const int64_t s = ht_insert_slot(ht_keys, mask, k, &inserted);
+  const int64_t s = ht_insert_slot_k(ht_keys, mask, k, &inserted);
   if (s < 0) {
     set_error(err, CMG_ERR_INVALID_ARG);
     return;
@@ -90,27 +117,29 @@ __global__ void k_insert_keys(const uint64_t *__restrict__ keys, int64_t n, uint
   ht_vals[s] = (int32_t)t;
 }
 
-__global__ void k_lookup(const uint64_t *__restrict__ ht_keys, const int32_t *__restrict__ ht_vals, uint64_t mask,
-                         const uint64_t *__restrict__ q, int64_t n, int32_t *__restrict__ out) {
+template <class K>
+__global__ void k_lookup(const K *__restrict__ ht_keys, const int32_t *__restrict__ ht_vals, uint64_t mask,
+                         const K *__restrict__ q, int64_t n, int32_t *__restrict__ out) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= n) return;
-  out[t] = ht_find(ht_keys, ht_vals, mask, q[t]);
+  out[t] = ht_find_k(ht_keys, ht_vals, mask, q[t]);
 }
 
 // Neighbour cache (App. D.1 Eq. (nbor_precompute)), SoA [6][n]; missing
 // neighbours get `missing` (patched later for ghosts).
-__global__ void k_neighbors(const uint64_t *__restrict__ keys, int64_t n, uint32_t npd, int pmask,
-                            const uint64_t *__restrict__ ht_keys, const int32_t *__restrict__ ht_vals,
-                            uint64_t mask, int32_t missing, int32_t *__restrict__ nbr,
-                            int32_t *__restrict__ n_missing) {
+template <class K>
+__global__ void k_neighbors(const K *__restrict__ keys, int64_t n, uint64_t npd, int pmask,
+                            const K *__restrict__ ht_keys, const int32_t *__restrict__ ht_vals, uint64_t mask,
+                            int32_t missing, int32_t *__restrict__ nbr, int32_t *__restrict__ n_missing) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const uint64_t k = keys[i];
+  const K k = keys[i];
+  const K e = KeyOps<K>::empty();
   int miss = 0;
 #pragma unroll
   for (int d = 0; d < 6; ++d) {
-    const uint64_t nk = neighbor_key(k, d, npd, pmask);
-    int32_t v = nk == kEmptyKey ? -1 : ht_find(ht_keys, ht_vals, mask, nk);
+    const K nk = neighbor_key_k(k, d, npd, pmask);
+    int32_t v = nk == e ? -1 : ht_find_k(ht_keys, ht_vals, mask, nk);
     if (v < 0) {
       v = missing;
       ++miss;
@@ -121,22 +150,23 @@ __global__ void k_neighbors(const uint64_t *__restrict__ keys, int64_t n, uint32
 }
 
 // Ghost octs: one per distinct missing-neighbour position.
-__global__ void k_ghost_insert(const uint64_t *__restrict__ keys, int64_t n, uint32_t npd, int pmask,
-                               const int32_t *__restrict__ nbr, int32_t missing, uint64_t *g_ht_keys,
-                               int32_t *g_ht_vals, uint64_t g_mask, int32_t *counter,
-                               uint64_t *__restrict__ ghost_keys, int *err) {
+template <class K>
+__global__ void k_ghost_insert(const K *__restrict__ keys, int64_t n, uint64_t npd, int pmask,
+                               const int32_t *__restrict__ nbr, int32_t missing, K *g_ht_keys, int32_t *g_ht_vals,
+                               uint64_t g_mask, int32_t *counter, K *__restrict__ ghost_keys, int *err) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const K e = KeyOps<K>::empty();
 #pragma unroll 1
   for (int d = 0; d < 6; ++d) {
     if (nbr[d * n + i] != missing) continue;
-    const uint64_t nk = neighbor_key(keys[i], d, npd, pmask);
-    if (nk == kEmptyKey) {  // outside a non-periodic box: no parent cell to interpolate from
+    const K nk = neighbor_key_k(keys[i], d, npd, pmask);
+    if (nk == e) {  // outside a non-periodic box: no parent cell to interpolate from
       set_error(err, CMG_ERR_MISSING_PARENT);
       continue;
     }
     bool inserted = false;
-    const int64_t s = ht_insert_slot(g_ht_keys, g_mask, nk, &inserted);
+    const int64_t s = ht_insert_slot_k(g_ht_keys, g_mask, nk, &inserted);
     if (s < 0) {
       set_error(err, CMG_ERR_INVALID_ARG);
       continue;
@@ -151,18 +181,20 @@ __global__ void k_ghost_insert(const uint64_t *__restrict__ keys, int64_t n, uin
 
 // Patch missing neighbours to ghost octs (index n + g) and record which ghost
 // cells are read: the face of the ghost oct that touches oct i.
-__global__ void k_ghost_resolve(const uint64_t *__restrict__ keys, int64_t n, uint32_t npd, int pmask,
-                                int32_t *__restrict__ nbr, int32_t missing, const uint64_t *__restrict__ g_ht_keys,
+template <class K>
+__global__ void k_ghost_resolve(const K *__restrict__ keys, int64_t n, uint64_t npd, int pmask,
+                                int32_t *__restrict__ nbr, int32_t missing, const K *__restrict__ g_ht_keys,
                                 const int32_t *__restrict__ g_ht_vals, uint64_t g_mask,
                                 uint32_t *__restrict__ ghost_mask) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const K e = KeyOps<K>::empty();
 #pragma unroll 1
   for (int d = 0; d < 6; ++d) {
     if (nbr[d * n + i] != missing) continue;
-    const uint64_t nk = neighbor_key(keys[i], d, npd, pmask);
-    if (nk == kEmptyKey) continue;
-    const int32_t gi = ht_find(g_ht_keys, g_ht_vals, g_mask, nk);
+    const K nk = neighbor_key_k(keys[i], d, npd, pmask);
+    if (nk == e) continue;
+    const int32_t gi = ht_find_k(g_ht_keys, g_ht_vals, g_mask, nk);
     nbr[d * n + i] = (int32_t)n + gi;
     // cells of the ghost oct on its face opposite to direction d
     const int a = d >> 1, side_in_ghost = (d & 1) ? 0 : 1;
@@ -173,33 +205,37 @@ __global__ void k_ghost_resolve(const uint64_t *__restrict__ keys, int64_t n, ui
   }
 }
 
-// 2x2x2 block of octs (in the coarse table) around the father cell (key >> 3,
-// octant key & 7) of an oct with key `k` one level finer: block entry
+// 2x2x2 block of octs (in the coarse table) around the father cell (parent
+// key, octant) of an oct with key `k` one level finer: block entry
 // bx + 2 by + 4 bz is the oct displaced by b toward the octant.
-__device__ inline void father_block(uint64_t k, uint32_t cnpd, int pmask, const uint64_t *__restrict__ ht_keys,
+template <class K>
+__device__ inline void father_block(const K &k, uint64_t cnpd, int pmask, const K *__restrict__ ht_keys,
                                     const int32_t *__restrict__ ht_vals, uint64_t mask, int32_t zero_oct,
                                     int32_t out[8]) {
-  const uint64_t pk = k >> 3;
-  const int cc = (int)(k & 7);
-  uint32_t c[3];
-  morton_decode(pk, c[0], c[1], c[2]);
+  const int cc = KeyOps<K>::octant(k);
+  uint64_t c[3];
+  KeyOps<K>::decode(KeyOps<K>::parent(k), c);
 #pragma unroll
   for (int b = 0; b < 8; ++b) {
     bool ok = true;
-    uint32_t q[3];
+    uint64_t q[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      int64_t v = c[a];
-      if ((b >> a) & 1) v += ((cc >> a) & 1) ? 1 : -1;
-      if ((pmask >> a) & 1) {
-        if (v < 0) v += cnpd;
-        if (v >= (int64_t)cnpd) v -= cnpd;
-      } else if (v < 0 || v >= (int64_t)cnpd) {
-        ok = false;
+      uint64_t v = c[a];
+      if ((b >> a) & 1) {
+        if ((cc >> a) & 1) {
+          if (v + 1 < cnpd) v += 1;
+          else if ((pmask >> a) & 1) v = 0;
+          else ok = false;
+        } else {
+          if (v > 0) v -= 1;
+          else if ((pmask >> a) & 1) v = cnpd - 1;
+          else ok = false;
+        }
       }
-      q[a] = (uint32_t)v;
+      q[a] = v;
     }
-    int32_t idx = ok ? ht_find(ht_keys, ht_vals, mask, morton_encode(q[0], q[1], q[2])) : -1;
+    int32_t idx = ok ? ht_find_k(ht_keys, ht_vals, mask, KeyOps<K>::encode(q[0], q[1], q[2])) : -1;
     out[b] = idx < 0 ? zero_oct : idx;
   }
 }
@@ -216,20 +252,21 @@ __device__ inline void axis_cell(int cx, int e, int &a, int &bit) {
   }
 }
 
-__global__ void k_ghost_blocks(const uint64_t *__restrict__ ghost_keys, int64_t n_ghost,
-                               const uint32_t *__restrict__ ghost_mask, uint32_t pnpd, int pmask,
-                               const uint64_t *__restrict__ p_ht_keys, const int32_t *__restrict__ p_ht_vals,
+template <class K>
+__global__ void k_ghost_blocks(const K *__restrict__ ghost_keys, int64_t n_ghost,
+                               const uint32_t *__restrict__ ghost_mask, uint64_t pnpd, int pmask,
+                               const K *__restrict__ p_ht_keys, const int32_t *__restrict__ p_ht_vals,
                                uint64_t p_mask, int32_t p_zero, int32_t *__restrict__ blk, int *err) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= n_ghost) return;
-  const uint64_t k = ghost_keys[g];
+  const K k = ghost_keys[g];
   int32_t b[8];
   father_block(k, pnpd, pmask, p_ht_keys, p_ht_vals, p_mask, p_zero, b);
 #pragma unroll
   for (int t = 0; t < 8; ++t) blk[t * n_ghost + g] = b[t];
   // every needed ghost cell must find its 8 interpolation cells in the parent
   const uint32_t need = ghost_mask[g];
-  const int cc = (int)(k & 7);
+  const int cc = KeyOps<K>::octant(k);
   for (int c = 0; c < 8; ++c) {
     if (!((need >> c) & 1)) continue;
     for (int t = 0; t < 8; ++t) {
@@ -249,64 +286,68 @@ __global__ void k_ghost_blocks(const uint64_t *__restrict__ ghost_keys, int64_t 
 
 // ---- hierarchy
 
-__global__ void k_parent_first(const uint64_t *__restrict__ keys, const uint8_t *__restrict__ active, bool all_active,
-                               int64_t n, uint64_t *t_keys, int32_t *t_min, uint64_t t_mask) {
+template <class K>
+__global__ void k_parent_first(const K *__restrict__ keys, const uint8_t *__restrict__ active, bool all_active,
+                               int64_t n, K *t_keys, int32_t *t_min, uint64_t t_mask) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (!all_active && active[i] != 0xFF) return;
   bool inserted;
-  const int64_t s = ht_insert_slot(t_keys, t_mask, keys[i] >> 3, &inserted);
+  const int64_t s = ht_insert_slot_k(t_keys, t_mask, KeyOps<K>::parent(keys[i]), &inserted);
   if (s >= 0) atomicMin(t_min + s, (int32_t)i);
 }
 
-__global__ void k_parent_flag(const uint64_t *__restrict__ keys, const uint8_t *__restrict__ active, bool all_active,
-                              int64_t n, const uint64_t *__restrict__ t_keys, const int32_t *__restrict__ t_min,
+template <class K>
+__global__ void k_parent_flag(const K *__restrict__ keys, const uint8_t *__restrict__ active, bool all_active,
+                              int64_t n, const K *__restrict__ t_keys, const int32_t *__restrict__ t_min,
                               uint64_t t_mask, int32_t *__restrict__ flag) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   int32_t f = 0;
   if (all_active || active[i] == 0xFF) {
-    const int64_t s = ht_slot(t_keys, t_mask, keys[i] >> 3);
+    const int64_t s = ht_slot_k(t_keys, t_mask, KeyOps<K>::parent(keys[i]));
     f = (s >= 0 && t_min[s] == (int32_t)i);
   }
   flag[i] = f;
 }
 
-__global__ void k_parent_emit(const uint64_t *__restrict__ keys, int64_t n, const int32_t *__restrict__ flag,
-                              const int32_t *__restrict__ pos, uint64_t *__restrict__ ckeys) {
+template <class K>
+__global__ void k_parent_emit(const K *__restrict__ keys, int64_t n, const int32_t *__restrict__ flag,
+                              const int32_t *__restrict__ pos, K *__restrict__ ckeys) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  if (flag[i]) ckeys[pos[i]] = keys[i] >> 3;
+  if (flag[i]) ckeys[pos[i]] = KeyOps<K>::parent(keys[i]);
 }
 
 // Coarse cell active iff a fully active fine oct refines it (pull).
-__global__ void k_coarse_active(const uint64_t *__restrict__ ckeys, int64_t cn, const uint64_t *__restrict__ f_ht_keys,
+template <class K>
+__global__ void k_coarse_active(const K *__restrict__ ckeys, int64_t cn, const K *__restrict__ f_ht_keys,
                                 const int32_t *__restrict__ f_ht_vals, uint64_t f_mask,
                                 const uint8_t *__restrict__ f_active, bool f_all_active,
                                 uint8_t *__restrict__ cactive) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= cn) return;
-  const uint64_t k = ckeys[p];
+  const K k = ckeys[p];
   uint8_t m = 0;
   for (int c = 0; c < 8; ++c) {
-    const int32_t i = ht_find(f_ht_keys, f_ht_vals, f_mask, (k << 3) | (uint64_t)c);
+    const int32_t i = ht_find_k(f_ht_keys, f_ht_vals, f_mask, KeyOps<K>::child(k, c));
     if (i >= 0 && (f_all_active || f_active[i] == 0xFF)) m |= (uint8_t)(1u << c);
   }
   cactive[p] = m;
 }
 
-__global__ void k_father_and_block(const uint64_t *__restrict__ keys, const uint8_t *__restrict__ active,
-                                   bool all_active, int64_t n, uint32_t cnpd, int pmask,
-                                   const uint64_t *__restrict__ c_ht_keys, const int32_t *__restrict__ c_ht_vals,
-                                   uint64_t c_mask, int32_t c_zero, int32_t *__restrict__ father,
-                                   int32_t *__restrict__ blk) {
+template <class K>
+__global__ void k_father_and_block(const K *__restrict__ keys, const uint8_t *__restrict__ active, bool all_active,
+                                   int64_t n, uint64_t cnpd, int pmask, const K *__restrict__ c_ht_keys,
+                                   const int32_t *__restrict__ c_ht_vals, uint64_t c_mask, int32_t c_zero,
+                                   int32_t *__restrict__ father, int32_t *__restrict__ blk) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const uint64_t k = keys[i];
+  const K k = keys[i];
   int32_t fa = -1;
   if (all_active || active[i] == 0xFF) {
-    const int32_t p = ht_find(c_ht_keys, c_ht_vals, c_mask, k >> 3);
-    if (p >= 0) fa = p * 8 + (int32_t)(k & 7);
+    const int32_t p = ht_find_k(c_ht_keys, c_ht_vals, c_mask, KeyOps<K>::parent(k));
+    if (p >= 0) fa = p * 8 + (int32_t)KeyOps<K>::octant(k);
   }
   father[i] = fa;
   int32_t b[8];
@@ -341,19 +382,21 @@ __global__ void k_ext_neighbors(const int32_t *__restrict__ nbr, int64_t n, int3
   }
 }
 
-__global__ void k_father_cells(const uint64_t *__restrict__ keys, const int32_t *__restrict__ nbr, int64_t n,
-                               uint32_t npd, int pmask, bool has_parent, const uint64_t *__restrict__ p_ht_keys,
+template <class K>
+__global__ void k_father_cells(const K *__restrict__ keys, const int32_t *__restrict__ nbr, int64_t n, uint64_t npd,
+                               int pmask, bool has_parent, const K *__restrict__ p_ht_keys,
                                const int32_t *__restrict__ p_ht_vals, uint64_t p_mask, int32_t *__restrict__ out) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const K e = KeyOps<K>::empty();
 #pragma unroll 1
   for (int d = 0; d < 6; ++d) {
     int32_t p = -1, oc = -1;
     if (has_parent && nbr[d * n + i] >= n) {
-      const uint64_t nk = neighbor_key(keys[i], d, npd, pmask);
-      if (nk != kEmptyKey) {
-        p = ht_find(p_ht_keys, p_ht_vals, p_mask, nk >> 3);
-        oc = p >= 0 ? (int32_t)(nk & 7) : -1;
+      const K nk = neighbor_key_k(keys[i], d, npd, pmask);
+      if (nk != e) {
+        p = ht_find_k(p_ht_keys, p_ht_vals, p_mask, KeyOps<K>::parent(nk));
+        oc = p >= 0 ? (int32_t)KeyOps<K>::octant(nk) : -1;
       }
     }
     out[12 * i + 2 * d] = p;
@@ -393,62 +436,38 @@ const char *status_text(int e) {
   }
 }
 
-void build_hash(cmg_level *L, cmg::MgLev &g, uint32_t npd) {
+template <class K>
+void build_hash(cmg_level *L, cmg::MgLev &g, uint64_t npd) {
   cudaStream_t s = L->ctx->stream;
   g.cap = hash_capacity(g.n);
-  g.ht_keys = L->mem.alloc<uint64_t>(g.cap);
+  K *&tab = LevelKeys<K>::table(g);
+  tab = L->mem.alloc<K>(g.cap);
   g.ht_vals = L->mem.alloc<int32_t>(g.cap);
-  CMG_CUDA(cudaMemsetAsync(g.ht_keys, 0xFF, sizeof(uint64_t) * g.cap, s));
+  CMG_CUDA(cudaMemsetAsync(tab, 0xFF, sizeof(K) * g.cap, s));
   if (g.n > 0)
-    k_insert_keys<<<blocks_for(g.n), kThreads, 0, s>>>(g.keys, g.n, npd, g.ht_keys, g.ht_vals,
-                                                         (uint64_t)g.cap - 1, L->ctx->d_err);
+    k_insert_keys<K><<<blocks_for(g.n), kThreads, 0, s>>>(LevelKeys<K>::keys(g), g.n, npd, tab, g.ht_vals,
+                                                            (uint64_t)g.cap - 1, L->ctx->d_err);
   CMG_CUDA(cudaGetLastError());
 }
 
-}  // namespace
-
-void encode_keys(const uint32_t *ijk, int64_t n, uint64_t *keys, int *err, cudaStream_t s) {
-  if (n > 0) k_encode<<<blocks_for(n), kThreads, 0, s>>>(ijk, n, keys, err);
-  CMG_CUDA(cudaGetLastError());
+// 128-bit levels keep their keys' low words for the solver kernels
+template <class K>
+void low_words(cmg_level *L, cmg::MgLev &g) {
+  if constexpr (sizeof(K) == 16) {
+    g.keys = L->mem.alloc<uint64_t>(g.n > 0 ? g.n : 1);
+    if (g.n > 0) k_low_words<<<blocks_for(g.n), kThreads, 0, L->ctx->stream>>>(g.keys128, g.n, g.keys);
+    CMG_CUDA(cudaGetLastError());
+  }
 }
 
-void decode_keys(const uint64_t *keys, int64_t n, uint32_t *ijk, cudaStream_t s) {
-  if (n > 0) k_decode<<<blocks_for(n), kThreads, 0, s>>>(keys, n, ijk);
-  CMG_CUDA(cudaGetLastError());
-}
-
-void hash_lookup(const MgLev &g, const uint64_t *q, int64_t n, int32_t *out, cudaStream_t s) {
-  if (n > 0) k_lookup<<<blocks_for(n), kThreads, 0, s>>>(g.ht_keys, g.ht_vals, (uint64_t)g.cap - 1, q, n, out);
-  CMG_CUDA(cudaGetLastError());
-}
-
-void ext_neighbors(const cmg_level *L, int32_t *out, cudaStream_t s) {
-  const MgLev &g = L->mg[0];
-  if (g.n > 0) k_ext_neighbors<<<blocks_for(g.n), kThreads, 0, s>>>(g.nbr, g.n, out);
-  CMG_CUDA(cudaGetLastError());
-}
-
-void father_cells(const cmg_level *L, int32_t *out, cudaStream_t s) {
-  const MgLev &g = L->mg[0];
-  const bool hp = L->parent != nullptr;
-  const MgLev *pg = hp ? &L->parent->mg[0] : nullptr;
-  if (g.n > 0)
-    k_father_cells<<<blocks_for(g.n), kThreads, 0, s>>>(
-        g.keys, g.nbr, g.n, (uint32_t)((uint64_t)L->nx << (L->lev - 1)), L->pmask, hp, hp ? pg->ht_keys : nullptr,
-        hp ? pg->ht_vals : nullptr, hp ? (uint64_t)pg->cap - 1 : 0, out);
-  CMG_CUDA(cudaGetLastError());
-}
-
-void mg_active_bytes(const MgLev &g, uint8_t *out, cudaStream_t s) {
-  if (g.n > 0) k_active_bytes<<<blocks_for(8 * g.n), kThreads, 0, s>>>(g.active, g.all_active, g.n, out);
-  CMG_CUDA(cudaGetLastError());
-}
+uint64_t octs_per_dim(const cmg_level *L, int lev) { return (uint64_t)L->nx << (lev - 1); }
 
 // Build L->mg[0] from keys, then the ghosts and the MG hierarchy.
-void build_level(cmg_level *L, const uint64_t *keys, cmg_mem mem) {
+template <class K>
+void build_level_t(cmg_level *L, const K *keys, cmg_mem mem) {
   cmg_ctx *ctx = L->ctx;
   cudaStream_t s = ctx->stream;
-  const uint32_t npd = (uint32_t)((uint64_t)L->nx << (L->lev - 1));
+  const uint64_t npd = octs_per_dim(L, L->lev);
   L->mg.clear();
   L->mg.emplace_back();
   MgLev &top = L->mg[0];
@@ -456,47 +475,57 @@ void build_level(cmg_level *L, const uint64_t *keys, cmg_mem mem) {
   top.n = L->n;
   top.h = std::ldexp(1.0, -L->lev) / L->nx;
   top.all_active = true;
-  top.keys = L->mem.alloc<uint64_t>(top.n);
+  K *&tkeys = LevelKeys<K>::keys(top);
+  tkeys = L->mem.alloc<K>(top.n);
   if (top.n > 0)
-    CMG_CUDA(cudaMemcpyAsync(top.keys, keys, sizeof(uint64_t) * top.n,
+    CMG_CUDA(cudaMemcpyAsync(tkeys, keys, sizeof(K) * top.n,
                              mem == CMG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
   CMG_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s));
-  build_hash(L, top, npd);
+  build_hash<K>(L, top, npd);
+  low_words<K>(L, top);
   int e = read_error(ctx);
   if (e) throw Error(e, status_text(e));
+  const K *ttab = LevelKeys<K>::table(top);
 
   // neighbour cache; INT_MIN marks "missing" until ghosts are assigned
   int32_t *d_cnt = L->mem.alloc<int32_t>(4, true, s);
   top.nbr = L->mem.alloc<int32_t>(6 * top.n);
   if (top.n > 0)
-    k_neighbors<<<blocks_for(top.n), kThreads, 0, s>>>(top.keys, top.n, npd, L->pmask, top.ht_keys, top.ht_vals,
-                                                        (uint64_t)top.cap - 1, INT_MIN, top.nbr, d_cnt);
+    k_neighbors<K><<<blocks_for(top.n), kThreads, 0, s>>>(tkeys, top.n, npd, L->pmask, ttab, top.ht_vals,
+                                                           (uint64_t)top.cap - 1, INT_MIN, top.nbr, d_cnt);
   CMG_CUDA(cudaGetLastError());
   const int32_t n_missing = read_i32(ctx, d_cnt);
 
   top.n_ghost = 0;
   if (L->parent && n_missing > 0) {
     const int64_t gcap = hash_capacity(n_missing);
-    uint64_t *g_keys = L->mem.alloc<uint64_t>(gcap);
+    K *g_keys = L->mem.alloc<K>(gcap);
     int32_t *g_vals = L->mem.alloc<int32_t>(gcap);
-    CMG_CUDA(cudaMemsetAsync(g_keys, 0xFF, sizeof(uint64_t) * gcap, s));
-    L->ghost_keys = L->mem.alloc<uint64_t>(n_missing);
-    k_ghost_insert<<<blocks_for(top.n), kThreads, 0, s>>>(top.keys, top.n, npd, L->pmask, top.nbr, INT_MIN, g_keys,
-                                                           g_vals, (uint64_t)gcap - 1, d_cnt + 1, L->ghost_keys,
-                                                           ctx->d_err);
+    CMG_CUDA(cudaMemsetAsync(g_keys, 0xFF, sizeof(K) * gcap, s));
+    K *gk = L->mem.alloc<K>(n_missing);
+    k_ghost_insert<K><<<blocks_for(top.n), kThreads, 0, s>>>(tkeys, top.n, npd, L->pmask, top.nbr, INT_MIN, g_keys,
+                                                              g_vals, (uint64_t)gcap - 1, d_cnt + 1, gk, ctx->d_err);
     CMG_CUDA(cudaGetLastError());
     e = read_error(ctx);
     if (e) throw Error(e, status_text(e));
     top.n_ghost = read_i32(ctx, d_cnt + 1);
+    if constexpr (sizeof(K) == 16) {
+      L->ghost_keys128 = gk;
+      L->ghost_keys = L->mem.alloc<uint64_t>(top.n_ghost > 0 ? top.n_ghost : 1);
+      if (top.n_ghost > 0)
+        k_low_words<<<blocks_for(top.n_ghost), kThreads, 0, s>>>(gk, top.n_ghost, L->ghost_keys);
+    } else {
+      L->ghost_keys = gk;
+    }
     L->ghost_mask = L->mem.alloc<uint32_t>(top.n_ghost, true, s);
-    k_ghost_resolve<<<blocks_for(top.n), kThreads, 0, s>>>(top.keys, top.n, npd, L->pmask, top.nbr, INT_MIN, g_keys,
-                                                            g_vals, (uint64_t)gcap - 1, L->ghost_mask);
+    k_ghost_resolve<K><<<blocks_for(top.n), kThreads, 0, s>>>(tkeys, top.n, npd, L->pmask, top.nbr, INT_MIN, g_keys,
+                                                               g_vals, (uint64_t)gcap - 1, L->ghost_mask);
     CMG_CUDA(cudaGetLastError());
     const MgLev &pg = L->parent->mg[0];
     L->ghost_blk = L->mem.alloc<int32_t>(8 * top.n_ghost);
-    k_ghost_blocks<<<blocks_for(top.n_ghost), kThreads, 0, s>>>(
-        L->ghost_keys, top.n_ghost, L->ghost_mask, (uint32_t)((uint64_t)L->nx << (L->lev - 2)), L->pmask,
-        pg.ht_keys, pg.ht_vals, (uint64_t)pg.cap - 1, (int32_t)(pg.n_alloc - 1), L->ghost_blk, ctx->d_err);
+    k_ghost_blocks<K><<<blocks_for(top.n_ghost), kThreads, 0, s>>>(
+        gk, top.n_ghost, L->ghost_mask, octs_per_dim(L, L->lev - 1), L->pmask, LevelKeys<K>::table(pg), pg.ht_vals,
+        (uint64_t)pg.cap - 1, (int32_t)(pg.n_alloc - 1), L->ghost_blk, ctx->d_err);
     CMG_CUDA(cudaGetLastError());
     e = read_error(ctx);
     if (e) throw Error(e, status_text(e));
@@ -521,16 +550,16 @@ void build_level(cmg_level *L, const uint64_t *keys, cmg_mem mem) {
     if (L->mg[m].lev == 1 || L->mg[m].n == 0) break;
     const int64_t n = L->mg[m].n;
     const int64_t tcap = hash_capacity(n);
-    uint64_t *t_keys = L->mem.alloc<uint64_t>(tcap);
+    K *t_keys = L->mem.alloc<K>(tcap);
     int32_t *t_min = L->mem.alloc<int32_t>(tcap);
-    CMG_CUDA(cudaMemsetAsync(t_keys, 0xFF, sizeof(uint64_t) * tcap, s));
+    CMG_CUDA(cudaMemsetAsync(t_keys, 0xFF, sizeof(K) * tcap, s));
     k_fill_i32<<<blocks_for(tcap), kThreads, 0, s>>>(t_min, tcap, INT_MAX);
     {
-      const MgLev &f = L->mg[m];
-      k_parent_first<<<blocks_for(n), kThreads, 0, s>>>(f.keys, f.active, f.all_active, n, t_keys, t_min,
-                                                          (uint64_t)tcap - 1);
-      k_parent_flag<<<blocks_for(n), kThreads, 0, s>>>(f.keys, f.active, f.all_active, n, t_keys, t_min,
-                                                         (uint64_t)tcap - 1, flag);
+      MgLev &f = L->mg[m];
+      k_parent_first<K><<<blocks_for(n), kThreads, 0, s>>>(LevelKeys<K>::keys(f), f.active, f.all_active, n, t_keys,
+                                                             t_min, (uint64_t)tcap - 1);
+      k_parent_flag<K><<<blocks_for(n), kThreads, 0, s>>>(LevelKeys<K>::keys(f), f.active, f.all_active, n, t_keys,
+                                                            t_min, (uint64_t)tcap - 1, flag);
     }
     CMG_CUDA(cudaGetLastError());
     scan_exclusive(flag, pos, n, d_cnt + 2, scratch, scratch_n, s);
@@ -545,22 +574,25 @@ void build_level(cmg_level *L, const uint64_t *keys, cmg_mem mem) {
     c.n_alloc = np + 1;
     c.h = 2.0 * f.h;
     c.all_active = L->periodic_full;
-    c.keys = L->mem.alloc<uint64_t>(np);
-    k_parent_emit<<<blocks_for(n), kThreads, 0, s>>>(f.keys, n, flag, pos, c.keys);
+    K *&ckeys = LevelKeys<K>::keys(c);
+    ckeys = L->mem.alloc<K>(np);
+    k_parent_emit<K><<<blocks_for(n), kThreads, 0, s>>>(LevelKeys<K>::keys(f), n, flag, pos, ckeys);
     CMG_CUDA(cudaGetLastError());
-    const uint32_t cnpd = (uint32_t)((uint64_t)L->nx << (c.lev - 1));
-    build_hash(L, c, cnpd);
+    const uint64_t cnpd = octs_per_dim(L, c.lev);
+    build_hash<K>(L, c, cnpd);
+    low_words<K>(L, c);
+    const K *ctab = LevelKeys<K>::table(c);
     c.nbr = L->mem.alloc<int32_t>(6 * np);
-    k_neighbors<<<blocks_for(np), kThreads, 0, s>>>(c.keys, np, cnpd, L->pmask, c.ht_keys, c.ht_vals,
-                                                     (uint64_t)c.cap - 1, (int32_t)np, c.nbr, nullptr);
+    k_neighbors<K><<<blocks_for(np), kThreads, 0, s>>>(ckeys, np, cnpd, L->pmask, ctab, c.ht_vals,
+                                                        (uint64_t)c.cap - 1, (int32_t)np, c.nbr, nullptr);
     c.active = L->mem.alloc<uint8_t>(np);
-    k_coarse_active<<<blocks_for(np), kThreads, 0, s>>>(c.keys, np, f.ht_keys, f.ht_vals, (uint64_t)f.cap - 1,
-                                                         f.active, f.all_active, c.active);
+    k_coarse_active<K><<<blocks_for(np), kThreads, 0, s>>>(ckeys, np, LevelKeys<K>::table(f), f.ht_vals,
+                                                            (uint64_t)f.cap - 1, f.active, f.all_active, c.active);
     f.father = L->mem.alloc<int32_t>(n);
     f.blk = L->mem.alloc<int32_t>(8 * n);
-    k_father_and_block<<<blocks_for(n), kThreads, 0, s>>>(f.keys, f.active, f.all_active, n, cnpd, L->pmask,
-                                                           c.ht_keys, c.ht_vals, (uint64_t)c.cap - 1, (int32_t)np,
-                                                           f.father, f.blk);
+    k_father_and_block<K><<<blocks_for(n), kThreads, 0, s>>>(LevelKeys<K>::keys(f), f.active, f.all_active, n, cnpd,
+                                                              L->pmask, ctab, c.ht_vals, (uint64_t)c.cap - 1,
+                                                              (int32_t)np, f.father, f.blk);
     CMG_CUDA(cudaGetLastError());
     c.phi = L->mem.alloc<double>(8 * c.n_alloc, true, s);
     c.g = L->mem.alloc<double>(8 * c.n, true, s);
@@ -570,6 +602,74 @@ void build_level(cmg_level *L, const uint64_t *keys, cmg_mem mem) {
   const MgLev &last = L->mg.back();
   L->exact_coarse = L->periodic_full && last.lev == 1 && L->nx == 1 && last.n == 1;
   CMG_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace
+
+void encode_keys(const uint32_t *ijk, int64_t n, uint64_t *keys, int *err, cudaStream_t s) {
+  if (n > 0) k_encode<<<blocks_for(n), kThreads, 0, s>>>(ijk, n, keys, err);
+  CMG_CUDA(cudaGetLastError());
+}
+
+void decode_keys(const uint64_t *keys, int64_t n, uint32_t *ijk, cudaStream_t s) {
+  if (n > 0) k_decode<<<blocks_for(n), kThreads, 0, s>>>(keys, n, ijk);
+  CMG_CUDA(cudaGetLastError());
+}
+
+void encode_keys128(const uint64_t *ijk, int64_t n, Key128 *keys, int *err, cudaStream_t s) {
+  if (n > 0) k_encode128<<<blocks_for(n), kThreads, 0, s>>>(ijk, n, keys, err);
+  CMG_CUDA(cudaGetLastError());
+}
+
+void decode_keys128(const Key128 *keys, int64_t n, uint64_t *ijk, cudaStream_t s) {
+  if (n > 0) k_decode128<<<blocks_for(n), kThreads, 0, s>>>(keys, n, ijk);
+  CMG_CUDA(cudaGetLastError());
+}
+
+void hash_lookup(const MgLev &g, const uint64_t *q, int64_t n, int32_t *out, cudaStream_t s) {
+  if (n > 0) k_lookup<uint64_t><<<blocks_for(n), kThreads, 0, s>>>(g.ht_keys, g.ht_vals, (uint64_t)g.cap - 1, q, n, out);
+  CMG_CUDA(cudaGetLastError());
+}
+
+void hash_lookup128(const MgLev &g, const Key128 *q, int64_t n, int32_t *out, cudaStream_t s) {
+  if (n > 0)
+    k_lookup<Key128><<<blocks_for(n), kThreads, 0, s>>>(g.ht_keys128, g.ht_vals, (uint64_t)g.cap - 1, q, n, out);
+  CMG_CUDA(cudaGetLastError());
+}
+
+void ext_neighbors(const cmg_level *L, int32_t *out, cudaStream_t s) {
+  const MgLev &g = L->mg[0];
+  if (g.n > 0) k_ext_neighbors<<<blocks_for(g.n), kThreads, 0, s>>>(g.nbr, g.n, out);
+  CMG_CUDA(cudaGetLastError());
+}
+
+void father_cells(const cmg_level *L, int32_t *out, cudaStream_t s) {
+  const MgLev &g = L->mg[0];
+  const bool hp = L->parent != nullptr;
+  const MgLev *pg = hp ? &L->parent->mg[0] : nullptr;
+  if (g.n == 0) return;
+  const uint64_t npd = (uint64_t)L->nx << (L->lev - 1);
+  if (L->key_bits == 128)
+    k_father_cells<Key128><<<blocks_for(g.n), kThreads, 0, s>>>(
+        g.keys128, g.nbr, g.n, npd, L->pmask, hp, hp ? pg->ht_keys128 : nullptr, hp ? pg->ht_vals : nullptr,
+        hp ? (uint64_t)pg->cap - 1 : 0, out);
+  else
+    k_father_cells<uint64_t><<<blocks_for(g.n), kThreads, 0, s>>>(
+        g.keys, g.nbr, g.n, npd, L->pmask, hp, hp ? pg->ht_keys : nullptr, hp ? pg->ht_vals : nullptr,
+        hp ? (uint64_t)pg->cap - 1 : 0, out);
+  CMG_CUDA(cudaGetLastError());
+}
+
+void mg_active_bytes(const MgLev &g, uint8_t *out, cudaStream_t s) {
+  if (g.n > 0) k_active_bytes<<<blocks_for(8 * g.n), kThreads, 0, s>>>(g.active, g.all_active, g.n, out);
+  CMG_CUDA(cudaGetLastError());
+}
+
+void build_level(cmg_level *L, const void *keys, cmg_mem mem) {
+  if (L->key_bits == 128)
+    build_level_t<Key128>(L, static_cast<const Key128 *>(keys), mem);
+  else
+    build_level_t<uint64_t>(L, static_cast<const uint64_t *>(keys), mem);
 }
 
 }  // namespace cmg

@@ -206,20 +206,64 @@ int cmg_morton_decode(cmg_ctx *ctx, const uint64_t *keys, int64_t n, uint32_t *i
   });
 }
 
-int cmg_level_build(cmg_ctx *ctx, int level, int nx, int periodic_mask, const uint64_t *keys, int64_t n_octs,
-                    cmg_mem mem, cmg_level *parent, cmg_level **out) {
+int cmg_morton_encode128(cmg_ctx *ctx, const uint64_t *ijk, int64_t n, uint64_t *keys, cmg_mem mem) {
+  return guard([&] {
+    need(ctx && n >= 0 && (n == 0 || (ijk && keys)), "bad arguments");
+    check_mem(mem);
+    DeviceScope ds(ctx->device);
+    CMG_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    accept(ctx, ijk, sizeof(uint64_t) * 3 * n, mem, [&](const void *din) {
+      deliver(ctx, keys, sizeof(cmg::Key128) * n, mem, [&](void *dout) {
+        cmg::encode_keys128(static_cast<const uint64_t *>(din), n, static_cast<cmg::Key128 *>(dout), ctx->d_err,
+                            ctx->stream);
+      });
+    });
+    CMG_CUDA(cudaMemcpyAsync(ctx->h_pinned, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CMG_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (ctx->h_pinned[0]) {
+      CMG_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+      throw cmg::Error(ctx->h_pinned[0], "coordinate outside [0, 2^42)");
+    }
+    return CMG_OK;
+  });
+}
+
+int cmg_morton_decode128(cmg_ctx *ctx, const uint64_t *keys, int64_t n, uint64_t *ijk, cmg_mem mem) {
+  return guard([&] {
+    need(ctx && n >= 0 && (n == 0 || (ijk && keys)), "bad arguments");
+    check_mem(mem);
+    DeviceScope ds(ctx->device);
+    accept(ctx, keys, sizeof(cmg::Key128) * n, mem, [&](const void *din) {
+      deliver(ctx, ijk, sizeof(uint64_t) * 3 * n, mem, [&](void *dout) {
+        cmg::decode_keys128(static_cast<const cmg::Key128 *>(din), n, static_cast<uint64_t *>(dout), ctx->stream);
+      });
+    });
+    return CMG_OK;
+  });
+}
+
+namespace {
+
+int level_build(cmg_ctx *ctx, int level, int nx, int periodic_mask, const void *keys, int64_t n_octs, cmg_mem mem,
+                cmg_level *parent, cmg_level **out, int key_bits) {
   return guard([&] {
     need(out != nullptr, "out is NULL");
     *out = nullptr;
     need(ctx != nullptr, "ctx is NULL");
-    need(level >= 1 && level <= 22 && nx >= 1, "level must be in [1, 22] and nx >= 1");
-    need(((uint64_t)nx << (level - 1)) <= (1ull << cmg::kMortonBits), "2^(level-1) nx exceeds 2^21");
+    const int bits = key_bits == 128 ? 42 : cmg::kMortonBits;
+    const int max_level = bits + 1;
+    need(level >= 1 && level <= max_level && nx >= 1,
+         key_bits == 128 ? "level must be in [1, 43] and nx >= 1" : "level must be in [1, 22] and nx >= 1");
+    need(nx <= (1 << 20) && ((uint64_t)nx << (level - 1)) <= (1ull << bits),
+         key_bits == 128 ? "2^(level-1) nx exceeds 2^42" : "2^(level-1) nx exceeds 2^21");
     need(periodic_mask >= 0 && periodic_mask <= 7, "periodic_mask must be in [0, 7]");
     need(n_octs >= 0 && n_octs < (1ll << 31) - 1 && (n_octs == 0 || keys), "bad keys / n_octs");
     check_mem(mem);
-    if (parent)
+    if (parent) {
       need(parent->ctx == ctx && parent->lev == level - 1 && parent->nx == nx && parent->pmask == periodic_mask,
            "parent must be level-1 of the same context, nx and periodic_mask");
+      need(parent->key_bits == key_bits, "parent must use the same Morton key width");
+    }
     DeviceScope ds(ctx->device);
     cmg_level *L = new cmg_level();
     L->ctx = ctx;
@@ -230,8 +274,9 @@ int cmg_level_build(cmg_ctx *ctx, int level, int nx, int periodic_mask, const ui
     L->pmask = periodic_mask;
     L->n = n_octs;
     L->parent = parent;
+    L->key_bits = key_bits;
     const uint64_t npd = (uint64_t)nx << (level - 1);
-    L->periodic_full = parent == nullptr && periodic_mask == 7 && (uint64_t)n_octs == npd * npd * npd;
+    L->periodic_full = parent == nullptr && periodic_mask == 7 && npd <= 2048 && (uint64_t)n_octs == npd * npd * npd;
     try {
       cmg::build_level(L, keys, mem);
       L->partials = L->mem.alloc<double>(cmg::blocks_for(n_octs > 0 ? n_octs : 1));
@@ -244,6 +289,26 @@ int cmg_level_build(cmg_ctx *ctx, int level, int nx, int periodic_mask, const ui
       throw;
     }
     *out = L;
+    return CMG_OK;
+  });
+}
+
+}  // namespace
+
+int cmg_level_build(cmg_ctx *ctx, int level, int nx, int periodic_mask, const uint64_t *keys, int64_t n_octs,
+                    cmg_mem mem, cmg_level *parent, cmg_level **out) {
+  return level_build(ctx, level, nx, periodic_mask, keys, n_octs, mem, parent, out, 64);
+}
+
+int cmg_level_build128(cmg_ctx *ctx, int level, int nx, int periodic_mask, const uint64_t *keys, int64_t n_octs,
+                       cmg_mem mem, cmg_level *parent, cmg_level **out) {
+  return level_build(ctx, level, nx, periodic_mask, keys, n_octs, mem, parent, out, 128);
+}
+
+int cmg_level_key_bits(const cmg_level *lvl, int *bits) {
+  return guard([&] {
+    need(lvl && bits, "bad arguments");
+    *bits = lvl->key_bits;
     return CMG_OK;
   });
 }
@@ -281,6 +346,7 @@ int cmg_level_hash_capacity(const cmg_level *lvl, int64_t *cap) {
 int cmg_level_lookup(cmg_level *lvl, const uint64_t *q, int64_t n, int32_t *idx, cmg_mem mem) {
   return guard([&] {
     need(lvl && n >= 0 && (n == 0 || (q && idx)), "bad arguments");
+    need(lvl->key_bits == 64, "the level has 128-bit keys: use cmg_level_lookup128");
     check_mem(mem);
     cmg_ctx *ctx = lvl->ctx;
     DeviceScope ds(ctx->device);
@@ -288,6 +354,23 @@ int cmg_level_lookup(cmg_level *lvl, const uint64_t *q, int64_t n, int32_t *idx,
       deliver(ctx, idx, sizeof(int32_t) * n, mem, [&](void *dout) {
         cmg::hash_lookup(lvl->mg[0], static_cast<const uint64_t *>(din), n, static_cast<int32_t *>(dout),
                          ctx->stream);
+      });
+    });
+    return CMG_OK;
+  });
+}
+
+int cmg_level_lookup128(cmg_level *lvl, const uint64_t *q, int64_t n, int32_t *idx, cmg_mem mem) {
+  return guard([&] {
+    need(lvl && n >= 0 && (n == 0 || (q && idx)), "bad arguments");
+    need(lvl->key_bits == 128, "the level has 64-bit keys: use cmg_level_lookup");
+    check_mem(mem);
+    cmg_ctx *ctx = lvl->ctx;
+    DeviceScope ds(ctx->device);
+    accept(ctx, q, sizeof(cmg::Key128) * n, mem, [&](const void *din) {
+      deliver(ctx, idx, sizeof(int32_t) * n, mem, [&](void *dout) {
+        cmg::hash_lookup128(lvl->mg[0], static_cast<const cmg::Key128 *>(din), n, static_cast<int32_t *>(dout),
+                            ctx->stream);
       });
     });
     return CMG_OK;
@@ -502,12 +585,29 @@ int cmg_level_mg_info(const cmg_level *lvl, int m, int64_t *n_octs, int *amr_lev
 int cmg_level_mg_keys(cmg_level *lvl, int m, uint64_t *out, cmg_mem mem) {
   return guard([&] {
     need(lvl && m >= 0 && m < (int)lvl->mg.size(), "bad MG level");
+    need(lvl->key_bits == 64, "the level has 128-bit keys: use cmg_level_mg_keys128");
     check_mem(mem);
     const cmg::MgLev &g = lvl->mg[m];
     need(g.n == 0 || out, "out is NULL");
     DeviceScope ds(lvl->ctx->device);
     deliver(lvl->ctx, out, sizeof(uint64_t) * g.n, mem, [&](void *d) {
       if (g.n) CMG_CUDA(cudaMemcpyAsync(d, g.keys, sizeof(uint64_t) * g.n, cudaMemcpyDeviceToDevice, lvl->ctx->stream));
+    });
+    return CMG_OK;
+  });
+}
+
+int cmg_level_mg_keys128(cmg_level *lvl, int m, uint64_t *out, cmg_mem mem) {
+  return guard([&] {
+    need(lvl && m >= 0 && m < (int)lvl->mg.size(), "bad MG level");
+    need(lvl->key_bits == 128, "the level has 64-bit keys: use cmg_level_mg_keys");
+    check_mem(mem);
+    const cmg::MgLev &g = lvl->mg[m];
+    need(g.n == 0 || out, "out is NULL");
+    DeviceScope ds(lvl->ctx->device);
+    deliver(lvl->ctx, out, sizeof(cmg::Key128) * g.n, mem, [&](void *d) {
+      if (g.n)
+        CMG_CUDA(cudaMemcpyAsync(d, g.keys128, sizeof(cmg::Key128) * g.n, cudaMemcpyDeviceToDevice, lvl->ctx->stream));
     });
     return CMG_OK;
   });

@@ -31,6 +31,12 @@ namespace cmg {
 constexpr uint64_t kEmptyKey = ~0ull;
 constexpr int kMortonBits = 21;
 
+// A 128-bit Morton key (B = 42 bits per coordinate, Sec. 4.2): key bits 0..63
+// in lo, 64..127 in hi (keys.cuh).
+struct alignas(16) Key128 {
+  uint64_t lo, hi;
+};
+
 // ------------------------------------------------------------------ errors
 
 struct Error : std::runtime_error {
@@ -173,8 +179,10 @@ struct MgLev {
   int64_t n_alloc = 0;  // n + n_ghost + 1 (zero oct last)
   double h = 0.0;
   bool all_active = true;
-  uint64_t *keys = nullptr;      // [n]
-  uint64_t *ht_keys = nullptr;   // [cap]
+  uint64_t *keys = nullptr;      // [n] (128-bit levels: the keys' low words)
+  uint64_t *ht_keys = nullptr;   // [cap] (64-bit levels)
+  Key128 *keys128 = nullptr;     // [n] (128-bit levels)
+  Key128 *ht_keys128 = nullptr;  // [cap] (128-bit levels)
   int32_t *ht_vals = nullptr;    // [cap]
   int64_t cap = 0;
   int32_t *nbr = nullptr;        // [6][n] internal neighbour index (>= n: ghost / zero oct)
@@ -254,7 +262,9 @@ struct cmg_level {
   bool exact_coarse = false;
   std::vector<cmg::MgLev> mg;
   // ghosts of level 0
-  uint64_t *ghost_keys = nullptr;  // [n_ghost]
+  uint64_t *ghost_keys = nullptr;  // [n_ghost] (128-bit levels: the low words)
+  cmg::Key128 *ghost_keys128 = nullptr;  // [n_ghost] (128-bit levels)
+  int key_bits = 64;               // Morton key width of the level (and of its parent)
   int32_t *ghost_blk = nullptr;    // [8][n_ghost] parent octs around the ghost's father cell
   uint32_t *ghost_mask = nullptr;  // [n_ghost] cells some real oct reads
   // reductions
@@ -338,10 +348,14 @@ void scan_exclusive(const int32_t *in, int32_t *out, int64_t n, int32_t *d_total
 int64_t scan_scratch_size(int64_t n);
 
 // build.cu
-void build_level(cmg_level *L, const uint64_t *keys, cmg_mem mem);
+// keys: [n] uint64 (L->key_bits == 64) or [n] Key128 (128), host or device
+void build_level(cmg_level *L, const void *keys, cmg_mem mem);
 void hash_lookup(const MgLev &g, const uint64_t *q, int64_t n, int32_t *out, cudaStream_t s);
+void hash_lookup128(const MgLev &g, const Key128 *q, int64_t n, int32_t *out, cudaStream_t s);
 void encode_keys(const uint32_t *ijk, int64_t n, uint64_t *keys, int *err, cudaStream_t s);
 void decode_keys(const uint64_t *keys, int64_t n, uint32_t *ijk, cudaStream_t s);
+void encode_keys128(const uint64_t *ijk, int64_t n, Key128 *keys, int *err, cudaStream_t s);
+void decode_keys128(const Key128 *keys, int64_t n, uint64_t *ijk, cudaStream_t s);
 void ext_neighbors(const cmg_level *L, int32_t *out, cudaStream_t s);
 void father_cells(const cmg_level *L, int32_t *out, cudaStream_t s);
 void mg_active_bytes(const MgLev &g, uint8_t *out, cudaStream_t s);

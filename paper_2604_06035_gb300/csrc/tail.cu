@@ -25,7 +25,7 @@ namespace cmg {
 namespace {
 
 constexpr int kTailThreads = 512;
-constexpr int kMaxTail = 24;
+constexpr int kMaxTail = 48;  // MG levels of a level at up to level 43 (128-bit keys)
 
 struct TailLevel {
   int64_t n, n_alloc;

@@ -282,3 +282,29 @@ def mixed_amr(base_level=8, n_refine=3, sigma=2.0, seed=3):
     """Periodic lognormal base (sigma_ln rho = 2) plus three refined levels at
     threshold 8 rho_bar each (the 256^3 mixed-precision workload)."""
     return amr_lognormal(base_level, n_refine, sigma, seed)
+
+
+def deep_zoom(base_level=4, top_level=30, cube=8, centre=(0.3217, 0.5791, 0.7123), seed=6):
+    """A periodic base level plus a chain of refined levels up to top_level,
+    each a cube of `cube`^3 octs centred on the same point (so every level sits
+    inside its parent with the one-cell margin the coarse-fine stencils need).
+    Levels above 22 need 128-bit Morton keys.  Densities: rho = 1 + a seeded
+    uniform perturbation of amplitude 0.5 per cell.
+
+    Returns {"levels", "coords": [n, 3] uint64 oct coordinates per level,
+    "rho": [n, 8] per level, "rho_bar": base mean}."""
+    rng = np.random.default_rng(seed)
+    levels, coords, rhos = [base_level], [uniform_oct_coords(base_level).astype(np.uint64)], []
+    for lev in range(base_level + 1, top_level + 1):
+        npd = 1 << (lev - 1)
+        assert cube + 4 <= npd, "the cube must leave room for its Dirichlet boundary"
+        lo = [int(c * npd) - cube // 2 for c in centre]
+        r = [np.arange(l, l + cube, dtype=np.uint64) for l in lo]
+        z, y, x = np.meshgrid(r[2], r[1], r[0], indexing="ij")
+        levels.append(lev)
+        coords.append(np.stack([x.ravel(), y.ravel(), z.ravel()], 1))
+    for c in coords:
+        rhos.append(1.0 + 0.5 * (2.0 * rng.random((len(c), 8)) - 1.0))
+    rho_bar = float(rhos[0].mean())
+    return {"levels": levels, "coords": coords, "rho": rhos, "rho_bar": rho_bar}
+
