@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--block", choices=["smoother", "learned", "forward", "fft", "pcg", "amr3"], default=None,
                     help="run one sub-benchmark alone and print its JSON (profiling runs)")
     ap.add_argument("--smoother-level", type=int, default=9, help="level of the full periodic grid (9 = 512^3)")
+    ap.add_argument("--fft-level", type=int, default=9, help="level of the fft block's full periodic grid")
     ap.add_argument("--fwd-batches", default="1,8", help="batch sizes of --block forward")
     ap.add_argument("--fwd-paths", default="tcgen05,mma_sync", help="kernel paths of --block forward")
     return ap.parse_args()
@@ -331,13 +332,14 @@ def bench_fft(cmg, ctx, dev, B, rho_b, args, peaks):
         return out
 
     res = {"base_128": time_level(B, rho_b)}
-    coords = torch.from_numpy(inputs.uniform_oct_coords(9)).to(dev)
-    L = cmg.cmg_level_build(ctx, 9, cmg.cmg_morton_encode(ctx, coords))
+    lev = getattr(args, "fft_level", 9)
+    coords = torch.from_numpy(inputs.uniform_oct_coords(lev)).to(dev)
+    L = cmg.cmg_level_build(ctx, lev, cmg.cmg_morton_encode(ctx, coords))
     del coords
     g = torch.Generator(device=dev)
     g.manual_seed(7)
     rho = torch.rand((cmg.cmg_level_n_octs(L), 8), dtype=torch.float64, device=dev, generator=g) + 0.5
-    res["periodic_512"] = time_level(L, rho, reps=3)
+    res["periodic_%d" % (1 << lev)] = time_level(L, rho, reps=3)
     del rho
     cmg.cmg_level_destroy(L)
     torch.cuda.synchronize()
