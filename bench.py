@@ -326,8 +326,11 @@ def bench_fft(cmg, ctx, dev, B, rho_b, args, peaks):
         cmg.cmg_ctx_set_profiling(ctx, False)
         f = cmg.cmg_ctx_get_profile(ctx)["fft_fp32"]
         gbs = f["bytes"] / (f["ms"] / 1e3) / 1e9
+        n = cmg.cmg_level_n_octs(L)
         out["fft_kernels"] = {"launches": f["launches"], "ms": f["ms"], "achieved_GBs": gbs,
-                              "frac_of_hbm": gbs / peaks["hbm"], "hbm_source": peaks["hbm_src"]}
+                              "frac_of_hbm": gbs / peaks["hbm"], "hbm_source": peaks["hbm_src"],
+                              "bytes_per_launch": f["bytes"] / f["launches"],
+                              "traffic": traffic_for("fft_fp32_%d" % round((8 * n) ** (1 / 3)))}
         out["speedup_fft_vs_fp64"] = out["fp64"]["ms_to_tol"] / out["fft"]["ms_to_tol"]
         return out
 
