@@ -183,6 +183,18 @@ int cmg_level_get_ghosts(cmg_level *lvl, double *out, cmg_mem mem);
  * black Gauss-Seidel smoothing of App. D.2 Eq. (gs_update)).  Periodic base
  * levels return zero-mean phi.  stats may be NULL. */
 int cmg_level_solve(cmg_level *lvl, const cmg_solve_params *params, cmg_solve_stats *stats);
+/* The same solve split in two: cmg_level_solve_async validates the
+ * parameters, queues the solve on the context's stream and returns without
+ * waiting (errors: INVALID_ARG, including a solve of this level still
+ * pending; CUDA); cmg_level_solve_wait waits for it and returns its status
+ * and statistics (INVALID_ARG when none is pending).  Queueing the solves of
+ * several levels before waiting keeps the GPU busy between them: later calls
+ * on the same stream (a finer level's coarse-fine values reading this
+ * level's phi, a read-back) are ordered after the queued solve.  With
+ * profiling on, the solve runs when queued (its host-driven loop waits every
+ * cycle). */
+int cmg_level_solve_async(cmg_level *lvl, const cmg_solve_params *params);
+int cmg_level_solve_wait(cmg_level *lvl, cmg_solve_stats *stats);
 
 /* Execution schedule of the V-cycle (no effect on the arithmetic): MG levels
  * with at most tail_octs_fp64 (FP64 cycles) / tail_octs_fp32 (FP32 inner

@@ -105,6 +105,8 @@ _SIGS = {
     "cmg_level_get_residual": (_I, [_P, _P, _I]),
     "cmg_level_get_ghosts": (_I, [_P, _P, _I]),
     "cmg_level_solve": (_I, [_P, C.POINTER(cmg_solve_params), C.POINTER(cmg_solve_stats)]),
+    "cmg_level_solve_async": (_I, [_P, C.POINTER(cmg_solve_params)]),
+    "cmg_level_solve_wait": (_I, [_P, C.POINTER(cmg_solve_stats)]),
     "cmg_level_set_schedule": (_I, [_P, _I64, _I64]),
     "cmg_level_set_spin_budget": (_I, [_P, _I64]),
     "cmg_level_mg_depth": (_I, [_P, C.POINTER(_I)]),
@@ -547,6 +549,21 @@ def cmg_level_solve(lvl, params=None, raise_on_error=True, **kw):
     rc = lib().cmg_level_solve(lvl.h, C.byref(prm), C.byref(st))
     if raise_on_error:
         _check(rc, "cmg_level_solve")
+    return rc, _stats(st)
+
+
+def cmg_level_solve_async(lvl, params=None, **kw):
+    """Queue a solve without waiting; cmg_level_solve_wait reports it."""
+    prm = params if params is not None else solve_params(**kw)
+    _check(lib().cmg_level_solve_async(lvl.h, C.byref(prm)), "cmg_level_solve_async")
+
+
+def cmg_level_solve_wait(lvl, raise_on_error=True):
+    """Returns (status, stats dict) of the level's queued solve."""
+    st = cmg_solve_stats()
+    rc = lib().cmg_level_solve_wait(lvl.h, C.byref(st))
+    if raise_on_error:
+        _check(rc, "cmg_level_solve_wait")
     return rc, _stats(st)
 
 

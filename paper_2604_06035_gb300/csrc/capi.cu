@@ -321,6 +321,8 @@ int cmg_level_destroy(cmg_level *lvl) {
   cudaStreamSynchronize(lvl->stream);
   cmg::destroy_graphs(lvl);
   if (lvl->h_ctrl) cudaFreeHost(lvl->h_ctrl);
+  if (lvl->ev_start) cudaEventDestroy(lvl->ev_start);
+  if (lvl->ev_end) cudaEventDestroy(lvl->ev_end);
   lvl->mem.release();
   delete lvl;
   if (prev >= 0) cudaSetDevice(prev);
@@ -459,6 +461,26 @@ int cmg_level_solve(cmg_level *lvl, const cmg_solve_params *params, cmg_solve_st
     need(lvl && params, "NULL argument");
     DeviceScope ds(lvl->ctx->device);
     const int st = cmg::solve(lvl, params, stats);
+    if (st == CMG_ERR_NOT_CONVERGED) g_last_error = "max_cycles reached above tol";
+    if (st == CMG_ERR_DIVERGED) g_last_error = "residual diverged";
+    return st;
+  });
+}
+
+int cmg_level_solve_async(cmg_level *lvl, const cmg_solve_params *params) {
+  return guard([&] {
+    need(lvl && params, "NULL argument");
+    DeviceScope ds(lvl->ctx->device);
+    cmg::solve_launch(lvl, params);
+    return CMG_OK;
+  });
+}
+
+int cmg_level_solve_wait(cmg_level *lvl, cmg_solve_stats *stats) {
+  return guard([&] {
+    need(lvl != nullptr, "NULL level");
+    DeviceScope ds(lvl->ctx->device);
+    const int st = cmg::solve_wait(lvl, stats);
     if (st == CMG_ERR_NOT_CONVERGED) g_last_error = "max_cycles reached above tol";
     if (st == CMG_ERR_DIVERGED) g_last_error = "residual diverged";
     return st;

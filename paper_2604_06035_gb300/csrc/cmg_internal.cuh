@@ -273,6 +273,13 @@ struct cmg_level {
   double *rbuf = nullptr;      // [n][8] residual for the API (lazy)
   uint8_t *ctrl = nullptr;     // device solve control block (cycles, status, history)
   void *h_ctrl = nullptr;      // pinned host copy
+  // a queued solve (solve_launch) until solve_wait reports it
+  struct Pending {
+    bool empty = false;
+    int64_t launches_fixed = 0, launches_body = 0, updates_per_cycle = 0;
+  } pend;
+  bool solve_pending = false;
+  cudaEvent_t ev_start = nullptr, ev_end = nullptr;  // around the queued solve
   std::vector<void *> graphs;  // instantiated solve graphs, keyed by parameters
   bool has32 = false;
   // schedule: MG levels with at most this many octs (and all coarser ones) run
@@ -410,6 +417,8 @@ void batch_autotune(cmg_batch *b, const cmg_solve_params *p, cmg_batch_schedule 
 
 // solve.cu
 int solve(cmg_level *L, const cmg_solve_params *p, cmg_solve_stats *st);
+void solve_launch(cmg_level *L, const cmg_solve_params *p);
+int solve_wait(cmg_level *L, cmg_solve_stats *st);
 void destroy_graphs(cmg_level *L);
 
 }  // namespace cmg

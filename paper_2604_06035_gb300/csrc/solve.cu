@@ -349,7 +349,11 @@ void destroy_graphs(cmg_level *L) {
   L->graphs.clear();
 }
 
-int solve(cmg_level *L, const cmg_solve_params *p, cmg_solve_stats *st) {
+// Queue a solve of the level on the context's stream: the cached graph (built
+// on first use) and a copy of the control block to pinned host memory, with
+// the level's own timing events around them; with profiling on, the
+// host-driven loop (which waits every cycle).  solve_wait() completes it.
+void solve_launch(cmg_level *L, const cmg_solve_params *p) {
   if (!p || p->n_pre < 0 || p->n_post < 0 || p->coarse_sweeps < 0 || p->max_cycles < 0 || p->max_cycles > 256 ||
       p->fixed_cycles < 0 || p->fixed_cycles > 256 || !(p->tol >= 0.0) ||
       (p->precision != CMG_PREC_FP64 && p->precision != CMG_PREC_MIXED && p->precision != CMG_PREC_FFT) ||
@@ -363,9 +367,7 @@ int solve(cmg_level *L, const cmg_solve_params *p, cmg_solve_stats *st) {
     throw Error(CMG_ERR_INVALID_ARG, "mixed precision needs at least two multigrid levels");
   if (p->precision == CMG_PREC_FFT && !fft_supported(L))
     throw Error(CMG_ERR_INVALID_ARG, "the FFT solve needs a full periodic level of 4^3 .. 512^3 cells");
-  cmg_solve_stats local;
-  cmg_solve_stats &S = st ? *st : local;
-  S = cmg_solve_stats{};
+  if (L->solve_pending) throw Error(CMG_ERR_INVALID_ARG, "a solve of this level is still pending");
   cmg_ctx *ctx = L->ctx;
   if (p->precision != CMG_PREC_FP64) ensure_fp32(L);
   if (p->precision == CMG_PREC_FFT) fft_prepare(L);
@@ -374,12 +376,17 @@ int solve(cmg_level *L, const cmg_solve_params *p, cmg_solve_stats *st) {
     L->ctrl = L->mem.alloc<uint8_t>(sizeof(SolveCtrl), true, ctx->stream);
     CMG_CUDA(cudaMallocHost(&L->h_ctrl, sizeof(SolveCtrl)));
   }
-  if (L->n == 0) {
-    S.status = CMG_OK;
-    return CMG_OK;
+  if (!L->ev_start) {
+    CMG_CUDA(cudaEventCreate(&L->ev_start));
+    CMG_CUDA(cudaEventCreate(&L->ev_end));
   }
-  CMG_CUDA(cudaEventRecord(ctx->ev0, ctx->stream));
-  int64_t updates_per_cycle = 0;
+  L->pend = cmg_level::Pending{};
+  if (L->n == 0) {
+    L->pend.empty = true;
+    L->solve_pending = true;
+    return;
+  }
+  CMG_CUDA(cudaEventRecord(L->ev_start, ctx->stream));
   if (!ctx->profiling) {
     CachedGraph *cg = nullptr;
     for (void *v : L->graphs)
@@ -390,11 +397,10 @@ int solve(cmg_level *L, const cmg_solve_params *p, cmg_solve_stats *st) {
       L->graphs.push_back(cg);
     }
     CMG_CUDA(cudaGraphLaunch(cg->exec, ctx->stream));
-    CMG_CUDA(cudaEventRecord(ctx->ev1, ctx->stream));
-    CMG_CUDA(cudaEventSynchronize(ctx->ev1));
-    const SolveCtrl &c = *reinterpret_cast<const SolveCtrl *>(L->h_ctrl);
-    ctx->launches += cg->launches_pre + cg->launches_post + (int64_t)c.cycles * cg->launches_body;
-    updates_per_cycle = cg->updates_per_cycle;
+    CMG_CUDA(cudaEventRecord(L->ev_end, ctx->stream));
+    L->pend.launches_fixed = cg->launches_pre + cg->launches_post;
+    L->pend.launches_body = cg->launches_body;
+    L->pend.updates_per_cycle = cg->updates_per_cycle;
   } else {
     // host-driven loop, every launch visible to the profiler
     cudaGraphConditionalHandle none{};
@@ -402,6 +408,7 @@ int solve(cmg_level *L, const cmg_solve_params *p, cmg_solve_stats *st) {
     copy_ctrl_to_host(L);
     CMG_CUDA(cudaStreamSynchronize(ctx->stream));
     const SolveCtrl &c = *reinterpret_cast<const SolveCtrl *>(L->h_ctrl);
+    int64_t updates_per_cycle = 0;
     while (c.go) {
       int64_t u = 0;
       segment_body(L, p, none, 0, &u);
@@ -411,14 +418,36 @@ int solve(cmg_level *L, const cmg_solve_params *p, cmg_solve_stats *st) {
     }
     segment_post(L, p);
     copy_ctrl_to_host(L);
-    CMG_CUDA(cudaEventRecord(ctx->ev1, ctx->stream));
-    CMG_CUDA(cudaEventSynchronize(ctx->ev1));
+    CMG_CUDA(cudaEventRecord(L->ev_end, ctx->stream));
+    L->pend.updates_per_cycle = updates_per_cycle;
   }
-  fill_stats(L, S, updates_per_cycle);
+  L->solve_pending = true;
+}
+
+// Wait for the level's queued solve and report it.
+int solve_wait(cmg_level *L, cmg_solve_stats *st) {
+  if (!L->solve_pending) throw Error(CMG_ERR_INVALID_ARG, "no solve of this level is pending");
+  L->solve_pending = false;
+  cmg_solve_stats local;
+  cmg_solve_stats &S = st ? *st : local;
+  S = cmg_solve_stats{};
+  if (L->pend.empty) {
+    S.status = CMG_OK;
+    return CMG_OK;
+  }
+  CMG_CUDA(cudaEventSynchronize(L->ev_end));
+  const SolveCtrl &c = *reinterpret_cast<const SolveCtrl *>(L->h_ctrl);
+  L->ctx->launches += L->pend.launches_fixed + (int64_t)c.cycles * L->pend.launches_body;
+  fill_stats(L, S, L->pend.updates_per_cycle);
   float ms = 0.f;
-  CMG_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+  CMG_CUDA(cudaEventElapsedTime(&ms, L->ev_start, L->ev_end));
   S.ms = ms;
   return S.status;
+}
+
+int solve(cmg_level *L, const cmg_solve_params *p, cmg_solve_stats *st) {
+  solve_launch(L, p);
+  return solve_wait(L, st);
 }
 
 }  // namespace cmg

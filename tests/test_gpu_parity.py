@@ -388,6 +388,39 @@ def test_tail_schedule_matches_per_operation_launches(cmg, ctx, precision):
             assert relerr(out[(tail, base)], out[(0, base)]) <= 1e-13, (tail, base)
 
 
+def test_queued_solves_match_blocking_solves(cmg, ctx):
+    """cmg_level_solve_async + cmg_level_solve_wait on both levels of the
+    two-level workload (the fine level queued behind its parent, whose phi it
+    reads in stream order) give the blocking solves' phi and statistics
+    bit-for-bit; waiting with nothing queued and queueing twice are errors."""
+    cfg, GB, GF, RB, RF = _two_level(cmg, ctx, 6)
+    out = {}
+    for mode in ("blocking", "queued"):
+        for G, rho in ((GB, cfg["rho"][0]), (GF, cfg["rho"][1])):
+            cmg.cmg_level_set_density(G, rho, 1.0)
+            cmg.cmg_level_set_phi(G, np.zeros((cmg.cmg_level_n_octs(G), 8)))
+        if mode == "blocking":
+            sts = [cmg.cmg_level_solve(G, tol=1e-10)[1] for G in (GB, GF)]
+        else:
+            for G in (GB, GF):
+                cmg.cmg_level_solve_async(G, tol=1e-10)
+            sts = [cmg.cmg_level_solve_wait(G)[1] for G in (GB, GF)]
+        out[mode] = ([cmg.cmg_level_get_phi(G) for G in (GB, GF)], sts)
+    for a, b in zip(out["blocking"][0], out["queued"][0]):
+        assert np.array_equal(a, b)
+    for a, b in zip(out["blocking"][1], out["queued"][1]):
+        assert a["cycles"] == b["cycles"] and a["rel_history"] == b["rel_history"]
+    with pytest.raises(cmg.CmgError) as e:
+        cmg.cmg_level_solve_wait(GB)
+    assert e.value.code == cmg.CMG_ERR_INVALID_ARG
+    cmg.cmg_level_solve_async(GB, tol=1e-10)
+    with pytest.raises(cmg.CmgError) as e:
+        cmg.cmg_level_solve_async(GB, tol=1e-10)
+    assert e.value.code == cmg.CMG_ERR_INVALID_ARG
+    rc, st = cmg.cmg_level_solve_wait(GB)
+    assert rc == cmg.CMG_OK
+
+
 def test_grid_tail_barrier_timeout_returns_status(cmg, ctx):
     """A grid-tail barrier wait that runs out of spin budget ends the launch
     and the solve with CMG_ERR_TIMEOUT; the context stays usable and the next
