@@ -51,25 +51,6 @@ struct DeviceScope {
   }
 };
 
-// Temporary device buffer for host-memory arguments (freed on scope exit).
-struct Temp {
-  void *p = nullptr;
-  explicit Temp(size_t bytes) {
-    if (bytes == 0) bytes = 1;
-    if (cudaMalloc(&p, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      throw cmg::Error(CMG_ERR_OOM, "temporary device buffer");
-    }
-  }
-  ~Temp() {
-    if (p) cudaFree(p);
-  }
-  template <class T>
-  T *as() {
-    return static_cast<T *>(p);
-  }
-};
-
 void check_mem(int mem) {
   if (mem != CMG_MEM_HOST && mem != CMG_MEM_DEVICE) throw cmg::Error(CMG_ERR_INVALID_ARG, "bad cmg_mem tag");
 }
@@ -79,6 +60,29 @@ void need(bool ok, const char *what) {
 }
 
 // Run `produce(device_out)` and deliver `bytes` to `out` in memory space mem.
+// The context's staging buffer `which` with at least `bytes` (grow-only: a
+// cudaMalloc / cudaFree per call would synchronise the device every time).
+// Every user synchronises the stream before returning, so the next call may
+// reuse it.
+void *staging(cmg_ctx *ctx, int which, size_t bytes) {
+  if (bytes == 0) bytes = 1;
+  if (ctx->stage_bytes[which] < bytes) {
+    if (ctx->stage[which]) {
+      CMG_CUDA(cudaStreamSynchronize(ctx->stream));
+      cudaFree(ctx->stage[which]);
+      ctx->stage[which] = nullptr;
+      ctx->stage_bytes[which] = 0;
+    }
+    if (cudaMalloc(&ctx->stage[which], bytes) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->stage[which] = nullptr;
+      throw cmg::Error(CMG_ERR_OOM, "device staging buffer");
+    }
+    ctx->stage_bytes[which] = bytes;
+  }
+  return ctx->stage[which];
+}
+
 template <class F>
 void deliver(cmg_ctx *ctx, void *out, size_t bytes, int mem, F &&produce) {
   if (mem == CMG_MEM_DEVICE) {
@@ -86,9 +90,9 @@ void deliver(cmg_ctx *ctx, void *out, size_t bytes, int mem, F &&produce) {
     CMG_CUDA(cudaGetLastError());
     return;
   }
-  Temp t(bytes);
-  produce(t.p);
-  if (bytes) CMG_CUDA(cudaMemcpyAsync(out, t.p, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  void *t = staging(ctx, 1, bytes);
+  produce(t);
+  if (bytes) CMG_CUDA(cudaMemcpyAsync(out, t, bytes, cudaMemcpyDeviceToHost, ctx->stream));
   CMG_CUDA(cudaStreamSynchronize(ctx->stream));
 }
 
@@ -99,9 +103,9 @@ void accept(cmg_ctx *ctx, const void *in, size_t bytes, int mem, F &&use) {
     use(in);
     return;
   }
-  Temp t(bytes);
-  if (bytes) CMG_CUDA(cudaMemcpyAsync(t.p, in, bytes, cudaMemcpyHostToDevice, ctx->stream));
-  use(static_cast<const void *>(t.p));
+  void *t = staging(ctx, 0, bytes);
+  if (bytes) CMG_CUDA(cudaMemcpyAsync(t, in, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  use(static_cast<const void *>(t));
   CMG_CUDA(cudaStreamSynchronize(ctx->stream));
 }
 
@@ -153,6 +157,8 @@ int cmg_ctx_destroy(cmg_ctx *ctx) {
   if (ctx->h_dpinned) cudaFreeHost(ctx->h_dpinned);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  for (void *p : ctx->stage)
+    if (p) cudaFree(p);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->cap_stream2) cudaStreamDestroy(ctx->cap_stream2);

@@ -227,6 +227,9 @@ struct cmg_ctx {
   int *h_pinned = nullptr;    // pinned staging (ints)
   double *h_dpinned = nullptr;  // pinned staging (doubles)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // device staging of host-memory arguments (grow-only; [0] inputs, [1] outputs)
+  void *stage[2] = {nullptr, nullptr};
+  size_t stage_bytes[2] = {0, 0};
   // graph capture (private streams; the caller's stream may be the legacy one)
   cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
   bool capturing = false;
