@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--train-seconds", type=float, default=60.0, help="U-Net training budget")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start block")
     ap.add_argument("--no-amr3", action="store_true", help="skip the 256^3 + 3-level mixed-precision block")
-    ap.add_argument("--block", choices=["smoother", "learned", "forward", "fft", "pcg", "amr3"], default=None,
+    ap.add_argument("--block", choices=["smoother", "learned", "forward", "fft", "pcg", "amr3", "batched"], default=None,
                     help="run one sub-benchmark alone and print its JSON (profiling runs)")
     ap.add_argument("--smoother-level", type=int, default=9, help="level of the full periodic grid (9 = 512^3)")
     ap.add_argument("--fft-level", type=int, default=9, help="level of the fft block's full periodic grid")
@@ -213,7 +213,8 @@ def bench_batched(cmg, ctx, dev, stream, args):
     """512 independent refined patches (log-uniform 64..200000 octs, level 11,
     Dirichlet values from a smooth coarse field): one persistent cooperative
     kernel per solve.  Autotunes the schedule, then times mixed-precision and
-    FP64 solves from phi = 0 to rel. residual tol on every patch."""
+    FP64 solves from phi = 0 to rel. residual tol on every patch, as V-cycle
+    iterations and as per-patch CG preconditioned by them."""
     import torch
     from paper_2604_06035_gb300 import inputs
     t0 = time.perf_counter()
@@ -238,14 +239,15 @@ def bench_batched(cmg, ctx, dev, stream, args):
     res = {"patches": 512, "octs": int(len(b["coords"])), "cells": int(8 * len(b["coords"])),
            "level": lev, "schedule": best, "autotune_s": tune_s, "build_ms": build_ms, "generate_s": gen_s}
     reps = max(3, min(args.steps, 5))
-    for name, prec in (("mixed", cmg.CMG_PREC_MIXED), ("fp64", cmg.CMG_PREC_FP64)):
+    for name, prec, kr in (("mixed", cmg.CMG_PREC_MIXED, 0), ("fp64", cmg.CMG_PREC_FP64, 0),
+                           ("mixed_pcg", cmg.CMG_PREC_MIXED, 1), ("fp64_pcg", cmg.CMG_PREC_FP64, 1)):
         cmg.cmg_level_set_phi(F, zeros)
-        cmg.cmg_batch_solve(B, tol=args.tol, precision=prec)  # records the graph
+        cmg.cmg_batch_solve(B, tol=args.tol, precision=prec, krylov=kr)  # records the graph
         ms, upd = [], 0
         for _ in range(reps):
             cmg.cmg_level_set_phi(F, zeros)
             torch.cuda.synchronize()
-            rc, st = cmg.cmg_batch_solve(B, tol=args.tol, precision=prec)
+            rc, st = cmg.cmg_batch_solve(B, tol=args.tol, precision=prec, krylov=kr)
             ms.append(st["ms"])
             upd += st["cell_updates"]
         res[name] = {"ms_per_solve": statistics.median(ms), "Mcell_updates_per_s": upd / (sum(ms) / 1e3) / 1e6,
@@ -839,6 +841,8 @@ def run_block(args):
         B = cmg.cmg_level_build(ctx, 7, cmg.cmg_morton_encode(ctx, torch.from_numpy(cfg["coords"][0]).to(dev)))
         out = bench_fft(cmg, ctx, dev, B, torch.from_numpy(cfg["rho"][0]).to(dev), args, peaks)
         cmg.cmg_level_destroy(B)
+    elif args.block == "batched":
+        out = bench_batched(cmg, ctx, dev, torch.cuda.current_stream(dev), args)
     elif args.block == "amr3":
         out = bench_amr3(cmg, ctx, dev, args)
     elif args.block == "pcg":

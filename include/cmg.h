@@ -70,8 +70,10 @@ typedef struct {
                         the fastest to 1e-10 on the two-level 128^3 workload) */
   int krylov;        /* 0: stationary V-cycle iteration; 1: conjugate gradients
                         preconditioned by one V-cycle per iteration (App. D.2
-                        names multigrid as the CG preconditioner), FP64 only;
-                        cycles then counts CG iterations.  Batches: 0 only. */
+                        names multigrid as the CG preconditioner); cycles then
+                        counts CG iterations.  Level solves: FP64 only.
+                        Batches: per-patch CG, preconditioned by an FP64 V-cycle
+                        or (MIXED) by FP32 V-cycles on r / ||r||. */
 } cmg_solve_params;
 
 typedef struct {
@@ -258,7 +260,12 @@ int cmg_level_mg_step(cmg_level *lvl, int m, int op, int precision, int n, doubl
  * all patches iterate until the slowest one has.  With MIXED precision the
  * cycles are FP32 V-cycles inside FP64 refinement, scaled per patch.
  * The coarsest solve of every patch is n_pre + n_post red-black sweeps (the
- * schedule's), so a patch's result equals the solve of that patch alone. */
+ * schedule's), so a patch's result equals the solve of that patch alone.
+ * With krylov = 1 every patch runs its own flexible conjugate-gradient
+ * iteration (its own alpha and beta; a patch that reached tol stops
+ * updating) with the batch's V-cycle from zero as the preconditioner
+ * (MIXED: FP32 V-cycles on the residual scaled by its previous norm; needs at
+ * least two multigrid levels). */
 typedef struct cmg_batch cmg_batch;
 typedef struct {
   int threads;        /* threads per block of the persistent kernel (multiple of 32, <= 1024) */
@@ -282,8 +289,8 @@ int cmg_batch_set_schedule(cmg_batch *batch, const cmg_batch_schedule *schedule)
 int cmg_batch_get_schedule(cmg_batch *batch, cmg_batch_schedule *schedule);
 /* Spin budget of the grid barriers in SM clock cycles (default 2e9, ~1 s). */
 int cmg_batch_set_spin_budget(cmg_batch *batch, int64_t cycles);
-/* params: tol, max_cycles, fixed_cycles and precision are used; the sweep
- * counts come from the batch schedule. */
+/* params: tol, max_cycles, fixed_cycles, precision and krylov are used; the
+ * sweep counts come from the batch schedule. */
 int cmg_batch_solve(cmg_batch *batch, const cmg_solve_params *params, cmg_batch_stats *stats);
 /* Per-patch results of the last solve (host arrays of n_patches; any may be
  * NULL): relative residual, cycle at which the patch reached tol (-1 if it

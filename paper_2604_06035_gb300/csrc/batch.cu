@@ -56,6 +56,11 @@ struct BatchPlan {
   // control: [0] status, [1] cycles, [2..3] unconverged counters, [4] barriers, [5] n_converged
   int *ctrl;
   unsigned *bar;  // grid barrier word
+  // conjugate gradients (krylov = 1): top-level vectors in the phi layout
+  // ([2][n_alloc][4]; gsave in the g layout) and per-patch scalars
+  double *cx, *cp0, *cp1, *cq, *gsave;
+  double *zr, *zq, *zr_old, *beta, *pq, *alpha;
+  int32_t *done;
 };
 
 // Grid-wide barrier (gridsync.cuh): waits give up after spin_budget SM clock
@@ -189,12 +194,9 @@ __device__ void top_residual(const BatchPlan &P, double *acc_out, int64_t tid, i
   }
 }
 
-template <bool MIXED>
-__global__ void __launch_bounds__(512, 1) k_batch(const __grid_constant__ BatchPlan P) {
-  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Dirichlet ghosts of the top level from the parent's phi.
+__device__ void fill_top_ghosts(const BatchPlan &P, int64_t tid, int64_t nthr) {
   const BLevel &T0 = P.lv[0];
-  // Dirichlet ghosts from the parent's phi; per-patch accumulators cleared
   for (int64_t t = tid; t < P.n_ghost; t += nthr) {
     const int cc = (int)(__ldg(P.gkeys + t) & 7);
     int32_t b[8];
@@ -214,14 +216,234 @@ __global__ void __launch_bounds__(512, 1) k_batch(const __grid_constant__ BatchP
       dev::store4(T0.phi + (p * T0.n_alloc + T0.n + t) * 4, v);
     }
   }
-  for (int64_t p = tid; p < P.n_patches; p += nthr) {
-    P.n0[p] = 0.0;
-    P.norm[p] = 0.0;
-    P.conv_at[p] = -1;
+}
+
+// ---- flexible (Polak-Ribiere) conjugate gradients per patch (krylov = 1),
+// the multigrid V-cycle from zero as the preconditioner (the paper names
+// multigrid as a CG preconditioner, App. D.2): the level solve's PCG
+// (pcg.cu) with a separate alpha and beta for every patch.  A patch that has
+// reached tol keeps alpha = beta = 0 (frozen) while the others iterate.
+
+__device__ __forceinline__ int64_t at_phi(int64_t o, int c, int64_t ps) {
+  return (int64_t)cell_parity(c) * ps + o * 4 + (c >> 1);
+}
+
+// z at phi-layout index k of a cell of patch p: the FP64 V-cycle leaves z in
+// phi; the FP32 one leaves e = z / s_acc in phi32
+template <bool MIXED>
+__device__ __forceinline__ double zval(const BatchPlan &P, int64_t k, double s) {
+  if constexpr (MIXED) return s * (double)__ldcg(P.lv[0].phi32 + k);
+  else return __ldcg(P.lv[0].phi + k);
+}
+
+template <bool MIXED>
+__device__ bool krylov_solve(const BatchPlan &P, int64_t tid, int64_t nthr) {
+  const BLevel &T = P.lv[0];
+  const int64_t n = T.n, ps = T.n_alloc * 4, gs = n * 4;
+  const int64_t wbase = tid & ~(int64_t)31;
+  // r0 = f - L phi0 (Dirichlet ghosts) in place of g (saved), x = phi0, ||r0||^2
+  for (int64_t base = wbase; base < n; base += nthr) {
+    const int64_t i = base + (threadIdx.x & 31);
+    double acc = 0.0;
+    int pp = -1;
+    if (i < n) {
+      pp = __ldg(P.pid + i);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        double sum = 0.0;
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+          const int a = d >> 1, side = d & 1, c2 = c ^ (1 << a);
+          const int64_t o = (((c >> a) & 1) != side) ? i : (int64_t)__ldg(T.nbr + d * n + i);
+          sum += __ldcg(T.phi + at_phi(o, c2, ps));
+        }
+        const int64_t gi = at_phi(i, c, gs), k = at_phi(i, c, ps);
+        const double gv = __ldcg(T.g + gi), ph = __ldcg(T.phi + k);
+        const double v = fma(sum, 1.0 / 6.0, gv) - ph;
+        P.gsave[gi] = gv;
+        T.g[gi] = v;
+        P.cx[k] = ph;
+        acc += v * v;
+      }
+    }
+    patch_add(P.norm, pp, acc);
   }
-  if (!grid_sync(P)) return;
-  top_residual<false, true>(P, P.n0, tid, nthr);  // ||f - L 0||^2 per patch
-  if (!grid_sync(P)) return;
+  for (int64_t p = tid; p < P.n_patches; p += nthr) {
+    P.zr[p] = P.zq[p] = P.zr_old[p] = P.beta[p] = P.pq[p] = P.alpha[p] = 0.0;
+    P.done[p] = 0;
+  }
+  if (!grid_sync(P)) return false;
+  // corrections see zero coarse-fine values: clear phi's ghost octs
+  for (int64_t t = tid; t < 8 * (T.n_alloc - n); t += nthr) {
+    const int pl = (int)(t / (4 * (T.n_alloc - n)));
+    const int64_t r = t - pl * 4 * (T.n_alloc - n);
+    T.phi[pl * ps + 4 * n + r] = 0.0;
+  }
+  for (int64_t p = tid; p < P.n_patches; p += nthr) {
+    const double nr = __ldcg(P.norm + p);
+    P.s_emit[p] = nr > 0.0 ? sqrt(nr) : 1.0;
+  }
+  if (!grid_sync(P)) return false;
+  if (MIXED) {  // the first FP32 right-hand side r0 / s
+    for (int64_t t = tid; t < 8 * n; t += nthr) {
+      const int64_t i = (t >> 2) % n;
+      T.g32[t] = (float)(T.g[t] / __ldcg(P.s_emit + __ldg(P.pid + i)));
+    }
+    if (!grid_sync(P)) return false;
+  }
+  int cur = 0;  // direction buffer written this iteration
+  for (int cycle = 0;; ++cycle) {
+    // stop test on ||r||; alpha of the last step kept for the next beta
+    for (int64_t p = tid; p < P.n_patches; p += nthr) {
+      const double n0 = __ldcg(P.n0 + p), nr = __ldcg(P.norm + p);
+      const double rel = n0 > 0.0 ? sqrt(nr / n0) : 0.0;
+      P.rel[p] = rel;
+      if (!(rel == rel) || isinf(rel)) atomicCAS(P.ctrl, 0, CMG_ERR_DIVERGED);
+      const int was_done = __ldcg(P.done + p);
+      if (cycle > 0) {
+        const double pq = __ldcg(P.pq + p), zo = __ldcg(P.zr_old + p);
+        P.alpha[p] = (was_done || pq == 0.0) ? 0.0 : zo / pq;
+      }
+      if (rel <= P.tol) {
+        if (__ldcg(P.conv_at + p) < 0) P.conv_at[p] = cycle;
+        P.done[p] = 1;
+      } else {
+        atomicAdd(P.ctrl + 2 + (cycle & 1), 1);
+      }
+      if (MIXED) {
+        P.s_acc[p] = __ldcg(P.s_emit + p);
+        P.s_emit[p] = nr > 0.0 ? sqrt(nr) : 1.0;
+      }
+      P.norm[p] = 0.0;
+    }
+    if (!grid_sync(P)) return false;
+    const int unconverged = __ldcg(P.ctrl + 2 + (cycle & 1));
+    const int status = __ldcg(P.ctrl);
+    bool stop = status != 0;
+    if (P.fixed_cycles > 0) stop = stop || cycle >= P.fixed_cycles;
+    else stop = stop || unconverged == 0 || cycle >= P.max_cycles;
+    if (stop) {
+      if (tid == 0) {
+        P.ctrl[1] = cycle;
+        P.ctrl[5] = P.n_patches - unconverged;
+        if (status == 0 && P.fixed_cycles == 0 && unconverged > 0) P.ctrl[0] = CMG_ERR_NOT_CONVERGED;
+      }
+      break;
+    }
+    if (tid == 0) P.ctrl[2 + ((cycle + 1) & 1)] = 0;
+    // z = M r: one V-cycle from zero (FP64 on g = r, or FP32 on g32 = r / s)
+    if (MIXED) {
+      for (int k = 0; k < P.inner; ++k)
+        if (!vcycle<float>(P, k == 0, tid, nthr)) return false;
+    } else {
+      if (!vcycle<double>(P, true, tid, nthr)) return false;
+    }
+    // (z, r) and (z, q) per patch; q is the last iteration's L0 p
+    for (int64_t base = wbase; base < n; base += nthr) {
+      const int64_t i = base + (threadIdx.x & 31);
+      double a = 0.0, b = 0.0;
+      int pp = -1;
+      if (i < n) {
+        pp = __ldg(P.pid + i);
+        const double sz = MIXED ? __ldcg(P.s_acc + pp) : 1.0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int64_t k = at_phi(i, c, ps);
+          const double z = zval<MIXED>(P, k, sz);
+          a += z * __ldcg(T.g + at_phi(i, c, gs));
+          b += z * __ldcg(P.cq + k);
+        }
+      }
+      patch_add(P.zr, pp, a);
+      patch_add(P.zq, pp, b);
+    }
+    if (!grid_sync(P)) return false;
+    // beta = -alpha (z', q) / (z, r)_old (0 on the first iteration and once frozen)
+    for (int64_t p = tid; p < P.n_patches; p += nthr) {
+      const double zo = __ldcg(P.zr_old + p);
+      const bool fresh = cycle == 0 || __ldcg(P.done + p) || zo == 0.0;
+      P.beta[p] = fresh ? 0.0 : -__ldcg(P.alpha + p) * __ldcg(P.zq + p) / zo;
+      P.zr_old[p] = __ldcg(P.zr + p);
+      P.zr[p] = 0.0;
+      P.zq[p] = 0.0;
+      P.pq[p] = 0.0;
+    }
+    if (!grid_sync(P)) return false;
+    // p = z + beta p_old into the other direction buffer, q = L0 p with the
+    // neighbours' p formed on the fly (neighbours share the patch; ghost and
+    // zero octs hold zero in z and p_old); (p, q) per patch
+    double *pn = cur ? P.cp1 : P.cp0;
+    const double *po = cur ? P.cp0 : P.cp1;
+    for (int64_t base = wbase; base < n; base += nthr) {
+      const int64_t i = base + (threadIdx.x & 31);
+      double acc = 0.0;
+      int pp = -1;
+      if (i < n) {
+        pp = __ldg(P.pid + i);
+        const double bt = __ldcg(P.beta + pp), sz = MIXED ? __ldcg(P.s_acc + pp) : 1.0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int64_t k = at_phi(i, c, ps);
+          const double pv = fma(bt, __ldcg(po + k), zval<MIXED>(P, k, sz));
+          double sum = 0.0;
+#pragma unroll
+          for (int d = 0; d < 6; ++d) {
+            const int a = d >> 1, side = d & 1, c2 = c ^ (1 << a);
+            const int64_t o = (((c >> a) & 1) != side) ? i : (int64_t)__ldg(T.nbr + d * n + i);
+            const int64_t k2 = at_phi(o, c2, ps);
+            sum += fma(bt, __ldcg(po + k2), zval<MIXED>(P, k2, sz));
+          }
+          const double qv = pv - sum * (1.0 / 6.0);
+          pn[k] = pv;
+          P.cq[k] = qv;
+          acc += pv * qv;
+        }
+      }
+      patch_add(P.pq, pp, acc);
+    }
+    if (!grid_sync(P)) return false;
+    // alpha = (z, r) / (p, q); x += alpha p; r -= alpha q; ||r||^2 per patch;
+    // MIXED: the next FP32 right-hand side r / s
+    for (int64_t base = wbase; base < n; base += nthr) {
+      const int64_t i = base + (threadIdx.x & 31);
+      double acc = 0.0;
+      int pp = -1;
+      if (i < n) {
+        pp = __ldg(P.pid + i);
+        const double pq = __ldcg(P.pq + pp);
+        const double al = (__ldcg(P.done + pp) || pq == 0.0) ? 0.0 : __ldcg(P.zr_old + pp) / pq;
+        const double inv_s = MIXED ? 1.0 / __ldcg(P.s_emit + pp) : 0.0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int64_t k = at_phi(i, c, ps), gi = at_phi(i, c, gs);
+          P.cx[k] += al * __ldcg(pn + k);
+          const double rv = __ldcg(T.g + gi) - al * __ldcg(P.cq + k);
+          T.g[gi] = rv;
+          if (MIXED) T.g32[gi] = (float)(rv * inv_s);
+          acc += rv * rv;
+        }
+      }
+      patch_add(P.norm, pp, acc);
+    }
+    if (!grid_sync(P)) return false;
+    cur ^= 1;
+  }
+  // wrap-up: phi = x, the source restored, the coarse-fine ghosts refilled
+  for (int64_t t = tid; t < 8 * n; t += nthr) {
+    const int pl = (int)(t / (4 * n));
+    const int64_t r = t - pl * 4 * n;
+    T.phi[pl * ps + r] = __ldcg(P.cx + pl * ps + r);
+    T.g[t] = __ldcg(P.gsave + t);
+  }
+  fill_top_ghosts(P, tid, nthr);
+  return grid_sync(P);
+}
+
+// The stationary iteration: V-cycles (FP64, or FP32 inside FP64 refinement)
+// until every patch reaches tol.
+template <bool MIXED>
+__device__ void stationary_solve(const BatchPlan &P, int64_t tid, int64_t nthr) {
+  const BLevel &T0 = P.lv[0];
   for (int64_t p = tid; p < P.n_patches; p += nthr) {
     const double n0 = __ldcg(P.n0 + p);
     P.s_emit[p] = n0 > 0.0 ? sqrt(n0) : 1.0;
@@ -286,6 +508,26 @@ __global__ void __launch_bounds__(512, 1) k_batch(const __grid_constant__ BatchP
   }
 }
 
+template <bool MIXED, bool KRYLOV>
+__global__ void __launch_bounds__(512, 1) k_batch(const __grid_constant__ BatchPlan P) {
+  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // Dirichlet ghosts from the parent's phi; per-patch accumulators cleared
+  fill_top_ghosts(P, tid, nthr);
+  for (int64_t p = tid; p < P.n_patches; p += nthr) {
+    P.n0[p] = 0.0;
+    P.norm[p] = 0.0;
+    P.conv_at[p] = -1;
+  }
+  if (!grid_sync(P)) return;
+  top_residual<false, true>(P, P.n0, tid, nthr);  // ||f - L 0||^2 per patch
+  if (!grid_sync(P)) return;
+  if constexpr (KRYLOV)
+    krylov_solve<MIXED>(P, tid, nthr);
+  else
+    stationary_solve<MIXED>(P, tid, nthr);
+}
+
 __global__ void k_patch_ids(const int64_t *__restrict__ offsets, int n_patches, int32_t *__restrict__ pid, int64_t n) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -345,11 +587,16 @@ bool same_sched(const cmg_batch_schedule &a, const cmg_batch_schedule &b) {
 
 bool same_params(const cmg_solve_params &a, const cmg_solve_params &b) {
   return a.tol == b.tol && a.max_cycles == b.max_cycles && a.fixed_cycles == b.fixed_cycles &&
-         a.precision == b.precision;
+         a.precision == b.precision && a.krylov == b.krylov;
 }
 
-int grid_size(cmg_batch *b, bool mixed) {
-  const void *fn = mixed ? (const void *)k_batch<true> : (const void *)k_batch<false>;
+const void *batch_kernel(bool mixed, bool krylov) {
+  if (mixed) return krylov ? (const void *)k_batch<true, true> : (const void *)k_batch<true, false>;
+  return krylov ? (const void *)k_batch<false, true> : (const void *)k_batch<false, false>;
+}
+
+int grid_size(cmg_batch *b, bool mixed, bool krylov) {
+  const void *fn = batch_kernel(mixed, krylov);
   int per_sm = 0;
   CMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, b->sched.threads, 0));
   if (per_sm < 1) throw Error(CMG_ERR_INVALID_ARG, "the batch kernel does not fit this block size");
@@ -400,17 +647,43 @@ BatchPlan make_plan(cmg_batch *b, const cmg_solve_params *p) {
   P.conv_at = b->conv_at;
   P.ctrl = b->ctrl;
   P.bar = b->bar;
+  if (b->cg) {
+    const int64_t nv = 8 * L->mg[0].n_alloc;
+    P.cx = b->cg;
+    P.cp0 = P.cx + nv;
+    P.cp1 = P.cp0 + nv;
+    P.cq = P.cp1 + nv;
+    P.gsave = P.cq + nv;
+    P.zr = P.gsave + 8 * L->mg[0].n;
+    P.zq = P.zr + n;
+    P.zr_old = P.zq + n;
+    P.beta = P.zr_old + n;
+    P.pq = P.beta + n;
+    P.alpha = P.pq + n;
+    P.done = b->cg_done;
+  }
   return P;
 }
 
-// Records: clear control words, the cooperative persistent kernel, copy of
-// the control words to pinned host memory.
+// CG vectors and per-patch scalars (krylov = 1), allocated on first use
+void ensure_cg(cmg_batch *b) {
+  if (b->cg) return;
+  cmg_level *L = b->lvl;
+  const int64_t nv = 8 * L->mg[0].n_alloc;
+  b->cg = b->mem.alloc<double>(4 * nv + 8 * L->mg[0].n + 6 * (int64_t)b->n_patches, true, L->ctx->stream);
+  b->cg_done = b->mem.alloc<int32_t>(b->n_patches, true, L->ctx->stream);
+  CMG_CUDA(cudaStreamSynchronize(L->ctx->stream));
+}
+
+// Records: clear control words (and the CG direction buffers), the
+// cooperative persistent kernel, copy of the control words to pinned host
+// memory.
 void record(cmg_batch *b, const cmg_solve_params *p) {
   cmg_level *L = b->lvl;
   cmg_ctx *ctx = L->ctx;
-  const bool mixed = p->precision == CMG_PREC_MIXED;
+  const bool mixed = p->precision == CMG_PREC_MIXED, krylov = p->krylov == 1;
   BatchPlan P = make_plan(b, p);
-  const int grid = grid_size(b, mixed);
+  const int grid = grid_size(b, mixed, krylov);
   if (!ctx->cap_stream) {
     CMG_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
     CMG_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream2, cudaStreamNonBlocking));
@@ -421,6 +694,8 @@ void record(cmg_batch *b, const cmg_solve_params *p) {
   try {
     CMG_CUDA(cudaMemsetAsync(b->ctrl, 0, 8 * sizeof(int), s));
     CMG_CUDA(cudaMemsetAsync(b->bar, 0, 2 * sizeof(unsigned), s));
+    if (krylov)  // both direction buffers and q start at zero (finite) every solve
+      CMG_CUDA(cudaMemsetAsync(P.cp0, 0, sizeof(double) * 3 * 8 * L->mg[0].n_alloc, s));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(b->sched.threads);
@@ -430,10 +705,14 @@ void record(cmg_batch *b, const cmg_solve_params *p) {
     attr.val.cooperative = 1;
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
-    if (mixed)
-      CMG_CUDA(cudaLaunchKernelEx(&cfg, k_batch<true>, P));
+    if (mixed && krylov)
+      CMG_CUDA(cudaLaunchKernelEx(&cfg, k_batch<true, true>, P));
+    else if (mixed)
+      CMG_CUDA(cudaLaunchKernelEx(&cfg, k_batch<true, false>, P));
+    else if (krylov)
+      CMG_CUDA(cudaLaunchKernelEx(&cfg, k_batch<false, true>, P));
     else
-      CMG_CUDA(cudaLaunchKernelEx(&cfg, k_batch<false>, P));
+      CMG_CUDA(cudaLaunchKernelEx(&cfg, k_batch<false, false>, P));
     CMG_CUDA(cudaMemcpyAsync(b->h_ctrl, b->ctrl, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
   } catch (...) {
     cudaGraph_t g;
@@ -458,23 +737,20 @@ int64_t updates_per_cycle(const cmg_batch *b, bool mixed) {
   return mixed ? u * b->sched.inner_cycles : u;
 }
 
-int64_t barriers_per_cycle(const cmg_batch *b, bool mixed) {
-  const int depth = (int)b->lvl->mg.size();
-  const int nsw = b->sched.n_pre + b->sched.n_post;
-  const int64_t vc = (int64_t)(depth - 1) * (2 * nsw + 2) + 2 * nsw + (mixed ? 2 : 0);
-  return (mixed ? vc * b->sched.inner_cycles + 1 : vc) + 2;
-}
 
 }  // namespace
 
 int batch_solve(cmg_batch *b, const cmg_solve_params *p, cmg_batch_stats *st) {
   if (!p || !(p->tol >= 0.0) || p->max_cycles < 0 || p->fixed_cycles < 0 ||
-      (p->precision != CMG_PREC_FP64 && p->precision != CMG_PREC_MIXED) || p->krylov != 0)
+      (p->precision != CMG_PREC_FP64 && p->precision != CMG_PREC_MIXED) || (p->krylov != 0 && p->krylov != 1))
     throw Error(CMG_ERR_INVALID_ARG, "invalid solve parameters");
   cmg_level *L = b->lvl;
   cmg_ctx *ctx = L->ctx;
   const bool mixed = p->precision == CMG_PREC_MIXED;
+  if (p->krylov == 1 && mixed && L->mg.size() < 2)
+    throw Error(CMG_ERR_INVALID_ARG, "mixed-precision CG needs at least two multigrid levels");
   if (mixed) ensure_fp32(L);
+  if (p->krylov == 1) ensure_cg(b);
   if (!b->exec || !same_sched(b->sched, b->g_sched) || !same_params(*p, b->g_params) ||
       b->spin_budget != b->g_budget)
     record(b, p);
@@ -606,7 +882,7 @@ void batch_autotune(cmg_batch *b, const cmg_solve_params *p, cmg_batch_schedule 
     for (const auto &c : cands) {
       b->sched = c;
       int per_sm = 0;
-      const void *fn = mixed ? (const void *)k_batch<true> : (const void *)k_batch<false>;
+      const void *fn = batch_kernel(mixed, p->krylov == 1);
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, c.threads, 0) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         continue;

@@ -310,6 +310,8 @@ struct cmg_batch {
   int *ctrl = nullptr;         // 8 ints
   unsigned *bar = nullptr;     // grid barrier words
   int *h_ctrl = nullptr;       // pinned copy of ctrl
+  double *cg = nullptr;        // CG vectors and per-patch scalars (krylov = 1, lazy)
+  int32_t *cg_done = nullptr;  // per-patch "reached tol" flags of the CG iteration
   cmg::DeviceBuffers mem;
   // the recorded solve graph and what it was recorded for
   cudaGraphExec_t exec = nullptr;

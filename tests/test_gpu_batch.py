@@ -5,7 +5,8 @@ With the V(2,2) schedule the coarsest solve of every patch is 4 red-black
 sweeps, so a patch's result in the batch must equal the oracle's solve of
 that patch alone with coarse_sweeps = 4: FP64 to 1e-12 relative at equal
 cycle counts, the same cycle at which each patch reaches tol, and mixed
-precision within 1e-10 of the FP64 solution."""
+precision within 1e-10 of the FP64 solution.  With krylov = 1 each patch runs
+the oracle's preconditioned CG of that patch alone."""
 import numpy as np
 import pytest
 
@@ -90,6 +91,63 @@ def test_batch_mixed_matches_fp64(cmg, setup):
     cmg.cmg_level_set_phi(F, np.zeros((len(b["coords"]), 8)))
     rc, st = cmg.cmg_batch_solve(B, tol=1e-11, precision=cmg.CMG_PREC_MIXED)
     assert rc == cmg.CMG_OK and st["n_converged"] == 12
+    phi = cmg.cmg_level_get_phi(F)
+    for k in (0, 5, 11):
+        R, sl = _oracle_patch(b, RP, k)
+        R.solve(tol=1e-13, coarse_sweeps=4)
+        assert _relerr(phi[sl], R.get_phi()) <= 1e-10, k
+
+
+def test_batch_pcg_fixed_iterations_match_per_patch_oracle(cmg, setup):
+    """krylov = 1: every patch runs its own flexible CG with the batch's
+    V-cycle from zero as the preconditioner -- the oracle's PCG of the patch
+    alone (coarsest = 4 sweeps).  Per-patch dot products are summed with
+    atomics in the batch (a different order than the oracle's), which moves
+    alpha and beta at the 1e-16 level: 1e-11 after three iterations."""
+    b, P, F, B, RP = setup
+    cmg.cmg_level_set_phi(F, np.zeros((len(b["coords"]), 8)))
+    rc, st = cmg.cmg_batch_solve(B, tol=1e-10, fixed_cycles=3, krylov=1)
+    assert rc == cmg.CMG_OK and st["cycles"] == 3
+    phi = cmg.cmg_level_get_phi(F)
+    for k in range(len(b["offsets"]) - 1):
+        R, sl = _oracle_patch(b, RP, k)
+        R.solve_pcg(tol=1e-10, fixed_cycles=3, coarse_sweeps=4)
+        assert _relerr(phi[sl], R.get_phi()) <= 1e-11, k
+
+
+def test_batch_pcg_to_tolerance(cmg, setup):
+    b, P, F, B, RP = setup
+    z = np.zeros((len(b["coords"]), 8))
+    cmg.cmg_level_set_phi(F, z)
+    rc, st_mg = cmg.cmg_batch_solve(B, tol=1e-10)
+    cmg.cmg_level_set_phi(F, z)
+    rc, st = cmg.cmg_batch_solve(B, tol=1e-10, krylov=1)
+    assert rc == cmg.CMG_OK and st["n_converged"] == 12
+    assert st["cycles"] < st_mg["cycles"]
+    rel, conv, n0 = cmg.cmg_batch_patch_stats(B)
+    assert np.all(rel <= 1e-10) and st["cycles"] == conv.max()
+    phi = cmg.cmg_level_get_phi(F)
+    for k in range(12):
+        R, sl = _oracle_patch(b, RP, k)
+        rc_o, so = R.solve_pcg(tol=1e-10, coarse_sweeps=4)
+        assert abs(so["cycles"] - conv[k]) <= 1, k
+        R.solve(tol=1e-13, coarse_sweeps=4)
+        assert _relerr(phi[sl], R.get_phi()) <= 1e-8, k
+    # the level is left as a solve leaves it (source restored, ghosts refilled):
+    # a stationary solve from this phi has nothing to do
+    rc, st2 = cmg.cmg_batch_solve(B, tol=1e-10)
+    assert rc == cmg.CMG_OK and st2["cycles"] == 0
+
+
+def test_batch_pcg_mixed_matches_fp64(cmg, setup):
+    b, P, F, B, RP = setup
+    z = np.zeros((len(b["coords"]), 8))
+    cmg.cmg_level_set_phi(F, z)
+    rc, st_mg = cmg.cmg_batch_solve(B, tol=1e-11, precision=cmg.CMG_PREC_MIXED)
+    cmg.cmg_level_set_phi(F, z)
+    rc, st = cmg.cmg_batch_solve(B, tol=1e-11, precision=cmg.CMG_PREC_MIXED, krylov=1)
+    assert rc == cmg.CMG_OK and st["n_converged"] == 12
+    assert st["cycles"] <= st_mg["cycles"]
     phi = cmg.cmg_level_get_phi(F)
     for k in (0, 5, 11):
         R, sl = _oracle_patch(b, RP, k)
