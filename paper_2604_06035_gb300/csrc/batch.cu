@@ -369,32 +369,40 @@ __device__ bool krylov_solve(const BatchPlan &P, int64_t tid, int64_t nthr) {
       P.pq[p] = 0.0;
     }
     if (!grid_sync(P)) return false;
-    // p = z + beta p_old into the other direction buffer, q = L0 p with the
-    // neighbours' p formed on the fly (neighbours share the patch; ghost and
-    // zero octs hold zero in z and p_old); (p, q) per patch
+    // p = z + beta p_old into the other direction buffer (ghost and zero octs
+    // stay zero), then q = L0 p and (p, q) per patch (neighbours share the
+    // patch).  Two passes: forming the neighbours' p on the fly would cost six
+    // more FP64 FMAs per cell than the extra pass costs bandwidth.
     double *pn = cur ? P.cp1 : P.cp0;
     const double *po = cur ? P.cp0 : P.cp1;
+    for (int64_t i = tid; i < n; i += nthr) {
+      const int pp = __ldg(P.pid + i);
+      const double bt = __ldcg(P.beta + pp), sz = MIXED ? __ldcg(P.s_acc + pp) : 1.0;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int64_t k = at_phi(i, c, ps);
+        pn[k] = fma(bt, __ldcg(po + k), zval<MIXED>(P, k, sz));
+      }
+    }
+    if (!grid_sync(P)) return false;
     for (int64_t base = wbase; base < n; base += nthr) {
       const int64_t i = base + (threadIdx.x & 31);
       double acc = 0.0;
       int pp = -1;
       if (i < n) {
         pp = __ldg(P.pid + i);
-        const double bt = __ldcg(P.beta + pp), sz = MIXED ? __ldcg(P.s_acc + pp) : 1.0;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           const int64_t k = at_phi(i, c, ps);
-          const double pv = fma(bt, __ldcg(po + k), zval<MIXED>(P, k, sz));
+          const double pv = __ldcg(pn + k);
           double sum = 0.0;
 #pragma unroll
           for (int d = 0; d < 6; ++d) {
             const int a = d >> 1, side = d & 1, c2 = c ^ (1 << a);
             const int64_t o = (((c >> a) & 1) != side) ? i : (int64_t)__ldg(T.nbr + d * n + i);
-            const int64_t k2 = at_phi(o, c2, ps);
-            sum += fma(bt, __ldcg(po + k2), zval<MIXED>(P, k2, sz));
+            sum += __ldcg(pn + at_phi(o, c2, ps));
           }
           const double qv = pv - sum * (1.0 / 6.0);
-          pn[k] = pv;
           P.cq[k] = qv;
           acc += pv * qv;
         }
