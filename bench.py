@@ -355,18 +355,20 @@ def bench_fft(cmg, ctx, dev, B, rho_b, args, peaks):
 def bench_pcg(cmg, ctx, dev, levels, args):
     """Time to rel. residual tol of the two-level workload's levels from
     phi = 0: the stationary V-cycle iteration against V-cycle-preconditioned
-    CG, each one CUDA graph with the stop test on the device."""
+    CG, in FP64 and in mixed precision (FP32 V-cycles), each one CUDA graph
+    with the stop test on the device."""
     import torch
     out = {}
     for name, L, rho in levels:
         z = torch.zeros_like(rho)
         cmg.cmg_level_set_density(L, rho, 1.0)
         r = {}
-        for kind, kr in (("vcycle", 0), ("pcg", 1)):
+        for kind, kr, prec in (("vcycle", 0, cmg.CMG_PREC_FP64), ("pcg", 1, cmg.CMG_PREC_FP64),
+                               ("mixed", 0, cmg.CMG_PREC_MIXED), ("pcg_mixed", 1, cmg.CMG_PREC_MIXED)):
             ms = []
             for _ in range(6):
                 cmg.cmg_level_set_phi(L, z)
-                rc, st = cmg.cmg_level_solve(L, tol=args.tol, krylov=kr)
+                rc, st = cmg.cmg_level_solve(L, tol=args.tol, krylov=kr, precision=prec)
                 ms.append(st["ms"])
             r[kind] = {"ms_to_tol": statistics.median(ms[1:]), "iterations": st["cycles"],
                        "rel_final": st["rel_final"]}
@@ -374,7 +376,7 @@ def bench_pcg(cmg, ctx, dev, levels, args):
             cmg.cmg_level_set_phi(L, z)
             cmg.cmg_ctx_reset_profile(ctx)
             cmg.cmg_ctx_set_profiling(ctx, True)
-            cmg.cmg_level_solve(L, tol=args.tol, krylov=kr)
+            cmg.cmg_level_solve(L, tol=args.tol, krylov=kr, precision=prec)
             cmg.cmg_ctx_set_profiling(ctx, False)
             r[kind]["kernel_ms"] = {k: round(v["ms"], 4) for k, v in cmg.cmg_ctx_get_profile(ctx).items()
                                     if v["launches"]}

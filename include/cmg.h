@@ -71,9 +71,10 @@ typedef struct {
   int krylov;        /* 0: stationary V-cycle iteration; 1: conjugate gradients
                         preconditioned by one V-cycle per iteration (App. D.2
                         names multigrid as the CG preconditioner); cycles then
-                        counts CG iterations.  Level solves: FP64 only.
-                        Batches: per-patch CG, preconditioned by an FP64 V-cycle
-                        or (MIXED) by FP32 V-cycles on r / ||r||. */
+                        counts CG iterations.  The preconditioner is an FP64
+                        V-cycle (FP64) or inner_cycles FP32 V-cycles on
+                        r / ||r|| (MIXED); FFT is rejected.  Batches: per-patch
+                        CG with the same preconditioners. */
 } cmg_solve_params;
 
 typedef struct {

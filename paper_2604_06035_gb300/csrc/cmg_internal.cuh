@@ -381,6 +381,7 @@ void get_ghosts(cmg_level *L, double *out);
 void ensure_fp32(cmg_level *L);
 // pcg.cu (and the V-cycle it preconditions with, solve.cu)
 void vcycle64_from_zero(cmg_level *L, const cmg_solve_params *p, int64_t *updates);
+void vcycle32_from_zero(cmg_level *L, const cmg_solve_params *p, int64_t *updates);
 void pcg_prepare(cmg_level *L);
 void pcg_pre(cmg_level *L);
 void pcg_body(cmg_level *L, const cmg_solve_params *p, int64_t *updates);

@@ -10,7 +10,9 @@
 // residual is never stored)
 // M = one V-cycle from zero with homogeneous coarse-fine values (the level's
 // own V-cycle, reading its right-hand side array, which holds r during the
-// iteration); L0 = the operator with homogeneous coarse-fine values.  On a
+// iteration), or in mixed precision inner_cycles FP32 V-cycles on r / ||r||
+// scaled back by ||r|| (flexible CG tolerates the inexact FP32 solve);
+// L0 = the operator with homogeneous coarse-fine values.  On a
 // periodic level z is projected to zero mean (the operator's null space).
 // Everything is FP64 and in the solver's pre-scaled units (d = -h^2 r / 6;
 // the iteration is invariant to that scale); r lives in the level's
@@ -215,6 +217,27 @@ __global__ void k_pcg_fin(const double *__restrict__ part, int np, double *sc, d
   }
 }
 
+// FP32 right-hand side of the mixed-precision preconditioner: r / ||r||
+// (||r||^2 in sc[6]), g layout [2][n][4]
+__global__ void k_pcg_emit32(const double *__restrict__ r, int64_t n, const double *__restrict__ sc,
+                             float *__restrict__ g32) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= 8 * n) return;
+  const double s = sqrt(sc[6]);
+  g32[t] = (float)(r[t] * (s > 0.0 ? 1.0 / s : 1.0));
+}
+
+// z = ||r|| e in phi (real octs; FP64) from the FP32 correction e
+__global__ void k_pcg_z64(const float *__restrict__ e, int64_t n, int64_t ps, const double *__restrict__ sc,
+                          double *__restrict__ z) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= 8 * n) return;
+  const int pl = (int)(t / (4 * n));
+  const int64_t k = pl * ps + (t - pl * 4 * n);
+  const double s = sqrt(sc[6]);
+  z[k] = (s > 0.0 ? s : 1.0) * (double)e[k];
+}
+
 struct PcgView {
   double *x, *p0, *p1, *q, *gsave, *part, *sc;
   int64_t n, ps, nv;
@@ -294,7 +317,20 @@ void pcg_body(cmg_level *L, const cmg_solve_params *p, int64_t *updates) {
   cudaStream_t s = L->ctx->stream;
   const PcgView v = view(L);
   int64_t upc = 0;
-  vcycle64_from_zero(L, p, &upc);  // z = M r in phi
+  if (p->precision == CMG_PREC_MIXED) {
+    // z = ||r|| e, e = FP32 V-cycles on r / ||r|| (FP32 right-hand side)
+    {
+      LaunchScope ls(L->ctx, K_CONVERT, 8.0 * v.n * 12.0, 8.0 * v.n);
+      k_pcg_emit32<<<blocks_for(8 * v.n), kThreads, 0, s>>>(g.g, v.n, v.sc, g.g32);
+    }
+    vcycle32_from_zero(L, p, &upc);
+    {
+      LaunchScope ls(L->ctx, K_CONVERT, 8.0 * v.n * 12.0, 8.0 * v.n);
+      k_pcg_z64<<<blocks_for(8 * v.n), kThreads, 0, s>>>(g.phi32, v.n, v.ps, v.sc, g.phi);
+    }
+  } else {
+    vcycle64_from_zero(L, p, &upc);  // z = M r in phi
+  }
   *updates += upc;
   if (L->periodic_full) subtract_mean(L);
   {

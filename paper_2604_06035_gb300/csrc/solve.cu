@@ -339,6 +339,16 @@ void vcycle64_from_zero(cmg_level *L, const cmg_solve_params *p, int64_t *update
   vcycle<double>(L, 0, p, true, updates);
 }
 
+// inner_cycles FP32 V-cycles on MG level 0's FP32 right-hand side, from zero
+void vcycle32_from_zero(cmg_level *L, const cmg_solve_params *p, int64_t *updates) {
+  MgLev &g = L->mg[0];
+  if (p->n_pre == 0) {
+    CMG_CUDA(cudaMemsetAsync(g.phi32, 0, sizeof(float) * 4 * g.n, L->ctx->stream));
+    CMG_CUDA(cudaMemsetAsync(g.phi32 + 4 * g.n_alloc, 0, sizeof(float) * 4 * g.n, L->ctx->stream));
+  }
+  for (int k = 0; k < p->inner_cycles; ++k) vcycle<float>(L, 0, p, k == 0, updates);
+}
+
 void destroy_graphs(cmg_level *L) {
   for (void *v : L->graphs) {
     auto *cg = static_cast<CachedGraph *>(v);
@@ -359,8 +369,8 @@ void solve_launch(cmg_level *L, const cmg_solve_params *p) {
       (p->precision != CMG_PREC_FP64 && p->precision != CMG_PREC_MIXED && p->precision != CMG_PREC_FFT) ||
       (p->precision == CMG_PREC_MIXED && p->inner_cycles < 1) || (p->krylov != 0 && p->krylov != 1))
     throw Error(CMG_ERR_INVALID_ARG, "invalid solve parameters");
-  if (p->krylov == 1 && p->precision != CMG_PREC_FP64)
-    throw Error(CMG_ERR_INVALID_ARG, "the CG outer iteration runs in FP64 only");
+  if (p->krylov == 1 && p->precision == CMG_PREC_FFT)
+    throw Error(CMG_ERR_INVALID_ARG, "the CG outer iteration takes a V-cycle preconditioner (FP64 or MIXED)");
   if (L->periodic_full && L->nx != 1)
     throw Error(CMG_ERR_INVALID_ARG, "periodic base levels need n_x = 1 (exact 2^3 coarsest solve)");
   if (p->precision == CMG_PREC_MIXED && L->mg.size() < 2)
