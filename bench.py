@@ -127,6 +127,21 @@ def traffic_for(kernel):
     return e.get("dram_bytes_per_launch")
 
 
+def aggregate_ranks(dev_ms, updates, world, device=None):
+    """Whole-job figures of N replicas (one per rank, each timing its own
+    steps): the slowest rank's device time and the cell updates of all ranks,
+    by torch.distributed collectives (any backend; one rank: unchanged)."""
+    if world <= 1:
+        return dev_ms, updates
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(dev_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(updates)], dtype=torch.float64, device=device)
+    dist.all_reduce(u)
+    return float(t.item()), float(u.item())
+
+
 def read_peaks():
     """HBM GB/s and dense BF16 TFLOP/s (burst) from MEASURED_PEAKS.json, else
     the profiling recipe's fallback figures."""
@@ -675,15 +690,7 @@ def run_ours(args, rank, local, world):
     _, prof_ms, _ = timed(True)
     prof = cmg.cmg_ctx_get_profile(ctx)
     updates = sum(s["cell_updates"] for st in all_stats for s in st)
-    t_max = dev_ms
-    upd_total = updates
-    if world > 1:
-        t = torch.tensor([dev_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        u = torch.tensor([float(updates)], device=dev)
-        dist.all_reduce(u)
-        upd_total = float(u.item())
+    t_max, upd_total = aggregate_ranks(dev_ms, updates, world, dev)
     value = upd_total / (t_max / 1e3) / 1e6
     st_b, st_f = all_stats[-1]
 
