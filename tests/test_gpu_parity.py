@@ -108,6 +108,64 @@ def test_empty_level(cmg, ctx):
     assert rc == cmg.CMG_OK and st["cycles"] == 0
 
 
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "fft", "pcg"])
+def test_uniform_density_gives_zero_phi(cmg, ctx, mode):
+    """rho = rho_bar everywhere: the source vanishes and every solve returns
+    phi = 0 exactly, with no iteration."""
+    coords = inputs.uniform_oct_coords(4)
+    G = cmg.cmg_level_build(ctx, 4, O.morton_encode(coords))
+    cmg.cmg_level_set_density(G, np.full((len(coords), 8), 2.5), 2.5)
+    cmg.cmg_level_set_phi(G, np.random.default_rng(3).standard_normal((len(coords), 8)))
+    kw = {"fp64": {}, "mixed": {"precision": cmg.CMG_PREC_MIXED}, "fft": {"precision": cmg.CMG_PREC_FFT},
+          "pcg": {"krylov": 1}}[mode]
+    rc, st = cmg.cmg_level_solve(G, tol=1e-10, **kw)
+    assert rc == cmg.CMG_OK and st["cycles"] == 0
+    assert not cmg.cmg_level_get_phi(G).any()
+
+
+@pytest.mark.parametrize("level", [1, 2])
+def test_smallest_periodic_levels(cmg, ctx, level):
+    """One oct (the exact 2^3 solve at the top, a one-level hierarchy) and
+    eight octs: the discrete solution, as the oracle gives it."""
+    coords = inputs.uniform_oct_coords(level)
+    rho = 1.0 + np.random.default_rng(level).standard_normal((len(coords), 8))
+    G = cmg.cmg_level_build(ctx, level, O.morton_encode(coords))
+    R = O.Level(level, O.morton_encode(coords))
+    cmg.cmg_level_set_density(G, rho, float(rho.mean()))
+    R.set_density(rho, float(rho.mean()))
+    rc, st = cmg.cmg_level_solve(G, tol=1e-13)
+    R.solve(tol=1e-13)
+    assert rc == cmg.CMG_OK
+    assert relerr(cmg.cmg_level_get_phi(G), R.get_phi()) <= 1e-12
+    if level == 1:
+        assert st["cycles"] == 1  # exact in one cycle
+
+
+def test_single_oct_refined_level(cmg, ctx):
+    """A refined level of one oct: all six faces are coarse-fine ghosts."""
+    pc = inputs.uniform_oct_coords(4)
+    rng = np.random.default_rng(9)
+    rho_p = 1.0 + 0.3 * rng.standard_normal((len(pc), 8))
+    GP = cmg.cmg_level_build(ctx, 4, O.morton_encode(pc))
+    RP = O.Level(4, O.morton_encode(pc))
+    for L in (GP, RP):
+        (cmg.cmg_level_set_density(L, rho_p, float(rho_p.mean())) if L is GP
+         else L.set_density(rho_p, float(rho_p.mean())))
+    RP.solve(tol=1e-13)
+    cmg.cmg_level_set_phi(GP, RP.get_phi())
+    c = np.array([[5, 9, 2]], dtype=np.uint32)
+    G = cmg.cmg_level_build(ctx, 5, O.morton_encode(c), parent=GP)
+    R = O.Level(5, O.morton_encode(c), parent=RP)
+    rho = 1.0 + 0.3 * rng.standard_normal((1, 8))
+    cmg.cmg_level_set_density(G, rho, float(rho_p.mean()))
+    R.set_density(rho, float(rho_p.mean()))
+    assert cmg.cmg_level_get_neighbors(G).tolist() == [[0, -1, -1, -1, -1, -1, -1]]
+    rc, st = cmg.cmg_level_solve(G, tol=1e-12)
+    R.solve(tol=1e-13)
+    assert rc == cmg.CMG_OK
+    assert relerr(cmg.cmg_level_get_phi(G), R.get_phi()) <= 1e-11
+
+
 @pytest.mark.parametrize("pmask", [7, 0, 3])
 def test_neighbors_bitexact(cmg, ctx, pmask):
     rng = np.random.default_rng(20 + pmask)
