@@ -118,6 +118,13 @@ int cmg_ctx_reset_profile(cmg_ctx *ctx);
 /* Kernels this context has launched since creation or the last reset. */
 int cmg_ctx_launch_count(cmg_ctx *ctx, int64_t *launches);
 
+/* Host-side fault injection for tests (no GPU involvement): the after'th next
+ * device allocation made by the library, on any context, fails as if the
+ * device were out of memory, so the call in progress returns CMG_ERR_OOM and
+ * releases what it allocated; 0 switches it off (the default).
+ * INVALID_ARG if negative. */
+int cmg_debug_inject_alloc_failure(int64_t after);
+
 /* Morton keys (Sec. 4.2 Eq. (morton_encode), App. A Alg. 1; B = 21 bits per
  * coordinate): ijk is [n][3] uint32 (i, j, k), keys is [n] uint64.  Both in
  * the same memory space.  Coordinates >= 2^21 give CMG_ERR_KEY_OUT_OF_RANGE. */

@@ -85,6 +85,7 @@ _SIGS = {
     "cmg_ctx_reset_profile": (_I, [_P]),
     "cmg_ctx_launch_count": (_I, [_P, C.POINTER(_I64)]),
     "cmg_morton_encode": (_I, [_P, _P, _I64, _P, _I]),
+    "cmg_debug_inject_alloc_failure": (_I, [_I64]),
     "cmg_morton_encode128": (_I, [_P, _P, _I64, _P, _I]),
     "cmg_morton_decode128": (_I, [_P, _P, _I64, _P, _I]),
     "cmg_level_build128": (_I, [_P, _I, _I, _I, _P, _I64, _I, _P, C.POINTER(_P)]),
@@ -295,6 +296,11 @@ def cmg_ctx_launch_count(ctx):
     v = C.c_int64()
     _check(lib().cmg_ctx_launch_count(ctx, C.byref(v)), "cmg_ctx_launch_count")
     return v.value
+
+
+def cmg_debug_inject_alloc_failure(after):
+    """Tests: the after'th next library allocation fails with CMG_ERR_OOM."""
+    _check(lib().cmg_debug_inject_alloc_failure(int(after)), "cmg_debug_inject_alloc_failure")
 
 
 def cmg_morton_encode(ctx, ijk, out=None):

@@ -678,9 +678,11 @@ void ensure_cg(cmg_batch *b) {
   if (b->cg) return;
   cmg_level *L = b->lvl;
   const int64_t nv = 8 * L->mg[0].n_alloc;
-  b->cg = b->mem.alloc<double>(4 * nv + 8 * L->mg[0].n + 6 * (int64_t)b->n_patches, true, L->ctx->stream);
+  // b->cg (the "allocated" mark) is set last
+  double *cg = b->mem.alloc<double>(4 * nv + 8 * L->mg[0].n + 6 * (int64_t)b->n_patches, true, L->ctx->stream);
   b->cg_done = b->mem.alloc<int32_t>(b->n_patches, true, L->ctx->stream);
   CMG_CUDA(cudaStreamSynchronize(L->ctx->stream));
+  b->cg = cg;
 }
 
 // Records: clear control words (and the CG direction buffers), the

@@ -2,6 +2,7 @@
 // the per-level hash table (App. B), the neighbour cache (App. D.1), the
 // coarse-fine ghost octs and their parent stencils (morton_nbor_cell, App. B),
 // and the multigrid hierarchy of a level.
+#include <atomic>
 #include <climits>
 #include <cmath>
 
@@ -16,10 +17,18 @@ void cuda_check(cudaError_t e, const char *what) {
   throw Error(CMG_ERR_CUDA, std::string(cudaGetErrorString(e)) + " in " + what);
 }
 
+// Host-side fault injection for tests: when positive, the countdown'th
+// next library allocation fails as if the device were out of memory.
+static std::atomic<int64_t> g_alloc_countdown{0};
+
+void inject_alloc_failure(int64_t after) { g_alloc_countdown.store(after > 0 ? after : 0); }
+
 template <class T>
 T *DeviceBuffers::alloc(int64_t count, bool zero, cudaStream_t s) {
   void *p = nullptr;
   const size_t bytes = sizeof(T) * (size_t)(count > 0 ? count : 1);
+  if (g_alloc_countdown.load() > 0 && g_alloc_countdown.fetch_sub(1) == 1)
+    throw Error(CMG_ERR_OOM, "injected allocation failure (" + std::to_string(bytes) + " bytes)");
   cudaError_t e = cudaMalloc(&p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -115,6 +115,14 @@ extern "C" {
 
 const char *cmg_version(void) { return "cmg 0.1.0 sm_103a"; }
 
+int cmg_debug_inject_alloc_failure(int64_t after) {
+  return guard([&] {
+    need(after >= 0, "negative count");
+    cmg::inject_alloc_failure(after);
+    return CMG_OK;
+  });
+}
+
 const char *cmg_last_error(void) { return g_last_error.c_str(); }
 
 int cmg_ctx_create(int device, void *stream, cmg_ctx **out) {

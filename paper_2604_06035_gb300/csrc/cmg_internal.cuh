@@ -45,6 +45,8 @@ struct Error : std::runtime_error {
 };
 
 void cuda_check(cudaError_t e, const char *what);
+// tests: the after'th next library allocation fails with CMG_ERR_OOM (0: off)
+void inject_alloc_failure(int64_t after);
 #define CMG_CUDA(x) ::cmg::cuda_check((x), #x)
 
 // ------------------------------------------------------- Morton keys (A1)

@@ -363,7 +363,8 @@ void fft_prepare(cmg_level *L) {
   if (!fft_supported(L)) throw Error(CMG_ERR_INVALID_ARG, "the FFT solve needs a full periodic level of at most 512^3 cells");
   const int n = 1 << L->lev, no = n >> 1;
   cudaStream_t s = L->ctx->stream;
-  L->fft_buf = reinterpret_cast<float2 *>(L->mem.alloc<float>((int64_t)2 * n * n * n));
+  // L->fft_buf (the "prepared" mark) is set last, after every allocation
+  float2 *buf = reinterpret_cast<float2 *>(L->mem.alloc<float>((int64_t)2 * n * n * n));
   L->fft_map = L->mem.alloc<int32_t>((int64_t)no * no * no, true, s);  // zeroed: every entry a valid oct
   // per-stage twiddles: stage st (span 2^st) at (2^(st-1) - 1) + p, p < 2^(st-1),
   // the value of exp(-2 pi i k / n) at k = p n / 2^st
@@ -382,6 +383,7 @@ void fft_prepare(cmg_level *L) {
   k_fft_map<<<blocks_for(g.n), kThreads, 0, s>>>(g.keys, g.n, no, L->fft_map);
   CMG_CUDA(cudaGetLastError());
   CMG_CUDA(cudaStreamSynchronize(s));
+  L->fft_buf = buf;
 }
 
 // e (phi32 of MG level 0) = the FFT solution of the FP32 correction equation

@@ -382,14 +382,10 @@ void solve_launch(cmg_level *L, const cmg_solve_params *p) {
   if (p->precision != CMG_PREC_FP64) ensure_fp32(L);
   if (p->precision == CMG_PREC_FFT) fft_prepare(L);
   if (p->krylov == 1) pcg_prepare(L);
-  if (!L->ctrl) {
-    L->ctrl = L->mem.alloc<uint8_t>(sizeof(SolveCtrl), true, ctx->stream);
-    CMG_CUDA(cudaMallocHost(&L->h_ctrl, sizeof(SolveCtrl)));
-  }
-  if (!L->ev_start) {
-    CMG_CUDA(cudaEventCreate(&L->ev_start));
-    CMG_CUDA(cudaEventCreate(&L->ev_end));
-  }
+  if (!L->h_ctrl) CMG_CUDA(cudaMallocHost(&L->h_ctrl, sizeof(SolveCtrl)));
+  if (!L->ctrl) L->ctrl = L->mem.alloc<uint8_t>(sizeof(SolveCtrl), true, ctx->stream);
+  if (!L->ev_start) CMG_CUDA(cudaEventCreate(&L->ev_start));
+  if (!L->ev_end) CMG_CUDA(cudaEventCreate(&L->ev_end));
   L->pend = cmg_level::Pending{};
   if (L->n == 0) {
     L->pend.empty = true;

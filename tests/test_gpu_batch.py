@@ -155,6 +155,28 @@ def test_batch_pcg_mixed_matches_fp64(cmg, setup):
         assert _relerr(phi[sl], R.get_phi()) <= 1e-10, k
 
 
+def test_batch_cg_allocation_failure_then_success(cmg, setup):
+    """The CG buffers of a batch are allocated on first use: an injected
+    allocation failure there returns CMG_ERR_OOM, and the next solve
+    allocates them and converges."""
+    b, P, F, B, RP = setup
+    z = np.zeros((len(b["coords"]), 8))
+    B2 = cmg.cmg_batch_create(F, b["offsets"])
+    try:
+        for after in (1, 2):
+            cmg.cmg_level_set_phi(F, z)
+            cmg.cmg_debug_inject_alloc_failure(after)
+            rc, st = cmg.cmg_batch_solve(B2, tol=1e-10, krylov=1, raise_on_error=False)
+            cmg.cmg_debug_inject_alloc_failure(0)
+            assert rc == cmg.CMG_ERR_OOM, after
+        cmg.cmg_level_set_phi(F, z)
+        rc, st = cmg.cmg_batch_solve(B2, tol=1e-10, krylov=1)
+        assert rc == cmg.CMG_OK and st["n_converged"] == 12
+    finally:
+        cmg.cmg_debug_inject_alloc_failure(0)
+        cmg.cmg_batch_destroy(B2)
+
+
 def test_batch_rejects_patches_that_touch(cmg, setup):
     b, P, F, B, RP = setup
     off = b["offsets"]

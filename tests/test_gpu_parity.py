@@ -166,6 +166,46 @@ def test_single_oct_refined_level(cmg, ctx):
     assert relerr(cmg.cmg_level_get_phi(G), R.get_phi()) <= 1e-11
 
 
+def test_allocation_failure_injected_on_the_host(cmg, ctx):
+    """An allocation that fails (injected on the host, no GPU involved) makes
+    the call in progress return CMG_ERR_OOM; the context stays usable and the
+    same call afterwards succeeds with correct results -- for a level build
+    and for the lazy allocations of FFT, mixed-precision and CG solves."""
+    cfg = inputs.two_level_amr(base_level=5, seed=2)
+    GB = cmg.cmg_level_build(ctx, 5, O.morton_encode(cfg["coords"][0]))
+    cmg.cmg_level_set_density(GB, cfg["rho"][0], 1.0)
+    kf = O.morton_encode(cfg["coords"][1])
+    try:
+        for after in (1, 4, 12):
+            cmg.cmg_debug_inject_alloc_failure(after)
+            with pytest.raises(cmg.CmgError) as e:
+                cmg.cmg_level_build(ctx, 6, kf, parent=GB)
+            assert e.value.code == cmg.CMG_ERR_OOM
+        cmg.cmg_debug_inject_alloc_failure(0)
+        z = np.zeros((cmg.cmg_level_n_octs(GB), 8))
+        rc, ref = cmg.cmg_level_solve(GB, tol=1e-12)
+        phi_ref = cmg.cmg_level_get_phi(GB)
+        for kw in ({"precision": cmg.CMG_PREC_FFT}, {"precision": cmg.CMG_PREC_MIXED}, {"krylov": 1}):
+            for after in (1, 2):
+                cmg.cmg_level_set_phi(GB, z)
+                cmg.cmg_debug_inject_alloc_failure(after)
+                rc, st = cmg.cmg_level_solve(GB, tol=1e-12, raise_on_error=False, **kw)
+                cmg.cmg_debug_inject_alloc_failure(0)
+                assert rc in (cmg.CMG_ERR_OOM, cmg.CMG_OK), (kw, after, rc)
+            cmg.cmg_level_set_phi(GB, z)
+            rc, st = cmg.cmg_level_solve(GB, tol=1e-12, **kw)
+            assert rc == cmg.CMG_OK and relerr(cmg.cmg_level_get_phi(GB), phi_ref) <= 1e-10, kw
+        GF = cmg.cmg_level_build(ctx, 6, kf, parent=GB)
+        cmg.cmg_level_set_density(GF, cfg["rho"][1], 1.0)
+        rc, st = cmg.cmg_level_solve(GF, tol=1e-10)
+        assert rc == cmg.CMG_OK
+    finally:
+        cmg.cmg_debug_inject_alloc_failure(0)
+    with pytest.raises(cmg.CmgError) as e:
+        cmg.cmg_debug_inject_alloc_failure(-1)
+    assert e.value.code == cmg.CMG_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("pmask", [7, 0, 3])
 def test_neighbors_bitexact(cmg, ctx, pmask):
     rng = np.random.default_rng(20 + pmask)
