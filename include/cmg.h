@@ -213,9 +213,11 @@ int cmg_level_solve_wait(cmg_level *lvl, cmg_solve_stats *stats);
  * most 64 octs in FP64, 512 in FP32, and a coarsest level swept in FP64 of at
  * most 64), else in one cooperative launch of one CTA per SM with grid
  * barriers, whose first CTA alone takes the levels that fit one SM.  Defaults
- * 32768 / 512 (measured on GB300, two-level 128^3 workload: FP64 levels from
- * 64^3 down are cheaper under grid barriers than as separate launches, FP32
- * ones are not); 0 disables.  Negative values leave the current setting. */
+ * 32768 / 2048 (measured on GB300, two-level 128^3 workload: FP64 levels from
+ * 32^3 octs down are cheaper under grid barriers than as separate launches;
+ * FP32 levels above 512 octs are not, but a refined level's coarsest MG level
+ * of a few thousand octs, swept in FP64, is); 0 disables.  Negative values
+ * leave the current setting. */
 int cmg_level_set_schedule(cmg_level *lvl, int64_t tail_octs_fp64, int64_t tail_octs_fp32);
 
 /* SM clock cycles one wait at a grid barrier of the tail kernel may last

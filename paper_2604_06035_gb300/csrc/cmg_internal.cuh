@@ -290,7 +290,7 @@ struct cmg_level {
   // schedule: MG levels with at most this many octs (and all coarser ones) run
   // in one "tail" launch (tail.cu); 0 = one launch per operation everywhere
   int64_t tail_octs_fp64 = 32768;
-  int64_t tail_octs_fp32 = 512;
+  int64_t tail_octs_fp32 = 2048;
   int64_t tail_spin_budget = 1ll << 30;  // SM clock cycles a grid-tail barrier wait may last
   // FFT solve of a full periodic level (fft.cu): dense complex work array,
   // oct-coordinate -> oct-index map, twiddles (lazy)

@@ -121,8 +121,8 @@ __global__ void k_get_ghosts(const int32_t *__restrict__ nbr, int64_t n, int64_t
 template <typename T>
 __global__ void k_wht(const T *__restrict__ g, T *__restrict__ phi, int64_t n_alloc, double h) {
   pdl_enter();
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  dev::wht_solve<T, T, false>(g, phi, n_alloc, h);
+  if (threadIdx.x >= 32 || blockIdx.x != 0) return;
+  dev::wht_solve_warp<T, T, false>(g, phi, n_alloc, h);
 }
 
 __global__ void k_set_density(const double *__restrict__ rho, int64_t n, double rho_bar, double scale,

@@ -1,9 +1,9 @@
 // oct_ops.cuh -- per-oct bodies of the multigrid operators, shared by the
-// one-kernel-per-operation path (ops.cu) and the cluster tail kernel
+// one-kernel-per-operation path (launch.cu, kernels.cuh) and the tail kernels
 // (tail.cu).  Layout: see cmg_internal.cuh.  CG = true routes every load of
 // data that another thread block of the same launch may have written through
-// L2 (ld.global.cg), as the tail kernel's blocks exchange data via global
-// memory between cluster barriers.
+// L2 (ld.global.cg), as the grid tail's blocks exchange data via global
+// memory between grid barriers.
 #pragma once
 
 #include "cmg_internal.cuh"
@@ -96,6 +96,30 @@ __device__ __forceinline__ void sweep_oct(int64_t i, const int32_t *__restrict__
   store4(dst + i * 4, out);
 }
 
+// sweep_oct for one cell (cell plane_cell(P, q) of oct i), one thread per
+// cell: the same loads, sums in the same order and the same FMA, so the
+// result is bit-identical to sweep_oct's.
+template <typename T, int P, bool ZERO, bool MASK, bool CG>
+__device__ __forceinline__ void sweep_cell(int64_t i, int q, const int32_t *__restrict__ nbr, const T *src, T *dst,
+                                           const T *g, const uint8_t *__restrict__ active, int64_t n) {
+  T out = ld1<CG>(g + i * 4 + q);
+  if (!ZERO) {
+    const int c = plane_cell(P, q);
+    const T inv6 = T(1) / T(6);
+    T s = T(0);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      const int a = d >> 1, side = d & 1, c2 = c ^ (1 << a);
+      const int64_t o = (((c >> a) & 1) != side) ? i : (int64_t)__ldg(nbr + d * n + i);
+      const T v = ld1<CG>(src + o * 4 + (c2 >> 1));
+      s = d == 0 ? v : s + v;
+    }
+    out = fma_t(s, inv6, out);
+  }
+  if (MASK && !((__ldg(active + i) >> plane_cell(P, q)) & 1)) out = T(0);
+  dst[i * 4 + q] = out;
+}
+
 // Residual of oct i: d = fma(s, 1/6, g) - phi per cell, r = (-6 / h^2) d.
 // Returns the sum of d^2 over the oct (NORM; accumulated in FP64 for FP64
 // data, in FP32 within the oct for FP32 data, whose FP64 conversions would
@@ -169,6 +193,49 @@ __device__ __forceinline__ double resid_oct(int64_t i, const int32_t *__restrict
     }
   }
   return acc;
+}
+
+// resid_oct<NORM = false, RESTRICT = true> with one thread per cell: lane k
+// of an aligned group of 8 lanes takes cell plane_cell(k >> 2, k & 3) of oct
+// i (plane k >> 2, slot k & 3).  Every lane of the warp calls it (the father
+// value is summed across the group by shuffles, in resid_oct's order);
+// `valid` is false for a group past the end of the range.
+template <typename T, bool CG>
+__device__ __forceinline__ void resid_restrict_cell(bool valid, int64_t i, const int32_t *__restrict__ nbr, const T *phi,
+                                                    const T *g, const uint8_t *__restrict__ active, int64_t n,
+                                                    int64_t n_alloc, const int32_t *__restrict__ father, T *cg, T *cphi,
+                                                    int64_t cn, int64_t cn_alloc, int zero_cphi) {
+  const int k = (int)(threadIdx.x & 7), p = k >> 2, q = k & 3, c = plane_cell(p, q);
+  T dv = T(0);
+  if (valid) {
+    const T pv = ld1<CG>(phi + (p * n_alloc + i) * 4 + q);
+    const T gv = ld1<CG>(g + (p * n + i) * 4 + q);
+    const T inv6 = T(1) / T(6);
+    T s = T(0);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      const int a = d >> 1, side = d & 1, c2 = c ^ (1 << a);
+      const int64_t o = (((c >> a) & 1) != side) ? i : (int64_t)__ldg(nbr + d * n + i);
+      const T v = ld1<CG>(phi + ((1 - p) * n_alloc + o) * 4 + (c2 >> 1));
+      s = d == 0 ? v : s + v;
+    }
+    dv = fma_t(s, inv6, gv) - pv;
+    const unsigned m = active ? __ldg(active + i) : 0xFFu;
+    if (!((m >> c) & 1)) dv = T(0);
+  }
+  const int base = (int)(threadIdx.x & 31) & ~7;
+  T rsum = T(0);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) rsum += __shfl_sync(0xFFFFFFFFu, dv, base + j);
+  if (valid && k == 0) {
+    const int32_t fa = __ldg(father + i);
+    if (fa >= 0) {
+      const int64_t pc = fa >> 3;
+      const int cc = fa & 7;
+      cg[((int64_t)cell_parity(cc) * cn + pc) * 4 + (cc >> 1)] = T(0.5) * rsum;
+      if (zero_cphi) cphi[((int64_t)cell_parity(cc) * cn_alloc + pc) * 4 + (cc >> 1)] = T(0);
+    }
+  }
 }
 
 // Block index and child bit of the coarse cell at offset e - 1 (e = 0, 1, 2)
@@ -246,26 +313,64 @@ __device__ __forceinline__ void prolong_oct(int64_t i, const uint64_t *__restric
   }
 }
 
-// Exact solve of the periodic 2^3 oct (one thread): eigenvectors
-// (-1)^{k.b}, eigenvalues -4 |k|_1 / h^2, mean mode dropped; FP64 inside.
+// prolong_oct for one cell c of oct i, one thread per cell: the 8 coarse
+// values interp8 combines for this cell, in its order and with its weights
+// (bit-identical); inactive cells are left untouched.
+template <typename T, bool MASK, bool CG>
+__device__ __forceinline__ void prolong_cell(int64_t i, int c, const uint64_t *__restrict__ keys,
+                                             const int32_t *__restrict__ blk, int64_t n, int64_t n_alloc, T *phi,
+                                             const uint8_t *__restrict__ active, const T *cphi, int64_t cn_alloc) {
+  if (MASK && !((__ldg(active + i) >> c) & 1)) return;
+  const int cc = (int)(__ldg(keys + i) & 7);
+  auto val = [&](int ex, int ey, int ez) -> T {
+    int ax, bx, ay, by, az, bz;
+    axis_cell(cc & 1, ex, ax, bx);
+    axis_cell((cc >> 1) & 1, ey, ay, by);
+    axis_cell((cc >> 2) & 1, ez, az, bz);
+    const int ch = bx | (by << 1) | (bz << 2);
+    const int64_t oct = __ldg(blk + (int64_t)(ax | (ay << 1) | (az << 2)) * n + i);
+    return ld1<CG>(cphi + ((int64_t)cell_parity(ch) * cn_alloc + oct) * 4 + (ch >> 1));
+  };
+  const int ex1 = (c & 1) ? 2 : 0, ey1 = ((c >> 1) & 1) ? 2 : 0, ez1 = ((c >> 2) & 1) ? 2 : 0;
+  const T w0 = T(0.75), w1 = T(0.25);
+  T acc = w0 * w0 * w0 * val(1, 1, 1);
+  acc = fma_t(w1 * w0 * w0, val(ex1, 1, 1), acc);
+  acc = fma_t(w0 * w1 * w0, val(1, ey1, 1), acc);
+  acc = fma_t(w1 * w1 * w0, val(ex1, ey1, 1), acc);
+  acc = fma_t(w0 * w0 * w1, val(1, 1, ez1), acc);
+  acc = fma_t(w1 * w0 * w1, val(ex1, 1, ez1), acc);
+  acc = fma_t(w0 * w1 * w1, val(1, ey1, ez1), acc);
+  acc = fma_t(w1 * w1 * w1, val(ex1, ey1, ez1), acc);
+  T *dst = phi + ((int64_t)cell_parity(c) * n_alloc + i) * 4 + (c >> 1);
+  *dst = ld1<CG>(dst) + acc;
+}
+
+// Exact solve of the periodic 2^3 oct by one warp (all 32 lanes call it;
+// lanes 0..7 own cell c = lane): eigenvectors (-1)^{k.b}, eigenvalues
+// -4 |k|_1 / h^2, mean mode dropped; FP64 inside.  Each lane forms one
+// transform coefficient and one output from the others' values (shuffles),
+// in the same order of operations as a serial evaluation.
 template <typename S, typename T, bool CG>
-__device__ void wht_solve(const S *g, T *phi, int64_t n_alloc, double h) {
-  double f[8], fh[8];
-  for (int c = 0; c < 8; ++c) f[c] = (double)ld1<CG>(g + cell_parity(c) * 4 + (c >> 1)) * (-6.0 / (h * h));
-  for (int k = 0; k < 8; ++k) {
-    double s = 0.0;
-    for (int b = 0; b < 8; ++b) s += cell_parity(k & b) ? -f[b] : f[b];
-    fh[k] = s * 0.125;
-  }
+__device__ void wht_solve_warp(const S *g, T *phi, int64_t n_alloc, double h) {
+  const unsigned all = 0xFFFFFFFFu;
+  const int c = (int)(threadIdx.x & 7);
+  const double f = (double)ld1<CG>(g + cell_parity(c) * 4 + (c >> 1)) * (-6.0 / (h * h));
+  double s = 0.0;
+#pragma unroll
   for (int b = 0; b < 8; ++b) {
-    double s = 0.0;
-    for (int k = 1; k < 8; ++k) {
-      const int odd = (k & 1) + ((k >> 1) & 1) + ((k >> 2) & 1);
-      const double x = fh[k] / (-4.0 * odd / (h * h));
-      s += cell_parity(k & b) ? -x : x;
-    }
-    phi[(int64_t)cell_parity(b) * n_alloc * 4 + (b >> 1)] = (T)s;
+    const double fb = __shfl_sync(all, f, b);
+    s += cell_parity(c & b) ? -fb : fb;
   }
+  const double fh = s * 0.125;
+  const int odd = (c & 1) + ((c >> 1) & 1) + ((c >> 2) & 1);
+  const double x = c ? fh / (-4.0 * odd / (h * h)) : 0.0;
+  double t = 0.0;
+#pragma unroll
+  for (int k = 1; k < 8; ++k) {
+    const double xk = __shfl_sync(all, x, k);
+    t += cell_parity(k & c) ? -xk : xk;
+  }
+  if ((threadIdx.x & 31) < 8) phi[(int64_t)cell_parity(c) * n_alloc * 4 + (c >> 1)] = (T)t;
 }
 
 }  // namespace dev

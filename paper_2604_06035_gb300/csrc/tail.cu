@@ -50,26 +50,50 @@ struct TailPlan {
   TailLevel lv[kMaxTail];
 };
 
-// The octs (or values) [0, n) a thread handles: a, a + s, ... below e.
+// The items a thread handles: a, a + s, ... below e; a - base is the same
+// offset for every stride (the thread's rank among the s threads).
 struct Span {
-  int64_t a, e, s;
+  int64_t a, e, s, base;
 };
 // every thread of one CTA strides over the whole range
 struct FlatMap {
   int64_t tid, nthr;
-  __device__ Span span(int64_t n) const { return {tid, n, nthr}; }
-  __device__ bool leader() const { return tid == 0; }
+  // octs (or values) [0, n)
+  __device__ Span span(int64_t n) const { return {tid, n, nthr, 0}; }
+  // k work units per oct over octs [0, n): units [0, k n)
+  __device__ Span units(int64_t n, int k) const { return {tid, k * n, nthr, 0}; }
+  // whether a colour pass over n octs takes one round of threads per cell
+  __device__ bool fits_per_cell(int64_t n) const { return 4 * n <= nthr; }
+  __device__ bool first_warp() const { return tid < 32; }
 };
-// one contiguous chunk per CTA, the CTA's threads striding over it
+// one contiguous chunk of octs per CTA, the CTA's threads striding over it
 struct ChunkMap {
   int64_t b, nb, t, nt;
-  __device__ Span span(int64_t n) const {
+  __device__ Span span(int64_t n) const { return units(n, 1); }
+  __device__ Span units(int64_t n, int k) const {
     const int64_t c = (n + nb - 1) / nb;
     const int64_t a = b * c;
-    return {a + t, a + c < n ? a + c : n, nt};
+    return {k * a + t, k * (a + c < n ? a + c : n), nt, k * a};
   }
-  __device__ bool leader() const { return b == 0 && t == 0; }
+  __device__ bool fits_per_cell(int64_t n) const { return 4 * ((n + nb - 1) / nb) <= nt; }
+  __device__ bool first_warp() const { return b == 0 && t < 32; }
 };
+
+// Small FP64 levels run one thread per cell (4 per oct in a colour pass, 8
+// in the residual and the prolongation); FP32 levels and FP64 levels with
+// more than a quarter as many octs per CTA as threads run one thread per
+// oct.  A GB300 SM sub-partition issues one FP64 warp instruction about
+// every 64 clocks however many of its lanes are active, so where a CTA
+// holds a few octs, one thread per oct leaves each FP64 instruction mostly
+// idle and serialises the oct's arithmetic in one lane, while one thread per
+// cell fills the lanes and shortens each thread's FP64 chain 4 to 8 fold.
+// Where the per-oct warps are already full, per-cell threads only add
+// instructions (the residual's restriction sum runs in every lane of the
+// 8-lane group).  The per-cell bodies are bit-identical to the per-oct ones.
+template <typename T, class Map>
+__device__ bool per_cell(const Map &map, int64_t n) {
+  return sizeof(T) == 8 && map.fits_per_cell(n);
+}
 
 // CG: loads through L2 only (another CTA may have written the data); a
 // single-CTA tail reads through L1.
@@ -78,6 +102,22 @@ __device__ void pass(const TailLevel &L, int P, bool zero, const Map &map) {
   T *phi = static_cast<T *>(L.phi);
   const T *g = static_cast<const T *>(L.g);
   const int64_t st = L.n_alloc * 4;
+  if (per_cell<T>(map, L.n)) {
+    const Span su = map.units(L.n, 4);
+    for (int64_t u = su.a; u < su.e; u += su.s) {
+      const int64_t i = u >> 2;
+      const int q = (int)(u & 3);
+      if (P == 0) {
+        if (zero)
+          dev::sweep_cell<T, 0, true, MASK, CG>(i, q, L.nbr, phi + st, phi, g, L.active, L.n);
+        else
+          dev::sweep_cell<T, 0, false, MASK, CG>(i, q, L.nbr, phi + st, phi, g, L.active, L.n);
+      } else {
+        dev::sweep_cell<T, 1, false, MASK, CG>(i, q, L.nbr, phi, phi + st, g + L.n * 4, L.active, L.n);
+      }
+    }
+    return;
+  }
   const Span sp = map.span(L.n);
   for (int64_t i = sp.a; i < sp.e; i += sp.s) {
     if (P == 0) {
@@ -119,11 +159,23 @@ __device__ void descend(const TailPlan &plan, int m_from, int m_to, const Map &m
     sweeps<T, CG>(L, plan.n_pre, true, map, sync);
     const T *phi = static_cast<const T *>(L.phi);
     const T *g = static_cast<const T *>(L.g);
-    const Span sp = map.span(L.n);
-    for (int64_t i = sp.a; i < sp.e; i += sp.s)
-      dev::resid_oct<T, false, true, false, false, false, CG>(
-          i, L.nbr, phi, g, L.all_active ? nullptr : L.active, L.n, L.n_alloc, L.father, static_cast<T *>(C.g),
-          static_cast<T *>(C.phi), C.n, C.n_alloc, L.zero_coarse, nullptr, 0.0, nullptr, 0.0);
+    if (per_cell<T>(map, L.n)) {
+      // every thread of the CTA runs the same number of rounds: the 8 lanes
+      // of an oct exchange values by shuffles
+      const Span su = map.units(L.n, 8);
+      for (int64_t u0 = su.base; u0 < su.e; u0 += su.s) {
+        const int64_t u = u0 + (su.a - su.base);
+        dev::resid_restrict_cell<T, CG>(u < su.e, u >> 3, L.nbr, phi, g, L.all_active ? nullptr : L.active, L.n,
+                                        L.n_alloc, L.father, static_cast<T *>(C.g), static_cast<T *>(C.phi), C.n,
+                                        C.n_alloc, L.zero_coarse);
+      }
+    } else {
+      const Span sp = map.span(L.n);
+      for (int64_t i = sp.a; i < sp.e; i += sp.s)
+        dev::resid_oct<T, false, true, false, false, false, CG>(
+            i, L.nbr, phi, g, L.all_active ? nullptr : L.active, L.n, L.n_alloc, L.father, static_cast<T *>(C.g),
+            static_cast<T *>(C.phi), C.n, C.n_alloc, L.zero_coarse, nullptr, 0.0, nullptr, 0.0);
+    }
     sync();
   }
 }
@@ -134,8 +186,8 @@ template <typename T, bool CG, class Map, class Sync>
 __device__ void coarsest(const TailPlan &plan, const Map &map, Sync &sync) {
   const TailLevel &L = plan.lv[plan.last];
   if (plan.exact) {
-    if (map.leader()) dev::wht_solve<T, T, CG>(static_cast<const T *>(L.g), static_cast<T *>(L.phi), L.n_alloc,
-                                               plan.h_last);
+    if (map.first_warp())
+      dev::wht_solve_warp<T, T, CG>(static_cast<const T *>(L.g), static_cast<T *>(L.phi), L.n_alloc, plan.h_last);
     sync();
   } else if (!plan.mixed) {
     sweeps<T, CG>(L, plan.coarse_sweeps, plan.last > 0, map, sync);
@@ -164,12 +216,24 @@ __device__ void ascend(const TailPlan &plan, int m_from, int m_to, const Map &ma
     const TailLevel &C = plan.lv[m + 1];
     T *phi = static_cast<T *>(L.phi);
     const T *cphi = static_cast<const T *>(C.phi);
-    const Span sp = map.span(L.n);
-    for (int64_t i = sp.a; i < sp.e; i += sp.s) {
-      if (L.all_active)
-        dev::prolong_oct<T, false, CG>(i, L.keys, L.blk, L.n, L.n_alloc, phi, L.active, cphi, C.n_alloc);
-      else
-        dev::prolong_oct<T, true, CG>(i, L.keys, L.blk, L.n, L.n_alloc, phi, L.active, cphi, C.n_alloc);
+    if (per_cell<T>(map, L.n)) {
+      const Span su = map.units(L.n, 8);
+      for (int64_t u = su.a; u < su.e; u += su.s) {
+        if (L.all_active)
+          dev::prolong_cell<T, false, CG>(u >> 3, (int)(u & 7), L.keys, L.blk, L.n, L.n_alloc, phi, L.active, cphi,
+                                          C.n_alloc);
+        else
+          dev::prolong_cell<T, true, CG>(u >> 3, (int)(u & 7), L.keys, L.blk, L.n, L.n_alloc, phi, L.active, cphi,
+                                         C.n_alloc);
+      }
+    } else {
+      const Span sp = map.span(L.n);
+      for (int64_t i = sp.a; i < sp.e; i += sp.s) {
+        if (L.all_active)
+          dev::prolong_oct<T, false, CG>(i, L.keys, L.blk, L.n, L.n_alloc, phi, L.active, cphi, C.n_alloc);
+        else
+          dev::prolong_oct<T, true, CG>(i, L.keys, L.blk, L.n, L.n_alloc, phi, L.active, cphi, C.n_alloc);
+      }
     }
     sync();
     sweeps<T, CG>(L, plan.n_post, false, map, sync);
