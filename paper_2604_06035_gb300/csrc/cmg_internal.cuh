@@ -332,8 +332,12 @@ inline unsigned blocks_for(int64_t n, int t = kThreads) { return (unsigned)((n +
 
 // Launch with programmatic dependent launch allowed: the next kernel on the
 // stream (or in the captured graph) may be scheduled while this one drains.
-// Every kernel launched this way starts with pdl_enter(), which waits for the
-// preceding grid to complete before touching memory.
+// Every kernel launched this way calls pdl_enter(), which waits for the
+// preceding grid to complete, before it touches memory that any kernel
+// writes after the level build; only reads of the build's index arrays
+// (neighbours, masks, father cells, interpolation blocks, keys), which the
+// build finishes with a stream synchronisation and nothing writes again,
+// may come before it.
 template <typename... KArgs, typename... Args>
 inline void launch_k(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t s, Args... args) {
   cudaLaunchConfig_t cfg = {};

@@ -28,14 +28,31 @@ __device__ void block_sum_to(double v, double *partials) {
   }
 }
 
+// FP32 passes read their oct's index data (written only by the level build)
+// before the grid-dependency wait, overlapping the preceding kernel's tail:
+// measured on the two-level 128^3 workload, the mixed-precision solves got
+// 2-3 % faster.  FP64 passes, bound by GB300's FP64 issue rate, keep every
+// load after the wait: with the early reads the refined level's FP64 solve
+// got ~1-3 % slower.
+template <typename T>
+constexpr bool kPreloadIdx = sizeof(T) == 4;
+
 template <typename T, int P, bool ZERO, bool MASK>
 __global__ void __launch_bounds__(kThreads) k_sweep(const int32_t *__restrict__ nbr, const T *__restrict__ src,
                                                    T *__restrict__ dst, const T *__restrict__ g,
                                                    const uint8_t *__restrict__ active, int64_t n) {
-  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  dev::sweep_oct<T, P, ZERO, MASK, false>(i, nbr, src, dst, g, active, n);
+  if constexpr (kPreloadIdx<T>) {
+    dev::SweepIdx x;
+    if (i < n) x = dev::sweep_idx<ZERO, MASK>(i, nbr, active, n);
+    pdl_enter();
+    if (i >= n) return;
+    dev::sweep_oct_idx<T, P, ZERO, MASK, false>(i, x, src, dst, g);
+  } else {
+    pdl_enter();
+    if (i >= n) return;
+    dev::sweep_oct<T, P, ZERO, MASK, false>(i, nbr, src, dst, g, active, n);
+  }
 }
 
 template <typename T, bool NORM, bool RESTRICT, bool EMIT, bool ROUT, bool ZPHI>
@@ -46,14 +63,26 @@ __global__ void __launch_bounds__(kThreads) k_resid(const int32_t *__restrict__ 
                                                    int64_t cn_alloc, int zero_cphi, double *__restrict__ partials,
                                                    float *__restrict__ g32, const double *__restrict__ emit_scale,
                                                    double *__restrict__ rout, double rscale) {
-  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double acc = 0.0;
-  if (i < n) {
-    const double inv_s = EMIT ? 1.0 / *emit_scale : 0.0;
-    acc = dev::resid_oct<T, NORM, RESTRICT, EMIT, ROUT, ZPHI, false>(i, nbr, phi, g, active, n, n_alloc, father, cg,
-                                                                     cphi, cn, cn_alloc, zero_cphi, g32, inv_s,
-                                                                     rout, rscale);
+  if constexpr (kPreloadIdx<T>) {
+    dev::ResidIdx x;
+    if (i < n) x = dev::resid_idx<RESTRICT>(i, nbr, active, n, father);
+    pdl_enter();
+    if (i < n) {
+      const double inv_s = EMIT ? 1.0 / *emit_scale : 0.0;
+      acc = dev::resid_oct_idx<T, NORM, RESTRICT, EMIT, ROUT, ZPHI, false>(i, x, phi, g, n, n_alloc, cg, cphi, cn,
+                                                                           cn_alloc, zero_cphi, g32, inv_s, rout,
+                                                                           rscale);
+    }
+  } else {
+    pdl_enter();
+    if (i < n) {
+      const double inv_s = EMIT ? 1.0 / *emit_scale : 0.0;
+      acc = dev::resid_oct<T, NORM, RESTRICT, EMIT, ROUT, ZPHI, false>(i, nbr, phi, g, active, n, n_alloc, father,
+                                                                       cg, cphi, cn, cn_alloc, zero_cphi, g32, inv_s,
+                                                                       rout, rscale);
+    }
   }
   if (NORM) block_sum_to(acc, partials);
 }
@@ -63,10 +92,18 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const uint64_t *__restrict
                                                      int64_t n, int64_t n_alloc, T *__restrict__ phi,
                                                      const uint8_t *__restrict__ active,
                                                      const T *__restrict__ cphi, int64_t cn_alloc) {
-  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  dev::prolong_oct<T, MASK, false>(i, keys, blk, n, n_alloc, phi, active, cphi, cn_alloc);
+  if constexpr (kPreloadIdx<T>) {
+    dev::ProlongIdx x;
+    if (i < n) x = dev::prolong_idx<MASK>(i, keys, blk, n, active);
+    pdl_enter();
+    if (i >= n) return;
+    dev::prolong_oct_idx<T, MASK, false>(i, x, n_alloc, phi, cphi, cn_alloc);
+  } else {
+    pdl_enter();
+    if (i >= n) return;
+    dev::prolong_oct<T, MASK, false>(i, keys, blk, n, n_alloc, phi, active, cphi, cn_alloc);
+  }
 }
 
 __global__ void __launch_bounds__(kThreads) k_ghost_fill(const uint64_t *__restrict__ gkeys,

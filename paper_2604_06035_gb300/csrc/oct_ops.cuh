@@ -59,9 +59,27 @@ __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(
 // One colour pass of red-black Gauss-Seidel (App. D.2 Eq. (gs_update)) on
 // oct i: plane P from the other plane of the oct and of its six face
 // neighbours.  ZERO: the other plane is known to be zero, so phi = g.
+//
+// The *_idx loaders read an oct's index data (neighbours, active mask,
+// father, interpolation block, octant), which only the level build writes;
+// a one-launch-per-operation kernel reads it before its grid-dependency wait,
+// overlapping the preceding kernel, and passes it to the *_oct_idx body.
+struct SweepIdx {
+  int32_t nb[6];
+  unsigned m;
+};
+template <bool ZERO, bool MASK>
+__device__ __forceinline__ SweepIdx sweep_idx(int64_t i, const int32_t *__restrict__ nbr,
+                                              const uint8_t *__restrict__ active, int64_t n) {
+  SweepIdx x;
+#pragma unroll
+  for (int d = 0; d < 6; ++d) x.nb[d] = ZERO ? 0 : __ldg(nbr + d * n + i);
+  x.m = MASK ? __ldg(active + i) : 0xFFu;
+  return x;
+}
+
 template <typename T, int P, bool ZERO, bool MASK, bool CG>
-__device__ __forceinline__ void sweep_oct(int64_t i, const int32_t *__restrict__ nbr, const T *src, T *dst,
-                                          const T *g, const uint8_t *__restrict__ active, int64_t n) {
+__device__ __forceinline__ void sweep_oct_idx(int64_t i, const SweepIdx &x, const T *src, T *dst, const T *g) {
   T gv[4], out[4];
   load4<CG>(g + i * 4, gv);
   if (ZERO) {
@@ -70,9 +88,7 @@ __device__ __forceinline__ void sweep_oct(int64_t i, const int32_t *__restrict__
   } else {
     T own[4];
     load4<CG>(src + i * 4, own);
-    int32_t nb[6];
-#pragma unroll
-    for (int d = 0; d < 6; ++d) nb[d] = __ldg(nbr + d * n + i);
+    const int32_t *nb = x.nb;
     const T inv6 = T(1) / T(6);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -88,12 +104,17 @@ __device__ __forceinline__ void sweep_oct(int64_t i, const int32_t *__restrict__
     }
   }
   if (MASK) {
-    const unsigned m = __ldg(active + i);
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-      if (!((m >> plane_cell(P, q)) & 1)) out[q] = T(0);
+      if (!((x.m >> plane_cell(P, q)) & 1)) out[q] = T(0);
   }
   store4(dst + i * 4, out);
+}
+
+template <typename T, int P, bool ZERO, bool MASK, bool CG>
+__device__ __forceinline__ void sweep_oct(int64_t i, const int32_t *__restrict__ nbr, const T *src, T *dst,
+                                          const T *g, const uint8_t *__restrict__ active, int64_t n) {
+  sweep_oct_idx<T, P, ZERO, MASK, CG>(i, sweep_idx<ZERO, MASK>(i, nbr, active, n), src, dst, g);
 }
 
 // sweep_oct for one cell (cell plane_cell(P, q) of oct i), one thread per
@@ -127,12 +148,28 @@ __device__ __forceinline__ void sweep_cell(int64_t i, int q, const int32_t *__re
 // writes its father cell g_c = 0.5 * sum_8 d (= -h_c^2/6 * mean_8 r) and, if
 // zero_cphi, zeroes the father's phi.  EMIT: g32 = (float)(d * inv_s).
 // ROUT: r oct-major.  ZPHI: phi taken as zero on real octs.
+struct ResidIdx {
+  int32_t nb[6];
+  unsigned m;
+  int32_t fa;
+};
+template <bool RESTRICT>
+__device__ __forceinline__ ResidIdx resid_idx(int64_t i, const int32_t *__restrict__ nbr,
+                                              const uint8_t *__restrict__ active, int64_t n,
+                                              const int32_t *__restrict__ father) {
+  ResidIdx x;
+#pragma unroll
+  for (int d = 0; d < 6; ++d) x.nb[d] = __ldg(nbr + d * n + i);
+  x.m = active ? __ldg(active + i) : 0xFFu;
+  x.fa = RESTRICT ? __ldg(father + i) : -1;
+  return x;
+}
+
 template <typename T, bool NORM, bool RESTRICT, bool EMIT, bool ROUT, bool ZPHI, bool CG>
-__device__ __forceinline__ double resid_oct(int64_t i, const int32_t *__restrict__ nbr, const T *phi, const T *g,
-                                            const uint8_t *__restrict__ active, int64_t n, int64_t n_alloc,
-                                            const int32_t *__restrict__ father, T *cg, T *cphi, int64_t cn,
-                                            int64_t cn_alloc, int zero_cphi, float *g32, double inv_s,
-                                            double *rout, double rscale) {
+__device__ __forceinline__ double resid_oct_idx(int64_t i, const ResidIdx &x, const T *phi, const T *g, int64_t n,
+                                                int64_t n_alloc, T *cg, T *cphi, int64_t cn, int64_t cn_alloc,
+                                                int zero_cphi, float *g32, double inv_s, double *rout,
+                                                double rscale) {
   T pl[2][4], gv[2][4];
   if (ZPHI) {
 #pragma unroll
@@ -143,11 +180,9 @@ __device__ __forceinline__ double resid_oct(int64_t i, const int32_t *__restrict
   }
   load4<CG>(g + i * 4, gv[0]);
   load4<CG>(g + (n + i) * 4, gv[1]);
-  int32_t nb[6];
-#pragma unroll
-  for (int d = 0; d < 6; ++d) nb[d] = __ldg(nbr + d * n + i);
+  const int32_t *nb = x.nb;
   const T inv6 = T(1) / T(6);
-  const unsigned m = active ? __ldg(active + i) : 0xFFu;
+  const unsigned m = x.m;
   T rsum = T(0);
   double acc = 0.0;
   T tacc = T(0);  // FP32 data: the oct's squares summed in FP32, one conversion
@@ -184,7 +219,7 @@ __device__ __forceinline__ double resid_oct(int64_t i, const int32_t *__restrict
   }
   if (NORM && sizeof(T) == 4) acc = (double)tacc;
   if (RESTRICT) {
-    const int32_t fa = __ldg(father + i);
+    const int32_t fa = x.fa;
     if (fa >= 0) {
       const int64_t pc = fa >> 3;
       const int cc = fa & 7;
@@ -193,6 +228,17 @@ __device__ __forceinline__ double resid_oct(int64_t i, const int32_t *__restrict
     }
   }
   return acc;
+}
+
+template <typename T, bool NORM, bool RESTRICT, bool EMIT, bool ROUT, bool ZPHI, bool CG>
+__device__ __forceinline__ double resid_oct(int64_t i, const int32_t *__restrict__ nbr, const T *phi, const T *g,
+                                            const uint8_t *__restrict__ active, int64_t n, int64_t n_alloc,
+                                            const int32_t *__restrict__ father, T *cg, T *cphi, int64_t cn,
+                                            int64_t cn_alloc, int zero_cphi, float *g32, double inv_s,
+                                            double *rout, double rscale) {
+  return resid_oct_idx<T, NORM, RESTRICT, EMIT, ROUT, ZPHI, CG>(i, resid_idx<RESTRICT>(i, nbr, active, n, father),
+                                                                phi, g, n, n_alloc, cg, cphi, cn, cn_alloc,
+                                                                zero_cphi, g32, inv_s, rout, rscale);
 }
 
 // resid_oct<NORM = false, RESTRICT = true> with one thread per cell: lane k
@@ -289,17 +335,29 @@ __device__ __forceinline__ void interp8(const T *cphi, int64_t cn_alloc, const i
 }
 
 // phi[i] += trilinear interpolation of the coarse correction (active cells).
-template <typename T, bool MASK, bool CG>
-__device__ __forceinline__ void prolong_oct(int64_t i, const uint64_t *__restrict__ keys,
-                                            const int32_t *__restrict__ blk, int64_t n, int64_t n_alloc, T *phi,
-                                            const uint8_t *__restrict__ active, const T *cphi, int64_t cn_alloc) {
-  const int cc = (int)(__ldg(keys + i) & 7);
+struct ProlongIdx {
   int32_t b[8];
+  int cc;
+  unsigned m;
+};
+template <bool MASK>
+__device__ __forceinline__ ProlongIdx prolong_idx(int64_t i, const uint64_t *__restrict__ keys,
+                                                  const int32_t *__restrict__ blk, int64_t n,
+                                                  const uint8_t *__restrict__ active) {
+  ProlongIdx x;
+  x.cc = (int)(__ldg(keys + i) & 7);
 #pragma unroll
-  for (int t = 0; t < 8; ++t) b[t] = __ldg(blk + t * n + i);
+  for (int t = 0; t < 8; ++t) x.b[t] = __ldg(blk + t * n + i);
+  x.m = MASK ? __ldg(active + i) : 0xFFu;
+  return x;
+}
+
+template <typename T, bool MASK, bool CG>
+__device__ __forceinline__ void prolong_oct_idx(int64_t i, const ProlongIdx &x, int64_t n_alloc, T *phi,
+                                                const T *cphi, int64_t cn_alloc) {
   T corr[8];
-  interp8<T, CG>(cphi, cn_alloc, b, cc, corr);
-  const unsigned m = MASK ? __ldg(active + i) : 0xFFu;
+  interp8<T, CG>(cphi, cn_alloc, x.b, x.cc, corr);
+  const unsigned m = x.m;
 #pragma unroll
   for (int p = 0; p < 2; ++p) {
     T v[4];
@@ -311,6 +369,13 @@ __device__ __forceinline__ void prolong_oct(int64_t i, const uint64_t *__restric
     }
     store4(phi + (p * n_alloc + i) * 4, v);
   }
+}
+
+template <typename T, bool MASK, bool CG>
+__device__ __forceinline__ void prolong_oct(int64_t i, const uint64_t *__restrict__ keys,
+                                            const int32_t *__restrict__ blk, int64_t n, int64_t n_alloc, T *phi,
+                                            const uint8_t *__restrict__ active, const T *cphi, int64_t cn_alloc) {
+  prolong_oct_idx<T, MASK, CG>(i, prolong_idx<MASK>(i, keys, blk, n, active), n_alloc, phi, cphi, cn_alloc);
 }
 
 // prolong_oct for one cell c of oct i, one thread per cell: the 8 coarse
