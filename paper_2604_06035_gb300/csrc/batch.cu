@@ -137,10 +137,18 @@ __device__ bool vcycle(const BatchPlan &P, bool zero_top, int64_t tid, int64_t n
     const BLevel &C = P.lv[m + 1];
     if (!sweeps<T>(P, L, P.n_pre, m > 0 || zero_top, tid, nthr, phi_t<T>(L), g_t<T>(L))) return false;
     const int zc = (m + 1 < last) ? (P.n_pre == 0) : (nsw == 0);
-    for (int64_t i = tid; i < L.n; i += nthr)
-      dev::resid_oct<T, false, true, false, false, false, true>(
-          i, L.nbr, phi_t<T>(L), g_t<T>(L), L.all_active ? nullptr : L.active, L.n, L.n_alloc, L.father, g_t<T>(C),
-          phi_t<T>(C), C.n, C.n_alloc, zc, nullptr, 0.0, nullptr, 0.0);
+    // after pre-smoothing (n_pre >= 1) the colour-1 residuals are exactly 0
+    if (P.n_pre >= 1) {
+      for (int64_t i = tid; i < L.n; i += nthr)
+        dev::resid_oct<T, false, true, false, false, false, true, true>(
+            i, L.nbr, phi_t<T>(L), g_t<T>(L), L.all_active ? nullptr : L.active, L.n, L.n_alloc, L.father,
+            g_t<T>(C), phi_t<T>(C), C.n, C.n_alloc, zc, nullptr, 0.0, nullptr, 0.0);
+    } else {
+      for (int64_t i = tid; i < L.n; i += nthr)
+        dev::resid_oct<T, false, true, false, false, false, true>(
+            i, L.nbr, phi_t<T>(L), g_t<T>(L), L.all_active ? nullptr : L.active, L.n, L.n_alloc, L.father,
+            g_t<T>(C), phi_t<T>(C), C.n, C.n_alloc, zc, nullptr, 0.0, nullptr, 0.0);
+    }
     if (!grid_sync(P)) return false;
   }
   {
@@ -174,8 +182,10 @@ __device__ bool vcycle(const BatchPlan &P, bool zero_top, int64_t tid, int64_t n
 }
 
 // Top-level FP64 residual, per-patch norms into P.norm; MIXED also writes the
-// FP32 right-hand side g32 = d / s_emit[patch].
-template <bool MIXED, bool ZPHI>
+// FP32 right-hand side g32 = d / s_emit[patch].  C1Z: right after an FP64
+// V-cycle whose last operation on the top level is a colour-1 pass (the
+// colour-1 residuals are exactly zero and are not evaluated).
+template <bool MIXED, bool ZPHI, bool C1Z = false>
 __device__ void top_residual(const BatchPlan &P, double *acc_out, int64_t tid, int64_t nthr) {
   const BLevel &L = P.lv[0];
   const int64_t wbase = tid & ~(int64_t)31;
@@ -186,7 +196,7 @@ __device__ void top_residual(const BatchPlan &P, double *acc_out, int64_t tid, i
     if (i < L.n) {
       p = __ldg(P.pid + i);
       const double inv_s = MIXED ? 1.0 / __ldcg(P.s_emit + p) : 0.0;
-      acc = dev::resid_oct<double, true, false, MIXED, false, ZPHI, true>(
+      acc = dev::resid_oct<double, true, false, MIXED, false, ZPHI, true, C1Z>(
           i, L.nbr, L.phi, L.g, nullptr, L.n, L.n_alloc, nullptr, nullptr, nullptr, 0, 0, 0, L.g32, inv_s, nullptr,
           0.0);
     }
@@ -508,10 +518,15 @@ __device__ void stationary_solve(const BatchPlan &P, int64_t tid, int64_t nthr) 
         dev::store4(T0.phi + (pl * T0.n_alloc + i) * 4, v);
       }
       if (!grid_sync(P)) return;
+      top_residual<MIXED, false>(P, P.norm, tid, nthr);
     } else {
       if (!vcycle<double>(P, false, tid, nthr)) return;
+      const bool c1 = P.depth > 1 ? P.n_post >= 1 : P.n_pre + P.n_post >= 1;
+      if (c1)
+        top_residual<false, false, true>(P, P.norm, tid, nthr);
+      else
+        top_residual<false, false>(P, P.norm, tid, nthr);
     }
-    top_residual<MIXED, false>(P, P.norm, tid, nthr);
     if (!grid_sync(P)) return;
   }
 }

@@ -398,9 +398,11 @@ void fft_prepare(cmg_level *L);
 void fft_solve32(cmg_level *L);
 template <typename T>
 void sweep(cmg_level *L, int m, bool zero_init);
+// c1_swept: the last operation on MG level m was a colour-1 pass over all of
+// it (the colour-1 residuals are exactly zero and are not evaluated).
 template <typename T>
 void resid_restrict(cmg_level *L, int m, bool restrict_to_coarse, bool norm, bool zero_coarse_phi,
-                    double *norm_out, const double *emit_scale = nullptr);
+                    double *norm_out, const double *emit_scale = nullptr, bool c1_swept = false);
 void residual_out(cmg_level *L, int m, int prec, double *out);
 double residual_norm2_host(cmg_level *L, int m, int prec);
 template <typename T>

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const int32_t *__restrict__ 
   }
 }
 
-template <typename T, bool NORM, bool RESTRICT, bool EMIT, bool ROUT, bool ZPHI>
+template <typename T, bool NORM, bool RESTRICT, bool EMIT, bool ROUT, bool ZPHI, bool C1Z = false>
 __global__ void __launch_bounds__(kThreads) k_resid(const int32_t *__restrict__ nbr, const T *__restrict__ phi,
                                                    const T *__restrict__ g, const uint8_t *__restrict__ active,
                                                    int64_t n, int64_t n_alloc, const int32_t *__restrict__ father,
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kThreads) k_resid(const int32_t *__restrict__ 
     pdl_enter();
     if (i < n) {
       const double inv_s = EMIT ? 1.0 / *emit_scale : 0.0;
-      acc = dev::resid_oct_idx<T, NORM, RESTRICT, EMIT, ROUT, ZPHI, false>(i, x, phi, g, n, n_alloc, cg, cphi, cn,
+      acc = dev::resid_oct_idx<T, NORM, RESTRICT, EMIT, ROUT, ZPHI, false, C1Z>(i, x, phi, g, n, n_alloc, cg, cphi, cn,
                                                                            cn_alloc, zero_cphi, g32, inv_s, rout,
                                                                            rscale);
     }
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kThreads) k_resid(const int32_t *__restrict__ 
     pdl_enter();
     if (i < n) {
       const double inv_s = EMIT ? 1.0 / *emit_scale : 0.0;
-      acc = dev::resid_oct<T, NORM, RESTRICT, EMIT, ROUT, ZPHI, false>(i, nbr, phi, g, active, n, n_alloc, father,
+      acc = dev::resid_oct<T, NORM, RESTRICT, EMIT, ROUT, ZPHI, false, C1Z>(i, nbr, phi, g, active, n, n_alloc, father,
                                                                        cg, cphi, cn, cn_alloc, zero_cphi, g32, inv_s,
                                                                        rout, rscale);
     }

@@ -50,7 +50,7 @@ template void sweep<float>(cmg_level *, int, bool);
 
 template <typename T>
 void resid_restrict(cmg_level *L, int m, bool restrict_to_coarse, bool norm, bool zero_coarse_phi, double *norm_out,
-                    const double *emit_scale) {
+                    const double *emit_scale, bool c1_swept) {
   MgLev &g = L->mg[m];
   cudaStream_t s = L->ctx->stream;
   const unsigned nb = blocks_for(g.n);
@@ -62,12 +62,22 @@ void resid_restrict(cmg_level *L, int m, bool restrict_to_coarse, bool norm, boo
   const double cells = 8.0 * (double)g.n;
   const double bytes = cells * 2.0 * sizeof(T) + 24.0 * g.n + (restrict_to_coarse ? g.n * sizeof(T) : 0.0) +
                        (emit_scale ? cells * 4.0 : 0.0);
-  const double flops = cells * (8.0 + (norm ? 2.0 : 0.0) + (restrict_to_coarse ? 1.0 : 0.0));
+  const double flops = cells * (c1_swept ? 0.5 : 1.0) * (8.0 + (norm ? 2.0 : 0.0)) + (restrict_to_coarse ? cells : 0.0);
   const int cls = sizeof(T) == 8 ? K_RESID64 : K_RESID32;
   if (g.n > 0) {
     LaunchScope ls(L->ctx, cls, bytes, flops);
-    if (restrict_to_coarse && !norm && !emit_scale)
-      launch_k(k_resid<T, false, true, false, false, false>, nb, kThreads, s, 
+    if (restrict_to_coarse && !norm && !emit_scale && c1_swept)
+      launch_k(k_resid<T, false, true, false, false, false, true>, nb, kThreads, s,
+          g.nbr, phi_of<T>(g), g_of<T>(g), act, g.n, g.n_alloc, g.father, cg, cphi, cn, cna, zero_coarse_phi,
+          nullptr, nullptr, nullptr, nullptr, 0.0);
+    else if (!restrict_to_coarse && norm && !emit_scale && c1_swept)
+      launch_k(k_resid<T, true, false, false, false, false, true>, nb, kThreads, s,
+          g.nbr, phi_of<T>(g), g_of<T>(g), act, g.n, g.n_alloc, nullptr, nullptr, nullptr, 0, 0, 0, L->partials,
+          nullptr, nullptr, nullptr, 0.0);
+    else if (c1_swept)
+      throw Error(CMG_ERR_INVALID_ARG, "unsupported residual variant");
+    else if (restrict_to_coarse && !norm && !emit_scale)
+      launch_k(k_resid<T, false, true, false, false, false>, nb, kThreads, s,
           g.nbr, phi_of<T>(g), g_of<T>(g), act, g.n, g.n_alloc, g.father, cg, cphi, cn, cna, zero_coarse_phi,
           nullptr, nullptr, nullptr, nullptr, 0.0);
     else if (restrict_to_coarse && norm && !emit_scale)
@@ -97,8 +107,8 @@ void resid_restrict(cmg_level *L, int m, bool restrict_to_coarse, bool norm, boo
     }
   }
 }
-template void resid_restrict<double>(cmg_level *, int, bool, bool, bool, double *, const double *);
-template void resid_restrict<float>(cmg_level *, int, bool, bool, bool, double *, const double *);
+template void resid_restrict<double>(cmg_level *, int, bool, bool, bool, double *, const double *, bool);
+template void resid_restrict<float>(cmg_level *, int, bool, bool, bool, double *, const double *, bool);
 
 void residual_out(cmg_level *L, int m, int prec, double *out) {
   MgLev &g = L->mg[m];

@@ -165,7 +165,16 @@ __device__ __forceinline__ ResidIdx resid_idx(int64_t i, const int32_t *__restri
   return x;
 }
 
-template <typename T, bool NORM, bool RESTRICT, bool EMIT, bool ROUT, bool ZPHI, bool CG>
+//
+// C1Z: the last operation on this level was a colour-1 pass over every oct
+// with the colour-0 values, g and ghost values the residual now reads.  That
+// pass wrote fma(s, 1/6, g) at each active colour-1 cell, and this function
+// forms the same s from the same values in the same order, so each
+// colour-1 residual is exactly +0 (inactive cells are +0 anyway): their
+// stencils are skipped.  Skipping changes no result bit: the norm gains
+// +0 terms (acc >= +0 throughout), the restriction sum gains +0 four times,
+// which equals adding +0 once, and EMIT / ROUT write what dv = +0 gives.
+template <typename T, bool NORM, bool RESTRICT, bool EMIT, bool ROUT, bool ZPHI, bool CG, bool C1Z = false>
 __device__ __forceinline__ double resid_oct_idx(int64_t i, const ResidIdx &x, const T *phi, const T *g, int64_t n,
                                                 int64_t n_alloc, T *cg, T *cphi, int64_t cn, int64_t cn_alloc,
                                                 int zero_cphi, float *g32, double inv_s, double *rout,
@@ -179,7 +188,7 @@ __device__ __forceinline__ double resid_oct_idx(int64_t i, const ResidIdx &x, co
     load4<CG>(phi + (n_alloc + i) * 4, pl[1]);
   }
   load4<CG>(g + i * 4, gv[0]);
-  load4<CG>(g + (n + i) * 4, gv[1]);
+  if (!C1Z) load4<CG>(g + (n + i) * 4, gv[1]);
   const int32_t *nb = x.nb;
   const T inv6 = T(1) / T(6);
   const unsigned m = x.m;
@@ -188,6 +197,15 @@ __device__ __forceinline__ double resid_oct_idx(int64_t i, const ResidIdx &x, co
   T tacc = T(0);  // FP32 data: the oct's squares summed in FP32, one conversion
 #pragma unroll
   for (int p = 0; p < 2; ++p) {
+    if (C1Z && p == 1) {
+      if (RESTRICT) rsum += T(0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (EMIT) g32[(p * n + i) * 4 + q] = (float)((double)T(0) * inv_s);
+        if (ROUT) rout[i * 8 + plane_cell(p, q)] = rscale * 0.0;
+      }
+      continue;
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int c = plane_cell(p, q);
@@ -230,13 +248,13 @@ __device__ __forceinline__ double resid_oct_idx(int64_t i, const ResidIdx &x, co
   return acc;
 }
 
-template <typename T, bool NORM, bool RESTRICT, bool EMIT, bool ROUT, bool ZPHI, bool CG>
+template <typename T, bool NORM, bool RESTRICT, bool EMIT, bool ROUT, bool ZPHI, bool CG, bool C1Z = false>
 __device__ __forceinline__ double resid_oct(int64_t i, const int32_t *__restrict__ nbr, const T *phi, const T *g,
                                             const uint8_t *__restrict__ active, int64_t n, int64_t n_alloc,
                                             const int32_t *__restrict__ father, T *cg, T *cphi, int64_t cn,
                                             int64_t cn_alloc, int zero_cphi, float *g32, double inv_s,
                                             double *rout, double rscale) {
-  return resid_oct_idx<T, NORM, RESTRICT, EMIT, ROUT, ZPHI, CG>(i, resid_idx<RESTRICT>(i, nbr, active, n, father),
+  return resid_oct_idx<T, NORM, RESTRICT, EMIT, ROUT, ZPHI, CG, C1Z>(i, resid_idx<RESTRICT>(i, nbr, active, n, father),
                                                                 phi, g, n, n_alloc, cg, cphi, cn, cn_alloc,
                                                                 zero_cphi, g32, inv_s, rout, rscale);
 }

@@ -148,7 +148,7 @@ void vcycle(cmg_level *L, int m, const cmg_solve_params *p, bool zero_top, int64
     return;
   }
   for (int k = 0; k < p->n_pre; ++k) sweep<T>(L, m, k == 0 && (m > 0 || zero_top));
-  resid_restrict<T>(L, m, true, false, coarse_needs_zero(L, m, p), nullptr);
+  resid_restrict<T>(L, m, true, false, coarse_needs_zero(L, m, p), nullptr, nullptr, p->n_pre >= 1);
   vcycle<T>(L, m + 1, p, false, updates);
   prolong<T>(L, m);
   for (int k = 0; k < p->n_post; ++k) sweep<T>(L, m, false);
@@ -156,6 +156,13 @@ void vcycle(cmg_level *L, int m, const cmg_solve_params *p, bool zero_top, int64
 }
 
 SolveCtrl *ctrl_dev(cmg_level *L) { return reinterpret_cast<SolveCtrl *>(L->ctrl); }
+
+// Whether a V-cycle's last operation on MG level 0 is a colour-1 pass over
+// all of it: post-smoothing, or the sweeps of a one-level hierarchy.
+bool vcycle_ends_with_colour1(const cmg_level *L, const cmg_solve_params *p) {
+  if (L->mg.size() > 1) return p->n_post >= 1;
+  return !L->exact_coarse && p->coarse_sweeps >= 1;
+}
 
 // Set-up: ghosts, ||f - L0||, initial residual (and, in mixed mode, the
 // first FP32 right-hand side), control block.
@@ -195,7 +202,7 @@ void segment_body(cmg_level *L, const cmg_solve_params *p, cudaGraphConditionalH
     pcg_body(L, p, updates);
   } else if (p->precision == CMG_PREC_FP64) {
     vcycle<double>(L, 0, p, false, updates);
-    resid_restrict<double>(L, 0, false, true, false, scal + 2);
+    resid_restrict<double>(L, 0, false, true, false, scal + 2, nullptr, vcycle_ends_with_colour1(L, p));
   } else {
     MgLev &g = L->mg[0];
     if (p->precision == CMG_PREC_FFT) {

@@ -170,11 +170,19 @@ __device__ void descend(const TailPlan &plan, int m_from, int m_to, const Map &m
                                         C.n_alloc, L.zero_coarse);
       }
     } else {
+      // after pre-smoothing (n_pre >= 1) the colour-1 residuals are exactly 0
       const Span sp = map.span(L.n);
-      for (int64_t i = sp.a; i < sp.e; i += sp.s)
-        dev::resid_oct<T, false, true, false, false, false, CG>(
-            i, L.nbr, phi, g, L.all_active ? nullptr : L.active, L.n, L.n_alloc, L.father, static_cast<T *>(C.g),
-            static_cast<T *>(C.phi), C.n, C.n_alloc, L.zero_coarse, nullptr, 0.0, nullptr, 0.0);
+      if (plan.n_pre >= 1) {
+        for (int64_t i = sp.a; i < sp.e; i += sp.s)
+          dev::resid_oct<T, false, true, false, false, false, CG, true>(
+              i, L.nbr, phi, g, L.all_active ? nullptr : L.active, L.n, L.n_alloc, L.father, static_cast<T *>(C.g),
+              static_cast<T *>(C.phi), C.n, C.n_alloc, L.zero_coarse, nullptr, 0.0, nullptr, 0.0);
+      } else {
+        for (int64_t i = sp.a; i < sp.e; i += sp.s)
+          dev::resid_oct<T, false, true, false, false, false, CG>(
+              i, L.nbr, phi, g, L.all_active ? nullptr : L.active, L.n, L.n_alloc, L.father, static_cast<T *>(C.g),
+              static_cast<T *>(C.phi), C.n, C.n_alloc, L.zero_coarse, nullptr, 0.0, nullptr, 0.0);
+      }
     }
     sync();
   }

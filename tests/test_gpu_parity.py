@@ -486,6 +486,27 @@ def test_tail_schedule_matches_per_operation_launches(cmg, ctx, precision):
             assert relerr(out[(tail, base)], out[(0, base)]) <= 1e-13, (tail, base)
 
 
+@pytest.mark.parametrize("n_post", [1, 2])
+def test_colour1_residual_is_exactly_zero_after_a_cycle(cmg, ctx, n_post):
+    """An FP64 cycle ends with a colour-1 pass on the top level, which wrote
+    fma(s, 1/6, g) at every colour-1 cell from the colour-0 values that the
+    residual reads, summed in the same order: each colour-1 residual is
+    exactly 0.0 while the colour-0 ones are not.  The stopping residual and
+    the V-cycle's restrictions skip those stencils on this ground (bit-
+    identical results); a change to either kernel's summation order breaks
+    this test first.  Refined level (no mean subtraction after the solve)."""
+    cfg, GB, GF, RB, RF = _two_level(cmg, ctx, 6)
+    for G, rho in ((GB, cfg["rho"][0]), (GF, cfg["rho"][1])):
+        cmg.cmg_level_set_density(G, rho, 1.0)
+        cmg.cmg_level_set_phi(G, np.zeros((cmg.cmg_level_n_octs(G), 8)))
+    cmg.cmg_level_solve(GB, tol=1e-10)
+    cmg.cmg_level_solve(GF, fixed_cycles=2, n_post=n_post)
+    r = cmg.cmg_level_get_residual(GF)
+    odd, even = [1, 2, 4, 7], [0, 3, 5, 6]
+    assert np.all(r[:, odd] == 0.0)
+    assert np.count_nonzero(r[:, even]) > 0.9 * r[:, even].size
+
+
 def test_queued_solves_match_blocking_solves(cmg, ctx):
     """cmg_level_solve_async + cmg_level_solve_wait on both levels of the
     two-level workload (the fine level queued behind its parent, whose phi it
