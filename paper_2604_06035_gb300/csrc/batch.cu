@@ -167,10 +167,17 @@ __device__ bool vcycle(const BatchPlan &P, bool zero_top, int64_t tid, int64_t n
   for (int m = last - 1; m >= 0; --m) {
     const BLevel &L = P.lv[m];
     const BLevel &C = P.lv[m + 1];
+    // with post-smoothing, the colour-0 corrections are overwritten unread
     for (int64_t i = tid; i < L.n; i += nthr) {
-      if (L.all_active)
+      if (L.all_active && P.n_post >= 1)
+        dev::prolong_oct<T, false, true, true>(i, L.keys, L.blk, L.n, L.n_alloc, phi_t<T>(L), L.active, phi_t<T>(C),
+                                               C.n_alloc);
+      else if (L.all_active)
         dev::prolong_oct<T, false, true>(i, L.keys, L.blk, L.n, L.n_alloc, phi_t<T>(L), L.active, phi_t<T>(C),
                                          C.n_alloc);
+      else if (P.n_post >= 1)
+        dev::prolong_oct<T, true, true, true>(i, L.keys, L.blk, L.n, L.n_alloc, phi_t<T>(L), L.active, phi_t<T>(C),
+                                              C.n_alloc);
       else
         dev::prolong_oct<T, true, true>(i, L.keys, L.blk, L.n, L.n_alloc, phi_t<T>(L), L.active, phi_t<T>(C),
                                         C.n_alloc);

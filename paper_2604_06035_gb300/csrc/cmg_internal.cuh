@@ -406,7 +406,7 @@ void resid_restrict(cmg_level *L, int m, bool restrict_to_coarse, bool norm, boo
 void residual_out(cmg_level *L, int m, int prec, double *out);
 double residual_norm2_host(cmg_level *L, int m, int prec);
 template <typename T>
-void prolong(cmg_level *L, int m);
+void prolong(cmg_level *L, int m, bool c0_dead = false);  // c0_dead: a colour-0 pass follows
 void coarse_solve(cmg_level *L, int prec, int coarse_sweeps);
 void zero_phi_norm(cmg_level *L, double *out);
 void subtract_mean(cmg_level *L);

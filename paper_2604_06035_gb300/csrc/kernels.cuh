@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kThreads) k_resid(const int32_t *__restrict__ 
   if (NORM) block_sum_to(acc, partials);
 }
 
-template <typename T, bool MASK>
+template <typename T, bool MASK, bool C0D>
 __global__ void __launch_bounds__(kThreads) k_prolong(const uint64_t *__restrict__ keys, const int32_t *__restrict__ blk,
                                                      int64_t n, int64_t n_alloc, T *__restrict__ phi,
                                                      const uint8_t *__restrict__ active,
@@ -98,11 +98,11 @@ __global__ void __launch_bounds__(kThreads) k_prolong(const uint64_t *__restrict
     if (i < n) x = dev::prolong_idx<MASK>(i, keys, blk, n, active);
     pdl_enter();
     if (i >= n) return;
-    dev::prolong_oct_idx<T, MASK, false>(i, x, n_alloc, phi, cphi, cn_alloc);
+    dev::prolong_oct_idx<T, MASK, false, C0D>(i, x, n_alloc, phi, cphi, cn_alloc);
   } else {
     pdl_enter();
     if (i >= n) return;
-    dev::prolong_oct<T, MASK, false>(i, keys, blk, n, n_alloc, phi, active, cphi, cn_alloc);
+    dev::prolong_oct<T, MASK, false, C0D>(i, keys, blk, n, n_alloc, phi, active, cphi, cn_alloc);
   }
 }
 

@@ -151,23 +151,30 @@ void zero_phi_norm(cmg_level *L, double *out) {
 }
 
 template <typename T>
-void prolong(cmg_level *L, int m) {
+void prolong(cmg_level *L, int m, bool c0_dead) {
   MgLev &g = L->mg[m];
   MgLev &c = L->mg[m + 1];
   if (g.n == 0) return;
   cudaStream_t s = L->ctx->stream;
   LaunchScope ls(L->ctx, sizeof(T) == 8 ? K_PROLONG64 : K_PROLONG32,
-                 g.n * 17.0 * sizeof(T), g.n * 128.0);
-  if (g.all_active)
-    launch_k(k_prolong<T, false>, blocks_for(g.n), kThreads, s, g.keys, g.blk, g.n, g.n_alloc, phi_of<T>(g), g.active,
-                                                             phi_of<T>(c), c.n_alloc);
+                 g.n * (c0_dead ? 9.0 : 17.0) * sizeof(T), g.n * (c0_dead ? 64.0 : 128.0));
+  const unsigned nb = blocks_for(g.n);
+  if (g.all_active && c0_dead)
+    launch_k(k_prolong<T, false, true>, nb, kThreads, s, g.keys, g.blk, g.n, g.n_alloc, phi_of<T>(g), g.active,
+             phi_of<T>(c), c.n_alloc);
+  else if (g.all_active)
+    launch_k(k_prolong<T, false, false>, nb, kThreads, s, g.keys, g.blk, g.n, g.n_alloc, phi_of<T>(g), g.active,
+             phi_of<T>(c), c.n_alloc);
+  else if (c0_dead)
+    launch_k(k_prolong<T, true, true>, nb, kThreads, s, g.keys, g.blk, g.n, g.n_alloc, phi_of<T>(g), g.active,
+             phi_of<T>(c), c.n_alloc);
   else
-    launch_k(k_prolong<T, true>, blocks_for(g.n), kThreads, s, g.keys, g.blk, g.n, g.n_alloc, phi_of<T>(g), g.active,
-                                                            phi_of<T>(c), c.n_alloc);
+    launch_k(k_prolong<T, true, false>, nb, kThreads, s, g.keys, g.blk, g.n, g.n_alloc, phi_of<T>(g), g.active,
+             phi_of<T>(c), c.n_alloc);
   CMG_CUDA(cudaGetLastError());
 }
-template void prolong<double>(cmg_level *, int);
-template void prolong<float>(cmg_level *, int);
+template void prolong<double>(cmg_level *, int, bool);
+template void prolong<float>(cmg_level *, int, bool);
 
 void fill_ghosts(cmg_level *L) {
   MgLev &g = L->mg[0];

@@ -370,14 +370,18 @@ __device__ __forceinline__ ProlongIdx prolong_idx(int64_t i, const uint64_t *__r
   return x;
 }
 
-template <typename T, bool MASK, bool CG>
+// C0D: a colour-0 pass over every oct comes next; it overwrites each
+// colour-0 value without reading it (the update uses only the colour-1
+// neighbours and g), so the colour-0 corrections are dead and only colour-1
+// cells are corrected (the unused interpolation terms and loads drop out).
+template <typename T, bool MASK, bool CG, bool C0D = false>
 __device__ __forceinline__ void prolong_oct_idx(int64_t i, const ProlongIdx &x, int64_t n_alloc, T *phi,
                                                 const T *cphi, int64_t cn_alloc) {
   T corr[8];
   interp8<T, CG>(cphi, cn_alloc, x.b, x.cc, corr);
   const unsigned m = x.m;
 #pragma unroll
-  for (int p = 0; p < 2; ++p) {
+  for (int p = C0D ? 1 : 0; p < 2; ++p) {
     T v[4];
     load4<CG>(phi + (p * n_alloc + i) * 4, v);
 #pragma unroll
@@ -389,11 +393,11 @@ __device__ __forceinline__ void prolong_oct_idx(int64_t i, const ProlongIdx &x, 
   }
 }
 
-template <typename T, bool MASK, bool CG>
+template <typename T, bool MASK, bool CG, bool C0D = false>
 __device__ __forceinline__ void prolong_oct(int64_t i, const uint64_t *__restrict__ keys,
                                             const int32_t *__restrict__ blk, int64_t n, int64_t n_alloc, T *phi,
                                             const uint8_t *__restrict__ active, const T *cphi, int64_t cn_alloc) {
-  prolong_oct_idx<T, MASK, CG>(i, prolong_idx<MASK>(i, keys, blk, n, active), n_alloc, phi, cphi, cn_alloc);
+  prolong_oct_idx<T, MASK, CG, C0D>(i, prolong_idx<MASK>(i, keys, blk, n, active), n_alloc, phi, cphi, cn_alloc);
 }
 
 // prolong_oct for one cell c of oct i, one thread per cell: the 8 coarse

@@ -150,7 +150,7 @@ void vcycle(cmg_level *L, int m, const cmg_solve_params *p, bool zero_top, int64
   for (int k = 0; k < p->n_pre; ++k) sweep<T>(L, m, k == 0 && (m > 0 || zero_top));
   resid_restrict<T>(L, m, true, false, coarse_needs_zero(L, m, p), nullptr, nullptr, p->n_pre >= 1);
   vcycle<T>(L, m + 1, p, false, updates);
-  prolong<T>(L, m);
+  prolong<T>(L, m, p->n_post >= 1);
   for (int k = 0; k < p->n_post; ++k) sweep<T>(L, m, false);
   *updates += (int64_t)(p->n_pre + p->n_post) * 8 * L->mg[m].n;
 }

@@ -224,21 +224,29 @@ __device__ void ascend(const TailPlan &plan, int m_from, int m_to, const Map &ma
     const TailLevel &C = plan.lv[m + 1];
     T *phi = static_cast<T *>(L.phi);
     const T *cphi = static_cast<const T *>(C.phi);
+    // with post-smoothing (n_post >= 1) the colour-0 corrections are
+    // overwritten unread by the next pass: only colour-1 cells are corrected
+    const bool c0d = plan.n_post >= 1;
     if (per_cell<T>(map, L.n)) {
-      const Span su = map.units(L.n, 8);
+      const int k = c0d ? 4 : 8;  // cells per oct: colour 1, or all
+      const Span su = map.units(L.n, k);
       for (int64_t u = su.a; u < su.e; u += su.s) {
+        const int64_t i = c0d ? u >> 2 : u >> 3;
+        const int c = c0d ? plane_cell(1, (int)(u & 3)) : (int)(u & 7);
         if (L.all_active)
-          dev::prolong_cell<T, false, CG>(u >> 3, (int)(u & 7), L.keys, L.blk, L.n, L.n_alloc, phi, L.active, cphi,
-                                          C.n_alloc);
+          dev::prolong_cell<T, false, CG>(i, c, L.keys, L.blk, L.n, L.n_alloc, phi, L.active, cphi, C.n_alloc);
         else
-          dev::prolong_cell<T, true, CG>(u >> 3, (int)(u & 7), L.keys, L.blk, L.n, L.n_alloc, phi, L.active, cphi,
-                                         C.n_alloc);
+          dev::prolong_cell<T, true, CG>(i, c, L.keys, L.blk, L.n, L.n_alloc, phi, L.active, cphi, C.n_alloc);
       }
     } else {
       const Span sp = map.span(L.n);
       for (int64_t i = sp.a; i < sp.e; i += sp.s) {
-        if (L.all_active)
+        if (L.all_active && c0d)
+          dev::prolong_oct<T, false, CG, true>(i, L.keys, L.blk, L.n, L.n_alloc, phi, L.active, cphi, C.n_alloc);
+        else if (L.all_active)
           dev::prolong_oct<T, false, CG>(i, L.keys, L.blk, L.n, L.n_alloc, phi, L.active, cphi, C.n_alloc);
+        else if (c0d)
+          dev::prolong_oct<T, true, CG, true>(i, L.keys, L.blk, L.n, L.n_alloc, phi, L.active, cphi, C.n_alloc);
         else
           dev::prolong_oct<T, true, CG>(i, L.keys, L.blk, L.n, L.n_alloc, phi, L.active, cphi, C.n_alloc);
       }
