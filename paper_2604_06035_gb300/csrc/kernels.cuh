@@ -28,21 +28,24 @@ __device__ void block_sum_to(double v, double *partials) {
   }
 }
 
-// FP32 passes read their oct's index data (written only by the level build)
+// FP32 kernels read their oct's index data (written only by the level build)
 // before the grid-dependency wait, overlapping the preceding kernel's tail:
 // measured on the two-level 128^3 workload, the mixed-precision solves got
-// 2-3 % faster.  FP64 passes, bound by GB300's FP64 issue rate, keep every
+// 2-3 % faster.  FP64 kernels, bound by GB300's FP64 issue rate, keep every
 // load after the wait: with the early reads the refined level's FP64 solve
-// got ~1-3 % slower.
+// got ~1-3 % slower.  FP32 colour passes preload only on levels of at most
+// kPreloadSweepOcts octs: the HBM-bound pass over a 512^3 level got 3 %
+// slower with it (the residual there got faster).
 template <typename T>
 constexpr bool kPreloadIdx = sizeof(T) == 4;
+constexpr int64_t kPreloadSweepOcts = int64_t(1) << 20;
 
-template <typename T, int P, bool ZERO, bool MASK>
+template <typename T, int P, bool ZERO, bool MASK, bool PRE>
 __global__ void __launch_bounds__(kThreads) k_sweep(const int32_t *__restrict__ nbr, const T *__restrict__ src,
                                                    T *__restrict__ dst, const T *__restrict__ g,
                                                    const uint8_t *__restrict__ active, int64_t n) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if constexpr (kPreloadIdx<T>) {
+  if constexpr (PRE) {
     dev::SweepIdx x;
     if (i < n) x = dev::sweep_idx<ZERO, MASK>(i, nbr, active, n);
     pdl_enter();

@@ -29,11 +29,16 @@ void sweep(cmg_level *L, int m, bool zero_init) {
   const double u = 4.0 * (double)g.n;  // cells updated per colour pass
   const double nbr_bytes = 12.0 * (double)g.n;
   const double full_bytes = 3.0 * u * sizeof(T) + nbr_bytes, full_flops = 7.0 * u;
+  const bool pre = kPreloadIdx<T> && g.n <= kPreloadSweepOcts;
 #define CMG_SWEEP(P, Z, M)                                                                                  \
   do {                                                                                                      \
     LaunchScope ls(L->ctx, cls, (Z) ? 2.0 * u * sizeof(T) + nbr_bytes : full_bytes, (Z) ? 0.0 : full_flops); \
-    launch_k(k_sweep<T, P, Z, M>, nb, kThreads, s, g.nbr, phi + (1 - P) * st, phi + P * st, gg + P * g.n * 4, \
-                                                g.active, g.n);                                             \
+    if (pre)                                                                                                \
+      launch_k(k_sweep<T, P, Z, M, kPreloadIdx<T>>, nb, kThreads, s, g.nbr, phi + (1 - P) * st, phi + P * st, \
+               gg + P * g.n * 4, g.active, g.n);                                                            \
+    else                                                                                                    \
+      launch_k(k_sweep<T, P, Z, M, false>, nb, kThreads, s, g.nbr, phi + (1 - P) * st, phi + P * st,        \
+               gg + P * g.n * 4, g.active, g.n);                                                            \
   } while (0)
   if (mask) {
     if (zero_init) CMG_SWEEP(0, true, true); else CMG_SWEEP(0, false, true);
