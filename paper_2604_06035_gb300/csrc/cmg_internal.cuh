@@ -400,9 +400,12 @@ template <typename T>
 void sweep(cmg_level *L, int m, bool zero_init);
 // c1_swept: the last operation on MG level m was a colour-1 pass over all of
 // it (the colour-1 residuals are exactly zero and are not evaluated).
+// finalize = false: a norm's per-block partial sums are left in L->partials
+// for the caller's reduction (norm_out is not written).
 template <typename T>
 void resid_restrict(cmg_level *L, int m, bool restrict_to_coarse, bool norm, bool zero_coarse_phi,
-                    double *norm_out, const double *emit_scale = nullptr, bool c1_swept = false);
+                    double *norm_out, const double *emit_scale = nullptr, bool c1_swept = false,
+                    bool finalize = true);
 void residual_out(cmg_level *L, int m, int prec, double *out);
 double residual_norm2_host(cmg_level *L, int m, int prec);
 template <typename T>

@@ -55,7 +55,7 @@ template void sweep<float>(cmg_level *, int, bool);
 
 template <typename T>
 void resid_restrict(cmg_level *L, int m, bool restrict_to_coarse, bool norm, bool zero_coarse_phi, double *norm_out,
-                    const double *emit_scale, bool c1_swept) {
+                    const double *emit_scale, bool c1_swept, bool finalize) {
   MgLev &g = L->mg[m];
   cudaStream_t s = L->ctx->stream;
   const unsigned nb = blocks_for(g.n);
@@ -101,7 +101,7 @@ void resid_restrict(cmg_level *L, int m, bool restrict_to_coarse, bool norm, boo
       throw Error(CMG_ERR_INVALID_ARG, "unsupported residual variant");
     CMG_CUDA(cudaGetLastError());
   }
-  if (norm) {
+  if (norm && finalize) {
     const double scale = 36.0 / (g.h * g.h * g.h * g.h);
     if (g.n == 0) {
       CMG_CUDA(cudaMemsetAsync(norm_out, 0, 2 * sizeof(double), s));
@@ -112,8 +112,8 @@ void resid_restrict(cmg_level *L, int m, bool restrict_to_coarse, bool norm, boo
     }
   }
 }
-template void resid_restrict<double>(cmg_level *, int, bool, bool, bool, double *, const double *, bool);
-template void resid_restrict<float>(cmg_level *, int, bool, bool, bool, double *, const double *, bool);
+template void resid_restrict<double>(cmg_level *, int, bool, bool, bool, double *, const double *, bool, bool);
+template void resid_restrict<float>(cmg_level *, int, bool, bool, bool, double *, const double *, bool, bool);
 
 void residual_out(cmg_level *L, int m, int prec, double *out) {
   MgLev &g = L->mg[m];

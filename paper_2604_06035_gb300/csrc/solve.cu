@@ -90,14 +90,49 @@ __global__ void k_ctrl_init(SolveCtrl *c, const double *scal, double tol, int fi
   decide(c, tol, 0, maxc, h, use_handle);
 }
 
-__global__ void k_ctrl_check(SolveCtrl *c, const double *scal, double tol, int fixed, int maxc,
-                             cudaGraphConditionalHandle h, int use_handle) {
-  const double rel = sqrt(scal[2] / c->n0sq);
+// The check after a cycle: record rel = sqrt(||r||^2 / ||f - L0||^2), decide.
+__device__ void record_and_decide(SolveCtrl *c, double n2, double tol, int fixed, int maxc,
+                                  cudaGraphConditionalHandle h, int use_handle) {
+  const double rel = sqrt(n2 / c->n0sq);
   const int k = c->cycles;
   if (k < 256) c->hist[k] = rel;
   c->cycles = k + 1;
   c->rel_final = rel;
   decide(c, tol, fixed, maxc, h, use_handle);
+}
+
+__global__ void k_ctrl_check(SolveCtrl *c, const double *scal, double tol, int fixed, int maxc,
+                             cudaGraphConditionalHandle h, int use_handle) {
+  record_and_decide(c, scal[2], tol, fixed, maxc, h, use_handle);
+}
+
+// The last step of the residual norm fused with the check (one launch per
+// cycle fewer): the block reduction of the residual kernel's per-block
+// partial sums in k_finalize's order (the norm is bit-identical), written to
+// scal[2] (||r||^2) and scal[3] (||r||), then the check.  One block of 1024
+// threads.
+__global__ void __launch_bounds__(1024) k_norm_check(const double *__restrict__ partials, int np, double scale,
+                                                     double *scal, SolveCtrl *c, double tol, int fixed, int maxc,
+                                                     cudaGraphConditionalHandle h, int use_handle) {
+  pdl_enter();
+  __shared__ double ws[32];
+  double v = 0.0;
+  for (int t = threadIdx.x; t < np; t += blockDim.x) v += partials[t];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+    if (threadIdx.x == 0) {
+      const double n2 = scale * w;
+      scal[2] = n2;
+      scal[3] = sqrt(n2);
+      record_and_decide(c, n2, tol, fixed, maxc, h, use_handle);
+    }
+  }
 }
 
 __global__ void k_zero_if(const SolveCtrl *c, double *phi, int64_t n, int64_t n_alloc) {
@@ -191,6 +226,17 @@ void segment_pre(cmg_level *L, const cmg_solve_params *p, cudaGraphConditionalHa
   CMG_CUDA(cudaGetLastError());
 }
 
+// The residual norm's reduction (its partial sums written by a residual
+// launch with finalize = false) and the check, in one launch.
+void norm_check(cmg_level *L, const cmg_solve_params *p, cudaGraphConditionalHandle h, int use_handle) {
+  const MgLev &g = L->mg[0];
+  const unsigned nb = blocks_for(g.n);
+  LaunchScope ls(L->ctx, K_REDUCE, nb * 8.0 + 64.0, nb);
+  launch_k(k_norm_check, 1, 1024, L->ctx->stream, L->partials, (int)nb, 36.0 / (g.h * g.h * g.h * g.h), L->scal,
+           ctrl_dev(L), p->tol, p->fixed_cycles, p->max_cycles, h, use_handle);
+  CMG_CUDA(cudaGetLastError());
+}
+
 // One iteration: a V-cycle (FP64), or an FP32 V-cycle (mixed) or FP32 FFT
 // solve (fft) of the scaled correction equation + FP64 accumulation, then
 // the FP64 residual norm and the check.
@@ -202,7 +248,9 @@ void segment_body(cmg_level *L, const cmg_solve_params *p, cudaGraphConditionalH
     pcg_body(L, p, updates);
   } else if (p->precision == CMG_PREC_FP64) {
     vcycle<double>(L, 0, p, false, updates);
-    resid_restrict<double>(L, 0, false, true, false, scal + 2, nullptr, vcycle_ends_with_colour1(L, p));
+    resid_restrict<double>(L, 0, false, true, false, scal + 2, nullptr, vcycle_ends_with_colour1(L, p), false);
+    norm_check(L, p, h, use_handle);
+    return;
   } else {
     MgLev &g = L->mg[0];
     if (p->precision == CMG_PREC_FFT) {
@@ -219,7 +267,9 @@ void segment_body(cmg_level *L, const cmg_solve_params *p, cudaGraphConditionalH
       LaunchScope ls(L->ctx, K_REDUCE, 16.0, 0.0);
       k_copy_scalar<<<1, 1, 0, s>>>(scal + 4, scal + 3);
     }
-    resid_restrict<double>(L, 0, false, true, false, scal + 2, scal + 4);
+    resid_restrict<double>(L, 0, false, true, false, scal + 2, scal + 4, false, false);
+    norm_check(L, p, h, use_handle);
+    return;
   }
   LaunchScope ls(L->ctx, K_REDUCE, 64.0, 0.0);
   k_ctrl_check<<<1, 1, 0, s>>>(ctrl_dev(L), scal, p->tol, p->fixed_cycles, p->max_cycles, h, use_handle);
