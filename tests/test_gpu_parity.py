@@ -466,11 +466,12 @@ def test_device_arrays_match_host_arrays(cmg, ctx):
 @pytest.mark.parametrize("precision", [0, 1])
 def test_tail_schedule_matches_per_operation_launches(cmg, ctx, precision):
     """The tail kernels (one CTA for the smallest levels, a cooperative grid
-    launch above) run the same per-oct arithmetic as the
-    one-launch-per-operation path: the schedule must not change phi.  Tails
-    from 64 octs (one CTA in FP64 and FP32), 512 (grid in FP64 with the levels
-    of at most 64 octs on CTA 0; one CTA in FP32), 4096 (grid in FP64, one CTA
-    in FP32) and the whole hierarchy below the level itself (grid)."""
+    launch above; one thread per oct, or per cell on small FP64 levels) run
+    the same arithmetic, in the same order, as the one-launch-per-operation
+    path: the schedule must not change a bit of phi.  Tails from 64 octs (one
+    CTA in FP64 and FP32), 512 (grid in FP64 with the levels of at most 64
+    octs on CTA 0; one CTA in FP32), 4096 (grid in FP64, one CTA in FP32) and
+    the whole hierarchy below the level itself (grid)."""
     cfg, GB, GF, RB, RF = _two_level(cmg, ctx, 6)
     out = {}
     tails = (0, 64, 512, 4096, 1 << 20)
@@ -483,7 +484,7 @@ def test_tail_schedule_matches_per_operation_launches(cmg, ctx, precision):
             out[(tail, G is GB)] = cmg.cmg_level_get_phi(G)
     for tail in tails[1:]:
         for base in (True, False):
-            assert relerr(out[(tail, base)], out[(0, base)]) <= 1e-13, (tail, base)
+            assert np.array_equal(out[(tail, base)], out[(0, base)]), (tail, base)
 
 
 @pytest.mark.parametrize("n_post", [1, 2])
