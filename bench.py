@@ -166,6 +166,12 @@ def cycle_updates(n_octs_per_mg, n_pre=2, n_post=2, coarse_sweeps=4, exact_coars
 
 # ------------------------------------------------------------- reference
 
+def two_level_workload(n_fine_octs, tol):
+    """The `config.workload` text of the two-level benchmark (both arms)."""
+    return ("two_level_128: 128^3 periodic lognormal base (sigma 1.5, k^-2) + 1 refined level "
+            "(rho > 8 rho_bar, %d fine octs); FP64 V(2,2) to rel. residual %g per level" % (n_fine_octs, tol))
+
+
 def run_reference(args, rank, world):
     import numpy as np  # noqa: F401
     import oracle as O
@@ -196,7 +202,8 @@ def run_reference(args, rank, world):
         "metric": "poisson_cell_updates_per_s", "value": value, "unit": "Mcell-updates/s", "impl": "reference",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "two_level_128: 128^3 periodic lognormal base + 1 refined level (rho > 8 rho_bar)"},
+        "config": {"workload": two_level_workload(F.n, args.tol), "l2": "not applicable (CPU oracle)",
+                   "parallelism": "single"},
         "cpu_baseline": {"value": value, "unit": "Mcell-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "Mcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -726,9 +733,7 @@ def run_ours(args, rank, local, world):
         "metric": "poisson_cell_updates_per_s", "value": value, "unit": "Mcell-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "two_level_128: 128^3 periodic lognormal base (sigma 1.5, k^-2) + 1 refined level "
-                               "(rho > 8 rho_bar, %d fine octs); FP64 V(2,2) to rel. residual %g per level"
-                               % (cmg.cmg_level_n_octs(F), args.tol),
+        "config": {"workload": two_level_workload(cmg.cmg_level_n_octs(F), args.tol),
                    "l2": "flushed before each timed step (512 MiB write)", "parallelism": "replicas" if world > 1
                    else "single"},
         "time_to_tol_ms": {"base": st_b["ms"], "fine": st_f["ms"]},
