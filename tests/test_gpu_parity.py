@@ -508,6 +508,34 @@ def test_colour1_residual_is_exactly_zero_after_a_cycle(cmg, ctx, n_post):
     assert np.count_nonzero(r[:, even]) > 0.9 * r[:, even].size
 
 
+@pytest.mark.parametrize("n_pre,n_post", [(0, 2), (2, 0), (1, 1), (1, 3)])
+def test_smoothing_counts_match_oracle(cmg, ctx, n_pre, n_post):
+    """V(n_pre, n_post) cycles other than V(2,2).  With n_pre = 0 no colour-1
+    pass precedes the restriction, which then evaluates every residual (and
+    the coarse phi is zeroed); with n_post = 0 the prolongation corrects every
+    cell and the stopping residual is evaluated in full.  Fixed FP64 cycles
+    against the oracle (1e-12), both levels with the same parent phi; mixed
+    precision refined to 1e-12 against the oracle converged to 1e-13."""
+    cfg, GB, GF, RB, RF = _two_level(cmg, ctx, 6)
+    for k, (G, R, rho) in enumerate(((GB, RB, cfg["rho"][0]), (GF, RF, cfg["rho"][1]))):
+        if k == 1:
+            cmg.cmg_level_set_phi(GB, RB.get_phi())
+        cmg.cmg_level_set_density(G, rho, 1.0)
+        R.set_density(rho, 1.0)
+        z = np.zeros((R.n, 8))
+        cmg.cmg_level_set_phi(G, z)
+        R.set_phi(z)
+        rc, st = cmg.cmg_level_solve(G, fixed_cycles=3, n_pre=n_pre, n_post=n_post)
+        ro, so = R.solve(fixed_cycles=3, n_pre=n_pre, n_post=n_post)
+        assert relerr(cmg.cmg_level_get_phi(G), R.get_phi()) <= RTOL64, k
+        np.testing.assert_allclose(st["rel_history"], so["rel_history"], rtol=1e-9)
+        R.solve(tol=1e-13, n_pre=n_pre, n_post=n_post)
+        cmg.cmg_level_set_phi(G, z)
+        rc, st = cmg.cmg_level_solve(G, tol=1e-12, n_pre=n_pre, n_post=n_post, precision=cmg.CMG_PREC_MIXED)
+        assert rc == cmg.CMG_OK and st["rel_final"] <= 1e-12, k
+        assert relerr(cmg.cmg_level_get_phi(G), R.get_phi()) <= 1e-10, k
+
+
 def test_queued_solves_match_blocking_solves(cmg, ctx):
     """cmg_level_solve_async + cmg_level_solve_wait on both levels of the
     two-level workload (the fine level queued behind its parent, whose phi it
