@@ -801,15 +801,17 @@ def run_ours(args, rank, local, world):
             flush.fill_(k & 0xFF)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            for L, r, z in zip((B, F), pin_rho, zeros):
+            # per level: upload (overlapping the parent's queued solve), solve,
+            # queued read-back (overlapping the next level's solve)
+            for L, r, z, o in zip((B, F), pin_rho, zeros, pin_phi):
                 cmg.cmg_level_set_phi(L, z)  # zero initial guess, already on the device
                 cmg.cmg_level_set_density(L, r, 1.0)
-            for L in (B, F):
                 cmg.cmg_level_solve_async(L, tol=args.tol)
-            for L, o in zip((B, F), pin_phi):
+                cmg.cmg_level_get_phi_async(L, out=o)
+            for L in (B, F):
                 rc, st = cmg.cmg_level_solve_wait(L)
-                cmg.cmg_level_get_phi(L, out=o)
                 e2e_upd += st["cell_updates"]
+            cmg.cmg_ctx_synchronize(ctx)
             e2e_ms += (time.perf_counter() - t0) * 1e3
         h2d = sum(r.nbytes for r in pin_rho)
         d2h = sum(o.nbytes for o in pin_phi)

@@ -97,6 +97,8 @@ const char *cmg_last_error(void);
  * legacy default stream); the caller keeps it alive while the context lives. */
 int cmg_ctx_create(int device, void *stream, cmg_ctx **out);
 int cmg_ctx_destroy(cmg_ctx *ctx);
+/* Waits for all work queued by the context: on its stream and on the copy
+ * streams of host-memory arguments (cmg_level_get_phi_async downloads). */
 int cmg_ctx_synchronize(cmg_ctx *ctx);
 
 /* ---- instrumentation (no counterpart in the paper; used by the benchmark) ----
@@ -182,6 +184,15 @@ int cmg_level_set_density(cmg_level *lvl, const double *rho, cmg_mem mem, double
 /* phi [n][8] FP64: the initial guess (warm start) of the next solve. */
 int cmg_level_set_phi(cmg_level *lvl, const double *phi, cmg_mem mem);
 int cmg_level_get_phi(cmg_level *lvl, double *out, cmg_mem mem);
+/* cmg_level_get_phi without waiting: the read-back is queued behind the work
+ * already queued on the context's stream (e.g. a cmg_level_solve_async), and
+ * a host-memory `out` is written by a download on a copy stream of its own,
+ * so that work queued afterwards (the next level's solve) overlaps it.
+ * `out` must stay valid, and holds phi, once cmg_ctx_synchronize returns.
+ * A host-memory argument of any call (cmg_level_set_density, ...) is
+ * likewise uploaded on a copy stream, overlapping queued work; those calls
+ * return once their upload has finished. */
+int cmg_level_get_phi_async(cmg_level *lvl, double *out, cmg_mem mem);
 /* r = f - lap_h(phi) of the current phi, [n][8] FP64. */
 int cmg_level_get_residual(cmg_level *lvl, double *out, cmg_mem mem);
 /* Dirichlet ghost values last interpolated from the parent (by a solve or by

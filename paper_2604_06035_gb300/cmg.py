@@ -103,6 +103,7 @@ _SIGS = {
     "cmg_level_set_density": (_I, [_P, _P, _I, C.c_double, C.c_double]),
     "cmg_level_set_phi": (_I, [_P, _P, _I]),
     "cmg_level_get_phi": (_I, [_P, _P, _I]),
+    "cmg_level_get_phi_async": (_I, [_P, _P, _I]),
     "cmg_level_get_residual": (_I, [_P, _P, _I]),
     "cmg_level_get_ghosts": (_I, [_P, _P, _I]),
     "cmg_level_solve": (_I, [_P, C.POINTER(cmg_solve_params), C.POINTER(cmg_solve_stats)]),
@@ -516,6 +517,12 @@ def cmg_level_get_father_cells(lvl, device=False, out=None):
 
 def cmg_level_get_phi(lvl, device=False, out=None):
     return _get("cmg_level_get_phi", lvl, (cmg_level_n_octs(lvl), 8), np.float64, device, out)
+
+
+def cmg_level_get_phi_async(lvl, device=False, out=None):
+    """Queued read-back of phi: the returned array (or `out`, which must stay
+    alive) holds phi once cmg_ctx_synchronize(ctx) returns."""
+    return _get("cmg_level_get_phi_async", lvl, (cmg_level_n_octs(lvl), 8), np.float64, device, out)
 
 
 def cmg_level_get_residual(lvl, device=False, out=None):

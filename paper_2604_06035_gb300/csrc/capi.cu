@@ -69,6 +69,9 @@ void *staging(cmg_ctx *ctx, int which, size_t bytes) {
   if (ctx->stage_bytes[which] < bytes) {
     if (ctx->stage[which]) {
       CMG_CUDA(cudaStreamSynchronize(ctx->stream));
+      if (ctx->h2d_stream) CMG_CUDA(cudaStreamSynchronize(ctx->h2d_stream));
+      if (ctx->d2h_stream) CMG_CUDA(cudaStreamSynchronize(ctx->d2h_stream));
+      ctx->d2h_pending = false;
       cudaFree(ctx->stage[which]);
       ctx->stage[which] = nullptr;
       ctx->stage_bytes[which] = 0;
@@ -83,6 +86,23 @@ void *staging(cmg_ctx *ctx, int which, size_t bytes) {
   return ctx->stage[which];
 }
 
+// The copy streams and their events, on first use.
+void copy_streams(cmg_ctx *ctx) {
+  if (ctx->d2h_done) return;
+  if (!ctx->h2d_stream) CMG_CUDA(cudaStreamCreateWithFlags(&ctx->h2d_stream, cudaStreamNonBlocking));
+  if (!ctx->d2h_stream) CMG_CUDA(cudaStreamCreateWithFlags(&ctx->d2h_stream, cudaStreamNonBlocking));
+  for (cudaEvent_t *e : {&ctx->h2d_done, &ctx->stage0_free, &ctx->stage1_ready})
+    if (!*e) CMG_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  cudaEvent_t e = nullptr;  // set last: marks the whole set ready
+  CMG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  ctx->d2h_done = e;
+}
+
+// A queued download may still read stage[1]: later writes to it wait.
+void wait_stage1(cmg_ctx *ctx) {
+  if (ctx->d2h_pending) CMG_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->d2h_done, 0));
+}
+
 template <class F>
 void deliver(cmg_ctx *ctx, void *out, size_t bytes, int mem, F &&produce) {
   if (mem == CMG_MEM_DEVICE) {
@@ -91,12 +111,40 @@ void deliver(cmg_ctx *ctx, void *out, size_t bytes, int mem, F &&produce) {
     return;
   }
   void *t = staging(ctx, 1, bytes);
+  wait_stage1(ctx);
   produce(t);
   if (bytes) CMG_CUDA(cudaMemcpyAsync(out, t, bytes, cudaMemcpyDeviceToHost, ctx->stream));
   CMG_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->d2h_pending = false;
 }
 
-// Make `in` device-resident for the duration of `use(device_in)`.
+// deliver() without waiting: produce() is queued on the context's stream and
+// the download on the download stream, behind it; `out` is written once
+// cmg_ctx_synchronize() returns.  Work queued afterwards on the context's
+// stream overlaps the download.
+template <class F>
+void deliver_async(cmg_ctx *ctx, void *out, size_t bytes, int mem, F &&produce) {
+  if (mem == CMG_MEM_DEVICE) {
+    produce(out);
+    CMG_CUDA(cudaGetLastError());
+    return;
+  }
+  void *t = staging(ctx, 1, bytes);
+  copy_streams(ctx);
+  wait_stage1(ctx);
+  produce(t);
+  CMG_CUDA(cudaGetLastError());
+  CMG_CUDA(cudaEventRecord(ctx->stage1_ready, ctx->stream));
+  CMG_CUDA(cudaStreamWaitEvent(ctx->d2h_stream, ctx->stage1_ready, 0));
+  if (bytes) CMG_CUDA(cudaMemcpyAsync(out, t, bytes, cudaMemcpyDeviceToHost, ctx->d2h_stream));
+  CMG_CUDA(cudaEventRecord(ctx->d2h_done, ctx->d2h_stream));
+  ctx->d2h_pending = true;
+}
+
+// Make `in` device-resident for the duration of `use(device_in)`.  A host
+// buffer is uploaded on the upload stream (overlapping work already queued
+// on the context's stream) and `use` is queued behind the upload; the call
+// returns once the upload has finished, so the caller may reuse its buffer.
 template <class F>
 void accept(cmg_ctx *ctx, const void *in, size_t bytes, int mem, F &&use) {
   if (mem == CMG_MEM_DEVICE) {
@@ -104,9 +152,16 @@ void accept(cmg_ctx *ctx, const void *in, size_t bytes, int mem, F &&use) {
     return;
   }
   void *t = staging(ctx, 0, bytes);
-  if (bytes) CMG_CUDA(cudaMemcpyAsync(t, in, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  copy_streams(ctx);
+  if (ctx->stage0_used) CMG_CUDA(cudaStreamWaitEvent(ctx->h2d_stream, ctx->stage0_free, 0));
+  if (bytes) CMG_CUDA(cudaMemcpyAsync(t, in, bytes, cudaMemcpyHostToDevice, ctx->h2d_stream));
+  CMG_CUDA(cudaEventRecord(ctx->h2d_done, ctx->h2d_stream));
+  CMG_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->h2d_done, 0));
   use(static_cast<const void *>(t));
-  CMG_CUDA(cudaStreamSynchronize(ctx->stream));
+  CMG_CUDA(cudaGetLastError());
+  CMG_CUDA(cudaEventRecord(ctx->stage0_free, ctx->stream));
+  ctx->stage0_used = true;
+  CMG_CUDA(cudaEventSynchronize(ctx->h2d_done));
 }
 
 }  // namespace
@@ -160,6 +215,12 @@ int cmg_ctx_destroy(cmg_ctx *ctx) {
   cudaGetDevice(&prev);
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->h2d_stream) cudaStreamSynchronize(ctx->h2d_stream);
+  if (ctx->d2h_stream) cudaStreamSynchronize(ctx->d2h_stream);
+  for (cudaEvent_t e : {ctx->h2d_done, ctx->stage0_free, ctx->stage1_ready, ctx->d2h_done})
+    if (e) cudaEventDestroy(e);
+  if (ctx->h2d_stream) cudaStreamDestroy(ctx->h2d_stream);
+  if (ctx->d2h_stream) cudaStreamDestroy(ctx->d2h_stream);
   if (ctx->d_err) cudaFree(ctx->d_err);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
   if (ctx->h_dpinned) cudaFreeHost(ctx->h_dpinned);
@@ -180,6 +241,9 @@ int cmg_ctx_synchronize(cmg_ctx *ctx) {
     need(ctx != nullptr, "ctx is NULL");
     DeviceScope ds(ctx->device);
     CMG_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (ctx->h2d_stream) CMG_CUDA(cudaStreamSynchronize(ctx->h2d_stream));
+    if (ctx->d2h_stream) CMG_CUDA(cudaStreamSynchronize(ctx->d2h_stream));
+    ctx->d2h_pending = false;
     return CMG_OK;
   });
 }
@@ -433,6 +497,17 @@ int cmg_level_set_phi(cmg_level *lvl, const double *phi, cmg_mem mem) {
     DeviceScope ds(lvl->ctx->device);
     accept(lvl->ctx, phi, sizeof(double) * 8 * lvl->n, mem,
            [&](const void *d) { cmg::pack_field(lvl, 0, CMG_FIELD_PHI, CMG_PREC_FP64, d); });
+    return CMG_OK;
+  });
+}
+
+int cmg_level_get_phi_async(cmg_level *lvl, double *out, cmg_mem mem) {
+  return guard([&] {
+    need(lvl && (lvl->n == 0 || out), "bad arguments");
+    check_mem(mem);
+    DeviceScope ds(lvl->ctx->device);
+    deliver_async(lvl->ctx, out, sizeof(double) * 8 * lvl->n, mem,
+                  [&](void *d) { cmg::unpack_field(lvl, 0, CMG_FIELD_PHI, CMG_PREC_FP64, d); });
     return CMG_OK;
   });
 }

@@ -232,6 +232,15 @@ struct cmg_ctx {
   // device staging of host-memory arguments (grow-only; [0] inputs, [1] outputs)
   void *stage[2] = {nullptr, nullptr};
   size_t stage_bytes[2] = {0, 0};
+  // host<->device copies of host-memory arguments run on streams of their own
+  // (created on first use), so that they overlap work queued on `stream`
+  cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr;
+  cudaEvent_t h2d_done = nullptr;      // the last upload into stage[0] has finished
+  cudaEvent_t stage0_free = nullptr;   // `stream` has finished reading stage[0]
+  cudaEvent_t stage1_ready = nullptr;  // `stream` has finished writing stage[1]
+  cudaEvent_t d2h_done = nullptr;      // the last download from stage[1] has finished
+  bool stage0_used = false;            // stage0_free has been recorded
+  bool d2h_pending = false;            // a queued download may still read stage[1]
   // graph capture (private streams; the caller's stream may be the legacy one)
   cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
   bool capturing = false;

@@ -569,6 +569,38 @@ def test_queued_solves_match_blocking_solves(cmg, ctx):
     assert rc == cmg.CMG_OK
 
 
+def test_async_read_back_overlapping_the_next_solve(cmg, ctx):
+    """Host-memory upload and read-back on the copy streams: the base level's
+    density upload, solve and queued phi read-back, then the fine level's
+    (its upload overlapping the base solve, the base read-back overlapping
+    the fine solve) give, after cmg_ctx_synchronize, the phi of blocking
+    calls bit-for-bit, in pinned and in pageable host buffers; a second
+    queued read-back of the same staging buffer waits for the first."""
+    import torch
+    cfg, GB, GF, RB, RF = _two_level(cmg, ctx, 6)
+    z = [np.zeros((cmg.cmg_level_n_octs(G), 8)) for G in (GB, GF)]
+    for G, rho, zz in zip((GB, GF), cfg["rho"], z):
+        cmg.cmg_level_set_phi(G, zz)
+        cmg.cmg_level_set_density(G, rho, 1.0)
+        cmg.cmg_level_solve(G, tol=1e-10)
+    ref = [cmg.cmg_level_get_phi(G) for G in (GB, GF)]
+    for pinned in (True, False):
+        rho = [torch.from_numpy(r).pin_memory().numpy() if pinned else r.copy() for r in cfg["rho"]]
+        out = [torch.empty(r.shape, dtype=torch.float64).pin_memory().numpy() if pinned else np.empty(r.shape)
+               for r in ref]
+        for G, r, zz, o in zip((GB, GF), rho, z, out):
+            cmg.cmg_level_set_phi(G, zz)
+            cmg.cmg_level_set_density(G, r, 1.0)
+            cmg.cmg_level_solve_async(G, tol=1e-10)
+            cmg.cmg_level_get_phi_async(G, out=o)
+        for G in (GB, GF):
+            rc, st = cmg.cmg_level_solve_wait(G)
+            assert rc == cmg.CMG_OK
+        cmg.cmg_ctx_synchronize(ctx)
+        for o, r in zip(out, ref):
+            assert np.array_equal(o, r), pinned
+
+
 def test_grid_tail_barrier_timeout_returns_status(cmg, ctx):
     """A grid-tail barrier wait that runs out of spin budget ends the launch
     and the solve with CMG_ERR_TIMEOUT; the context stays usable and the next
