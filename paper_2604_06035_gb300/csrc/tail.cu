@@ -79,11 +79,12 @@ struct ChunkMap {
   __device__ bool first_warp() const { return b == 0 && t < 32; }
 };
 
-// Small FP64 levels run one thread per cell (4 per oct in a colour pass, 8
-// in the residual and the prolongation); FP32 levels and FP64 levels with
+// Small FP64 levels run one thread per cell (4 per oct in a colour pass and
+// in a prolongation that only corrects colour 1, 8 in the residual and in a
+// full prolongation); FP32 levels and FP64 levels with
 // more than a quarter as many octs per CTA as threads run one thread per
 // oct.  A GB300 SM sub-partition issues one FP64 warp instruction about
-// every 64 clocks however many of its lanes are active, so where a CTA
+// every 68 clocks however many of its lanes are active, so where a CTA
 // holds a few octs, one thread per oct leaves each FP64 instruction mostly
 // idle and serialises the oct's arithmetic in one lane, while one thread per
 // cell fills the lanes and shortens each thread's FP64 chain 4 to 8 fold.
