@@ -268,6 +268,35 @@ def test_sweep_residual_vs_dense():
     assert abs(n2 - np.sum(rd * rd)) <= 1e-12 * np.sum(rd * rd)
 
 
+def test_gauss_seidel_zeroes_the_residual_it_just_updated():
+    """Red-black Gauss-Seidel solves each updated cell's equation exactly
+    given its neighbours (App. D.2 Eq. (gs_update)), and the neighbours of a
+    black cell are all red: after a sweep (red, then black) the residual
+    vanishes on every black cell, up to rounding, while the red cells keep an
+    O(|f|) residual.  Periodic 32^3 level and the refined level of a
+    two-level pair (coarse-fine ghosts)."""
+    L, coords, n, rng = _periodic(5)
+    L.set_phi(rng.standard_normal((L.n, 8)))
+    L.set_f(rng.standard_normal((L.n, 8)))
+    levels = [(L, False)]
+    cfg = inputs.two_level_amr(base_level=4, seed=3)
+    B = O.Level(4, keys_of(cfg["coords"][0]))
+    F = O.Level(5, keys_of(cfg["coords"][1]), parent=B)
+    B.set_phi(rng.standard_normal((B.n, 8)))
+    F.set_phi(rng.standard_normal((F.n, 8)))
+    F.set_f(rng.standard_normal((F.n, 8)))
+    levels.append((F, True))
+    black = [c for c in range(8) if bin(c).count("1") % 2 == 1]
+    red = [c for c in range(8) if bin(c).count("1") % 2 == 0]
+    for G, ghost in levels:
+        G.rb_sweeps(0, 1, use_ghost=ghost)
+        G.residual(0, use_ghost=ghost)
+        r = G.mg_get(0, "r")
+        scale = np.abs(r[:, red]).max()
+        assert scale > 0.1
+        assert np.abs(r[:, black]).max() <= 1e-10 * scale
+
+
 def test_restrict_prolong_vs_dense():
     L, coords, n, rng = _periodic(4)
     r = rng.standard_normal((n, n, n))
