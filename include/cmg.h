@@ -381,12 +381,12 @@ int cmg_dense_octs(cmg_ctx *ctx, const double *src, int grid_dim, double *dst, i
 /* ---- residual norm without allocation (the paper has no counterpart) ----
  * The level objects above allocate device memory when they are built, and
  * their residual norm reduces through scratch the level owns.  Callers that
- * cannot allocate when they need a residual check -- code running while a
- * CUDA graph is being captured (cudaMalloc cannot be captured), real-time
- * loops that forbid allocation after start-up, hosts whose device memory is a
- * fixed arena of their own -- can use this entry point: it allocates nothing
- * and reduces through a fixed scratch array compiled into the library
- * (512 KiB, held by every GPU that loads the library until the process exits).
+ * cannot allocate when they need a residual check -- real-time loops that
+ * forbid allocation after start-up (cudaMalloc can block and synchronise the
+ * device), hosts whose device memory is a fixed arena handed out by their own
+ * allocator -- can use this entry point: it allocates nothing and reduces
+ * through a fixed scratch array compiled into the library (512 KiB, held by
+ * every GPU that loads the library until the process exits).
  *
  * Computes *norm2 = sum over cells of r^2, r = f - (sum_6 phi_nb - 6 phi) / h^2
  * (the residual of Sec. 5.1.1 item (iii)), on the current device, on `stream`
@@ -400,8 +400,11 @@ int cmg_dense_octs(cmg_ctx *ctx, const double *src, int grid_dim, double *dst, i
  * the first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress), so make that first call before any stream capture;
  * all calls share the scratch array, so calls that overlap on the GPU race
- * and the caller must serialise them.  Returns CMG_OK, CMG_ERR_INVALID_ARG or
- * CMG_ERR_CUDA; it does not set cmg_last_error(). */
+ * and the caller must serialise them.  The looked-up address is kept for the
+ * life of the process: after a cudaDeviceReset (or any other teardown of the
+ * device's primary context) the entry point must not be called again in that
+ * process.  Returns CMG_OK, CMG_ERR_INVALID_ARG or CMG_ERR_CUDA; it does not
+ * set cmg_last_error(). */
 int cmg_residual_norm2_noalloc(const int32_t *neighbors, const double *ghosts, const double *phi, const double *f,
                                int64_t n_octs, double h, double *norm2, void *stream);
 

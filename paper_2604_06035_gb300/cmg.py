@@ -769,11 +769,28 @@ def cmg_dense_octs(ctx, src, grid_dim, dst, to_octs):
 
 def cmg_residual_norm2_noalloc(neighbors, ghosts, phi, f, h, norm2, stream=0):
     """Residual norm^2 into the one-double CUDA tensor norm2 with no device
-    allocation by the library (for callers that cannot allocate at that point,
-    e.g. during CUDA-graph capture; see include/cmg.h).  neighbors [n][7]
-    int32, ghosts [n][6][4] or None, phi and f [n][8] float64, all CUDA
-    tensors.  Runs on `stream` (raw handle or torch stream); the caller
-    synchronises before reading norm2."""
+    allocation by the library (for callers that cannot allocate at that point:
+    real-time loops, hosts that own all device memory in an arena; see
+    include/cmg.h).  neighbors [n][7] int32, ghosts [n][6][4] or None, phi and
+    f [n][8] float64, all CUDA tensors on the current device.  Runs on
+    `stream` (raw handle or torch stream); the caller synchronises before
+    reading norm2.
+
+    The library reads 7n neighbour entries, 8n values of phi and f and 24n
+    ghost values, so every size is checked here before the call (ValueError)."""
+    n = int(neighbors.shape[0]) if len(getattr(neighbors, "shape", ())) else -1
+    sizes = [("neighbors", neighbors, 7 * n), ("phi", phi, 8 * n), ("f", f, 8 * n)]
+    if ghosts is not None:
+        sizes.append(("ghosts", ghosts, 24 * n))
+    if n < 0:
+        raise ValueError("cmg_residual_norm2_noalloc: neighbors must be an [n][7] array")
+    for name, a, want in sizes:
+        got = int(np.prod(a.shape))
+        if got != want:
+            raise ValueError("cmg_residual_norm2_noalloc: %s holds %d values, expected %d for n = %d octs"
+                             % (name, got, want, n))
+    if int(np.prod(norm2.shape)) < 1:
+        raise ValueError("cmg_residual_norm2_noalloc: norm2 must hold at least one value")
     if not isinstance(stream, int):
         stream = stream.cuda_stream
     pn, mn, _ = _in(neighbors, np.int32)
@@ -781,13 +798,19 @@ def cmg_residual_norm2_noalloc(neighbors, ghosts, phi, f, h, norm2, stream=0):
     pf, mf, _ = _in(f, np.float64)
     po, mo, _ = _in(norm2, np.float64)
     pg = None
+    arrays = [neighbors, phi, f, norm2]
     if ghosts is not None:
         pg, mg, _ = _in(ghosts, np.float64)
         _same_mem(mg, CMG_MEM_DEVICE, "cmg_residual_norm2_noalloc")
+        arrays.append(ghosts)
     for m in (mn, mp, mf, mo):
         _same_mem(m, CMG_MEM_DEVICE, "cmg_residual_norm2_noalloc")
-    n = neighbors.shape[0]
+    import torch
+    cur = torch.cuda.current_device()
+    for a in arrays:
+        if a.device.index != cur:
+            raise ValueError("cmg_residual_norm2_noalloc: every tensor must be on the current device (cuda:%d), "
+                             "got %s" % (cur, a.device))
     rc = lib().cmg_residual_norm2_noalloc(pn, pg, pp, pf, n, float(h), po, C.c_void_p(stream))
     if rc != CMG_OK:
         raise CmgError(rc, "cmg_residual_norm2_noalloc", "invalid argument or CUDA error")
-

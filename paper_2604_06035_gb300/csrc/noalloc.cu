@@ -5,12 +5,16 @@
 // Why it exists: the level objects of this library allocate their tables and
 // fields with cudaMalloc when they are built, and the library's residual norm
 // reduces through a scratch buffer owned by the level.  Some callers cannot
-// allocate at the moment they need a residual check: code that runs while a
-// CUDA graph is being captured (cudaMalloc is not a capturable operation),
-// real-time solver loops that forbid allocation after start-up, and hosts
-// whose device memory is a fixed arena handed out by their own allocator.
-// This entry point reads arrays the caller already owns and reduces through
-// a fixed-size scratch array compiled into the library instead.
+// allocate at the moment they need a residual check: real-time solver loops
+// that forbid allocation after start-up (cudaMalloc may block and synchronise
+// the device), and hosts whose device memory is a fixed arena handed out by
+// their own allocator.  This entry point reads arrays the caller already owns
+// and reduces through a fixed-size scratch array compiled into the library
+// instead.
+//
+// The scratch address is looked up once per device and kept for the life of
+// the process; a cudaDeviceReset in the caller's process invalidates it, and
+// the entry point must not be used after one.
 //
 // The scratch array lives in the library image: every GPU that loads the
 // library holds its 512 KiB until the process exits.  All calls share it, so

@@ -64,3 +64,36 @@ def test_product_never_imports_the_oracle():
         if f.endswith((".c", ".h", ".py")):
             text = open(os.path.join(ROOT, "oracle", f)).read()
             assert "paper_2604_06035_gb300" not in text and "cmg_internal" not in text, f
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch(libpath):
+    """The size check comes before any CUDA call, so this runs without a GPU:
+    2^24 + 1 octs would need more block sums than the static scratch holds."""
+    from paper_2604_06035_gb300 import cmg
+    lib = cmg.lib()
+    dummy = ctypes.c_void_p(0x1000)
+    rc = lib.cmg_residual_norm2_noalloc(dummy, None, dummy, dummy, (1 << 24) + 1, 1.0, dummy, ctypes.c_void_p(0))
+    assert rc == cmg.CMG_ERR_INVALID_ARG
+    rc = lib.cmg_residual_norm2_noalloc(dummy, None, dummy, dummy, 8, -1.0, dummy, ctypes.c_void_p(0))
+    assert rc == cmg.CMG_ERR_INVALID_ARG
+
+
+def test_noalloc_binding_checks_array_sizes(libpath):
+    """The binding rejects arrays shorter (or longer) than the n octs the
+    neighbour table implies before it reaches the library."""
+    import numpy as np
+    from paper_2604_06035_gb300 import cmg
+    n = 16
+    nbr = np.zeros((n, 7), dtype=np.int32)
+    good = np.zeros((n, 8))
+    out = np.zeros(1)
+    cases = [
+        (nbr, None, good[:-1], good, out),          # phi short by one oct
+        (nbr, None, good, good[:, :6], out),        # f with 6 values per oct
+        (nbr, np.zeros((n, 6)), good, good, out),   # ghosts [n][6] instead of [n][6][4]
+        (nbr[:, :6], None, good, good, out),        # neighbours [n][6]
+        (nbr, None, good, good, np.zeros(0)),       # no room for the result
+    ]
+    for neighbors, ghosts, phi, f, norm2 in cases:
+        with pytest.raises(ValueError):
+            cmg.cmg_residual_norm2_noalloc(neighbors, ghosts, phi, f, 1.0, norm2)

@@ -1,11 +1,11 @@
 """The allocation-free residual norm (cmg_residual_norm2_noalloc).
 
 It serves callers that cannot allocate device memory when they check a
-residual: code running during CUDA-graph capture, real-time loops that forbid
-allocation after start-up, hosts that own all device memory in an arena.  It
-must agree with the library's own residual norm (cmg_level_mg_step with
-CMG_OP_RESIDUAL, which reduces through scratch the level allocated), call
-after call, since every call reuses the same static scratch array.
+residual: real-time loops that forbid allocation after start-up, hosts that
+own all device memory in an arena of their own.  It must agree with the
+library's own residual norm (cmg_level_mg_step with CMG_OP_RESIDUAL, which
+reduces through scratch the level allocated), call after call, since every
+call reuses the same static scratch array.
 
 This file sorts last so that a stop-at-first-failure run has already run every
 other test; it also passes on its own in a fresh process."""
