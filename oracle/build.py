@@ -1,4 +1,5 @@
-"""Compile the C oracle (oracle.c) into oracle/liboracle.so with gcc.
+"""Compile the C oracle (oracle.c) into oracle/liboracle.so with gcc (with
+OpenMP when available, for or_set_threads).
 
 Test infrastructure only.  -ffp-contract=off keeps the written arithmetic
 (no fused multiply-add contraction), so the oracle computes what it states.
@@ -20,7 +21,12 @@ def build(force: bool = False) -> str:
     tmp = LIB + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
            "-Wall", "-o", tmp] + srcs + ["-lm"]
-    subprocess.check_call(cmd)
+    # OpenMP (or_set_threads) where the compiler has it; a build without it
+    # runs every loop on one thread and computes the same bits.
+    try:
+        subprocess.check_call(cmd[:1] + ["-fopenmp"] + cmd[1:], stderr=subprocess.DEVNULL)
+    except (subprocess.CalledProcessError, OSError):
+        subprocess.check_call(cmd)
     os.replace(tmp, LIB)
     return LIB
 

@@ -13,6 +13,34 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the per-oct loops (1 unless or_set_threads asks for more).  A
+ * loop runs in parallel only where every iteration writes its own cells and
+ * reads nothing another iteration writes: the cells of one colour in a
+ * red-black pass (their neighbours are all of the other colour), the residual
+ * of each cell, restriction, prolongation, ghost values, element-wise vector
+ * updates.  Sums over cells (norms, dot products, the mean) stay serial in
+ * the same order, so results are bit-identical for any thread count. */
+static int or_threads = 1;
+#ifdef _OPENMP
+#define OR_PAR_FOR _Pragma("omp parallel for schedule(static) num_threads(or_threads) if (or_threads > 1)")
+#else
+#define OR_PAR_FOR
+#endif
+
+int or_set_threads(int n) {
+#ifdef _OPENMP
+  or_threads = n < 1 ? 1 : n;
+#else
+  (void)n;
+  or_threads = 1;
+#endif
+  return or_threads;
+}
+int or_get_threads(void) { return or_threads; }
 
 #define MORTON_BITS 21      /* 64-bit keys (Sec. 4.2) */
 #define MORTON_BITS_WIDE 42 /* 128-bit keys (Sec. 4.2) */
@@ -230,6 +258,7 @@ static int parity(int c) { return ((c & 1) + ((c >> 1) & 1) + ((c >> 2) & 1)) & 
 static int build_nbr(mglev *g, uint64_t npd, int pmask) {
   g->nbr = (int32_t *)malloc(sizeof(int32_t) * 7 * (g->n ? g->n : 1));
   if (!g->nbr) return OR_ERR_OOM;
+  OR_PAR_FOR
   for (int64_t i = 0; i < g->n; i++) {
     g->nbr[7 * i] = (int32_t)i;
     for (int d = 0; d < 6; d++) {
@@ -532,6 +561,7 @@ void or_level_father_cells(const or_level *L, int32_t *out) {
 
 /* Source term f = 4 pi G (rho - rho_bar) (Sec. 5.1.1 item (iii)). */
 void or_level_set_density(or_level *L, const double *rho, double rho_bar, double four_pi_g) {
+  OR_PAR_FOR
   for (int64_t t = 0; t < 8 * L->n; t++) L->mg[0].f[t] = four_pi_g * (rho[t] - rho_bar);
 }
 
@@ -549,6 +579,7 @@ void or_level_compute_ghosts(or_level *L) {
   if (!L->parent) return;
   const mglev *g = &L->mg[0];
   const mglev *pg = &L->parent->mg[0];
+  OR_PAR_FOR
   for (int64_t i = 0; i < L->n; i++)
     for (int d = 0; d < 6; d++) {
       if (g->nbr[7 * i + 1 + d] >= 0) continue;
@@ -621,6 +652,7 @@ void or_rb_sweeps(or_level *L, int m, int n_sweeps, int use_ghost) {
   double h = cell_h(g->lev, L->nx), h2 = h * h, inv6 = 1.0 / 6.0;
   for (int s = 0; s < n_sweeps; s++)
     for (int color = 0; color < 2; color++)
+      OR_PAR_FOR
       for (int64_t i = 0; i < g->n; i++)
         for (int c = 0; c < 8; c++) {
           if (parity(c) != color || !g->active[8 * i + c]) continue;
@@ -634,6 +666,7 @@ void or_rb_sweeps(or_level *L, int m, int n_sweeps, int use_ghost) {
 double or_residual(or_level *L, int m, int use_ghost) {
   mglev *g = &L->mg[m];
   double h = cell_h(g->lev, L->nx), h2 = h * h, norm2 = 0.0;
+  OR_PAR_FOR
   for (int64_t i = 0; i < g->n; i++)
     for (int c = 0; c < 8; c++) {
       double r = 0.0;
@@ -642,14 +675,15 @@ double or_residual(or_level *L, int m, int use_ghost) {
         r = g->f[8 * i + c] - (sum - 6.0 * g->phi[8 * i + c]) / h2;
       }
       g->r[8 * i + c] = r;
-      norm2 += r * r;
     }
+  for (int64_t t = 0; t < 8 * g->n; t++) norm2 += g->r[t] * g->r[t];
   return norm2;
 }
 
 /* Coarse value = mean of the eight fine children (Sec. 5.1.1). */
 void or_restrict(or_level *L, int m) {
   mglev *g = &L->mg[m], *cg = &L->mg[m + 1];
+  OR_PAR_FOR
   for (int64_t p = 0; p < cg->n; p++)
     for (int cc = 0; cc < 8; cc++) {
       double v = 0.0;
@@ -667,6 +701,7 @@ void or_restrict(or_level *L, int m) {
 /* phi[m] += trilinear interpolation of phi[m+1] (Sec. 5.1.1). */
 void or_prolong(or_level *L, int m) {
   mglev *g = &L->mg[m], *cg = &L->mg[m + 1];
+  OR_PAR_FOR
   for (int64_t i = 0; i < g->n; i++)
     for (int c = 0; c < 8; c++) {
       if (!g->active[8 * i + c]) continue;
@@ -730,6 +765,7 @@ static void subtract_mean(double *phi, int64_t n) {
   double s = 0.0;
   for (int64_t t = 0; t < n; t++) s += phi[t];
   s /= (double)n;
+  OR_PAR_FOR
   for (int64_t t = 0; t < n; t++) phi[t] -= s;
 }
 
@@ -812,6 +848,7 @@ static void sweeps32(or_level *L, int m, int n_sweeps) {
   float h = (float)cell_h(g->lev, L->nx), h2 = h * h, inv6 = 1.0f / 6.0f;
   for (int s = 0; s < n_sweeps; s++)
     for (int color = 0; color < 2; color++)
+      OR_PAR_FOR
       for (int64_t i = 0; i < g->n; i++)
         for (int c = 0; c < 8; c++) {
           if (parity(c) != color || !g->active[8 * i + c]) continue;
@@ -823,6 +860,7 @@ static void sweeps32(or_level *L, int m, int n_sweeps) {
 static void residual32(or_level *L, int m) {
   mglev *g = &L->mg[m];
   float h = (float)cell_h(g->lev, L->nx), h2 = h * h;
+  OR_PAR_FOR
   for (int64_t i = 0; i < g->n; i++)
     for (int c = 0; c < 8; c++) {
       float r = 0.0f;
@@ -833,6 +871,7 @@ static void residual32(or_level *L, int m) {
 
 static void restrict32(or_level *L, int m) {
   mglev *g = &L->mg[m], *cg = &L->mg[m + 1];
+  OR_PAR_FOR
   for (int64_t p = 0; p < cg->n; p++)
     for (int cc = 0; cc < 8; cc++) {
       float v = 0.0f;
@@ -849,6 +888,7 @@ static void restrict32(or_level *L, int m) {
 
 static void prolong32(or_level *L, int m) {
   mglev *g = &L->mg[m], *cg = &L->mg[m + 1];
+  OR_PAR_FOR
   for (int64_t i = 0; i < g->n; i++)
     for (int c = 0; c < 8; c++) {
       if (!g->active[8 * i + c]) continue;
@@ -920,11 +960,13 @@ int or_level_solve_mixed(or_level *L, const or_params *p, int inner_cycles, or_s
   if (p->fixed_cycles == 0 && rel <= p->tol) return OR_OK;
   for (int cyc = 1; cyc <= target; cyc++) {
     double nrm = sqrt(nr);
+    OR_PAR_FOR
     for (int64_t t = 0; t < 8 * L->n; t++) {
       g->f32[t] = (float)(g->r[t] / nrm);
       g->phi32[t] = 0.0f;
     }
     for (int k = 0; k < inner_cycles; k++) vcycle32(L, 0, p);
+    OR_PAR_FOR
     for (int64_t t = 0; t < 8 * L->n; t++) g->phi[t] += nrm * (double)g->phi32[t];
     if (L->periodic_full) subtract_mean(g->phi, 8 * L->n);
     nr = or_residual(L, 0, 1);

@@ -43,6 +43,15 @@ enum {
   OR_ERR_DIVERGED = -8
 };
 
+/* ---- threads ----
+ * Threads of the oracle's per-oct loops (default 1; needs an OpenMP build,
+ * else stays 1).  Returns the count now in force.  Results are bit-identical
+ * for every thread count: only loops whose iterations write disjoint cells
+ * and read nothing another iteration writes run in parallel, and every sum
+ * over cells stays serial. */
+int or_set_threads(int n);
+int or_get_threads(void);
+
 /* ---- keys ---- */
 uint64_t or_morton_encode(uint32_t i, uint32_t j, uint32_t k);
 void or_morton_decode(uint64_t m, uint32_t *i, uint32_t *j, uint32_t *k);

@@ -39,6 +39,8 @@ def lib():
         path = _build.build()
         L = C.CDLL(path)
         sig = {
+            "or_set_threads": (C.c_int, [C.c_int]),
+            "or_get_threads": (C.c_int, []),
             "or_morton_encode": (C.c_uint64, [C.c_uint32] * 3),
             "or_encode_many": (None, [_P, _I64, _P]),
             "or_decode_many": (None, [_P, _I64, _P]),
@@ -87,6 +89,16 @@ def lib():
             fn.argtypes = args
         _lib = L
     return _lib
+
+
+def set_threads(n):
+    """Threads of the oracle's per-oct loops (results are bit-identical for
+    any count); returns the count in force (1 without OpenMP)."""
+    return int(lib().or_set_threads(int(n)))
+
+
+def get_threads():
+    return int(lib().or_get_threads())
 
 
 def _ptr(a):
