@@ -2,20 +2,29 @@
 """Benchmark of the level-by-level multigrid Poisson solve (cuRAMSES,
 arXiv 2604.06035) on one GB300 per rank.
 
-Workload (default "two_level_128"): periodic 128^3 base level (lognormal
-density, sigma_ln rho = 1.5, P(k) ~ k^-2, seed 2) plus one refined level on
-the cells above 8 rho_bar (face-dilated, ~1.4 M fine cells).  A step solves
-both levels, base then fine (Dirichlet ghosts from the base phi), each from
-phi = 0 to relative residual 1e-10, through libcmg.so.  Inputs (keys,
-densities) are resident in HBM when the timed region starts; L2 is flushed
-(512 MiB write) before every timed step, outside its CUDA-event interval.
+Workload (default "amr3_256"): the periodic 256^3 base level (lognormal
+density, sigma_ln rho = 2, P(k) ~ k^-2, seed 3) plus three levels refined
+where rho > 8 rho_bar (face-dilated, properly nested): 2.10 M, 1.75 M,
+0.94 M and 1.64 M octs, 51.5 M cells.  A step solves the four levels in FP64,
+level by level (each after its parent, whose phi gives the coarse-fine
+Dirichlet values), each from phi = 0 to relative residual 1e-10, through
+libcmg.so.  Inputs (keys, densities) are resident in HBM when the timed
+region starts; every level's fields are far larger than L2, and L2 is also
+flushed (512 MiB write) before every timed step, outside its event interval.
 
 metric: cell-updates per second (a cell visited by one full red-black sweep,
 summed over all multigrid levels), whole job over all ranks.  With --gpus N
 each rank solves its own replica (the level solve is not sharded): "weak".
 
---impl reference times the CPU FP64 oracle (test infrastructure, single
-thread) on a bounded sample of the same workload: one V-cycle of each level.
+Extra blocks: the same workload in mixed precision and with the FFT base
+solve, the 128^3 two-level workload, the 32^3 periodic workload, 512 batched
+patches, the smoother alone on 512^3, FFT and CG comparisons, the learned warm
+start, and phi against the FP64 oracle for every workload (outside the timed
+region).
+
+cpu_baseline / --impl reference: the CPU FP64 oracle (test infrastructure)
+as it stands, on the host cores (OpenMP over its per-oct loops, bit-identical
+to one thread), on bounded samples of the same workload.
 """
 import argparse
 import json
@@ -30,7 +39,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-FP64_PEAK_TFLOPS = 1.25  # GB300 nominal FP64 (profiling recipe); FMA = 2 flops
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 
 
@@ -40,15 +48,18 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="two_level_128", choices=["two_level_128"])
-    ap.add_argument("--quick", action="store_true", help="timed steps only (profiling runs)")
+    ap.add_argument("--workload", default="amr3_256", choices=["amr3_256"])
+    ap.add_argument("--quick", action="store_true", help="timed steps only: no e2e, extra blocks or CPU baseline "
+                                                          "(profiling runs)")
     ap.add_argument("--tol", type=float, default=1e-10)
-    ap.add_argument("--learned-traj", type=int, default=128,
+    ap.add_argument("--learned-traj", type=int, default=256,
                     help="trajectories of 8 steps for the learned warm start (1/16 held out)")
     ap.add_argument("--train-seconds", type=float, default=60.0, help="U-Net training budget")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start block")
-    ap.add_argument("--no-amr3", action="store_true", help="skip the 256^3 + 3-level mixed-precision block")
-    ap.add_argument("--block", choices=["smoother", "learned", "forward", "fft", "pcg", "amr3", "batched"], default=None,
+    ap.add_argument("--no-extra", action="store_true", help="headline, e2e and cpu_baseline only")
+    ap.add_argument("--no-oracle-errors", action="store_true", help="skip the phi-vs-oracle block")
+    ap.add_argument("--block", choices=["smoother", "learned", "forward", "fft", "pcg", "amr3", "batched", "two_level",
+                                        "periodic32", "oracle_errors"], default=None,
                     help="run one sub-benchmark alone and print its JSON (profiling runs)")
     ap.add_argument("--smoother-level", type=int, default=9, help="level of the full periodic grid (9 = 512^3)")
     ap.add_argument("--fft-level", type=int, default=9, help="level of the fft block's full periodic grid")
@@ -157,6 +168,24 @@ def read_peaks():
     return out
 
 
+def vcycle_bytes(mg_octs, elem, n_sweeps, coarse_sweeps=None):
+    """Algorithmic HBM bytes of one V-cycle over a hierarchy of mg_octs octs
+    per level, with perfect reuse: a sweep reads the other colour and g and
+    writes its own colour (3 values) plus 3 B of neighbour index per cell; the
+    residual + restriction reads phi and g, 3 B of index, writes 1/8 of a
+    value; the prolongation reads 1/8 of a value and rewrites phi (2 values).
+    The coarsest level gets coarse_sweeps sweeps (default n_sweeps)."""
+    total = 0.0
+    last = len(mg_octs) - 1
+    for m, nm in enumerate(mg_octs):
+        cells = 8.0 * nm
+        sw = n_sweeps if m < last or coarse_sweeps is None else coarse_sweeps
+        total += sw * cells * (3 * elem + 3)
+        if m < last:
+            total += cells * (2 * elem + 3 + elem / 8.0) + cells * (2 * elem + elem / 8.0)
+    return total
+
+
 def cycle_updates(n_octs_per_mg, n_pre=2, n_post=2, coarse_sweeps=4, exact_coarse=True):
     u = sum((n_pre + n_post) * 8 * n for n in n_octs_per_mg[:-1])
     if not exact_coarse:
@@ -166,67 +195,141 @@ def cycle_updates(n_octs_per_mg, n_pre=2, n_post=2, coarse_sweeps=4, exact_coars
 
 # ------------------------------------------------------------- reference
 
-def two_level_workload(n_fine_octs, tol):
-    """The `config.workload` text of the two-level benchmark (both arms)."""
-    return ("two_level_128: 128^3 periodic lognormal base (sigma 1.5, k^-2) + 1 refined level "
-            "(rho > 8 rho_bar, %d fine octs); FP64 V(2,2) to rel. residual %g per level" % (n_fine_octs, tol))
+def host_cores():
+    """Cores this process may run on (the CPU baseline's thread count)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def amr3_workload(octs, tol):
+    """The `config.workload` text of the headline benchmark (both arms)."""
+    return ("amr3_256: 256^3 periodic lognormal base (sigma 2, k^-2, seed 3) + 3 levels refined at rho > 8 rho_bar "
+            "(%s octs, %d cells); FP64 V(2,2) from phi = 0 to rel. residual %g per level, level by level"
+            % ("/".join(str(int(o)) for o in octs), 8 * int(sum(octs)), tol))
+
+
+def oracle_levels(cfg, n=None):
+    """Oracle levels of a workload (each with its parent), densities set."""
+    import oracle as O
+    levels, parent = [], None
+    for lev, c, r in list(zip(cfg["levels"], cfg["coords"], cfg["rho"]))[:n]:
+        L = O.Level(lev, O.morton_encode(c), parent=parent)
+        L.set_density(r, cfg.get("rho_bar", 1.0))
+        levels.append(L)
+        parent = L
+    return levels
+
+
+def oracle_updates(L, k):
+    """Cell updates of one oracle V(2,2) cycle on the k-th level of a chain
+    (the base level's coarsest 2^3 level is solved exactly, a refined level's
+    coarsest gets its red-black sweeps), as the library counts them."""
+    return cycle_updates([L.mg_n_octs(m) for m in range(L.mg_depth)], exact_coarse=(k == 0))
 
 
 def run_reference(args, rank, world):
-    import numpy as np  # noqa: F401
+    """The oracle as it stands on the headline workload, on all host cores:
+    each step is one FP64 V(2,2) cycle of one level of the chain, the levels
+    taken in turn (level 8, 9, 10, 11, 8, ...), so that K steps sample every
+    level of the workload about equally.  Builds and the ghost values from
+    the parent's phi are outside the timed region."""
     import oracle as O
     from paper_2604_06035_gb300 import inputs
     if rank != 0:
         return
-    cfg = inputs.two_level_amr(base_level=7, seed=2)
-    B = O.Level(7, O.morton_encode(cfg["coords"][0]))
-    F = O.Level(8, O.morton_encode(cfg["coords"][1]), parent=B)
-    B.set_density(cfg["rho"][0], 1.0)
-    F.set_density(cfg["rho"][1], 1.0)
-    ub = cycle_updates([B.mg_n_octs(m) for m in range(B.mg_depth)], exact_coarse=True)
-    uf = cycle_updates([F.mg_n_octs(m) for m in range(F.mg_depth)], exact_coarse=False)
+    cores = host_cores()
+    threads = O.set_threads(cores)
+    cfg = inputs.mixed_amr()
+    levels = oracle_levels(cfg)
+    upd = [oracle_updates(L, k) for k, L in enumerate(levels)]
 
-    def step():
-        B.solve(fixed_cycles=1)
-        F.solve(fixed_cycles=1)
+    def step(k):
+        levels[k % len(levels)].solve(fixed_cycles=1)
 
-    for _ in range(args.warmup):
-        step()
+    for k in range(args.warmup):
+        step(k)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
+    total = 0
+    for k in range(args.steps):
+        step(k)
+        total += upd[k % len(levels)]
     dt = (time.perf_counter() - t0) / args.steps
-    value = (ub + uf) / dt / 1e6
-    sample = "one FP64 V(2,2) cycle on the 128^3 base and one on the refined level per step"
+    value = total / args.steps / dt / 1e6
+    sample = ("one FP64 V(2,2) cycle per step, of levels 8, 9, 10, 11 in turn (%d threads on %d host cores)"
+              % (threads, cores))
     print(json.dumps({
         "metric": "poisson_cell_updates_per_s", "value": value, "unit": "Mcell-updates/s", "impl": "reference",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": two_level_workload(F.n, args.tol), "l2": "not applicable (CPU oracle)",
-                   "parallelism": "single"},
-        "cpu_baseline": {"value": value, "unit": "Mcell-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "config": {"workload": amr3_workload([len(c) for c in cfg["coords"]], args.tol),
+                   "l2": "not applicable (CPU oracle)", "parallelism": "single"},
+        "cpu_baseline": {"value": value, "unit": "Mcell-updates/s", "cores": threads, "host_cores": cores,
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "Mcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+    O.set_threads(1)
 
 
-def cpu_baseline_sample():
-    """The oracle as it stands on a bounded sample: two V-cycles of each level
-    of the same workload, single thread."""
+def cpu_baseline_sample(cfg_amr3):
+    """The oracle as it stands, timed on the host cores on bounded samples:
+    one FP64 V(2,2) cycle of the headline workload's 256^3 base level on all
+    host cores (OpenMP; bit-identical to one thread) and on one thread, and,
+    labelled separately, one FP64 V(2,2) cycle of a 32-patch subset of the
+    512-patch batched workload on all cores."""
     import oracle as O
     from paper_2604_06035_gb300 import inputs
-    cfg = inputs.two_level_amr(base_level=7, seed=2)
-    B = O.Level(7, O.morton_encode(cfg["coords"][0]))
-    F = O.Level(8, O.morton_encode(cfg["coords"][1]), parent=B)
-    B.set_density(cfg["rho"][0], 1.0)
-    F.set_density(cfg["rho"][1], 1.0)
-    ub = cycle_updates([B.mg_n_octs(m) for m in range(B.mg_depth)], exact_coarse=True)
-    uf = cycle_updates([F.mg_n_octs(m) for m in range(F.mg_depth)], exact_coarse=False)
+    cores = host_cores()
+    threads = O.set_threads(cores)
     t0 = time.perf_counter()
-    B.solve(fixed_cycles=2)
-    F.solve(fixed_cycles=2)
-    dt = time.perf_counter() - t0
-    return {"value": 2 * (ub + uf) / dt / 1e6, "unit": "Mcell-updates/s", "cores": 1, "kind": "oracle",
-            "sample": "two FP64 V(2,2) cycles on the 128^3 base and two on the refined level (%.1f s)" % dt}
+    base = oracle_levels(cfg_amr3, n=1)[0]
+    build_s = time.perf_counter() - t0
+    u = oracle_updates(base, 0)
+    t0 = time.perf_counter()
+    base.solve(fixed_cycles=1)
+    dt_all = time.perf_counter() - t0
+    O.set_threads(1)
+    t0 = time.perf_counter()
+    base.solve(fixed_cycles=1)
+    dt_one = time.perf_counter() - t0
+    del base
+    out = {"value": u / dt_all / 1e6, "unit": "Mcell-updates/s", "cores": threads, "host_cores": cores,
+           "kind": "oracle",
+           "sample": "one FP64 V(2,2) cycle of the 256^3 base level (%d cell updates) on %d threads: %.2f s; "
+                     "oracle build %.1f s untimed" % (u, threads, dt_all, build_s),
+           "single_thread": {"value": u / dt_one / 1e6, "unit": "Mcell-updates/s", "cores": 1,
+                             "sample": "the same cycle on one thread: %.2f s" % dt_one}}
+    # 32-patch subset of the batched workload (every 16th patch by size rank)
+    O.set_threads(cores)
+    b = inputs.batched_patches(n_patches=512, seed=4)
+    sub = batched_subset(b, 32)
+    P = O.Level(b["level"] - 1, O.morton_encode(b["parent_coords"]))
+    P.set_phi(b["parent_phi"])
+    F = O.Level(b["level"], O.morton_encode(sub["coords"]), parent=P)
+    F.set_density(sub["rho"], 1.0)
+    uf = oracle_updates(F, 1)
+    t0 = time.perf_counter()
+    F.solve(fixed_cycles=1)
+    dt_p = time.perf_counter() - t0
+    out["batched_subset"] = {"value": uf / dt_p / 1e6, "unit": "Mcell-updates/s", "cores": threads,
+                             "sample": "one FP64 V(2,2) cycle of 32 of the 512 patches (%d octs, every 16th by size); "
+                                       "the batched block's GPU figure covers all 512" % len(sub["coords"])}
+    O.set_threads(1)
+    return out
+
+
+def batched_subset(b, k):
+    """k patches of a batched workload, every (n/k)-th by size rank: their
+    octs (in patch order), densities and offsets."""
+    import numpy as np
+    off = np.asarray(b["offsets"])
+    sizes = np.diff(off)
+    order = np.argsort(sizes, kind="stable")
+    pick = np.sort(order[::max(1, len(sizes) // k)][:k])
+    idx = np.concatenate([np.arange(off[p], off[p + 1]) for p in pick])
+    new_off = np.concatenate([[0], np.cumsum(sizes[pick])])
+    return {"coords": b["coords"][idx], "rho": b["rho"][idx], "offsets": new_off, "patches": pick, "index": idx}
 
 
 # ------------------------------------------------------------------- ours
@@ -275,6 +378,26 @@ def bench_batched(cmg, ctx, dev, stream, args):
         res[name] = {"ms_per_solve": statistics.median(ms), "Mcell_updates_per_s": upd / (sum(ms) / 1e3) / 1e6,
                      "cycles": st["cycles"], "rel_max": st["rel_max"], "n_converged": st["n_converged"],
                      "grid_barriers": st["grid_barriers"], "status": rc}
+        if kr == 0:
+            # algorithmic bytes of the solve: per outer step, the V-cycles
+            # (FP32 inner cycles in mixed precision) plus, per step, the FP64
+            # residual with its norm (phi, g, index: 19 B per fine cell) and in
+            # mixed precision the FP32 right-hand side (4 B) and phi += S e
+            # (20 B)
+            sch = cmg.cmg_batch_get_schedule(B)
+            nsw = sch["n_pre"] + sch["n_post"]
+            mg = [cmg.cmg_level_mg_info(F, m)[0] for m in range(cmg.cmg_level_mg_depth(F))]
+            cells0 = 8.0 * mg[0]
+            if prec == cmg.CMG_PREC_MIXED:
+                per_step = sch["inner_cycles"] * vcycle_bytes(mg, 4, nsw) + cells0 * (19 + 4 + 20)
+            else:
+                per_step = vcycle_bytes(mg, 8, nsw) + cells0 * 19
+            nbytes = per_step * st["cycles"]
+            gbs = nbytes / (res[name]["ms_per_solve"] / 1e3) / 1e9
+            res[name]["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": read_peaks()["hbm"], "unit": "GB/s",
+                                     "frac": gbs / read_peaks()["hbm"], "bytes_per_solve": nbytes,
+                                     "bytes_per_fine_cell_per_step": per_step / cells0,
+                                     "kernel": "k_batch (one persistent launch per solve)"}
     cmg.cmg_batch_destroy(B)
     cmg.cmg_level_destroy(F)
     cmg.cmg_level_destroy(P)
@@ -406,70 +529,179 @@ def bench_pcg(cmg, ctx, dev, levels, args):
     return out
 
 
-def bench_amr3(cmg, ctx, dev, args):
-    """The 256^3 mixed-precision workload: periodic lognormal base (sigma 2)
-    plus three levels refined where rho > 8 rho_bar, solved level by level
-    (each after its parent, whose phi gives the coarse-fine values) from phi = 0
-    to rel. residual tol: FP64 V-cycles, FP32 V-cycles inside FP64 refinement,
-    and the FFT solve of the base under mixed fine levels; phi of the mixed
-    chain against the FP64 one."""
+def load_chain(cmg, ctx, dev, cfg):
+    """Build a workload's levels on the device, each with its parent; returns
+    (levels, rho device tensors, zero tensors)."""
     import torch
-    from paper_2604_06035_gb300 import inputs
-    t0 = time.perf_counter()
-    cfg = inputs.mixed_amr()
-    gen_s = time.perf_counter() - t0
     levels, parent = [], None
-    for lev, c, r in zip(cfg["levels"], cfg["coords"], cfg["rho"]):
-        L = cmg.cmg_level_build(ctx, lev, cmg.cmg_morton_encode(ctx, torch.from_numpy(c).to(dev)), parent=parent)
-        rho = torch.from_numpy(r).to(dev)
-        cmg.cmg_level_set_density(L, rho, cfg["rho_bar"])
-        levels.append((lev, L, rho))
+    for lev, c in zip(cfg["levels"], cfg["coords"]):
+        keys = cmg.cmg_morton_encode(ctx, torch.from_numpy(c).to(dev))
+        L = cmg.cmg_level_build(ctx, lev, keys, parent=parent)
+        levels.append(L)
         parent = L
-    out = {"workload": "256^3 periodic lognormal base (sigma 2, k^-2) + 3 levels refined at rho > 8 rho_bar",
-           "levels": cfg["levels"], "octs": [len(c) for c in cfg["coords"]],
-           "cells": int(sum(8 * len(c) for c in cfg["coords"])), "generate_s": gen_s, "tol": args.tol}
+    rho = [torch.from_numpy(r).to(dev) for r in cfg["rho"]]
+    return levels, rho, [torch.zeros_like(r) for r in rho]
 
-    def chain(precs, reps=5):
-        per = [[] for _ in levels]
-        stats = [None] * len(levels)
-        for _ in range(reps):
-            for k, (lev, L, rho) in enumerate(levels):
-                cmg.cmg_level_set_phi(L, torch.zeros_like(rho))
-                rc, st = cmg.cmg_level_solve(L, tol=args.tol, precision=precs[k])
-                per[k].append(st["ms"])
-                stats[k] = st
-        ms = [statistics.median(p[1:]) for p in per]
-        upd = sum(st["cell_updates"] for st in stats)
-        return {"ms_to_tol_per_level": ms, "ms_total": sum(ms),
-                "iterations": [st["cycles"] for st in stats], "rel_final": [st["rel_final"] for st in stats],
-                "Mcell_updates_per_s": upd / (sum(ms) / 1e3) / 1e6}
 
+def chain_step(cmg, levels, rho, zeros, rho_bar, tol, precs):
+    """One step of a chain: every level's phi = 0 and density, every solve
+    queued level by level (a level's coarse-fine values read its parent's phi
+    in stream order), then every report."""
+    for L, r, z in zip(levels, rho, zeros):
+        cmg.cmg_level_set_phi(L, z)
+        cmg.cmg_level_set_density(L, r, rho_bar)
+    for L, p in zip(levels, precs):
+        cmg.cmg_level_solve_async(L, tol=tol, precision=p)
+    return [cmg.cmg_level_solve_wait(L)[1] for L in levels]
+
+
+def time_chain(cmg, levels, rho, zeros, rho_bar, tol, precs, reps=5, flush=None):
+    """Median per-level time to tol over reps steps (after one untimed)."""
+    per = [[] for _ in levels]
+    stats = None
+    for k in range(reps + 1):
+        if flush is not None:
+            flush.fill_(k & 0xFF)
+        stats = chain_step(cmg, levels, rho, zeros, rho_bar, tol, precs)
+        if k:
+            for j, st in enumerate(stats):
+                per[j].append(st["ms"])
+    ms = [statistics.median(p) for p in per]
+    upd = sum(st["cell_updates"] for st in stats)
+    return {"ms_to_tol_per_level": ms, "ms_total": sum(ms), "iterations": [st["cycles"] for st in stats],
+            "rel_final": [st["rel_final"] for st in stats], "Mcell_updates_per_s": upd / (sum(ms) / 1e3) / 1e6}
+
+
+def rel_err(a, b):
+    """max |a - b| / max |b| (torch or numpy)."""
+    import numpy as np
+    a = a.detach().cpu().numpy() if hasattr(a, "detach") else np.asarray(a)
+    b = b.detach().cpu().numpy() if hasattr(b, "detach") else np.asarray(b)
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def bench_amr3(cmg, ctx, dev, args, chain, phi64, flush=None):
+    """The headline workload in mixed precision (FP32 V-cycles inside FP64
+    refinement) and with the FFT solve of the base under mixed fine levels,
+    time to rel. residual tol level by level; phi of each chain against the
+    FP64 chain at the benchmark tolerance and with both refined to 1e-12; the
+    mixed chain's FP32 smoother rate."""
+    levels, rho, zeros, rho_bar = chain
     F64, MIX, FFT = cmg.CMG_PREC_FP64, cmg.CMG_PREC_MIXED, cmg.CMG_PREC_FFT
-    out["fp64"] = chain([F64] * len(levels))
-    phi64 = [cmg.cmg_level_get_phi(L, device=True).clone() for _, L, _ in levels]
-    out["mixed"] = chain([MIX] * len(levels))
-    err = []
-    for (lev, L, rho), p64 in zip(levels, phi64):
-        p = cmg.cmg_level_get_phi(L, device=True)
-        err.append(float((p - p64).abs().max() / p64.abs().max()))
-    out["mixed"]["phi_rel_err_vs_fp64"] = err
+    n = len(levels)
+    out = {"tol": args.tol}
+    out["mixed"] = time_chain(cmg, levels, rho, zeros, rho_bar, args.tol, [MIX] * n, flush=flush)
+    out["mixed"]["phi_rel_err_vs_fp64_gpu"] = [rel_err(cmg.cmg_level_get_phi(L, device=True), p)
+                                               for L, p in zip(levels, phi64)]
+    out["fft_base_mixed_fine"] = time_chain(cmg, levels, rho, zeros, rho_bar, args.tol, [FFT] + [MIX] * (n - 1),
+                                            flush=flush)
+    out["fft_base_mixed_fine"]["phi_rel_err_vs_fp64_gpu"] = [
+        rel_err(cmg.cmg_level_get_phi(L, device=True), p) for L, p in zip(levels, phi64)]
     # the precision effect alone: both chains refined to 1e-12 (untimed)
     tight = []
-    for precs in ([F64] * len(levels), [MIX] * len(levels)):
-        got = []
-        for k, (lev, L, rho) in enumerate(levels):
-            cmg.cmg_level_set_phi(L, torch.zeros_like(rho))
-            cmg.cmg_level_solve(L, tol=1e-12, precision=precs[k])
-            got.append(cmg.cmg_level_get_phi(L, device=True).clone())
-        tight.append(got)
-    out["mixed"]["phi_rel_err_vs_fp64_both_at_1e-12"] = [
-        float((b - a).abs().max() / a.abs().max()) for a, b in zip(*tight)]
-    out["fft_base_mixed_fine"] = chain([FFT] + [MIX] * (len(levels) - 1))
-    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_total"] / out["mixed"]["ms_total"]
-    out["speedup_fft_mixed_vs_fp64"] = out["fp64"]["ms_total"] / out["fft_base_mixed_fine"]["ms_total"]
-    for _, L, _ in reversed(levels):
-        cmg.cmg_level_destroy(L)
+    for precs in ([F64] * n, [MIX] * n):
+        chain_step(cmg, levels, rho, zeros, rho_bar, 1e-12, precs)
+        tight.append([cmg.cmg_level_get_phi(L, device=True).clone() for L in levels])
+    out["mixed"]["phi_rel_err_vs_fp64_gpu_both_at_1e-12"] = [rel_err(b, a) for a, b in zip(*tight)]
+    # the FP32 smoother of the mixed chain, launch by launch
+    cmg.cmg_ctx_reset_profile(ctx)
+    cmg.cmg_ctx_set_profiling(ctx, True)
+    chain_step(cmg, levels, rho, zeros, rho_bar, args.tol, [MIX] * n)
+    cmg.cmg_ctx_set_profiling(ctx, False)
+    prof = cmg.cmg_ctx_get_profile(ctx)
+    peaks = read_peaks()
+    sw = prof.get("rbgs_fp32")
+    if sw and sw["ms"] > 0:
+        gbs = sw["bytes"] / (sw["ms"] / 1e3) / 1e9
+        out["mixed"]["roofline_smoother"] = {
+            "bound": "hbm", "kernel": "rbgs_fp32", "achieved": gbs, "peak": peaks["hbm"], "unit": "GB/s",
+            "frac": gbs / peaks["hbm"], "peak_source": peaks["hbm_src"], "launches": sw["launches"],
+            "share_of_kernel_ms": sw["ms"] / sum(v["ms"] for v in prof.values())}
+    out["mixed"]["kernels"] = {k: {"launches": v["launches"], "ms": round(v["ms"], 4)} for k, v in prof.items()
+                               if v["launches"]}
     return out
+
+
+def bench_small_chain(cmg, ctx, dev, args, cfg, name):
+    """Time to rel. residual tol, FP64 and mixed, of a smaller workload (the
+    128^3 two-level and the 32^3 periodic ones)."""
+    levels, rho, zeros = load_chain(cmg, ctx, dev, cfg)
+    n = len(levels)
+    res = {"workload": name, "octs": [cmg.cmg_level_n_octs(L) for L in levels]}
+    for pname, prec in (("fp64", cmg.CMG_PREC_FP64), ("mixed", cmg.CMG_PREC_MIXED)):
+        res[pname] = time_chain(cmg, levels, rho, zeros, cfg["rho_bar"], args.tol, [prec] * n, reps=10)
+    return res, (levels, rho, zeros)
+
+
+def bench_oracle_errors(cmg, ctx, dev, args):
+    """phi of the GPU solves against the FP64 oracle converged to 1e-12, per
+    workload and level, outside any timed region: the GPU chain at the
+    benchmark tolerance and at 1e-12, FP64 and mixed precision.  Workloads:
+    32^3 periodic (full), 128^3 two-level (full), the 256^3 + 3-level
+    hierarchy on a 64^3 base (the full one needs minutes of oracle time), and
+    a 32-patch subset of the batched workload.  The learned warm start's
+    error is in its own block."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_2604_06035_gb300 import inputs
+    threads = O.set_threads(host_cores())
+    F64, MIX = cmg.CMG_PREC_FP64, cmg.CMG_PREC_MIXED
+    res = {"oracle_tol": 1e-12, "oracle_threads": threads,
+           "measure": "max |phi_gpu - phi_oracle| / max |phi_oracle| per level"}
+
+    def chain(cfg):
+        t0 = time.perf_counter()
+        ol = oracle_levels(cfg)
+        for L in ol:
+            L.solve(tol=1e-12, max_cycles=200)
+        ref = [L.get_phi() for L in ol]
+        out = {"oracle_s": time.perf_counter() - t0}
+        levels, rho, zeros = load_chain(cmg, ctx, dev, cfg)
+        for pname, prec in (("fp64", F64), ("mixed", MIX)):
+            for tol in (args.tol, 1e-12):
+                st = chain_step(cmg, levels, rho, zeros, cfg["rho_bar"], tol, [prec] * len(levels))
+                out["%s_tol_%g" % (pname, tol)] = [rel_err(cmg.cmg_level_get_phi(L), r) for L, r in zip(levels, ref)]
+                out["%s_tol_%g_cycles" % (pname, tol)] = [x["cycles"] for x in st]
+        for L in reversed(levels):
+            cmg.cmg_level_destroy(L)
+        return out
+
+    res["periodic_32"] = chain(inputs.periodic_grf_level(5, seed=1))
+    res["two_level_128"] = chain(inputs.two_level_amr(base_level=7, seed=2))
+    res["amr3_64_base"] = chain(inputs.mixed_amr(base_level=6))
+    # batched: 32 patches (every 16th by size) of the 512-patch workload
+    b = inputs.batched_patches(n_patches=512, seed=4)
+    sub = batched_subset(b, 32)
+    t0 = time.perf_counter()
+    P = O.Level(b["level"] - 1, O.morton_encode(b["parent_coords"]))
+    P.set_phi(b["parent_phi"])
+    F = O.Level(b["level"], O.morton_encode(sub["coords"]), parent=P)
+    F.set_density(sub["rho"], 1.0)
+    F.solve(tol=1e-12, max_cycles=200)
+    ref = F.get_phi()
+    out = {"patches": 32, "octs": int(len(sub["coords"])), "oracle_s": time.perf_counter() - t0}
+    Pg = cmg.cmg_level_build(ctx, b["level"] - 1,
+                             cmg.cmg_morton_encode(ctx, torch.from_numpy(b["parent_coords"]).to(dev)))
+    cmg.cmg_level_set_phi(Pg, torch.from_numpy(b["parent_phi"]).to(dev))
+    Fg = cmg.cmg_level_build(ctx, b["level"], cmg.cmg_morton_encode(ctx, torch.from_numpy(sub["coords"]).to(dev)),
+                             parent=Pg)
+    Bg = cmg.cmg_batch_create(Fg, sub["offsets"])
+    rho = torch.from_numpy(sub["rho"]).to(dev)
+    zeros = torch.zeros_like(rho)
+    cmg.cmg_level_set_density(Fg, rho, 1.0)
+    for pname, prec in (("fp64", F64), ("mixed", MIX)):
+        for tol in (args.tol, 1e-12):
+            cmg.cmg_level_set_phi(Fg, zeros)
+            rc, st = cmg.cmg_batch_solve(Bg, tol=tol, precision=prec)
+            out["%s_tol_%g" % (pname, tol)] = rel_err(cmg.cmg_level_get_phi(Fg), ref)
+            out["%s_tol_%g_cycles" % (pname, tol)] = st["cycles"]
+    cmg.cmg_batch_destroy(Bg)
+    cmg.cmg_level_destroy(Fg)
+    cmg.cmg_level_destroy(Pg)
+    res["batched_subset"] = out
+    O.set_threads(1)
+    return res
 
 
 def bench_forward(cmg, ctx, dev, peaks, D=64, batches=(1, 8), reps=20, paths=("tcgen05", "mma_sync")):
@@ -607,6 +839,27 @@ def bench_learned(cmg, ctx, dev, args, peaks):
                                 "launches": conv["launches"], "ms": conv["ms"],
                                 "flops_per_block": conv["flops"] / (5 * 8),
                                 "traffic": traffic_for("conv_fwd_b8"), "traffic_unit": "DRAM bytes per launch"}
+    # phi from the network's start at tol against the FP64 oracle converged to
+    # 1e-12 on the same held-out density (64^3 periodic level)
+    import oracle as O
+    from paper_2604_06035_gb300 import inputs
+    O.set_threads(host_cores())
+    lev = int(round(np.log2(D)))
+    coords = inputs.uniform_oct_coords(lev)
+    ol = O.Level(lev, O.morton_encode(coords))
+    rho_np = rho.double().cpu().numpy().transpose(2, 1, 0)  # (z, y, x) -> [x, y, z]
+    ol.set_density(inputs.dense_to_octs(rho_np, coords), float(rho_np.mean()))
+    ol.solve(tol=1e-12, max_cycles=200)
+    ref = inputs.octs_to_dense(ol.get_phi(), coords, D).transpose(2, 1, 0)
+    O.set_threads(1)
+    pred = W.predict(S, net, rho, prev)
+    errs = {}
+    for name, prec in (("fp64", cmg.CMG_PREC_FP64), ("mixed", cmg.CMG_PREC_MIXED)):
+        for tol in (args.tol, 1e-12):
+            phi, _ = S.solve(rho, pred, tol, prec)
+            errs["%s_tol_%g" % (name, tol)] = rel_err(phi, ref)
+    res["phi_vs_oracle"] = {"pair": "trajectory %d, step %d" % (k, t + 1), "start": "network prediction",
+                            "oracle_tol": 1e-12, **errs}
     f, m = res["fp64"], res["mixed"]
     ws = res["ms_warm_start_per_block_b8"]
     res["summary"] = {
@@ -619,6 +872,33 @@ def bench_learned(cmg, ctx, dev, args, peaks):
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     return res
+
+
+def headline_roofline(prof, peaks, sm_mhz):
+    """Roofline of the dominant kernel family of the timed steps: algorithmic
+    bytes per launch (field values plus the neighbour cache, 27 B per FP64
+    cell update in a colour pass) over its per-launch CUDA-event time, against
+    the measured HBM copy rate; an FP64 family also gets its FP64-issue
+    fraction (6 FP64 instructions per cell update against 2 lanes per SM per
+    clock, 152 SMs at the sampled SM clock), which bounds it first."""
+    dname, d = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    gbs = d["bytes"] / (d["ms"] / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm"], "unit": "GB/s", "frac": gbs / peaks["hbm"],
+            "kernel": dname, "peak_source": peaks["hbm_src"] + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    if dname.startswith("rbgs_") and dname.endswith("fp64"):
+        clk = (sm_mhz or 2070.0) * 1e6
+        instr = d["flops"] * 6.0 / 7.0 / (d["ms"] / 1e3)
+        peak_instr = 2.0 * 152 * clk
+        roof["fp64_issue_frac"] = instr / peak_instr
+        roof["fp64_issue_note"] = ("FP64 lane-instructions/s (6 per cell update: 5 DADD + 1 DFMA) against 2 per SM "
+                                   "per clock x 152 SMs at %.0f MHz; the HBM fraction this bound allows is "
+                                   "%.2f" % (clk / 1e6, (peak_instr / 6.0 * 27.0 / 1e9) / peaks["hbm"]))
+    roof["launches"] = d["launches"]
+    roof["ms_per_launch"] = d["ms"] / d["launches"]
+    roof["bytes_per_launch"] = d["bytes"] / d["launches"]
+    roof["share_of_kernel_ms"] = d["ms"] / sum(v["ms"] for v in prof.values())
+    roof["traffic"] = traffic_for(dname + "_amr3")
+    return roof
 
 
 def run_ours(args, rank, local, world):
@@ -639,7 +919,10 @@ def run_ours(args, rank, local, world):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     ctx = cmg.cmg_ctx_create(local, stream=stream.cuda_stream)
-    cfg = inputs.two_level_amr(base_level=7, seed=2)
+    t0 = time.perf_counter()
+    cfg = inputs.mixed_amr()
+    gen_s = time.perf_counter() - t0
+    rho_bar = cfg["rho_bar"]
     coords = [torch.from_numpy(c).to(dev) for c in cfg["coords"]]
     rho = [torch.from_numpy(r).to(dev) for r in cfg["rho"]]
     zeros = [torch.zeros_like(r) for r in rho]
@@ -647,21 +930,20 @@ def run_ours(args, rank, local, world):
     # setup: keys (a1), hash + neighbour cache + hierarchy (a2, a3), ghost stencils
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    keys = [cmg.cmg_morton_encode(ctx, c) for c in coords]
-    B = cmg.cmg_level_build(ctx, 7, keys[0])
-    F = cmg.cmg_level_build(ctx, 8, keys[1], parent=B)
+    levels, parent = [], None
+    for lev, c in zip(cfg["levels"], coords):
+        L = cmg.cmg_level_build(ctx, lev, cmg.cmg_morton_encode(ctx, c), parent=parent)
+        levels.append(L)
+        parent = L
     torch.cuda.synchronize()
     build_ms = (time.perf_counter() - t0) * 1e3
+    del coords
+    n = len(levels)
+    octs = [cmg.cmg_level_n_octs(L) for L in levels]
+    F64 = cmg.CMG_PREC_FP64
 
-    def step(precision=cmg.CMG_PREC_FP64):
-        # both levels' inputs, both solves queued (the fine level's coarse-fine
-        # values read the base phi in stream order), then both reports
-        for L, r, z in ((B, rho[0], zeros[0]), (F, rho[1], zeros[1])):
-            cmg.cmg_level_set_phi(L, z)
-            cmg.cmg_level_set_density(L, r, 1.0)
-        for L in (B, F):
-            cmg.cmg_level_solve_async(L, tol=args.tol, precision=precision)
-        return [cmg.cmg_level_solve_wait(L)[1] for L in (B, F)]
+    def step(precision=F64):
+        return chain_step(cmg, levels, rho, zeros, rho_bar, args.tol, [precision] * n)
 
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
@@ -699,141 +981,104 @@ def run_ours(args, rank, local, world):
     updates = sum(s["cell_updates"] for st in all_stats for s in st)
     t_max, upd_total = aggregate_ranks(dev_ms, updates, world, dev)
     value = upd_total / (t_max / 1e3) / 1e6
-    st_b, st_f = all_stats[-1]
-
-    # dominant kernel family of the timed region and its roofline
-    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
-    dname, d = dom
-    achieved_tflops = d["flops"] / (d["ms"] / 1e3) / 1e12
-    achieved_gbs = d["bytes"] / (d["ms"] / 1e3) / 1e9
+    last = all_stats[-1]
     peaks = read_peaks()
-    hbm, hbm_src = peaks["hbm"], peaks["hbm_src"]
-    fp64 = dname.endswith("fp64")
-    if fp64:
-        # the sweep issues 6 FP64-pipe instructions (5 DADD + 1 DFMA = 7 flop)
-        # per cell update against 2 per SM per clock: 7/12 of the nominal
-        # flop rate is the pipe's ceiling for this instruction mix
-        pipe_ops = achieved_tflops * 1e12 * 6.0 / 7.0
-        roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved_tflops / FP64_PEAK_TFLOPS, "kernel": dname,
-                    "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (FMA = 2)",
-                    "fp64_pipe_frac": pipe_ops / (FP64_PEAK_TFLOPS * 1e12 / 2.0),
-                    "fp64_pipe_note": "6 FP64 instructions per cell update vs 2 per SM per clock (nominal)",
-                    "hbm_equivalent_gbs": achieved_gbs, "hbm_frac_of_%s" % hbm_src: achieved_gbs / hbm}
-    else:
-        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved_gbs / hbm, "kernel": dname, "peak_source": hbm_src}
-    roofline["traffic"] = traffic_for(dname)
-    roofline["launches"] = d["launches"]
-    roofline["share_of_kernel_ms"] = d["ms"] / sum(v["ms"] for v in prof.values())
+    roofline = headline_roofline(prof, peaks, clocks.get("sm_mhz"))
     roofline["timing"] = ("per-launch CUDA events on the library stream over a repeat of the timed steps "
                           "launched kernel by kernel (%.2f ms/step there)" % (prof_ms / args.steps))
+    phi64 = [cmg.cmg_level_get_phi(L, device=True).clone() for L in levels]
 
     out = {
         "metric": "poisson_cell_updates_per_s", "value": value, "unit": "Mcell-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": two_level_workload(cmg.cmg_level_n_octs(F), args.tol),
-                   "l2": "flushed before each timed step (512 MiB write)", "parallelism": "replicas" if world > 1
-                   else "single"},
-        "time_to_tol_ms": {"base": st_b["ms"], "fine": st_f["ms"]},
-        "cycles": {"base": st_b["cycles"], "fine": st_f["cycles"]},
-        "rel_residual": {"base": st_b["rel_final"], "fine": st_f["rel_final"]},
-        "setup_ms": build_ms,
+        "config": {"workload": amr3_workload(octs, args.tol),
+                   "l2": "inputs larger than L2 (every level's phi + g > 129 MB), and flushed before each timed "
+                         "step (512 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "time_to_tol_ms": {"level_%d" % lv: st["ms"] for lv, st in zip(cfg["levels"], last)},
+        "cycles": {"level_%d" % lv: st["cycles"] for lv, st in zip(cfg["levels"], last)},
+        "rel_residual": {"level_%d" % lv: st["rel_final"] for lv, st in zip(cfg["levels"], last)},
+        "setup_ms": build_ms, "generate_s": gen_s,
         "roofline": roofline,
         "kernels": {k: {"launches": v["launches"], "ms": v["ms"], "GB/s": v["bytes"] / v["ms"] / 1e6,
-                        "TFLOP/s": v["flops"] / v["ms"] / 1e9} for k, v in prof.items()},
+                        "TFLOP/s": v["flops"] / v["ms"] / 1e9} for k, v in prof.items() if v["launches"]},
         "gpu_launches": launches,
         "clocks": clocks,
     }
 
-    if not args.quick:
-        # mixed precision on the same workload (FP32 V-cycles, FP64 refinement)
-        for _ in range(2):
-            step(cmg.CMG_PREC_MIXED)
-        mixed_ms, mixed_upd = 0.0, 0
-        for k in range(args.steps):
-            flush.fill_(k & 0xFF)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            sm = step(cmg.CMG_PREC_MIXED)
-            b.record(stream)
-            torch.cuda.synchronize()
-            mixed_ms += a.elapsed_time(b)
-            mixed_upd += sum(s["cell_updates"] for s in sm)
-        phi_mixed_f = cmg.cmg_level_get_phi(F)
-        cmg.cmg_ctx_reset_profile(ctx)
-        cmg.cmg_ctx_set_profiling(ctx, True)
-        for k in range(args.steps):
-            flush.fill_(k & 0xFF)
-            step(cmg.CMG_PREC_MIXED)
+    if args.quick:
+        # profiling runs: the timed steps only
+        out["e2e"] = None
+        if rank == 0:
+            print(json.dumps(out), flush=True)
         torch.cuda.synchronize()
-        cmg.cmg_ctx_set_profiling(ctx, False)
-        mprof = cmg.cmg_ctx_get_profile(ctx)
-        sw = mprof.get("rbgs_fp32")
-        mixed_roof = None
-        if sw and sw["ms"] > 0:
-            gbs = sw["bytes"] / (sw["ms"] / 1e3) / 1e9
-            mixed_roof = {"bound": "hbm", "kernel": "rbgs_fp32", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                          "frac": gbs / hbm, "peak_source": hbm_src, "launches": sw["launches"],
-                          "share_of_kernel_ms": sw["ms"] / sum(v["ms"] for v in mprof.values()),
-                          "traffic": traffic_for("rbgs_fp32")}
-        step()
-        phi_fp64_f = cmg.cmg_level_get_phi(F)
-        out["mixed"] = {"ms_per_step": mixed_ms / args.steps,
-                        "Mcell_updates_per_s": mixed_upd / (mixed_ms / 1e3) / 1e6,
-                        "time_to_tol_ms": {"base": sm[0]["ms"], "fine": sm[1]["ms"]},
-                        "refinement_steps": {"base": sm[0]["cycles"], "fine": sm[1]["cycles"]},
-                        "phi_rel_diff_vs_fp64_gpu": float(np.max(np.abs(phi_mixed_f - phi_fp64_f)) /
-                                                          np.max(np.abs(phi_fp64_f))),
-                        "roofline_smoother": mixed_roof,
-                        "kernels": {k: {"launches": v["launches"], "ms": v["ms"],
-                                        "GB/s": v["bytes"] / v["ms"] / 1e6 if v["ms"] else None}
-                                    for k, v in mprof.items()}}
+        for L in reversed(levels):
+            cmg.cmg_level_destroy(L)
+        cmg.cmg_ctx_destroy(ctx)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
-        # end to end through the C ABI with host buffers (pinned): H2D densities,
-        # both solves, D2H of both phi arrays
-        pin_rho = [torch.from_numpy(r).pin_memory().numpy() for r in cfg["rho"]]
-        pin_phi = [torch.empty((cmg.cmg_level_n_octs(L), 8), dtype=torch.float64).pin_memory().numpy()
-                   for L in (B, F)]
-        e2e_ms, e2e_upd = 0.0, 0
-        for k in range(args.steps):
-            flush.fill_(k & 0xFF)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            # per level: upload (overlapping the parent's queued solve), solve,
-            # queued read-back (overlapping the next level's solve)
-            for L, r, z, o in zip((B, F), pin_rho, zeros, pin_phi):
-                cmg.cmg_level_set_phi(L, z)  # zero initial guess, already on the device
-                cmg.cmg_level_set_density(L, r, 1.0)
-                cmg.cmg_level_solve_async(L, tol=args.tol)
-                cmg.cmg_level_get_phi_async(L, out=o)
-            for L in (B, F):
-                rc, st = cmg.cmg_level_solve_wait(L)
-                e2e_upd += st["cell_updates"]
-            cmg.cmg_ctx_synchronize(ctx)
-            e2e_ms += (time.perf_counter() - t0) * 1e3
-        h2d = sum(r.nbytes for r in pin_rho)
-        d2h = sum(o.nbytes for o in pin_phi)
-        out["e2e"] = {"value": e2e_upd * world / (e2e_ms / 1e3) / 1e6, "unit": "Mcell-updates/s",
-                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps}
+    # end to end through the C ABI with host buffers (pinned): H2D densities
+    # of the four levels, the four solves, D2H of the four phi arrays
+    pin_rho = [torch.from_numpy(r).pin_memory().numpy() for r in cfg["rho"]]
+    pin_phi = [torch.empty((o, 8), dtype=torch.float64).pin_memory().numpy() for o in octs]
+    e2e_ms, e2e_upd = 0.0, 0
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        # per level: upload (overlapping the parent's queued solve), solve,
+        # queued read-back (overlapping the next level's solve)
+        for L, r, z, o in zip(levels, pin_rho, zeros, pin_phi):
+            cmg.cmg_level_set_phi(L, z)  # zero initial guess, already on the device
+            cmg.cmg_level_set_density(L, r, rho_bar)
+            cmg.cmg_level_solve_async(L, tol=args.tol)
+            cmg.cmg_level_get_phi_async(L, out=o)
+        for L in levels:
+            rc, st = cmg.cmg_level_solve_wait(L)
+            e2e_upd += st["cell_updates"]
+        cmg.cmg_ctx_synchronize(ctx)
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+    h2d = sum(r.nbytes for r in pin_rho)
+    d2h = sum(o.nbytes for o in pin_phi)
+    e2e_max, e2e_upd_total = aggregate_ranks(e2e_ms, e2e_upd, world, dev)
+    out["e2e"] = {"value": e2e_upd_total / (e2e_max / 1e3) / 1e6, "unit": "Mcell-updates/s",
+                  "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_max / args.steps}
+    del pin_rho, pin_phi
+
+    if not args.no_extra:
+        chain = (levels, rho, zeros, rho_bar)
+        out["amr3_mixed"] = bench_amr3(cmg, ctx, dev, args, chain, phi64, flush=flush)
+        fp64_ms = sum(st["ms"] for st in last)
+        out["amr3_mixed"]["fp64_ms_total"] = fp64_ms
+        out["amr3_mixed"]["speedup_mixed_vs_fp64"] = fp64_ms / out["amr3_mixed"]["mixed"]["ms_total"]
+        out["amr3_mixed"]["speedup_fft_mixed_vs_fp64"] = fp64_ms / out["amr3_mixed"]["fft_base_mixed_fine"]["ms_total"]
+        del phi64
+        out["two_level_128"], (tl_levels, tl_rho, _) = bench_small_chain(
+            cmg, ctx, dev, args, inputs.two_level_amr(base_level=7, seed=2), "128^3 lognormal (sigma 1.5) + 1 level")
+        out["periodic_32"], (p32, _, _) = bench_small_chain(
+            cmg, ctx, dev, args, inputs.periodic_grf_level(5, seed=1), "32^3 periodic, rho = 1 + GRF (rms 0.5)")
+        cmg.cmg_level_destroy(p32[0])
         out["batched"] = bench_batched(cmg, ctx, dev, stream, args)
         out["smoother_512"] = bench_smoother(cmg, ctx, dev, peaks)
-        out["fft"] = bench_fft(cmg, ctx, dev, B, rho[0], args, peaks)
-        out["pcg"] = bench_pcg(cmg, ctx, dev, (("base", B, rho[0]), ("fine", F, rho[1])), args)
-        if not args.no_amr3:
-            out["amr3_256"] = bench_amr3(cmg, ctx, dev, args)
+        out["fft"] = bench_fft(cmg, ctx, dev, tl_levels[0], tl_rho[0], args, peaks)
+        out["pcg"] = bench_pcg(cmg, ctx, dev, (("base", tl_levels[0], tl_rho[0]), ("fine", tl_levels[1], tl_rho[1])),
+                               args)
+        for L in reversed(tl_levels):
+            cmg.cmg_level_destroy(L)
         if not args.no_learned:
             out["learned"] = bench_learned(cmg, ctx, dev, args, peaks)
-        if rank == 0 and world == 1:
-            out["cpu_baseline"] = cpu_baseline_sample()
-    else:
-        out["e2e"] = None
+        if not args.no_oracle_errors and rank == 0:
+            out["phi_vs_oracle"] = bench_oracle_errors(cmg, ctx, dev, args)
+    if rank == 0 and world == 1:
+        out["cpu_baseline"] = cpu_baseline_sample(cfg)
     if rank == 0:
         print(json.dumps(out), flush=True)
     torch.cuda.synchronize()
-    cmg.cmg_level_destroy(F)
-    cmg.cmg_level_destroy(B)
+    for L in reversed(levels):
+        cmg.cmg_level_destroy(L)
     cmg.cmg_ctx_destroy(ctx)
     if world > 1:
         dist.destroy_process_group()
@@ -860,7 +1105,25 @@ def run_block(args):
     elif args.block == "batched":
         out = bench_batched(cmg, ctx, dev, torch.cuda.current_stream(dev), args)
     elif args.block == "amr3":
-        out = bench_amr3(cmg, ctx, dev, args)
+        # the headline chain once in FP64 (its phi is the reference), then the
+        # mixed and FFT chains
+        from paper_2604_06035_gb300 import inputs
+        cfg = inputs.mixed_amr()
+        levels, rho, zeros = load_chain(cmg, ctx, dev, cfg)
+        chain_step(cmg, levels, rho, zeros, cfg["rho_bar"], args.tol, [cmg.CMG_PREC_FP64] * len(levels))
+        phi64 = [cmg.cmg_level_get_phi(L, device=True).clone() for L in levels]
+        out = bench_amr3(cmg, ctx, dev, args, (levels, rho, zeros, cfg["rho_bar"]), phi64)
+        for L in reversed(levels):
+            cmg.cmg_level_destroy(L)
+    elif args.block in ("two_level", "periodic32"):
+        from paper_2604_06035_gb300 import inputs
+        cfg = (inputs.two_level_amr(base_level=7, seed=2) if args.block == "two_level"
+               else inputs.periodic_grf_level(5, seed=1))
+        out, (levels, _, _) = bench_small_chain(cmg, ctx, dev, args, cfg, args.block)
+        for L in reversed(levels):
+            cmg.cmg_level_destroy(L)
+    elif args.block == "oracle_errors":
+        out = bench_oracle_errors(cmg, ctx, dev, args)
     elif args.block == "pcg":
         from paper_2604_06035_gb300 import inputs
         cfg = inputs.two_level_amr(base_level=7, seed=2)

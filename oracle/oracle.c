@@ -26,9 +26,14 @@
  * the same order, so results are bit-identical for any thread count. */
 static int or_threads = 1;
 #ifdef _OPENMP
-#define OR_PAR_FOR _Pragma("omp parallel for schedule(static) num_threads(or_threads) if (or_threads > 1)")
+#define OR_PRAGMA(x) _Pragma(#x)
+#define OR_PAR_FOR OR_PRAGMA(omp parallel for schedule(static) num_threads(or_threads) if (or_threads > 1))
+/* the same, OR-reducing an int flag set by any iteration */
+#define OR_PAR_FOR_OR(v) \
+  OR_PRAGMA(omp parallel for schedule(static) num_threads(or_threads) if (or_threads > 1) reduction(| : v))
 #else
 #define OR_PAR_FOR
+#define OR_PAR_FOR_OR(v)
 #endif
 
 int or_set_threads(int n) {
@@ -426,18 +431,20 @@ static int level_build(int level, int nx, int pmask, const okey *keys, int64_t n
   for (int64_t t = 0; t < 12 * n; t++) L->father[t] = -1;
   for (int64_t t = 0; t < 24 * n; t++) L->ghost[t] = NAN;
   if (parent) {
-    for (int64_t i = 0; i < n && st == OR_OK; i++)
-      for (int d = 0; d < 6 && st == OR_OK; d++) {
+    int bad = 0;
+    OR_PAR_FOR_OR(bad)
+    for (int64_t i = 0; i < n; i++)
+      for (int d = 0; d < 6; d++) {
         if (g->nbr[7 * i + 1 + d] >= 0) continue;
         okey nk;
         if (!key_neighbor(keys[i], d, npd, pmask, &nk)) {
-          st = OR_ERR_MISSING_PARENT;
-          break;
+          bad |= 1;
+          continue;
         }
         int32_t p = ht_find(&parent->mg[0].ht, nk >> 3);
         if (p < 0) {
-          st = OR_ERR_MISSING_PARENT;
-          break;
+          bad |= 1;
+          continue;
         }
         L->father[12 * i + 2 * d] = p;
         L->father[12 * i + 2 * d + 1] = (int32_t)(nk & 7);
@@ -448,9 +455,10 @@ static int level_build(int level, int nx, int pmask, const okey *keys, int64_t n
           ghost_position(keys[i], c, d, level, nx, pmask, G);
           int missing = 0;
           interp_coarse(&parent->mg[0].ht, parent->mg[0].phi, level - 1, nx, pmask, G, &missing);
-          if (missing) st = OR_ERR_MISSING_PARENT;
+          if (missing) bad |= 1;
         }
       }
+    if (bad) st = OR_ERR_MISSING_PARENT;
   }
   if (st != OR_OK) {
     or_level_free(L);
