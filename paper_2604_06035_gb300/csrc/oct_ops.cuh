@@ -49,6 +49,90 @@ __device__ __forceinline__ void store4(float *p, const float v[4]) {
   *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
+// ---------------------------------------------------------------------------
+// The six-neighbour sum of the 7-point stencil.
+//
+// GB300 issues FP64 at about 2 lanes per SM per clock, 1/64 of its FP32 rate,
+// while its integer pipes sit idle in these kernels.  An FP64 sum can instead
+// be formed exactly in integers: with E the largest biased exponent of the
+// operands, each operand's 53-bit significand is shifted to the common scale
+// 2^(E - 1082) (operands more than 7 binades below the largest lose the bits
+// under that scale: at most 2^-59 of the largest operand each), the signed
+// 64-bit integers are added (|sum| < 6 * 2^60, no overflow), and the integer
+// sum is rounded once to the nearest FP64 value, ties to even.  The result is
+// within half an ulp of the exact sum plus those truncations, more accurate
+// than five sequential FP64 additions, and does not depend on the order of
+// the operands.  Zeros and subnormals take exponent 1 without the implicit
+// bit; an infinite or NaN operand falls back to FP64 additions.
+template <int N>
+__device__ __forceinline__ double fixed_sum(const double *v) {
+  uint32_t hi[N], lo[N];
+  int e[N];
+  int E = 1;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    hi[k] = (uint32_t)__double2hiint(v[k]);
+    lo[k] = (uint32_t)__double2loint(v[k]);
+    e[k] = max((int)((hi[k] >> 20) & 0x7FFu), 1);
+    E = max(E, e[k]);
+  }
+  if (E == 0x7FF) {
+    double s = v[0];
+#pragma unroll
+    for (int k = 1; k < N; ++k) s += v[k];
+    return s;
+  }
+  long long S = 0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const uint32_t lead = (hi[k] & 0x7FF00000u) ? 0x100000u : 0u;
+    unsigned long long m = ((unsigned long long)((hi[k] & 0xFFFFFu) | lead) << 32) | lo[k];
+    m = (m << 7) >> min(E - e[k], 63);
+    const long long sg = (long long)((int)hi[k] >> 31);  // 0 or -1
+    S += ((long long)m ^ sg) - sg;
+  }
+  if (S == 0) return 0.0;
+  const unsigned long long neg = S < 0 ? 1ull : 0ull;
+  const unsigned long long a = neg ? 0ull - (unsigned long long)S : (unsigned long long)S;
+  const int p = 63 - __clzll((long long)a);  // leading bit of |S|, <= 62
+  const int eb = E + p - 59;                 // biased exponent of the sum
+  if (eb <= 0) return ldexp((double)S, E - 1082);  // subnormal sum (never in practice)
+  unsigned long long mant;
+  if (p > 52) {
+    const int r = p - 52;
+    const unsigned long long q = a >> r, rem = a & ((1ull << r) - 1ull), half = 1ull << (r - 1);
+    mant = q + (unsigned long long)((rem > half) | ((rem == half) & (q & 1ull)));
+  } else {
+    mant = a << (52 - p);
+  }
+  // mant carries the leading bit at 2^52 (2^53 after a rounding carry), which
+  // adds the last 1 (or 2) to the exponent field
+  return __longlong_as_double((long long)(((unsigned long long)(eb - 1) << 52) + mant + (neg << 63)));
+}
+
+// Neighbour sum in the order (-x, +x, -y, +y, -z, +z).  FP32: sequential
+// additions.  FP64 (CMG_NBSUM): 0 = five sequential FP64 additions; 1 = all
+// six in the integer sum; 2 = the four x and y neighbours in the integer sum,
+// then the two z neighbours by FP64 additions (the FP64 and integer pipes
+// share the work).  Every kernel forms every neighbour sum through this
+// function, so a residual formed right after a colour pass repeats that
+// pass's sums bit for bit.
+#ifndef CMG_NBSUM
+#define CMG_NBSUM 2
+#endif
+__device__ __forceinline__ float nbsum6(const float v[6]) {
+  return ((((v[0] + v[1]) + v[2]) + v[3]) + v[4]) + v[5];
+}
+__device__ __forceinline__ double nbsum6(const double v[6]) {
+#if CMG_NBSUM == 1
+  return fixed_sum<6>(v);
+#elif CMG_NBSUM == 2
+  return (fixed_sum<4>(v) + v[4]) + v[5];
+#else
+  return ((((v[0] + v[1]) + v[2]) + v[3]) + v[4]) + v[5];
+#endif
+}
+
 template <typename T>
 __device__ __forceinline__ T fma_t(T a, T b, T c);
 template <>
@@ -93,14 +177,13 @@ __device__ __forceinline__ void sweep_oct_idx(int64_t i, const SweepIdx &x, cons
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int c = plane_cell(P, q);
-      T s = T(0);
+      T v[6];
 #pragma unroll
       for (int d = 0; d < 6; ++d) {
         const int a = d >> 1, side = d & 1, c2 = c ^ (1 << a);
-        const T v = (((c >> a) & 1) != side) ? own[c2 >> 1] : ld1<CG>(src + (int64_t)nb[d] * 4 + (c2 >> 1));
-        s = d == 0 ? v : s + v;
+        v[d] = (((c >> a) & 1) != side) ? own[c2 >> 1] : ld1<CG>(src + (int64_t)nb[d] * 4 + (c2 >> 1));
       }
-      out[q] = fma_t(s, inv6, gv[q]);
+      out[q] = fma_t(nbsum6(v), inv6, gv[q]);
     }
   }
   if (MASK) {
@@ -127,15 +210,14 @@ __device__ __forceinline__ void sweep_cell(int64_t i, int q, const int32_t *__re
   if (!ZERO) {
     const int c = plane_cell(P, q);
     const T inv6 = T(1) / T(6);
-    T s = T(0);
+    T v[6];
 #pragma unroll
     for (int d = 0; d < 6; ++d) {
       const int a = d >> 1, side = d & 1, c2 = c ^ (1 << a);
       const int64_t o = (((c >> a) & 1) != side) ? i : (int64_t)__ldg(nbr + d * n + i);
-      const T v = ld1<CG>(src + o * 4 + (c2 >> 1));
-      s = d == 0 ? v : s + v;
+      v[d] = ld1<CG>(src + o * 4 + (c2 >> 1));
     }
-    out = fma_t(s, inv6, out);
+    out = fma_t(nbsum6(v), inv6, out);
   }
   if (MASK && !((__ldg(active + i) >> plane_cell(P, q)) & 1)) out = T(0);
   dst[i * 4 + q] = out;
@@ -209,20 +291,18 @@ __device__ __forceinline__ double resid_oct_idx(int64_t i, const ResidIdx &x, co
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int c = plane_cell(p, q);
-      T s = T(0);
+      T v[6];
 #pragma unroll
       for (int d = 0; d < 6; ++d) {
         const int a = d >> 1, side = d & 1, c2 = c ^ (1 << a);
-        T v;
         if (((c >> a) & 1) != side) {
-          v = pl[1 - p][c2 >> 1];
+          v[d] = pl[1 - p][c2 >> 1];
         } else {
           const int64_t o = nb[d];
-          v = (ZPHI && o < n) ? T(0) : ld1<CG>(phi + ((1 - p) * n_alloc + o) * 4 + (c2 >> 1));
+          v[d] = (ZPHI && o < n) ? T(0) : ld1<CG>(phi + ((1 - p) * n_alloc + o) * 4 + (c2 >> 1));
         }
-        s = d == 0 ? v : s + v;
       }
-      T dv = fma_t(s, inv6, gv[p][q]) - pl[p][q];
+      T dv = fma_t(nbsum6(v), inv6, gv[p][q]) - pl[p][q];
       if (!((m >> c) & 1)) dv = T(0);
       if (NORM) {
         if constexpr (sizeof(T) == 8)
@@ -275,15 +355,14 @@ __device__ __forceinline__ void resid_restrict_cell(bool valid, int64_t i, const
     const T pv = ld1<CG>(phi + (p * n_alloc + i) * 4 + q);
     const T gv = ld1<CG>(g + (p * n + i) * 4 + q);
     const T inv6 = T(1) / T(6);
-    T s = T(0);
+    T v[6];
 #pragma unroll
     for (int d = 0; d < 6; ++d) {
       const int a = d >> 1, side = d & 1, c2 = c ^ (1 << a);
       const int64_t o = (((c >> a) & 1) != side) ? i : (int64_t)__ldg(nbr + d * n + i);
-      const T v = ld1<CG>(phi + ((1 - p) * n_alloc + o) * 4 + (c2 >> 1));
-      s = d == 0 ? v : s + v;
+      v[d] = ld1<CG>(phi + ((1 - p) * n_alloc + o) * 4 + (c2 >> 1));
     }
-    dv = fma_t(s, inv6, gv) - pv;
+    dv = fma_t(nbsum6(v), inv6, gv) - pv;
     const unsigned m = active ? __ldg(active + i) : 0xFFu;
     if (!((m >> c) & 1)) dv = T(0);
   }
