@@ -63,7 +63,13 @@ __device__ __forceinline__ void store4(float *p, const float v[4]) {
 // within half an ulp of the exact sum plus those truncations, more accurate
 // than five sequential FP64 additions, and does not depend on the order of
 // the operands.  Zeros and subnormals take exponent 1 without the implicit
-// bit; an infinite or NaN operand falls back to FP64 additions.
+// bit.  The rounding is the int64 -> FP64 conversion (CMG_FXNORM = 1) or the
+// same rounding written out in integer operations (CMG_FXNORM = 0).
+// CMG_FXNORM = 1 measured slower in the 4 + 2 split on GB300 (512^3 FP64
+// colour pass 0.486 -> 0.603 ms): the conversion issues on the FP64 pipe.
+#ifndef CMG_FXNORM
+#define CMG_FXNORM 0
+#endif
 template <int N>
 __device__ __forceinline__ double fixed_sum(const double *v) {
   uint32_t hi[N], lo[N];
@@ -76,7 +82,13 @@ __device__ __forceinline__ double fixed_sum(const double *v) {
     e[k] = max((int)((hi[k] >> 20) & 0x7FFu), 1);
     E = max(E, e[k]);
   }
+#if CMG_FXNORM == 1
+  // the scaling below needs a normal result: operands all zero or below
+  // 2^-960, or an infinity or NaN, take FP64 additions
+  if (E == 0x7FF || E < 64) {
+#else
   if (E == 0x7FF) {
+#endif
     double s = v[0];
 #pragma unroll
     for (int k = 1; k < N; ++k) s += v[k];
@@ -91,6 +103,12 @@ __device__ __forceinline__ double fixed_sum(const double *v) {
     const long long sg = (long long)((int)hi[k] >> 31);  // 0 or -1
     S += ((long long)m ^ sg) - sg;
   }
+#if CMG_FXNORM == 1
+  // rounding by the int64 -> FP64 conversion (round to nearest even), then
+  // the exact scaling by 2^(E - 1082) through the exponent field
+  const double d = __ll2double_rn(S);
+  return d == 0.0 ? 0.0 : __hiloint2double(__double2hiint(d) + ((E - 1082) << 20), __double2loint(d));
+#else
   if (S == 0) return 0.0;
   const unsigned long long neg = S < 0 ? 1ull : 0ull;
   const unsigned long long a = neg ? 0ull - (unsigned long long)S : (unsigned long long)S;
@@ -108,13 +126,15 @@ __device__ __forceinline__ double fixed_sum(const double *v) {
   // mant carries the leading bit at 2^52 (2^53 after a rounding carry), which
   // adds the last 1 (or 2) to the exponent field
   return __longlong_as_double((long long)(((unsigned long long)(eb - 1) << 52) + mant + (neg << 63)));
+#endif
 }
 
 // Neighbour sum in the order (-x, +x, -y, +y, -z, +z).  FP32: sequential
 // additions.  FP64 (CMG_NBSUM): 0 = five sequential FP64 additions; 1 = all
 // six in the integer sum; 2 = the four x and y neighbours in the integer sum,
 // then the two z neighbours by FP64 additions (the FP64 and integer pipes
-// share the work).  Every kernel forms every neighbour sum through this
+// share the work).  Measured on GB300, 512^3 FP64 colour pass: 0.771 (0),
+// 0.556 (1), 0.486 ms (2); 256^3 + 3-level FP64 chain: 65.2, 52.1, 51.1 ms.  Every kernel forms every neighbour sum through this
 // function, so a residual formed right after a colour pass repeats that
 // pass's sums bit for bit.
 #ifndef CMG_NBSUM
