@@ -378,6 +378,54 @@ int cmg_unet_adam_step(cmg_unet *net, float lr, float beta1, float beta2, float 
  * (to_octs = 1: dense -> octs; 0: octs -> dense).  Both device pointers. */
 int cmg_dense_octs(cmg_ctx *ctx, const double *src, int grid_dim, double *dst, int to_octs);
 
+/* ---- sharded level solve (App. G, GPU V-cycle algorithm; Sec. 9.5, halo
+ * exchange between GPUs) ----
+ * Building blocks of a V-cycle split over ranks by owner-computes: each rank
+ * holds a replica of the level (built from the same keys, sorted so that each
+ * rank's octs, and the octs of every coarser MG level, form one contiguous
+ * range), runs every operation on its own range [lo, hi) only, and exchanges
+ * the cells other ranks read between operations (cmg_level_mg_gather /
+ * cmg_level_mg_scatter).  The range kernels are the whole-level kernels'
+ * per-oct bodies, so a sharded V-cycle computes the single-rank result cell
+ * for cell; only the order of the norm sums differs.  The driver that orders
+ * the calls and the exchanges is paper_2604_06035_gb300/shard.py.  FP64 only.
+ *
+ * cmg_level_mg_step_range(lvl, m, op, arg, lo, hi, value): octs [lo, hi) of
+ * MG level m (0 <= lo <= hi <= octs of the level, else CMG_ERR_INVALID_ARG),
+ * on the context's stream, synchronised before return.
+ *   CMG_OPR_SWEEP     one red-black colour pass; arg = colour (0 red, 1
+ *                     black) | 2 when the other colour is known to be zero
+ *                     (the first pass after a restriction, phi = g)
+ *   CMG_OPR_RESIDUAL  *value = sum of r^2 over the range; arg = 1 when the
+ *                     last operation on the level was a colour-1 pass (the
+ *                     colour-1 residuals are then exactly zero and skipped)
+ *   CMG_OPR_RESTRICT  the range's fully active octs write their father
+ *                     cell's source (mean of the 8 residuals) and zero its
+ *                     phi on MG level m + 1; arg as for CMG_OPR_RESIDUAL
+ *   CMG_OPR_PROLONG   phi += trilinear interpolation of phi at m + 1; arg =
+ *                     1 when a colour-0 pass follows (only colour-1 cells are
+ *                     corrected, the colour-0 corrections being dead)
+ *   CMG_OPR_SUM_PHI   *value = sum of phi over the range's cells
+ *   CMG_OPR_SHIFT_PHI phi -= *value on the range's cells
+ * cmg_level_mg_gather / _scatter(lvl, m, field, cells, n, buf): copy n cells
+ * of MG level m between the level and buf.  field 0 = phi, 1 = the stored
+ * source (the solver's internal scaling g = -h^2 f / 6, moved unchanged so
+ * that replicas stay bit-identical).  cells[k] = oct * 8 + child (child =
+ * bx + 2 by + 4 bz), DEVICE int32; buf DEVICE double[n]; both owned by the
+ * caller.  An index outside the level is CMG_ERR_INVALID_ARG (the other cells
+ * are still copied). */
+enum {
+  CMG_OPR_SWEEP = 0,
+  CMG_OPR_RESIDUAL = 1,
+  CMG_OPR_RESTRICT = 2,
+  CMG_OPR_PROLONG = 3,
+  CMG_OPR_SUM_PHI = 4,
+  CMG_OPR_SHIFT_PHI = 5
+};
+int cmg_level_mg_step_range(cmg_level *lvl, int m, int op, int arg, int64_t lo, int64_t hi, double *value);
+int cmg_level_mg_gather(cmg_level *lvl, int m, int field, const int32_t *cells, int64_t n, double *out);
+int cmg_level_mg_scatter(cmg_level *lvl, int m, int field, const int32_t *cells, int64_t n, const double *in);
+
 /* ---- residual norm without allocation (the paper has no counterpart) ----
  * The level objects above allocate device memory when they are built, and
  * their residual norm reduces through scratch the level owns.  Callers that

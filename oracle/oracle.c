@@ -653,20 +653,24 @@ static double nb_sum(const or_level *L, int m, int64_t i, int c, int use_ghost) 
   return s;
 }
 
-/* App. D.2 Eq. (gs_update): phi = (sum_j phi_j - h^2 f) * (1/6); red cells
- * ((i+j+k) even) first, then black. */
-void or_rb_sweeps(or_level *L, int m, int n_sweeps, int use_ghost) {
+/* App. D.2 Eq. (gs_update): phi = (sum_j phi_j - h^2 f) * (1/6) on the
+ * active cells of one colour (0 = red, (i+j+k) even; 1 = black). */
+void or_rb_colour_pass(or_level *L, int m, int color, int use_ghost) {
   mglev *g = &L->mg[m];
   double h = cell_h(g->lev, L->nx), h2 = h * h, inv6 = 1.0 / 6.0;
+  OR_PAR_FOR
+  for (int64_t i = 0; i < g->n; i++)
+    for (int c = 0; c < 8; c++) {
+      if (parity(c) != color || !g->active[8 * i + c]) continue;
+      double sum = nb_sum(L, m, i, c, use_ghost);
+      g->phi[8 * i + c] = (sum - h2 * g->f[8 * i + c]) * inv6;
+    }
+}
+
+/* n_sweeps red-black sweeps: red cells first, then black. */
+void or_rb_sweeps(or_level *L, int m, int n_sweeps, int use_ghost) {
   for (int s = 0; s < n_sweeps; s++)
-    for (int color = 0; color < 2; color++)
-      OR_PAR_FOR
-      for (int64_t i = 0; i < g->n; i++)
-        for (int c = 0; c < 8; c++) {
-          if (parity(c) != color || !g->active[8 * i + c]) continue;
-          double sum = nb_sum(L, m, i, c, use_ghost);
-          g->phi[8 * i + c] = (sum - h2 * g->f[8 * i + c]) * inv6;
-        }
+    for (int color = 0; color < 2; color++) or_rb_colour_pass(L, m, color, use_ghost);
 }
 
 /* r = f - lap_h(phi), lap_h = (sum_j phi_j - 6 phi) / h^2; returns sum r^2

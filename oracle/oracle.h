@@ -113,6 +113,7 @@ void or_level_mg_set(or_level *L, int m, int field, const double *in);
 
 /* ---- single steps (use_ghost = 1: Dirichlet ghosts at m = 0) ---- */
 void or_rb_sweeps(or_level *L, int m, int n_sweeps, int use_ghost);
+void or_rb_colour_pass(or_level *L, int m, int color, int use_ghost); /* one colour of a sweep */
 double or_residual(or_level *L, int m, int use_ghost); /* writes r, returns sum r^2 */
 void or_restrict(or_level *L, int m);    /* f[m+1] from r[m]; phi[m+1] = 0 */
 void or_prolong(or_level *L, int m);     /* phi[m] += P phi[m+1] */

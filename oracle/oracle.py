@@ -75,6 +75,7 @@ def lib():
             "or_level_mg_get": (None, [_P, C.c_int, C.c_int, _P]),
             "or_level_mg_set": (None, [_P, C.c_int, C.c_int, _P]),
             "or_rb_sweeps": (None, [_P, C.c_int, C.c_int, C.c_int]),
+            "or_rb_colour_pass": (None, [_P, C.c_int, C.c_int, C.c_int]),
             "or_residual": (C.c_double, [_P, C.c_int, C.c_int]),
             "or_restrict": (None, [_P, C.c_int]),
             "or_prolong": (None, [_P, C.c_int]),

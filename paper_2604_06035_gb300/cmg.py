@@ -35,6 +35,7 @@ CMG_PREC_FFT = 2
 CMG_FIELD_PHI = 0
 CMG_FIELD_F = 1
 CMG_OP_SWEEP, CMG_OP_RESIDUAL, CMG_OP_RESTRICT, CMG_OP_PROLONG, CMG_OP_COARSE, CMG_OP_GHOSTS = range(6)
+CMG_OPR_SWEEP, CMG_OPR_RESIDUAL, CMG_OPR_RESTRICT, CMG_OPR_PROLONG, CMG_OPR_SUM_PHI, CMG_OPR_SHIFT_PHI = range(6)
 
 
 class cmg_solve_params(C.Structure):
@@ -119,6 +120,9 @@ _SIGS = {
     "cmg_level_mg_set": (_I, [_P, _I, _I, _I, _P, _I]),
     "cmg_level_mg_step": (_I, [_P, _I, _I, _I, _I, C.POINTER(C.c_double)]),
     "cmg_residual_norm2_noalloc": (_I, [_P, _P, _P, _P, _I64, C.c_double, _P, _P]),
+    "cmg_level_mg_step_range": (_I, [_P, _I, _I, _I, _I64, _I64, C.POINTER(C.c_double)]),
+    "cmg_level_mg_gather": (_I, [_P, _I, _I, _P, _I64, _P]),
+    "cmg_level_mg_scatter": (_I, [_P, _I, _I, _P, _I64, _P]),
     "cmg_batch_create": (_I, [_P, _P, _I, C.POINTER(_P)]),
     "cmg_batch_destroy": (_I, [_P]),
     "cmg_batch_set_schedule": (_I, [_P, _P]),
@@ -640,6 +644,44 @@ def cmg_level_mg_step(lvl, m, op, precision=CMG_PREC_FP64, n=1):
     v = C.c_double(0.0)
     _check(lib().cmg_level_mg_step(lvl.h, m, op, precision, n, C.byref(v)), "cmg_level_mg_step")
     return v.value
+
+
+def cmg_level_mg_step_range(lvl, m, op, arg, lo, hi, value=0.0):
+    """One V-cycle operation on the octs [lo, hi) of MG level m (sharded
+    solve; FP64).  Returns the value the operation reports (norm^2 or sum),
+    else the value passed in."""
+    v = C.c_double(float(value))
+    _check(lib().cmg_level_mg_step_range(lvl.h, m, op, arg, int(lo), int(hi), C.byref(v)),
+           "cmg_level_mg_step_range")
+    return v.value
+
+
+def _cells_and_buf(cells, buf, fn):
+    pc, mc, _ = _in(cells, np.int32)
+    pb, mb, _ = _in(buf, np.float64)
+    if mc != CMG_MEM_DEVICE or mb != CMG_MEM_DEVICE:
+        raise TypeError("%s: cells and buf must be CUDA tensors" % fn)
+    if int(np.prod(buf.shape)) < int(np.prod(cells.shape)):
+        raise ValueError("%s: buf holds fewer values than cells" % fn)
+    return pc, pb, int(np.prod(cells.shape))
+
+
+def cmg_level_mg_gather(lvl, m, field, cells, out=None):
+    """Values of the listed cells (oct * 8 + child; int32 CUDA tensor) of MG
+    level m: field 0 = phi, 1 = the stored source.  Returns a float64 CUDA
+    tensor."""
+    import torch
+    if out is None:
+        out = torch.empty(int(np.prod(cells.shape)), dtype=torch.float64, device=cells.device)
+    pc, pb, n = _cells_and_buf(cells, out, "cmg_level_mg_gather")
+    _check(lib().cmg_level_mg_gather(lvl.h, m, field, pc, n, pb), "cmg_level_mg_gather")
+    return out
+
+
+def cmg_level_mg_scatter(lvl, m, field, cells, values):
+    """Write values (float64 CUDA tensor) into the listed cells of MG level m."""
+    pc, pb, n = _cells_and_buf(cells, values, "cmg_level_mg_scatter")
+    _check(lib().cmg_level_mg_scatter(lvl.h, m, field, pc, n, pb), "cmg_level_mg_scatter")
 
 
 class UnetHandle:

@@ -815,4 +815,95 @@ int cmg_level_mg_step(cmg_level *lvl, int m, int op, int precision, int n, doubl
   });
 }
 
+// ---- sharded level solve (App. G V-cycle per rank, Sec. 9.5 halo exchange)
+
+int cmg_level_mg_step_range(cmg_level *lvl, int m, int op, int arg, int64_t lo, int64_t hi, double *value) {
+  return guard([&] {
+    need(lvl && m >= 0 && m < (int)lvl->mg.size(), "bad MG level");
+    const int64_t n = lvl->mg[m].n;
+    need(lo >= 0 && lo <= hi && hi <= n, "range outside the MG level");
+    const int depth = (int)lvl->mg.size();
+    DeviceScope ds(lvl->ctx->device);
+    cmg_ctx *ctx = lvl->ctx;
+    switch (op) {
+      case CMG_OPR_SWEEP:
+        need(arg >= 0 && arg <= 3, "sweep arg: colour | 2 * zero_other");
+        cmg::range_sweep_pass(lvl, m, arg & 1, (arg & 2) != 0, lo, hi);
+        break;
+      case CMG_OPR_RESIDUAL:
+        need(value != nullptr, "value is NULL");
+        need(arg == 0 || arg == 1, "residual arg: c1_swept 0 or 1");
+        cmg::range_residual(lvl, m, false, arg == 1, lo, hi, lvl->scal + 2);
+        CMG_CUDA(cudaMemcpyAsync(ctx->h_dpinned, lvl->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CMG_CUDA(cudaStreamSynchronize(ctx->stream));
+        *value = ctx->h_dpinned[0];
+        break;
+      case CMG_OPR_RESTRICT:
+        need(m + 1 < depth, "no coarser MG level");
+        need(arg == 0 || arg == 1, "restrict arg: c1_swept 0 or 1");
+        cmg::range_residual(lvl, m, true, arg == 1, lo, hi, nullptr);
+        break;
+      case CMG_OPR_PROLONG:
+        need(m + 1 < depth, "no coarser MG level");
+        need(arg == 0 || arg == 1, "prolong arg: c0_dead 0 or 1");
+        cmg::range_prolong(lvl, m, arg == 1, lo, hi);
+        break;
+      case CMG_OPR_SUM_PHI:
+        need(value != nullptr, "value is NULL");
+        cmg::range_sum_phi(lvl, m, lo, hi, lvl->scal + 2);
+        CMG_CUDA(cudaMemcpyAsync(ctx->h_dpinned, lvl->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CMG_CUDA(cudaStreamSynchronize(ctx->stream));
+        *value = ctx->h_dpinned[0];
+        break;
+      case CMG_OPR_SHIFT_PHI:
+        need(value != nullptr, "value is NULL");
+        cmg::range_shift_phi(lvl, m, lo, hi, *value);
+        break;
+      default:
+        throw cmg::Error(CMG_ERR_INVALID_ARG, "unknown range op");
+    }
+    CMG_CUDA(cudaStreamSynchronize(ctx->stream));
+    return CMG_OK;
+  });
+}
+
+namespace {
+// Reads and clears the context's device error word (an index outside the
+// level in a gather or scatter).
+int take_device_error(cmg_ctx *ctx) {
+  CMG_CUDA(cudaMemcpyAsync(ctx->h_pinned, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CMG_CUDA(cudaStreamSynchronize(ctx->stream));
+  const int e = ctx->h_pinned[0];
+  if (e != 0) {
+    CMG_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    CMG_CUDA(cudaStreamSynchronize(ctx->stream));
+  }
+  return e;
+}
+}  // namespace
+
+int cmg_level_mg_gather(cmg_level *lvl, int m, int field, const int32_t *cells, int64_t n, double *out) {
+  return guard([&] {
+    need(lvl && m >= 0 && m < (int)lvl->mg.size(), "bad MG level");
+    need(field == 0 || field == 1, "field must be 0 (phi) or 1 (stored source)");
+    need(n >= 0 && (n == 0 || (cells && out)), "bad arguments");
+    DeviceScope ds(lvl->ctx->device);
+    cmg::gather_cells(lvl, m, field, cells, n, out, lvl->ctx->d_err);
+    if (take_device_error(lvl->ctx)) throw cmg::Error(CMG_ERR_INVALID_ARG, "cell index outside the MG level");
+    return CMG_OK;
+  });
+}
+
+int cmg_level_mg_scatter(cmg_level *lvl, int m, int field, const int32_t *cells, int64_t n, const double *in) {
+  return guard([&] {
+    need(lvl && m >= 0 && m < (int)lvl->mg.size(), "bad MG level");
+    need(field == 0 || field == 1, "field must be 0 (phi) or 1 (stored source)");
+    need(n >= 0 && (n == 0 || (cells && in)), "bad arguments");
+    DeviceScope ds(lvl->ctx->device);
+    cmg::scatter_cells(lvl, m, field, cells, n, in, lvl->ctx->d_err);
+    if (take_device_error(lvl->ctx)) throw cmg::Error(CMG_ERR_INVALID_ARG, "cell index outside the MG level");
+    return CMG_OK;
+  });
+}
+
 }  // extern "C"

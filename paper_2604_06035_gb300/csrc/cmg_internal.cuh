@@ -422,6 +422,17 @@ void prolong(cmg_level *L, int m, bool c0_dead = false);  // c0_dead: a colour-0
 void coarse_solve(cmg_level *L, int prec, int coarse_sweeps);
 void zero_phi_norm(cmg_level *L, double *out);
 void subtract_mean(cmg_level *L);
+// sharded level solve (shard.cu): operations on the octs [lo, hi) of MG level
+// m, FP64, and cell-granular gather / scatter (field 0 = phi, 1 = stored g;
+// cell = oct * 8 + child; an index outside the level sets *bad)
+void range_sweep_pass(cmg_level *L, int m, int colour, bool zero_other, int64_t lo, int64_t hi);
+void range_residual(cmg_level *L, int m, bool restrict_to_coarse, bool c1_swept, int64_t lo, int64_t hi,
+                    double *norm_out);
+void range_prolong(cmg_level *L, int m, bool c0_dead, int64_t lo, int64_t hi);
+void range_sum_phi(cmg_level *L, int m, int64_t lo, int64_t hi, double *out);
+void range_shift_phi(cmg_level *L, int m, int64_t lo, int64_t hi, double v);
+void gather_cells(cmg_level *L, int m, int field, const int32_t *idx, int64_t cnt, double *out, int *bad);
+void scatter_cells(cmg_level *L, int m, int field, const int32_t *idx, int64_t cnt, const double *in, int *bad);
 void accumulate(cmg_level *L, const double *scale);
 void finalize_norm(cmg_level *L, int n_partials, double scale, double *out);
 
