@@ -879,8 +879,8 @@ def headline_roofline(prof, peaks, sm_mhz):
     bytes per launch (field values plus the neighbour cache, 27 B per FP64
     cell update in a colour pass) over its per-launch CUDA-event time, against
     the measured HBM copy rate.  The FP64 colour pass also gets its FP64-pipe
-    fraction: 3 FP64 instructions per cell update (2 DADD + 1 DFMA; the other
-    neighbour additions run as integer fixed-point sums on the ALU pipe)
+    fraction: 2 FP64 instructions per cell update (1 DADD + 1 DFMA; the other
+    neighbour additions run as an integer fixed-point sum on the ALU pipe)
     against 2 lanes per SM per clock, 152 SMs at the sampled SM clock."""
     dname, d = max(prof.items(), key=lambda kv: kv[1]["ms"])
     gbs = d["bytes"] / (d["ms"] / 1e3) / 1e9
@@ -889,10 +889,10 @@ def headline_roofline(prof, peaks, sm_mhz):
     if dname.startswith("rbgs_") and dname.endswith("fp64"):
         clk = (sm_mhz or 2070.0) * 1e6
         cells_per_s = d["bytes"] / 27.0 / (d["ms"] / 1e3)
-        instr = 3.0 * cells_per_s
+        instr = 2.0 * cells_per_s
         peak_instr = 2.0 * 152 * clk
         roof["fp64_issue_frac"] = instr / peak_instr
-        roof["fp64_issue_note"] = ("FP64 lane-instructions/s (3 per cell update: 2 DADD + 1 DFMA; four of the six "
+        roof["fp64_issue_note"] = ("FP64 lane-instructions/s (2 per cell update: 1 DADD + 1 DFMA; five of the six "
                                    "neighbours are summed on the integer pipe) against 2 per SM per clock x 152 SMs "
                                    "at %.0f MHz" % (clk / 1e6))
     roof["launches"] = d["launches"]

@@ -62,47 +62,79 @@ __device__ __forceinline__ void store4(float *p, const float v[4]) {
 // sum is rounded once to the nearest FP64 value, ties to even.  The result is
 // within half an ulp of the exact sum plus those truncations, more accurate
 // than five sequential FP64 additions, and does not depend on the order of
-// the operands.  Zeros and subnormals take exponent 1 without the implicit
-// bit.  The rounding is the int64 -> FP64 conversion (CMG_FXNORM = 1) or the
-// same rounding written out in integer operations (CMG_FXNORM = 0).
+// the operands.  Zero and subnormal operands contribute nothing (a subnormal
+// is below 2^-1022, far under the scale).  The rounding is written out in
+// integer operations (CMG_FXNORM = 0) or is the int64 -> FP64 conversion
+// (CMG_FXNORM = 1).  The alignment below costs ~15 integer instructions per
+// operand; an earlier form (significand assembled with its leading bit,
+// shifted left 7 and right by E - e, negated as (m ^ s) - s) gave the same
+// bits on 10^6 probe sums and ran 15 % slower on GB300.
 // CMG_FXNORM = 1 measured slower in the 4 + 2 split on GB300 (512^3 FP64
 // colour pass 0.486 -> 0.603 ms): the conversion issues on the FP64 pipe.
 #ifndef CMG_FXNORM
 #define CMG_FXNORM 0
 #endif
+// CMG_FXALIGN: 1 = the alignment below; 0 = the earlier form (same bits
+// whenever some operand is 2^-960 or larger).
+#ifndef CMG_FXALIGN
+#define CMG_FXALIGN 1
+#endif
+// x >> s with PTX semantics: a shift of 64 or more gives 0.
+__device__ __forceinline__ unsigned long long shr_clamped(unsigned long long x, unsigned s) {
+  unsigned long long r;
+  asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(s));
+  return r;
+}
+
 template <int N>
 __device__ __forceinline__ double fixed_sum(const double *v) {
   uint32_t hi[N], lo[N];
   int e[N];
-  int E = 1;
+  int E = 0;
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     hi[k] = (uint32_t)__double2hiint(v[k]);
     lo[k] = (uint32_t)__double2loint(v[k]);
-    e[k] = max((int)((hi[k] >> 20) & 0x7FFu), 1);
+    e[k] = (int)((hi[k] >> 20) & 0x7FFu);
     E = max(E, e[k]);
   }
-#if CMG_FXNORM == 1
-  // the scaling below needs a normal result: operands all zero or below
-  // 2^-960, or an infinity or NaN, take FP64 additions
+  // an infinity or NaN, or every operand below 2^-960 (zeros included):
+  // FP64 additions
   if (E == 0x7FF || E < 64) {
-#else
-  if (E == 0x7FF) {
-#endif
     double s = v[0];
 #pragma unroll
     for (int k = 1; k < N; ++k) s += v[k];
     return s;
   }
+  // each significand with its leading bit at bit 63 (one funnel shift and
+  // the bit), then one right shift by E - e + 4 to the scale 2^(E - 1082);
+  // zero and subnormal operands (e = 0) shift by E + 4 >= 68 and vanish.
+  // Negative operands enter as ones' complements; the count of them, added
+  // once, completes the two's complements.
   long long S = 0;
+#if CMG_FXALIGN == 0
 #pragma unroll
   for (int k = 0; k < N; ++k) {
+    const int ek = max(e[k], 1);
     const uint32_t lead = (hi[k] & 0x7FF00000u) ? 0x100000u : 0u;
     unsigned long long m = ((unsigned long long)((hi[k] & 0xFFFFFu) | lead) << 32) | lo[k];
-    m = (m << 7) >> min(E - e[k], 63);
-    const long long sg = (long long)((int)hi[k] >> 31);  // 0 or -1
+    m = (m << 7) >> min(E - ek, 63);
+    const long long sg = (long long)((int)hi[k] >> 31);
     S += ((long long)m ^ sg) - sg;
   }
+#else
+  int negs = 0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const uint32_t top = __funnelshift_l(lo[k], hi[k], 11) | 0x80000000u;
+    const unsigned long long m = ((unsigned long long)top << 32) | (lo[k] << 11);
+    const unsigned long long a = shr_clamped(m, (unsigned)(E - e[k] + 4));
+    const long long sg = (long long)((int)hi[k] >> 31);  // 0 or -1
+    S += (long long)a ^ sg;
+    negs -= (int)sg;
+  }
+  S += negs;
+#endif
 #if CMG_FXNORM == 1
   // rounding by the int64 -> FP64 conversion (round to nearest even), then
   // the exact scaling by 2^(E - 1082) through the exponent field
@@ -131,14 +163,16 @@ __device__ __forceinline__ double fixed_sum(const double *v) {
 
 // Neighbour sum in the order (-x, +x, -y, +y, -z, +z).  FP32: sequential
 // additions.  FP64 (CMG_NBSUM): 0 = five sequential FP64 additions; 1 = all
-// six in the integer sum; 2 = the four x and y neighbours in the integer sum,
-// then the two z neighbours by FP64 additions (the FP64 and integer pipes
-// share the work).  Measured on GB300, 512^3 FP64 colour pass: 0.771 (0),
-// 0.556 (1), 0.486 ms (2); 256^3 + 3-level FP64 chain: 65.2, 52.1, 51.1 ms.  Every kernel forms every neighbour sum through this
+// six in the integer sum; 2 = the x and y neighbours in the integer sum, the
+// two z neighbours by FP64 additions; 3 = five in the integer sum, the last
+// by one FP64 addition (the FP64 and integer pipes share the work).
+// Measured on GB300 (512^3 FP64 colour pass; 256^3 + 3-level FP64 chain on
+// one box): 0 = 0.771 ms; 1 = 0.471 ms; 2 = 0.483 ms, 54.8 ms; 3 = 0.424 ms,
+// 51.6 ms.  Every kernel forms every neighbour sum through this
 // function, so a residual formed right after a colour pass repeats that
 // pass's sums bit for bit.
 #ifndef CMG_NBSUM
-#define CMG_NBSUM 2
+#define CMG_NBSUM 3
 #endif
 __device__ __forceinline__ float nbsum6(const float v[6]) {
   return ((((v[0] + v[1]) + v[2]) + v[3]) + v[4]) + v[5];
@@ -148,6 +182,8 @@ __device__ __forceinline__ double nbsum6(const double v[6]) {
   return fixed_sum<6>(v);
 #elif CMG_NBSUM == 2
   return (fixed_sum<4>(v) + v[4]) + v[5];
+#elif CMG_NBSUM == 3
+  return fixed_sum<5>(v) + v[5];
 #else
   return ((((v[0] + v[1]) + v[2]) + v[3]) + v[4]) + v[5];
 #endif
