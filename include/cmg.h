@@ -231,6 +231,18 @@ int cmg_level_solve_wait(cmg_level *lvl, cmg_solve_stats *stats);
  * leave the current setting. */
 int cmg_level_set_schedule(cmg_level *lvl, int64_t tail_octs_fp64, int64_t tail_octs_fp32);
 
+/* Colour passes of full periodic levels stored in lexicographic oct order (x
+ * fastest; every MG level of such a base level, when at least 16 octs per
+ * axis): the shared-memory brick kernel stages each CTA's 16 x 4 x 4 octs and
+ * their face halo in shared memory and finds neighbours by index arithmetic
+ * (App. D.1 and Sec. 9.4 describe the neighbour access it replaces), the
+ * neighbour-table kernel reads the level's neighbour cache.  Both give the
+ * same bits.  staged = 0: table kernel everywhere; 1 (default): brick kernel
+ * for FP32 passes (faster on GB300), table kernel for FP64 passes (faster
+ * there); 2: brick kernel for both.  Other levels always use the table
+ * kernel.  CMG_ERR_INVALID_ARG for another value. */
+int cmg_level_set_stencil(cmg_level *lvl, int staged);
+
 /* SM clock cycles one wait at a grid barrier of the tail kernel may last
  * (default 2^30, about half a second).  A wait that runs out records
  * CMG_ERR_TIMEOUT, every later barrier of that launch stops waiting, and the

@@ -121,6 +121,7 @@ _SIGS = {
     "cmg_level_mg_step": (_I, [_P, _I, _I, _I, _I, C.POINTER(C.c_double)]),
     "cmg_residual_norm2_noalloc": (_I, [_P, _P, _P, _P, _I64, C.c_double, _P, _P]),
     "cmg_level_mg_step_range": (_I, [_P, _I, _I, _I, _I64, _I64, C.POINTER(C.c_double)]),
+    "cmg_level_set_stencil": (_I, [_P, _I]),
     "cmg_level_mg_gather": (_I, [_P, _I, _I, _P, _I64, _P]),
     "cmg_level_mg_scatter": (_I, [_P, _I, _I, _P, _I64, _P]),
     "cmg_batch_create": (_I, [_P, _P, _I, C.POINTER(_P)]),
@@ -586,6 +587,13 @@ def cmg_level_solve_wait(lvl, raise_on_error=True):
 
 def cmg_level_set_schedule(lvl, tail_octs_fp64=-1, tail_octs_fp32=-1):
     _check(lib().cmg_level_set_schedule(lvl.h, int(tail_octs_fp64), int(tail_octs_fp32)), "cmg_level_set_schedule")
+
+
+def cmg_level_set_stencil(lvl, staged):
+    """Colour passes of lexicographic full periodic levels: 0 = neighbour-table
+    kernel, 1 = shared-memory brick kernel for FP32 passes (default), 2 =
+    brick kernel for FP32 and FP64 passes (same bits in every mode)."""
+    _check(lib().cmg_level_set_stencil(lvl.h, int(staged)), "cmg_level_set_stencil")
 
 
 def cmg_level_set_spin_budget(lvl, cycles):

@@ -679,6 +679,7 @@ void build_level(cmg_level *L, const void *keys, cmg_mem mem) {
     build_level_t<Key128>(L, static_cast<const Key128 *>(keys), mem);
   else
     build_level_t<uint64_t>(L, static_cast<const uint64_t *>(keys), mem);
+  mark_lexicographic(L);
 }
 
 }  // namespace cmg

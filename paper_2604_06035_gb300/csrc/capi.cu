@@ -588,6 +588,17 @@ int cmg_level_set_schedule(cmg_level *lvl, int64_t tail_octs_fp64, int64_t tail_
   });
 }
 
+int cmg_level_set_stencil(cmg_level *lvl, int staged) {
+  return guard([&] {
+    need(lvl != nullptr && staged >= 0 && staged <= 2, "bad arguments");
+    DeviceScope ds(lvl->device);
+    CMG_CUDA(cudaStreamSynchronize(lvl->stream));
+    lvl->staged = staged;
+    cmg::destroy_graphs(lvl);  // recorded graphs hold the old kernels
+    return CMG_OK;
+  });
+}
+
 int cmg_level_set_spin_budget(cmg_level *lvl, int64_t cycles) {
   return guard([&] {
     need(lvl != nullptr, "NULL level");

@@ -195,6 +195,10 @@ struct MgLev {
   double *g = nullptr;           // [2][n][4], g = -h^2 f / 6
   float *phi32 = nullptr;        // [2][n_alloc][4]
   float *g32 = nullptr;          // [2][n][4]
+  // log2 of the octs per axis when the level is a full periodic grid stored
+  // in lexicographic order (x fastest): its neighbours are implicit and the
+  // colour passes may run the shared-memory brick kernel; else -1
+  int lex_log2 = -1;
 };
 
 struct DeviceBuffers {
@@ -300,6 +304,10 @@ struct cmg_level {
   // in one "tail" launch (tail.cu); 0 = one launch per operation everywhere
   int64_t tail_octs_fp64 = 32768;
   int64_t tail_octs_fp32 = 2048;
+  // colour passes of lexicographic full periodic levels in the shared-memory
+  // brick kernel (brick.cu): 0 = never, 1 = FP32 passes (default; the FP64
+  // pass measured faster with the neighbour table), 2 = FP32 and FP64 passes
+  int staged = 1;
   int64_t tail_spin_budget = 1ll << 30;  // SM clock cycles a grid-tail barrier wait may last
   // FFT solve of a full periodic level (fft.cu): dense complex work array,
   // oct-coordinate -> oct-index map, twiddles (lazy)
@@ -422,6 +430,11 @@ void prolong(cmg_level *L, int m, bool c0_dead = false);  // c0_dead: a colour-0
 void coarse_solve(cmg_level *L, int prec, int coarse_sweeps);
 void zero_phi_norm(cmg_level *L, double *out);
 void subtract_mean(cmg_level *L);
+// brick.cu: one colour pass of a lexicographic full periodic MG level (lex_log2 >= 4)
+// through shared memory; mark_lexicographic sets lex_log2 on every MG level
+template <typename T>
+void brick_pass(cmg_level *L, int m, int colour);
+void mark_lexicographic(cmg_level *L);
 // sharded level solve (shard.cu): operations on the octs [lo, hi) of MG level
 // m, FP64, and cell-granular gather / scatter (field 0 = phi, 1 = stored g;
 // cell = oct * 8 + child; an index outside the level sets *bad)

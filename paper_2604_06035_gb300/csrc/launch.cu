@@ -40,12 +40,18 @@ void sweep(cmg_level *L, int m, bool zero_init) {
       launch_k(k_sweep<T, P, Z, M, false>, nb, kThreads, s, g.nbr, phi + (1 - P) * st, phi + P * st,        \
                gg + P * g.n * 4, g.active, g.n);                                                            \
   } while (0)
+  // full periodic levels in lexicographic order: the shared-memory brick
+  // kernel (brick.cu), same results bit for bit; by default for FP32 passes
+  // only (512^3: FP32 0.185 -> 0.158 ms, FP64 0.422 -> 0.439 ms)
+  const bool brick = L->staged >= (sizeof(T) == 4 ? 1 : 2) && g.lex_log2 >= 4 && !mask;
   if (mask) {
     if (zero_init) CMG_SWEEP(0, true, true); else CMG_SWEEP(0, false, true);
     CMG_SWEEP(1, false, true);
   } else {
-    if (zero_init) CMG_SWEEP(0, true, false); else CMG_SWEEP(0, false, false);
-    CMG_SWEEP(1, false, false);
+    if (zero_init) CMG_SWEEP(0, true, false);
+    else if (brick) brick_pass<T>(L, m, 0);
+    else CMG_SWEEP(0, false, false);
+    if (brick) brick_pass<T>(L, m, 1); else CMG_SWEEP(1, false, false);
   }
 #undef CMG_SWEEP
   CMG_CUDA(cudaGetLastError());
