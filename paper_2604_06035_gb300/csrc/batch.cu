@@ -625,8 +625,20 @@ const void *batch_kernel(bool mixed, bool krylov) {
   return krylov ? (const void *)k_batch<false, true> : (const void *)k_batch<false, false>;
 }
 
+// Blocks of this many threads can launch the kernel (its launch bounds).
+bool block_fits(const void *fn, int threads) {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return threads <= fa.maxThreadsPerBlock;
+}
+
 int grid_size(cmg_batch *b, bool mixed, bool krylov) {
   const void *fn = batch_kernel(mixed, krylov);
+  if (!block_fits(fn, b->sched.threads))
+    throw Error(CMG_ERR_INVALID_ARG, "the batch kernel does not take blocks of this size");
   int per_sm = 0;
   CMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, b->sched.threads, 0));
   if (per_sm < 1) throw Error(CMG_ERR_INVALID_ARG, "the batch kernel does not fit this block size");
@@ -915,6 +927,7 @@ void batch_autotune(cmg_batch *b, const cmg_solve_params *p, cmg_batch_schedule 
       b->sched = c;
       int per_sm = 0;
       const void *fn = batch_kernel(mixed, p->krylov == 1);
+      if (!block_fits(fn, c.threads)) continue;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, c.threads, 0) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         continue;
