@@ -95,21 +95,33 @@ __device__ __forceinline__ T *g_t(const BLevel &L) {
   if constexpr (sizeof(T) == 8) return L.g; else return L.g32;
 }
 
+// The per-oct bodies read the level fields through L1 (kCG = false) or
+// through L2 only (true).  Plain loads are enough: a block reads values
+// another block wrote only after a grid barrier, whose release add and
+// acquire load at GPU scope (with the block barriers around them) order those
+// writes before the reads in the PTX memory model; per-patch scalars and the
+// control words keep their L2 loads.  CMG_BATCH_CG = 1 restores L2-only
+// loads for the fields.
+#ifndef CMG_BATCH_CG
+#define CMG_BATCH_CG 0
+#endif
+constexpr bool kCG = CMG_BATCH_CG != 0;
+
 template <typename T>
 __device__ void colour_pass(const BLevel &L, int P, bool zero, int64_t tid, int64_t nthr, T *phi, const T *g) {
   const int64_t st = L.n_alloc * 4;
   for (int64_t i = tid; i < L.n; i += nthr) {
     if (P == 0) {
       if (zero) {
-        if (L.all_active) dev::sweep_oct<T, 0, true, false, true>(i, L.nbr, phi + st, phi, g, L.active, L.n);
-        else dev::sweep_oct<T, 0, true, true, true>(i, L.nbr, phi + st, phi, g, L.active, L.n);
+        if (L.all_active) dev::sweep_oct<T, 0, true, false, kCG>(i, L.nbr, phi + st, phi, g, L.active, L.n);
+        else dev::sweep_oct<T, 0, true, true, kCG>(i, L.nbr, phi + st, phi, g, L.active, L.n);
       } else {
-        if (L.all_active) dev::sweep_oct<T, 0, false, false, true>(i, L.nbr, phi + st, phi, g, L.active, L.n);
-        else dev::sweep_oct<T, 0, false, true, true>(i, L.nbr, phi + st, phi, g, L.active, L.n);
+        if (L.all_active) dev::sweep_oct<T, 0, false, false, kCG>(i, L.nbr, phi + st, phi, g, L.active, L.n);
+        else dev::sweep_oct<T, 0, false, true, kCG>(i, L.nbr, phi + st, phi, g, L.active, L.n);
       }
     } else {
-      if (L.all_active) dev::sweep_oct<T, 1, false, false, true>(i, L.nbr, phi, phi + st, g + L.n * 4, L.active, L.n);
-      else dev::sweep_oct<T, 1, false, true, true>(i, L.nbr, phi, phi + st, g + L.n * 4, L.active, L.n);
+      if (L.all_active) dev::sweep_oct<T, 1, false, false, kCG>(i, L.nbr, phi, phi + st, g + L.n * 4, L.active, L.n);
+      else dev::sweep_oct<T, 1, false, true, kCG>(i, L.nbr, phi, phi + st, g + L.n * 4, L.active, L.n);
     }
   }
 }
@@ -140,12 +152,12 @@ __device__ bool vcycle(const BatchPlan &P, bool zero_top, int64_t tid, int64_t n
     // after pre-smoothing (n_pre >= 1) the colour-1 residuals are exactly 0
     if (P.n_pre >= 1) {
       for (int64_t i = tid; i < L.n; i += nthr)
-        dev::resid_oct<T, false, true, false, false, false, true, true>(
+        dev::resid_oct<T, false, true, false, false, false, kCG, true>(
             i, L.nbr, phi_t<T>(L), g_t<T>(L), L.all_active ? nullptr : L.active, L.n, L.n_alloc, L.father,
             g_t<T>(C), phi_t<T>(C), C.n, C.n_alloc, zc, nullptr, 0.0, nullptr, 0.0);
     } else {
       for (int64_t i = tid; i < L.n; i += nthr)
-        dev::resid_oct<T, false, true, false, false, false, true>(
+        dev::resid_oct<T, false, true, false, false, false, kCG>(
             i, L.nbr, phi_t<T>(L), g_t<T>(L), L.all_active ? nullptr : L.active, L.n, L.n_alloc, L.father,
             g_t<T>(C), phi_t<T>(C), C.n, C.n_alloc, zc, nullptr, 0.0, nullptr, 0.0);
     }
@@ -170,16 +182,16 @@ __device__ bool vcycle(const BatchPlan &P, bool zero_top, int64_t tid, int64_t n
     // with post-smoothing, the colour-0 corrections are overwritten unread
     for (int64_t i = tid; i < L.n; i += nthr) {
       if (L.all_active && P.n_post >= 1)
-        dev::prolong_oct<T, false, true, true>(i, L.keys, L.blk, L.n, L.n_alloc, phi_t<T>(L), L.active, phi_t<T>(C),
+        dev::prolong_oct<T, false, kCG, true>(i, L.keys, L.blk, L.n, L.n_alloc, phi_t<T>(L), L.active, phi_t<T>(C),
                                                C.n_alloc);
       else if (L.all_active)
-        dev::prolong_oct<T, false, true>(i, L.keys, L.blk, L.n, L.n_alloc, phi_t<T>(L), L.active, phi_t<T>(C),
+        dev::prolong_oct<T, false, kCG>(i, L.keys, L.blk, L.n, L.n_alloc, phi_t<T>(L), L.active, phi_t<T>(C),
                                          C.n_alloc);
       else if (P.n_post >= 1)
-        dev::prolong_oct<T, true, true, true>(i, L.keys, L.blk, L.n, L.n_alloc, phi_t<T>(L), L.active, phi_t<T>(C),
+        dev::prolong_oct<T, true, kCG, true>(i, L.keys, L.blk, L.n, L.n_alloc, phi_t<T>(L), L.active, phi_t<T>(C),
                                               C.n_alloc);
       else
-        dev::prolong_oct<T, true, true>(i, L.keys, L.blk, L.n, L.n_alloc, phi_t<T>(L), L.active, phi_t<T>(C),
+        dev::prolong_oct<T, true, kCG>(i, L.keys, L.blk, L.n, L.n_alloc, phi_t<T>(L), L.active, phi_t<T>(C),
                                         C.n_alloc);
     }
     if (!grid_sync(P)) return false;
@@ -203,7 +215,7 @@ __device__ void top_residual(const BatchPlan &P, double *acc_out, int64_t tid, i
     if (i < L.n) {
       p = __ldg(P.pid + i);
       const double inv_s = MIXED ? 1.0 / __ldcg(P.s_emit + p) : 0.0;
-      acc = dev::resid_oct<double, true, false, MIXED, false, ZPHI, true, C1Z>(
+      acc = dev::resid_oct<double, true, false, MIXED, false, ZPHI, kCG, C1Z>(
           i, L.nbr, L.phi, L.g, nullptr, L.n, L.n_alloc, nullptr, nullptr, nullptr, 0, 0, 0, L.g32, inv_s, nullptr,
           0.0);
     }

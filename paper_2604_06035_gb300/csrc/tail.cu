@@ -96,8 +96,7 @@ __device__ bool per_cell(const Map &map, int64_t n) {
   return sizeof(T) == 8 && map.fits_per_cell(n);
 }
 
-// CG: loads through L2 only (another CTA may have written the data); a
-// single-CTA tail reads through L1.
+// CG: loads through L2 only; otherwise plain loads (see k_tailg).
 template <typename T, bool MASK, bool CG, class Map>
 __device__ void pass(const TailLevel &L, int P, bool zero, const Map &map) {
   T *phi = static_cast<T *>(L.phi);
@@ -282,25 +281,34 @@ struct GridSync {
 constexpr int kTailThreads1 = 1024;
 
 // Grid tail: levels [m0, split) on all CTAs, [split, last] on CTA 0.
+//
+// The level fields are read with plain (L1-cacheable) loads (kTailCG =
+// false): a CTA reads values another CTA wrote only after a grid barrier,
+// whose release add and acquire load at GPU scope, with the block barriers
+// around them, order those writes before the reads in the PTX memory model.
+// CMG_TAIL_CG = 1 routes them through L2 only.
+#ifndef CMG_TAIL_CG
+#define CMG_TAIL_CG 0
+#endif
+constexpr bool kTailCG = CMG_TAIL_CG != 0;
+
 template <typename T>
 __global__ void __launch_bounds__(kTailThreads) k_tailg(const __grid_constant__ TailPlan plan) {
   GridSync gs{plan.bar, plan.err, plan.spin_budget};
   const ChunkMap map{(int64_t)blockIdx.x, (int64_t)gridDim.x, (int64_t)threadIdx.x, (int64_t)blockDim.x};
   const int split = plan.split;
   if (split <= plan.last) {
-    descend<T, true>(plan, plan.m0, split, map, gs);
+    descend<T, kTailCG>(plan, plan.m0, split, map, gs);
     if (blockIdx.x == 0) {
-      // L1 loads are safe here: every level from split down is its own
-      // allocation that CTA 0 has not read earlier in this launch (L1 starts
-      // each launch empty), and below split only CTA 0 writes
+      // CTA 0 alone from split down: block barriers, loads through L1
       BlockSync bs;
       const FlatMap fm{(int64_t)threadIdx.x, (int64_t)blockDim.x};
       tail_body<T, false>(plan, split, fm, bs);
     }
     gs();
-    ascend<T, true>(plan, split - 1, plan.m0, map, gs);
+    ascend<T, kTailCG>(plan, split - 1, plan.m0, map, gs);
   } else {
-    tail_body<T, true>(plan, plan.m0, map, gs);
+    tail_body<T, kTailCG>(plan, plan.m0, map, gs);
   }
 }
 
