@@ -178,6 +178,21 @@ int cmg_debug_inject_alloc_failure(int64_t after) {
   });
 }
 
+int cmg_debug_neighbour_sum(cmg_ctx *ctx, const double *rows, int64_t n, double *out, cmg_mem mem) {
+  return guard([&] {
+    need(ctx && n >= 0 && (n == 0 || (rows && out)), "bad arguments");
+    check_mem(mem);
+    DeviceScope ds(ctx->device);
+    accept(ctx, rows, sizeof(double) * 6 * n, mem, [&](const void *din) {
+      deliver(ctx, out, sizeof(double) * n, mem, [&](void *dout) {
+        cmg::neighbour_sum(static_cast<const double *>(din), n, static_cast<double *>(dout), ctx->stream);
+      });
+    });
+    CMG_CUDA(cudaStreamSynchronize(ctx->stream));
+    return CMG_OK;
+  });
+}
+
 const char *cmg_last_error(void) { return g_last_error.c_str(); }
 
 int cmg_ctx_create(int device, void *stream, cmg_ctx **out) {

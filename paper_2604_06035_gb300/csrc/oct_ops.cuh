@@ -98,9 +98,10 @@ __device__ __forceinline__ double fixed_sum(const double *v) {
     e[k] = (int)((hi[k] >> 20) & 0x7FFu);
     E = max(E, e[k]);
   }
-  // an infinity or NaN, or every operand below 2^-960 (zeros included):
-  // FP64 additions
-  if (E == 0x7FF || E < 64) {
+  // an infinity or NaN, an operand of 2^1021 or more (whose sum could
+  // overflow the exponent field below), or every operand below 2^-960 (zeros
+  // included): FP64 additions
+  if (E >= 0x7FC || E < 64) {
     double s = v[0];
 #pragma unroll
     for (int k = 1; k < N; ++k) s += v[k];

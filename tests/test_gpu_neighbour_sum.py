@@ -1,0 +1,189 @@
+"""The FP64 neighbour sum every stencil kernel forms (Sec. 5.1.1's 7-point
+update sums the six face neighbours), checked on its own through
+cmg_debug_neighbour_sum, bit for bit.
+
+The library sums the first five neighbours as integers at the scale
+2^(E - 1082) (E the largest biased exponent among them), rounds that sum once
+to nearest (ties to even) and adds the sixth by one FP64 addition.  Two
+checks pin it to something other than its own description:
+
+* Rows whose five operands are all multiples of that scale (in particular,
+  within seven binades of one another) are summed exactly, so the first step
+  must equal Python's math.fsum, the correctly rounded sum.  Ties, exact
+  cancellations and signed mixtures are built in on purpose.
+* Any row: the result must equal an exact-arithmetic model of the same rule
+  (Python integers and correctly rounded int -> float conversion), and lie
+  within half an ulp plus the five truncations of the exact sum.
+
+Zeros are compared without their sign (the integer sum has no -0), NaN by
+being NaN."""
+import math
+import struct
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2604_06035_gb300 import cmg
+    c = cmg.cmg_ctx_create(0)
+    yield c
+    cmg.cmg_ctx_destroy(c)
+
+
+def _bits(x):
+    return struct.unpack("<Q", struct.pack("<d", float(x)))[0]
+
+
+def _biased_exp(x):
+    return (_bits(x) >> 52) & 0x7FF
+
+
+def _five_model(v):
+    """The integer-scaled sum of five FP64 values, in exact arithmetic."""
+    es = [_biased_exp(x) for x in v]
+    E = max(es)
+    if E >= 0x7FC or E < 64:
+        s = float(v[0])
+        for x in v[1:]:
+            s = s + float(x)
+        return s
+    S = 0
+    for x, e in zip(v, es):
+        if e == 0:  # zero or subnormal: far below the scale
+            continue
+        m = (_bits(x) & ((1 << 52) - 1)) | (1 << 52)  # |x| = m 2^(e - 1075)
+        k = E - e - 7  # |x| / 2^(E - 1082) = m 2^-k
+        t = m >> k if k >= 0 else m << -k  # truncated toward zero
+        S += -t if x < 0 else t
+    sh = E - 1082
+    return float(S * (1 << sh)) if sh >= 0 else S / (1 << -sh)
+
+
+def _model(row):
+    return _five_model(row[:5]) + float(row[5])
+
+
+def _same(a, b):
+    a, b = float(a), float(b)
+    if math.isnan(a) or math.isnan(b):
+        return math.isnan(a) and math.isnan(b)
+    if a == 0.0 and b == 0.0:
+        return True
+    return _bits(a) == _bits(b)
+
+
+def _gpu(ctx, rows):
+    import torch
+    from paper_2604_06035_gb300 import cmg
+    rows = np.ascontiguousarray(rows, dtype=np.float64)
+    out = cmg.cmg_debug_neighbour_sum(ctx, torch.from_numpy(rows).cuda())
+    host = cmg.cmg_debug_neighbour_sum(ctx, rows)
+    got = out.cpu().numpy()
+    assert np.array_equal(got.view(np.uint64), np.asarray(host).view(np.uint64))
+    return got
+
+
+def _exact_rows(rng, n):
+    """Rows whose five summed operands are multiples of the scale."""
+    rows = []
+    for _ in range(n):
+        kind = rng.integers(5)
+        base = math.ldexp(1.0, int(rng.integers(-300, 300)))
+        if kind == 0:  # same binade range: random significands, mixed signs
+            r = [float(x) * base for x in rng.uniform(-2, 2, 5)]
+            r = [x if abs(x) >= base / 64 else base / 3 for x in r]
+        elif kind == 1:  # exact cancellation leaving a small remainder
+            a, b = (float(x) * base for x in rng.uniform(1, 2, 2))
+            r = [a, -a, b, -b, base * 2.0 ** -int(rng.integers(0, 7))]
+        elif kind == 2:  # a tie: 1 + half an ulp (+ further half ulps)
+            one = base * (1.0 + math.ldexp(float(rng.integers(2)), -52))
+            h = math.ldexp(base, -53)
+            r = [one, h, 0.0, -0.0, 0.0] if rng.integers(2) else [one, h, h, -h, 0.0]
+        elif kind == 3:  # integers far apart in size (exact at the scale)
+            r = [float(int(x)) * base for x in rng.integers(-2**20, 2**20, 5)]
+            r[0] = base * 2.0 ** 21
+        else:  # the sum carries into a higher binade and ties there (2.5 ulps)
+            r = [base * (2.0 - math.ldexp(1.0, -52))] * 4 + [3 * math.ldexp(base, -49)]
+        rng.shuffle(r)
+        rows.append(r + [float(rng.normal()) * base])
+    return np.array(rows, dtype=np.float64)
+
+
+def _general_rows(rng, n):
+    e = rng.integers(-90, 90, size=(n, 6))
+    rows = rng.uniform(1, 2, size=(n, 6)) * np.exp2(e) * rng.choice([-1.0, 1.0], size=(n, 6))
+    # some rows at level-solve magnitudes, some with a far smaller sixth value
+    rows[: n // 4] = rng.normal(size=(n // 4, 6))
+    rows[n // 4: n // 2, 5] *= 1e-30
+    special = [
+        [0.0] * 6,
+        [-0.0] * 6,
+        [5e-324, -5e-324, 1e-310, 2.2e-308, 0.0, 1.0],  # five subnormals: FP64 additions
+        [1.0, 5e-324, -1e-310, 2.2e-308, -0.0, 0.0],  # subnormals beside a normal value vanish
+        [1e-300, 5e-324, -3e-310, 0.0, 0.0, 0.0],  # all below 2^-960: FP64 additions
+        [math.inf, 1.0, 2.0, 3.0, 4.0, 5.0],
+        [-math.inf, math.inf, 0.0, 0.0, 0.0, 0.0],
+        [math.nan, 1.0, 0.0, 0.0, 0.0, 0.0],
+        [1.7e308, 1.7e308, -1.0, 0.0, 0.0, 0.0],  # >= 2^1021: FP64 additions, overflow to inf
+        [math.ldexp(1.0, 1020) * 1.9] * 5 + [0.0],  # just under 2^1021: integers, near the top
+        [1.0, 2.0 ** -60, 2.0 ** -61, 3 * 2.0 ** -62, -(2.0 ** -59), 0.0],  # truncated bits
+    ]
+    return np.concatenate([rows, np.array(special)])
+
+
+def test_exact_rows_match_the_correctly_rounded_sum(ctx):
+    rng = np.random.default_rng(7)
+    rows = _exact_rows(rng, 4000)
+    got = _gpu(ctx, rows)
+    for r, g in zip(rows, got):
+        want = math.fsum(r[:5]) + r[5]
+        assert _same(g, want), (list(r), g, want)
+
+
+def test_every_row_matches_the_exact_model(ctx):
+    rng = np.random.default_rng(8)
+    rows = _general_rows(rng, 20000)
+    got = _gpu(ctx, rows)
+    for r, g in zip(rows, got):
+        assert _same(g, _model(r)), (list(r), g, _model(r))
+
+
+def test_error_bound_against_the_exact_sum(ctx):
+    """|fixed5 - exact| <= half an ulp of the result + 5 truncations, each
+    below 2^(E - 1082), on rows with operands spread over 100 binades."""
+    from fractions import Fraction
+    rng = np.random.default_rng(9)
+    rows = _general_rows(rng, 3000)[:3000]
+    rows[:, 5] = 0.0  # the sixth enters as +0.0: out is the five-operand sum
+    got = _gpu(ctx, rows)
+    for r, g in zip(rows, got):
+        E = max(_biased_exp(x) for x in r[:5])
+        if E < 64:
+            continue
+        exact = sum(Fraction(float(x)) for x in r[:5])
+        ulp = Fraction(math.ulp(float(g))) if g != 0 else Fraction(0)
+        bound = ulp / 2 + 5 * Fraction(2) ** (E - 1082)
+        assert abs(Fraction(float(g)) - exact) <= bound, list(r)
+
+
+def test_order_of_the_five_does_not_matter(ctx):
+    rng = np.random.default_rng(10)
+    rows = _general_rows(rng, 2000)[:2000]
+    perm = rows.copy()
+    for r in perm:
+        r[:5] = r[rng.permutation(5)]
+    a, b = _gpu(ctx, rows), _gpu(ctx, perm)
+    assert all(_same(x, y) for x, y in zip(a, b))
+
+
+def test_argument_checks(ctx):
+    from paper_2604_06035_gb300 import cmg
+    with pytest.raises(ValueError):
+        cmg.cmg_debug_neighbour_sum(ctx, np.zeros(7))
+    assert cmg.cmg_debug_neighbour_sum(ctx, np.zeros((0, 6))).shape == (0,)
