@@ -127,19 +127,23 @@ int cmg_ctx_launch_count(cmg_ctx *ctx, int64_t *launches);
  * INVALID_ARG if negative. */
 int cmg_debug_inject_alloc_failure(int64_t after);
 
-/* The FP64 stencil's neighbour sum on its own, for testing that arithmetic
- * (Sec. 5.1.1: the 7-point update sums the six face neighbours).  rows is
- * [n][6] FP64, the neighbours of one cell in the order -x, +x, -y, +y, -z,
- * +z; out[i] receives exactly the value every FP64 kernel of the library
- * forms as that cell's neighbour sum (the first five in one exact
- * integer-scaled sum rounded once to nearest, ties to even, each operand
- * more than seven binades below the largest truncated to 2^-59 of it; then
- * one FP64 addition of the sixth; FP64 additions throughout when an operand
- * is infinite, NaN or at least 2^1021, or all are below 2^-960).  rows and
- * out are both host or both device memory (mem), owned by the caller; the
- * call returns when out is written.  INVALID_ARG on a NULL context or
- * pointer, negative n or an unknown mem. */
-int cmg_debug_neighbour_sum(cmg_ctx *ctx, const double *rows, int64_t n, double *out, cmg_mem mem);
+/* The FP64 stencil's neighbour sums on their own, for testing that
+ * arithmetic (Sec. 5.1.1: the 7-point update sums the six face neighbours).
+ * rows is [n][6] FP64, the neighbours of one cell in the order -x, +x, -y,
+ * +y, -z, +z; out[i] receives exactly the value the library's FP64 kernels
+ * form as that cell's neighbour sum:
+ *   which = 0 (colour passes and colour-1 residuals): the first five in one
+ *     exact integer-scaled sum rounded once to nearest, ties to even, then one
+ *     FP64 addition of the sixth;
+ *   which = 1 (colour-0 residuals): all six in the integer-scaled sum.
+ * In the integer-scaled sum each operand more than seven binades below the
+ * largest is truncated at 2^-59 of the largest's binade; FP64 additions in
+ * order take its place when an operand is infinite, NaN or at least 2^1021,
+ * or all are below 2^-960.  rows and out are both host or both device memory
+ * (mem), owned by the caller; the call returns when out is written.
+ * INVALID_ARG on a NULL context or pointer, negative n, which not 0 or 1, or
+ * an unknown mem. */
+int cmg_debug_neighbour_sum(cmg_ctx *ctx, const double *rows, int64_t n, int which, double *out, cmg_mem mem);
 
 /* Morton keys (Sec. 4.2 Eq. (morton_encode), App. A Alg. 1; B = 21 bits per
  * coordinate): ijk is [n][3] uint32 (i, j, k), keys is [n] uint64.  Both in

@@ -87,7 +87,7 @@ _SIGS = {
     "cmg_ctx_launch_count": (_I, [_P, C.POINTER(_I64)]),
     "cmg_morton_encode": (_I, [_P, _P, _I64, _P, _I]),
     "cmg_debug_inject_alloc_failure": (_I, [_I64]),
-    "cmg_debug_neighbour_sum": (_I, [_P, _P, _I64, _P, _I]),
+    "cmg_debug_neighbour_sum": (_I, [_P, _P, _I64, _I, _P, _I]),
     "cmg_morton_encode128": (_I, [_P, _P, _I64, _P, _I]),
     "cmg_morton_decode128": (_I, [_P, _P, _I64, _P, _I]),
     "cmg_level_build128": (_I, [_P, _I, _I, _I, _P, _I64, _I, _P, C.POINTER(_P)]),
@@ -310,15 +310,16 @@ def cmg_debug_inject_alloc_failure(after):
     _check(lib().cmg_debug_inject_alloc_failure(int(after)), "cmg_debug_inject_alloc_failure")
 
 
-def cmg_debug_neighbour_sum(ctx, rows, out=None):
-    """Tests: the FP64 neighbour sum of each [6] row, as the kernels form it."""
+def cmg_debug_neighbour_sum(ctx, rows, which=0, out=None):
+    """Tests: the FP64 neighbour sum of each [6] row, as the kernels form it
+    (which = 0: colour passes and colour-1 residuals; 1: colour-0 residuals)."""
     p, mem, keep = _in(rows, np.float64)
     n = keep.numel() // 6 if _is_torch(keep) else keep.size // 6
     if (keep.numel() if _is_torch(keep) else keep.size) != 6 * n:
         raise ValueError("rows must hold a multiple of 6 values")
     q, mem2, res = _out((n,), np.float64, device=(mem == CMG_MEM_DEVICE), out=out)
     _same_mem(mem, mem2, "cmg_debug_neighbour_sum")
-    _check(lib().cmg_debug_neighbour_sum(ctx, p, n, q, mem), "cmg_debug_neighbour_sum")
+    _check(lib().cmg_debug_neighbour_sum(ctx, p, n, int(which), q, mem), "cmg_debug_neighbour_sum")
     return res
 
 

@@ -178,14 +178,15 @@ int cmg_debug_inject_alloc_failure(int64_t after) {
   });
 }
 
-int cmg_debug_neighbour_sum(cmg_ctx *ctx, const double *rows, int64_t n, double *out, cmg_mem mem) {
+int cmg_debug_neighbour_sum(cmg_ctx *ctx, const double *rows, int64_t n, int which, double *out, cmg_mem mem) {
   return guard([&] {
     need(ctx && n >= 0 && (n == 0 || (rows && out)), "bad arguments");
+    need(which == 0 || which == 1, "which must be 0 or 1");
     check_mem(mem);
     DeviceScope ds(ctx->device);
     accept(ctx, rows, sizeof(double) * 6 * n, mem, [&](const void *din) {
       deliver(ctx, out, sizeof(double) * n, mem, [&](void *dout) {
-        cmg::neighbour_sum(static_cast<const double *>(din), n, static_cast<double *>(dout), ctx->stream);
+        cmg::neighbour_sum(static_cast<const double *>(din), n, which, static_cast<double *>(dout), ctx->stream);
       });
     });
     CMG_CUDA(cudaStreamSynchronize(ctx->stream));

@@ -397,8 +397,9 @@ void mg_active_bytes(const MgLev &g, uint8_t *out, cudaStream_t s);
 
 // ops.cu
 void set_density(cmg_level *L, const double *rho, double rho_bar, double four_pi_g);
-// rows [n][6] -> out [n], device memory (the FP64 stencil's neighbour sum)
-void neighbour_sum(const double *rows, int64_t n, double *out, cudaStream_t s);
+// rows [n][6] -> out [n], device memory (the FP64 stencil's neighbour sums;
+// which: 0 = colour passes and colour-1 residuals, 1 = colour-0 residuals)
+void neighbour_sum(const double *rows, int64_t n, int which, double *out, cudaStream_t s);
 void pack_field(cmg_level *L, int m, int field, int prec, const void *in);
 void unpack_field(cmg_level *L, int m, int field, int prec, void *out);
 void fill_ghosts(cmg_level *L);

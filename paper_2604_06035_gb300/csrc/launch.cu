@@ -318,21 +318,27 @@ void unpack_field(cmg_level *L, int m, int field, int prec, void *out) {
   CMG_CUDA(cudaGetLastError());
 }
 
-// The stencil's neighbour sum applied to given rows of six values: out[i] =
-// the sum every kernel forms for a cell whose neighbours (-x, +x, -y, +y,
-// -z, +z) hold rows[i][0..5], for checking that arithmetic on its own.
+// The stencil's neighbour sums applied to given rows of six values: out[i] =
+// the sum the kernels form for a cell whose neighbours (-x, +x, -y, +y, -z,
+// +z) hold rows[i][0..5] -- in colour passes and colour-1 residuals (which =
+// 0) or in colour-0 residuals (which = 1) -- for checking that arithmetic on
+// its own.
+template <int WHICH>
 __global__ void k_neighbour_sum(const double *__restrict__ rows, int64_t n, double *__restrict__ out) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   double v[6];
 #pragma unroll
   for (int d = 0; d < 6; ++d) v[d] = rows[i * 6 + d];
-  out[i] = dev::nbsum6(v);
+  out[i] = WHICH == 0 ? dev::nbsum6(v) : dev::nbsum6_r0(v);
 }
 
-void neighbour_sum(const double *rows, int64_t n, double *out, cudaStream_t s) {
+void neighbour_sum(const double *rows, int64_t n, int which, double *out, cudaStream_t s) {
   if (n == 0) return;
-  k_neighbour_sum<<<blocks_for(n), kThreads, 0, s>>>(rows, n, out);
+  if (which == 0)
+    k_neighbour_sum<0><<<blocks_for(n), kThreads, 0, s>>>(rows, n, out);
+  else
+    k_neighbour_sum<1><<<blocks_for(n), kThreads, 0, s>>>(rows, n, out);
   CMG_CUDA(cudaGetLastError());
 }
 

@@ -190,6 +190,26 @@ __device__ __forceinline__ double nbsum6(const double v[6]) {
 #endif
 }
 
+// The neighbour sum of a colour-0 residual cell (CMG_RESID_NB): 0 = nbsum6;
+// 1 = all six in the integer sum.  No colour-0 residual has to repeat a
+// colour pass's sum (only the colour-1 residuals after a colour-1 pass do,
+// and they keep nbsum6), and the residual spends twice the sweep's FP64
+// instructions per cell (the subtraction of phi and the norm or restriction
+// sum), so its best split differs: measured on GB300 (256^3 + 3-level FP64
+// chain, one box), the residual family 11.6 -> 10.9 ms per step with all six
+// in integers.
+#ifndef CMG_RESID_NB
+#define CMG_RESID_NB 1
+#endif
+__device__ __forceinline__ float nbsum6_r0(const float v[6]) { return nbsum6(v); }
+__device__ __forceinline__ double nbsum6_r0(const double v[6]) {
+#if CMG_RESID_NB == 1
+  return fixed_sum<6>(v);
+#else
+  return nbsum6(v);
+#endif
+}
+
 template <typename T>
 __device__ __forceinline__ T fma_t(T a, T b, T c);
 template <>
@@ -311,8 +331,9 @@ __device__ __forceinline__ ResidIdx resid_idx(int64_t i, const int32_t *__restri
 // forms the same s from the same values in the same order, so each
 // colour-1 residual is exactly +0 (inactive cells are +0 anyway): their
 // stencils are skipped.  Skipping changes no result bit: the norm gains
-// +0 terms (acc >= +0 throughout), the restriction sum gains +0 four times,
-// which equals adding +0 once, and EMIT / ROUT write what dv = +0 gives.
+// +0 terms (acc >= +0 throughout), the restriction sum would gain +0 four
+// times, which leaves it unchanged (it is never -0), and EMIT / ROUT write
+// what dv = +0 gives.
 template <typename T, bool NORM, bool RESTRICT, bool EMIT, bool ROUT, bool ZPHI, bool CG, bool C1Z = false>
 __device__ __forceinline__ double resid_oct_idx(int64_t i, const ResidIdx &x, const T *phi, const T *g, int64_t n,
                                                 int64_t n_alloc, T *cg, T *cphi, int64_t cn, int64_t cn_alloc,
@@ -337,7 +358,8 @@ __device__ __forceinline__ double resid_oct_idx(int64_t i, const ResidIdx &x, co
 #pragma unroll
   for (int p = 0; p < 2; ++p) {
     if (C1Z && p == 1) {
-      if (RESTRICT) rsum += T(0);
+      // rsum needs no + 0 for the four zeros: it starts at +0 and a sum that
+      // cancels rounds to +0, so it is never -0
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         if (EMIT) g32[(p * n + i) * 4 + q] = (float)((double)T(0) * inv_s);
@@ -359,7 +381,7 @@ __device__ __forceinline__ double resid_oct_idx(int64_t i, const ResidIdx &x, co
           v[d] = (ZPHI && o < n) ? T(0) : ld1<CG>(phi + ((1 - p) * n_alloc + o) * 4 + (c2 >> 1));
         }
       }
-      T dv = fma_t(nbsum6(v), inv6, gv[p][q]) - pl[p][q];
+      T dv = fma_t(p == 0 ? nbsum6_r0(v) : nbsum6(v), inv6, gv[p][q]) - pl[p][q];
       if (!((m >> c) & 1)) dv = T(0);
       if (NORM) {
         if constexpr (sizeof(T) == 8)
@@ -419,7 +441,10 @@ __device__ __forceinline__ void resid_restrict_cell(bool valid, int64_t i, const
       const int64_t o = (((c >> a) & 1) != side) ? i : (int64_t)__ldg(nbr + d * n + i);
       v[d] = ld1<CG>(phi + ((1 - p) * n_alloc + o) * 4 + (c2 >> 1));
     }
-    dv = fma_t(nbsum6(v), inv6, gv) - pv;
+    if (p == 0)
+      dv = fma_t(nbsum6_r0(v), inv6, gv) - pv;
+    else
+      dv = fma_t(nbsum6(v), inv6, gv) - pv;
     const unsigned m = active ? __ldg(active + i) : 0xFFu;
     if (!((m >> c) & 1)) dv = T(0);
   }
@@ -454,7 +479,36 @@ __device__ __forceinline__ void axis_cell(int cx, int e, int &a, int &bit) {
 // Trilinear cell-centred interpolation of a coarse field onto the 8 children
 // of the coarse cell (block octs b, octant cc): per axis weight 3/4 for the
 // father, 1/4 for its neighbour toward the child (Sec. 5.1.1).
-template <typename T, bool CG>
+//
+// CMG_PROLONG_SEP = 1: separably, in units of 1/4 per axis: along x each pair
+// (father, neighbour) becomes 3 a + b in one FMA, then the same along y and
+// along z, giving 64 x the value (weights 27, 9, 3, 1).  A child costs 7 FMAs
+// and the children of an oct share their x and y stages (the 4 colour-1
+// children of an oct 26 FMAs, all 8 of them 38, against 32 and 64 for the
+// weighted eight-term sum); the 64 is divided out exactly (a power of two)
+// in the FMA that adds the correction to phi, or by a multiplication for a
+// plain value.  CMG_PROLONG_SEP = 0: the eight weighted terms in one FMA
+// chain.
+#ifndef CMG_PROLONG_SEP
+#define CMG_PROLONG_SEP 1
+#endif
+// 3 a + b with one rounding
+template <typename T>
+__device__ __forceinline__ T tri3(T father, T side) {
+  return fma_t(T(3), father, side);
+}
+// 64 x the interpolated value of one child from the coarse values around
+// it: vXYZ with 1 = the father's coordinate on that axis, s = its neighbour
+// toward the child.
+template <typename T>
+__device__ __forceinline__ T interp64(T v111, T vs11, T v1s1, T vss1, T v11s, T vs1s, T v1ss, T vsss) {
+  return tri3(tri3(tri3(v111, vs11), tri3(v1s1, vss1)), tri3(tri3(v11s, vs1s), tri3(v1ss, vsss)));
+}
+constexpr double kInv64 = 0.015625;
+
+// The 8 children's values (X64 = false) or, with CMG_PROLONG_SEP = 1 and
+// X64 = true, 64 x them.
+template <typename T, bool CG, bool X64 = false>
 __device__ __forceinline__ void interp8(const T *cphi, int64_t cn_alloc, const int32_t b[8], int cc, T out[8]) {
   T v[27];
 #pragma unroll
@@ -471,11 +525,17 @@ __device__ __forceinline__ void interp8(const T *cphi, int64_t cn_alloc, const i
         const int64_t oct = b[ax | (ay << 1) | (az << 2)];
         v[ex + 3 * ey + 9 * ez] = ld1<CG>(cphi + ((int64_t)cell_parity(ch) * cn_alloc + oct) * 4 + (ch >> 1));
       }
-  const T w0 = T(0.75), w1 = T(0.25);
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const int fx = c & 1, fy = (c >> 1) & 1, fz = (c >> 2) & 1;
     const int ex1 = fx ? 2 : 0, ey1 = fy ? 2 : 0, ez1 = fz ? 2 : 0;
+#if CMG_PROLONG_SEP
+    const T z = interp64(v[1 + 3 * 1 + 9 * 1], v[ex1 + 3 * 1 + 9 * 1], v[1 + 3 * ey1 + 9 * 1],
+                         v[ex1 + 3 * ey1 + 9 * 1], v[1 + 3 * 1 + 9 * ez1], v[ex1 + 3 * 1 + 9 * ez1],
+                         v[1 + 3 * ey1 + 9 * ez1], v[ex1 + 3 * ey1 + 9 * ez1]);
+    out[c] = X64 ? z : z * T(kInv64);
+#else
+    const T w0 = T(0.75), w1 = T(0.25);
     T acc = w0 * w0 * w0 * v[1 + 3 * 1 + 9 * 1];
     acc = fma_t(w1 * w0 * w0, v[ex1 + 3 * 1 + 9 * 1], acc);
     acc = fma_t(w0 * w1 * w0, v[1 + 3 * ey1 + 9 * 1], acc);
@@ -485,7 +545,18 @@ __device__ __forceinline__ void interp8(const T *cphi, int64_t cn_alloc, const i
     acc = fma_t(w0 * w1 * w1, v[1 + 3 * ey1 + 9 * ez1], acc);
     acc = fma_t(w1 * w1 * w1, v[ex1 + 3 * ey1 + 9 * ez1], acc);
     out[c] = acc;
+#endif
   }
+}
+
+// phi + the child's correction as interp8<..., true> gives it
+template <typename T>
+__device__ __forceinline__ T add_corr(T phi, T corr) {
+#if CMG_PROLONG_SEP
+  return fma_t(corr, T(kInv64), phi);
+#else
+  return phi + corr;
+#endif
 }
 
 // phi[i] += trilinear interpolation of the coarse correction (active cells).
@@ -514,7 +585,7 @@ template <typename T, bool MASK, bool CG, bool C0D = false>
 __device__ __forceinline__ void prolong_oct_idx(int64_t i, const ProlongIdx &x, int64_t n_alloc, T *phi,
                                                 const T *cphi, int64_t cn_alloc) {
   T corr[8];
-  interp8<T, CG>(cphi, cn_alloc, x.b, x.cc, corr);
+  interp8<T, CG, true>(cphi, cn_alloc, x.b, x.cc, corr);
   const unsigned m = x.m;
 #pragma unroll
   for (int p = C0D ? 1 : 0; p < 2; ++p) {
@@ -523,7 +594,7 @@ __device__ __forceinline__ void prolong_oct_idx(int64_t i, const ProlongIdx &x, 
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int c = plane_cell(p, q);
-      if ((m >> c) & 1) v[q] += corr[c];
+      if ((m >> c) & 1) v[q] = add_corr(v[q], corr[c]);
     }
     store4(phi + (p * n_alloc + i) * 4, v);
   }
@@ -555,6 +626,10 @@ __device__ __forceinline__ void prolong_cell(int64_t i, int c, const uint64_t *_
     return ld1<CG>(cphi + ((int64_t)cell_parity(ch) * cn_alloc + oct) * 4 + (ch >> 1));
   };
   const int ex1 = (c & 1) ? 2 : 0, ey1 = ((c >> 1) & 1) ? 2 : 0, ez1 = ((c >> 2) & 1) ? 2 : 0;
+#if CMG_PROLONG_SEP
+  const T acc = interp64(val(1, 1, 1), val(ex1, 1, 1), val(1, ey1, 1), val(ex1, ey1, 1), val(1, 1, ez1),
+                         val(ex1, 1, ez1), val(1, ey1, ez1), val(ex1, ey1, ez1));
+#else
   const T w0 = T(0.75), w1 = T(0.25);
   T acc = w0 * w0 * w0 * val(1, 1, 1);
   acc = fma_t(w1 * w0 * w0, val(ex1, 1, 1), acc);
@@ -564,8 +639,9 @@ __device__ __forceinline__ void prolong_cell(int64_t i, int c, const uint64_t *_
   acc = fma_t(w1 * w0 * w1, val(ex1, 1, ez1), acc);
   acc = fma_t(w0 * w1 * w1, val(1, ey1, ez1), acc);
   acc = fma_t(w1 * w1 * w1, val(ex1, ey1, ez1), acc);
+#endif
   T *dst = phi + ((int64_t)cell_parity(c) * n_alloc + i) * 4 + (c >> 1);
-  *dst = ld1<CG>(dst) + acc;
+  *dst = add_corr(ld1<CG>(dst), acc);
 }
 
 // Exact solve of the periodic 2^3 oct by one warp (all 32 lanes call it;
