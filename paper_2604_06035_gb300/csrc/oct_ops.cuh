@@ -64,15 +64,17 @@ __device__ __forceinline__ void store4(float *p, const float v[4]) {
 // than five sequential FP64 additions, and does not depend on the order of
 // the operands.  Zero and subnormal operands contribute nothing (a subnormal
 // is below 2^-1022, far under the scale).  The rounding is written out in
-// integer operations (CMG_FXNORM = 0) or is the int64 -> FP64 conversion
-// (CMG_FXNORM = 1).  The alignment below costs ~15 integer instructions per
+// integer operations: one biased truncation (CMG_FXNORM = 2, the default) or
+// the dropped part compared with half (0); or it is the int64 -> FP64
+// conversion (1).  The alignment below costs ~15 integer instructions per
 // operand; an earlier form (significand assembled with its leading bit,
 // shifted left 7 and right by E - e, negated as (m ^ s) - s) gave the same
 // bits on 10^6 probe sums and ran 15 % slower on GB300.
-// CMG_FXNORM = 1 measured slower in the 4 + 2 split on GB300 (512^3 FP64
-// colour pass 0.486 -> 0.603 ms): the conversion issues on the FP64 pipe.
+// Measured on GB300 (512^3 FP64 colour pass): CMG_FXNORM = 2 0.407 ms
+// against 0.422 ms for 0 (same bits); 1 was slower in the 4 + 2 split
+// (0.486 -> 0.603 ms): the conversion issues on the FP64 pipe.
 #ifndef CMG_FXNORM
-#define CMG_FXNORM 0
+#define CMG_FXNORM 2
 #endif
 // CMG_FXALIGN: 1 = the alignment below; 0 = the earlier form (same bits
 // whenever some operand is 2^-960 or larger).
@@ -150,9 +152,19 @@ __device__ __forceinline__ double fixed_sum(const double *v) {
   if (eb <= 0) return ldexp((double)S, E - 1082);  // subnormal sum (never in practice)
   unsigned long long mant;
   if (p > 52) {
-    const int r = p - 52;
+    const int r = p - 52;  // 1 .. 10
+#if CMG_FXNORM == 2
+    // round half to even by one biased truncation: adding 2^(r-1) - 1 plus
+    // the last kept bit carries into the kept bits exactly when the dropped
+    // part is above half, or equal to it with the kept part odd
+    const uint32_t lo = (uint32_t)a, hi = (uint32_t)(a >> 32);
+    const unsigned long long b = a + (((1u << (r - 1)) - 1u) + ((__funnelshift_r(lo, hi, r)) & 1u));
+    mant = ((unsigned long long)((uint32_t)(b >> 32) >> r) << 32) |
+           __funnelshift_r((uint32_t)b, (uint32_t)(b >> 32), r);
+#else
     const unsigned long long q = a >> r, rem = a & ((1ull << r) - 1ull), half = 1ull << (r - 1);
     mant = q + (unsigned long long)((rem > half) | ((rem == half) & (q & 1ull)));
+#endif
   } else {
     mant = a << (52 - p);
   }

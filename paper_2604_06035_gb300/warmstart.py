@@ -143,11 +143,15 @@ def output_scale(data, trajs):
     return float(np.sqrt(acc / len(pairs)))
 
 
-def train(net, data, train_trajs, epochs=10, batch=4, lr=1e-3, seconds=None, seed=0, calibrate=True):
+def train(net, data, train_trajs, epochs=10, batch=4, lr=1e-3, seconds=None, seed=0, calibrate=True,
+          warmup_steps=200):
     """Adam on the mean squared error of delta with a cosine learning-rate
     decay over `epochs`, or over a wall-clock budget of `seconds` when given
-    (then as many epochs as fit); the output scale is set from the training
-    pairs first when calibrate.  Returns the per-epoch mean loss."""
+    (then as many epochs as fit), after a linear warm-up over the first
+    `warmup_steps` steps (full-size first steps could switch off whole ReLU
+    layers of the freshly initialised network, leaving it at a zero
+    prediction); the output scale is set from the training pairs first when
+    calibrate.  Returns the per-epoch mean loss."""
     rng = np.random.default_rng(seed)
     pairs = _pairs(data, train_trajs)
     if calibrate:
@@ -155,6 +159,8 @@ def train(net, data, train_trajs, epochs=10, batch=4, lr=1e-3, seconds=None, see
     losses = []
     t0 = time.perf_counter()
     steps_total = epochs * ((len(pairs) + batch - 1) // batch)
+    if seconds is None:
+        warmup_steps = min(warmup_steps, steps_total // 10)
     step = 0
     ep = 0
     while True:
@@ -170,7 +176,8 @@ def train(net, data, train_trajs, epochs=10, batch=4, lr=1e-3, seconds=None, see
             chunk = [pairs[j] for j in order[i:i + batch]]
             rho, r, prev, nxt = _batch(data, chunk)
             loss, _ = cmg.cmg_unet_gradients(net, rho, r, nxt, base=prev, grads=False)
-            cmg.cmg_unet_adam_step(net, lr * 0.5 * (1 + np.cos(np.pi * progress)))
+            warm = min(1.0, (step + 1) / warmup_steps) if warmup_steps > 0 else 1.0
+            cmg.cmg_unet_adam_step(net, lr * warm * 0.5 * (1 + np.cos(np.pi * progress)))
             step += 1
             acc += loss / len(chunk)
             nb += 1
