@@ -347,9 +347,12 @@ int cmg_batch_solve(cmg_batch *batch, const cmg_solve_params *params, cmg_batch_
  * NULL): relative residual, cycle at which the patch reached tol (-1 if it
  * did not), and ||f - L 0|| of the patch. */
 int cmg_batch_patch_stats(cmg_batch *batch, double *rel, int32_t *converged_at, double *norm0);
-/* Times candidate schedules (block shape x sweep schedule x inner cycles)
- * with full solves on the batch's current data, keeps the fastest and sets
- * it; phi of the level is restored afterwards.  best / best_ms may be NULL. */
+/* Times candidate schedules with full solves (with params' precision and
+ * krylov) on the batch's current data, keeps the fastest and sets it; phi of
+ * the level is restored afterwards.  Two stages: block shapes {256, 512
+ * threads} x {1, 2, 4 blocks per SM} (x {1, 2} inner cycles in MIXED) with
+ * V(2,2), then V(1,1), V(2,3), V(3,2), V(3,3) with the best shape.
+ * best / best_ms may be NULL. */
 int cmg_batch_autotune(cmg_batch *batch, const cmg_solve_params *params, cmg_batch_schedule *best,
                        double *best_ms);
 

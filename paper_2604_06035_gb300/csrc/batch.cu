@@ -923,40 +923,43 @@ void batch_autotune(cmg_batch *b, const cmg_solve_params *p, cmg_batch_schedule 
   double *saved = nullptr;
   CMG_CUDA(cudaMalloc(&saved, sizeof(double) * cnt));
   CMG_CUDA(cudaMemcpyAsync(saved, top.phi, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, s));
-  std::vector<cmg_batch_schedule> cands;
-  for (int th : {256, 512})
-    for (int bps : {1, 2, 4})
-      for (int sw : {1, 2})
-        for (int inner : {1, 2}) {
-          if (!mixed && inner == 2) continue;
-          cands.push_back({th, bps, sw, sw, inner});
-        }
+  // two stages: the block shape (and inner cycles) with V(2,2), then the
+  // sweep schedule with the best shape
   const cmg_batch_schedule keep = b->sched;
   double best_t = 1e300;
   cmg_batch_schedule best_s = keep;
-  try {
-    for (const auto &c : cands) {
-      b->sched = c;
-      int per_sm = 0;
-      const void *fn = batch_kernel(mixed, p->krylov == 1);
-      if (!block_fits(fn, c.threads)) continue;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, c.threads, 0) != cudaSuccess || per_sm < 1) {
-        cudaGetLastError();
-        continue;
-      }
-      if (c.blocks_per_sm > per_sm) continue;
-      double t = 0.0;
-      for (int rep = 0; rep < 2; ++rep) {  // first run records the graph
-        CMG_CUDA(cudaMemcpyAsync(top.phi, saved, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, s));
-        cmg_batch_stats st;
-        const int rc = batch_solve(b, p, &st);
-        t = (rc == CMG_OK || rc == CMG_ERR_NOT_CONVERGED) && st.n_converged == b->n_patches ? st.ms : 1e300;
-      }
-      if (t < best_t) {
-        best_t = t;
-        best_s = c;
-      }
+  auto time_candidate = [&](const cmg_batch_schedule &c) {
+    b->sched = c;
+    int per_sm = 0;
+    const void *fn = batch_kernel(mixed, p->krylov == 1);
+    if (!block_fits(fn, c.threads)) return;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, c.threads, 0) != cudaSuccess || per_sm < 1) {
+      cudaGetLastError();
+      return;
     }
+    if (c.blocks_per_sm > per_sm) return;
+    double t = 0.0;
+    for (int rep = 0; rep < 2; ++rep) {  // first run records the graph
+      CMG_CUDA(cudaMemcpyAsync(top.phi, saved, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, s));
+      cmg_batch_stats st;
+      const int rc = batch_solve(b, p, &st);
+      t = (rc == CMG_OK || rc == CMG_ERR_NOT_CONVERGED) && st.n_converged == b->n_patches ? st.ms : 1e300;
+    }
+    if (t < best_t) {
+      best_t = t;
+      best_s = c;
+    }
+  };
+  try {
+    for (int th : {256, 512})
+      for (int bps : {1, 2, 4})
+        for (int inner : {1, 2}) {
+          if (!mixed && inner == 2) continue;
+          time_candidate({th, bps, 2, 2, inner});
+        }
+    const cmg_batch_schedule shape = best_s;
+    const int sweeps[][2] = {{1, 1}, {2, 3}, {3, 2}, {3, 3}};
+    for (const auto &sw : sweeps) time_candidate({shape.threads, shape.blocks_per_sm, sw[0], sw[1], shape.inner_cycles});
   } catch (...) {
     b->sched = keep;
     cudaMemcpyAsync(top.phi, saved, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, s);
