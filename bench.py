@@ -786,7 +786,7 @@ def bench_learned(cmg, ctx, dev, args, peaks):
     res = {"grid": "%d^3 periodic" % D, "pairs_train": len(train_trajs) * n_steps,
            "pairs_test": len(test_trajs) * n_steps, "dataset_s": gen_s, "train_s": train_s,
            "epochs": len(losses), "loss_first_epoch": losses[0], "loss_last_epoch": losses[-1],
-           "output_scale": cmg.cmg_unet_get_output_scale(net)}
+           "output_scale": cmg.cmg_unet_get_output_scale(net), "grad_clip": cmg.cmg_unet_grad_clip_stats(net)}
     for name, prec in (("fp64", cmg.CMG_PREC_FP64), ("mixed", cmg.CMG_PREC_MIXED)):
         W.evaluate(ctx, net, data, test_trajs[:1], tol=args.tol, precision=prec)  # warm the graphs
         m, _ = W.evaluate(ctx, net, data, test_trajs, tol=args.tol, precision=prec)

@@ -406,6 +406,18 @@ int cmg_unet_gradients(cmg_unet *net, const float *rho, const float *field, cons
                        int batch, float *grads, double *loss, cmg_mem mem);
 /* One Adam step on the master parameters with the last gradients. */
 int cmg_unet_adam_step(cmg_unet *net, float lr, float beta1, float beta2, float eps);
+/* Gradient-norm clipping of the Adam steps (training robustness; no
+ * counterpart in the paper): with k >= 1 each step's gradient 2-norm is
+ * capped at k times the running mean (weight 0.05 per step) of the earlier
+ * steps' capped norms, once 20 steps have formed that mean; computed on the
+ * device inside cmg_unet_adam_step, without a host synchronisation.  k = 0
+ * switches it off (the default).  INVALID_ARG for 0 < k < 1.
+ * cmg_unet_set_params resets the running mean and the counters. */
+int cmg_unet_set_grad_clip(cmg_unet *net, float k);
+/* The clipping record (synchronises the stream): last step's gradient norm
+ * (before capping), the running mean, steps seen and steps capped; any
+ * pointer may be NULL. */
+int cmg_unet_grad_clip_stats(cmg_unet *net, double *last_norm, double *mean_norm, int64_t *steps, int64_t *clipped);
 /* Device copy between a dense [D][D][D] (z, y, x) FP64 field and the oct-major
  * [n][8] field of the full periodic level whose octs are listed x fastest
  * (to_octs = 1: dense -> octs; 0: octs -> dense).  Both device pointers. */

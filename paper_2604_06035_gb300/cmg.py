@@ -144,6 +144,8 @@ _SIGS = {
     "cmg_unet_forward": (_I, [_P, _P, _P, _P, _I, _P, _P, _I]),
     "cmg_unet_gradients": (_I, [_P, _P, _P, _P, _P, _I, _P, C.POINTER(C.c_double), _I]),
     "cmg_unet_adam_step": (_I, [_P, C.c_float, C.c_float, C.c_float, C.c_float]),
+    "cmg_unet_set_grad_clip": (_I, [_P, C.c_float]),
+    "cmg_unet_grad_clip_stats": (_I, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(_I64), C.POINTER(_I64)]),
     "cmg_dense_octs": (_I, [_P, _P, _I, _P, _I]),
 }
 
@@ -820,6 +822,19 @@ def cmg_unet_gradients(net, rho, field, target, base=None, grads=True):
 
 def cmg_unet_adam_step(net, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     _check(lib().cmg_unet_adam_step(net.h, lr, beta1, beta2, eps), "cmg_unet_adam_step")
+
+
+def cmg_unet_set_grad_clip(net, k):
+    """Cap each Adam step's gradient norm at k x its running mean (0: off)."""
+    _check(lib().cmg_unet_set_grad_clip(net.h, float(k)), "cmg_unet_set_grad_clip")
+
+
+def cmg_unet_grad_clip_stats(net):
+    last, mean = C.c_double(), C.c_double()
+    steps, clipped = C.c_int64(), C.c_int64()
+    _check(lib().cmg_unet_grad_clip_stats(net.h, C.byref(last), C.byref(mean), C.byref(steps), C.byref(clipped)),
+           "cmg_unet_grad_clip_stats")
+    return {"last_norm": last.value, "mean_norm": mean.value, "steps": steps.value, "clipped": clipped.value}
 
 
 def cmg_dense_octs(ctx, src, grid_dim, dst, to_octs):

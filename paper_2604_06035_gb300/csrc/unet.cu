@@ -431,11 +431,49 @@ __global__ void k_skip_grad(const bf16 *__restrict__ dcat, int Ca, int Cb, const
   }
 }
 
-// Adam on the FP32 master parameters.
+// Sum of squares of the gradient into clip[0] (block sums, one atomic each).
+__global__ void k_grad_sq(const float *__restrict__ g, int64_t n, double *__restrict__ clip) {
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += (double)g[i] * (double)g[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+  __shared__ double ws[32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    atomicAdd(clip, t);
+  }
+}
+
+// The clipping scale of this step: the gradient's 2-norm is capped at k times
+// the running mean of the earlier steps' (capped) norms, once 20 steps have
+// formed that mean; the mean then takes the capped norm.  Resets the sum.
+__global__ void k_clip_scale(double *clip, float k) {
+  const double norm = sqrt(clip[0]);
+  const double mean = clip[1], seen = clip[2];
+  double scale = 1.0, kept = norm;
+  if (seen >= 20.0 && norm > k * mean && norm > 0.0) {
+    scale = k * mean / norm;
+    kept = k * mean;
+    clip[4] += 1.0;
+  }
+  clip[1] = seen == 0.0 ? kept : 0.95 * mean + 0.05 * kept;
+  clip[2] = seen + 1.0;
+  clip[3] = scale;
+  clip[5] = norm;
+  clip[0] = 0.0;
+}
+
+// Adam on the FP32 master parameters; with clip, the gradient is scaled by
+// clip[3] first.
 __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
-                       float *__restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1, float c2) {
+                       float *__restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1, float c2,
+                       const double *__restrict__ clip) {
+  const float gs = clip ? (float)clip[3] : 1.f;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const float gi = g[i];
+    const float gi = g[i] * gs;
     const float mi = b1 * m[i] + (1.f - b1) * gi;
     const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
     m[i] = mi;
@@ -519,6 +557,12 @@ struct cmg_unet {
   // the prediction is base + out_scale * rms(field) * delta
   float out_scale = 1.f;
   int adam_t = 0;
+  // gradient-norm clipping (cmg_unet_set_grad_clip): clip_k = 0 off; clip on
+  // the device: [0] sum of squares of the step's gradient, [1] running mean
+  // of the (clipped) norm, [2] steps seen, [3] scale applied, [4] steps
+  // clipped, [5] last norm
+  float clip_k = 0.f;
+  double *clip = nullptr;
   bool weights_ready = false;
   cmg::DeviceBuffers mem;
 };
@@ -859,6 +903,7 @@ int cmg_unet_create(cmg_ctx *ctx, int grid_dim, int max_batch, cmg_unet **out) {
       U->grads = M.alloc<float>(U->np, true, s);
       U->m = M.alloc<float>(U->np, true, s);
       U->v = M.alloc<float>(U->np, true, s);
+      U->clip = M.alloc<double>(8, true, s);
       for (int l = 0; l < 10; ++l) {
         const int64_t n = (int64_t)kLayers[l].cout * 27 * kLayers[l].cin;
         U->W[l] = reinterpret_cast<__nv_bfloat16 *>(M.alloc<uint16_t>(n));
@@ -929,6 +974,7 @@ int cmg_unet_set_params(cmg_unet *U, const float *params, cmg_mem mem) {
     cudaStream_t s = U->ctx->stream;
     CMG_CUDA(cudaMemsetAsync(U->m, 0, sizeof(float) * U->np, s));
     CMG_CUDA(cudaMemsetAsync(U->v, 0, sizeof(float) * U->np, s));
+    CMG_CUDA(cudaMemsetAsync(U->clip, 0, sizeof(double) * 8, s));
     U->adam_t = 0;
     U->weights_ready = false;
     CMG_CUDA(cudaStreamSynchronize(s));
@@ -1021,10 +1067,38 @@ int cmg_unet_adam_step(cmg_unet *U, float lr, float beta1, float beta2, float ep
     cudaSetDevice(U->ctx->device);
     U->adam_t += 1;
     const float c1 = 1.f - std::pow(beta1, (float)U->adam_t), c2 = 1.f - std::pow(beta2, (float)U->adam_t);
+    const bool clip = U->clip_k > 0.f;
+    if (clip) {
+      cmg::k_grad_sq<<<cmg::gsz(U->np), 256, 0, U->ctx->stream>>>(U->grads, U->np, U->clip);
+      cmg::k_clip_scale<<<1, 1, 0, U->ctx->stream>>>(U->clip, U->clip_k);
+    }
     cmg::k_adam<<<cmg::gsz(U->np), 256, 0, U->ctx->stream>>>(U->params, U->grads, U->m, U->v, U->np, lr, beta1,
-                                                              beta2, eps, c1, c2);
+                                                              beta2, eps, c1, c2, clip ? U->clip : nullptr);
     CMG_CUDA(cudaGetLastError());
     U->weights_ready = false;
+    return (int)CMG_OK;
+  });
+}
+
+int cmg_unet_set_grad_clip(cmg_unet *U, float k) {
+  return unet_guard([&] {
+    if (!U || !(k == 0.f || k >= 1.f)) return (int)CMG_ERR_INVALID_ARG;
+    U->clip_k = k;
+    return (int)CMG_OK;
+  });
+}
+
+int cmg_unet_grad_clip_stats(cmg_unet *U, double *last_norm, double *mean_norm, int64_t *steps, int64_t *clipped) {
+  return unet_guard([&] {
+    if (!U) return (int)CMG_ERR_INVALID_ARG;
+    cudaSetDevice(U->ctx->device);
+    double h[8];
+    CMG_CUDA(cudaMemcpyAsync(h, U->clip, sizeof(h), cudaMemcpyDeviceToHost, U->ctx->stream));
+    CMG_CUDA(cudaStreamSynchronize(U->ctx->stream));
+    if (last_norm) *last_norm = h[5];
+    if (mean_norm) *mean_norm = h[1];
+    if (steps) *steps = (int64_t)h[2];
+    if (clipped) *clipped = (int64_t)h[4];
     return (int)CMG_OK;
   });
 }

@@ -144,18 +144,21 @@ def output_scale(data, trajs):
 
 
 def train(net, data, train_trajs, epochs=10, batch=4, lr=1e-3, seconds=None, seed=0, calibrate=True,
-          warmup_steps=200):
+          warmup_steps=200, clip=4.0):
     """Adam on the mean squared error of delta with a cosine learning-rate
     decay over `epochs`, or over a wall-clock budget of `seconds` when given
     (then as many epochs as fit), after a linear warm-up over the first
     `warmup_steps` steps (full-size first steps could switch off whole ReLU
     layers of the freshly initialised network, leaving it at a zero
-    prediction); the output scale is set from the training pairs first when
-    calibrate.  Returns the per-epoch mean loss."""
+    prediction); each step's gradient norm is capped at `clip` times its
+    running mean (0: no cap), since a single outsized step has left the
+    network at a zero prediction too; the output scale is set from the
+    training pairs first when calibrate.  Returns the per-epoch mean loss."""
     rng = np.random.default_rng(seed)
     pairs = _pairs(data, train_trajs)
     if calibrate:
         cmg.cmg_unet_set_output_scale(net, output_scale(data, train_trajs))
+    cmg.cmg_unet_set_grad_clip(net, clip)
     losses = []
     t0 = time.perf_counter()
     steps_total = epochs * ((len(pairs) + batch - 1) // batch)

@@ -198,6 +198,37 @@ def test_adam_step_decreases_loss(cmg, ctx):
     assert losses[-1] < 0.5 * losses[0]
 
 
+def test_grad_clip_caps_a_spike(cmg, ctx):
+    """With clipping on, a step whose gradient norm jumps far above the
+    running mean is capped (counted), the mean does not take the spike, and
+    the same steps without clipping leave the record untouched."""
+    D = 16
+    rho, phi, phin = _sample(D, 9)
+    net = cmg.cmg_unet_create(ctx, D, 1)
+    with pytest.raises(cmg.CmgError):
+        cmg.cmg_unet_set_grad_clip(net, 0.5)
+    for k in (0.0, 3.0):
+        cmg.cmg_unet_set_params(net, _params(8))
+        cmg.cmg_unet_set_grad_clip(net, k)
+        for _ in range(25):
+            cmg.cmg_unet_gradients(net, rho[None], phi[None], phin[None], grads=False)
+            cmg.cmg_unet_adam_step(net, 1e-4)
+        st = cmg.cmg_unet_grad_clip_stats(net)
+        if k == 0.0:
+            assert st["steps"] == 0 and st["clipped"] == 0
+            continue
+        assert st["steps"] == 25 and st["clipped"] == 0 and st["mean_norm"] > 0
+        mean = st["mean_norm"]
+        # a target 1000 times further away: a gradient norm far above the mean
+        far = (phi + 1000.0 * (phin - phi)).astype(np.float32)
+        cmg.cmg_unet_gradients(net, rho[None], phi[None], far[None], grads=False)
+        cmg.cmg_unet_adam_step(net, 1e-4)
+        st = cmg.cmg_unet_grad_clip_stats(net)
+        assert st["clipped"] == 1 and st["last_norm"] > 3.0 * mean
+        assert st["mean_norm"] <= 0.95 * mean + 0.05 * 3.0 * mean + 1e-12 * mean
+    cmg.cmg_unet_destroy(net)
+
+
 def test_dense_octs_roundtrip(cmg, ctx):
     import torch
     from paper_2604_06035_gb300 import inputs
