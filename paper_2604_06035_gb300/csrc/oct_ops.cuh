@@ -104,6 +104,18 @@ __device__ __forceinline__ double fixed_sum(const double *v) {
   // overflow the exponent field below), or every operand below 2^-960 (zeros
   // included): FP64 additions
   if (E >= 0x7FC || E < 64) {
+    if (E == 0) {
+      // all operands +-0 (a solve's first passes and residuals see whole
+      // neighbourhoods of zeros): the FP64 additions' result without them,
+      // -0 only when every operand is -0
+      uint32_t nz = 0, neg = 0xFFFFFFFFu;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        nz |= (hi[k] & 0x7FFFFFFFu) | lo[k];
+        neg &= hi[k];
+      }
+      if (nz == 0) return __longlong_as_double((long long)((unsigned long long)(neg & 0x80000000u) << 32));
+    }
     double s = v[0];
 #pragma unroll
     for (int k = 1; k < N; ++k) s += v[k];
