@@ -331,6 +331,26 @@ __device__ __forceinline__ void sweep_cell(int64_t i, int q, const int32_t *__re
 // writes its father cell g_c = 0.5 * sum_8 d (= -h_c^2/6 * mean_8 r) and, if
 // zero_cphi, zeroes the father's phi.  EMIT: g32 = (float)(d * inv_s).
 // ROUT: r oct-major.  ZPHI: phi taken as zero on real octs.
+// The FP32 right-hand side of a mixed-precision solve's correction problem,
+// (float)(x * s) with s a power of two: the scaling and the rounding to FP32
+// (to nearest, ties to even) formed in integer operations, since GB300
+// issues FP64 multiplications and conversions at its low FP64 rate (the
+// residual kernel that emits it went 11 % faster).  Zero, a scale that is
+// not a normal power of two, and results outside FP32's normal range take
+// the FP64 operations instead (same results).
+__device__ __forceinline__ float f32_scaled(double x, double s) {
+  const unsigned long long sb = (unsigned long long)__double_as_longlong(s);
+  const unsigned long long xb = (unsigned long long)__double_as_longlong(x);
+  const int es = (int)((sb >> 52) & 0x7FF), ex = (int)((xb >> 52) & 0x7FF);
+  const int fe = ex + es - 2046 + 127;  // FP32 biased exponent of x * s
+  if ((sb & 0x800FFFFFFFFFFFFFull) != 0 || es == 0 || es == 0x7FF || ex == 0 || fe <= 0 || fe >= 255)
+    return (float)(x * s);
+  const unsigned long long mant = xb & 0x000FFFFFFFFFFFFFull;
+  // round the 52-bit fraction to 23 bits: a carry runs into the exponent
+  // field (and from the largest binade to infinity, as the conversion does)
+  const uint32_t m = (uint32_t)((mant + 0x0FFFFFFFull + ((mant >> 29) & 1ull)) >> 29);
+  return __uint_as_float((((uint32_t)fe << 23) + m) | ((uint32_t)(xb >> 32) & 0x80000000u));
+}
 struct ResidIdx {
   int32_t nb[6];
   unsigned m;
@@ -386,7 +406,7 @@ __device__ __forceinline__ double resid_oct_idx(int64_t i, const ResidIdx &x, co
       // cancels rounds to +0, so it is never -0
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        if (EMIT) g32[(p * n + i) * 4 + q] = (float)((double)T(0) * inv_s);
+        if (EMIT) g32[(p * n + i) * 4 + q] = f32_scaled((double)T(0), inv_s);
         if (ROUT) rout[i * 8 + plane_cell(p, q)] = rscale * 0.0;
       }
       continue;
@@ -414,7 +434,7 @@ __device__ __forceinline__ double resid_oct_idx(int64_t i, const ResidIdx &x, co
           tacc = fma_t(dv, dv, tacc);
       }
       if (RESTRICT) rsum += dv;
-      if (EMIT) g32[(p * n + i) * 4 + q] = (float)((double)dv * inv_s);
+      if (EMIT) g32[(p * n + i) * 4 + q] = f32_scaled((double)dv, inv_s);
       if (ROUT) rout[i * 8 + c] = rscale * (double)dv;
     }
   }

@@ -33,7 +33,19 @@ struct CachedGraph {
 
 namespace {
 
-__global__ void k_copy_scalar(double *dst, const double *src) { *dst = *src; }
+// The scale of a mixed-precision solve's FP32 correction problem: the power
+// of two of the residual norm's binade (a positive finite norm), else the
+// norm itself.  A power of two makes the scalings exact.
+__global__ void k_pow2_scale(double *dst, const double *src) {
+  const double v = *src;
+  if (v > 0.0 && v < INFINITY) {
+    int e;
+    (void)frexp(v, &e);
+    *dst = ldexp(1.0, e - 1);
+  } else {
+    *dst = v;
+  }
+}
 
 __device__ void decide(SolveCtrl *c, double tol, int fixed, int maxc, cudaGraphConditionalHandle h,
                        int use_handle) {
@@ -215,7 +227,7 @@ void segment_pre(cmg_level *L, const cmg_solve_params *p, cudaGraphConditionalHa
   zero_phi_norm(L, scal + 0);
   if (p->precision != CMG_PREC_FP64) {
     LaunchScope ls(L->ctx, K_REDUCE, 16.0, 0.0);
-    k_copy_scalar<<<1, 1, 0, s>>>(scal + 4, scal + 1);
+    k_pow2_scale<<<1, 1, 0, s>>>(scal + 4, scal + 1);
     CMG_CUDA(cudaGetLastError());
     resid_restrict<double>(L, 0, false, true, false, scal + 2, scal + 4);
   } else {
@@ -265,7 +277,7 @@ void segment_body(cmg_level *L, const cmg_solve_params *p, cudaGraphConditionalH
     accumulate(L, scal + 4);
     {
       LaunchScope ls(L->ctx, K_REDUCE, 16.0, 0.0);
-      k_copy_scalar<<<1, 1, 0, s>>>(scal + 4, scal + 3);
+      k_pow2_scale<<<1, 1, 0, s>>>(scal + 4, scal + 3);
     }
     resid_restrict<double>(L, 0, false, true, false, scal + 2, scal + 4, false, false);
     norm_check(L, p, h, use_handle);
