@@ -201,3 +201,18 @@ def test_argument_checks(ctx):
     with pytest.raises(cmg.CmgError):
         cmg.cmg_debug_neighbour_sum(ctx, np.zeros((2, 6)), which=2)
     assert cmg.cmg_debug_neighbour_sum(ctx, np.zeros((0, 6))).shape == (0,)
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_signed_zeros_bit_for_bit(ctx, which):
+    """Rows of zeros of every sign pattern: the integer sums return at once
+    with the sign sequential FP64 additions give (-0 only when every summed
+    operand is -0), compared bit for bit."""
+    import itertools
+    rows = np.array([list(sg) for sg in itertools.product([0.0, -0.0], repeat=6)], dtype=np.float64)
+    got = _gpu(ctx, rows, which)
+    for r, g in zip(rows, got):
+        s = float(r[0])
+        for x in r[1:]:
+            s = s + float(x)  # sequential FP64 additions: the same value and sign here
+        assert _bits(g) == _bits(s), (list(r), g, s)
