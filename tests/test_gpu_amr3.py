@@ -112,3 +112,33 @@ def test_amr3_full_size_mixed_chain(cmg, ctx):
         R[-1].set_phi(phim[k])
         n2 = R[-1].residual(0, use_ghost=k > 0)
         assert np.sqrt(n2) <= 1.0001 * tol * norm0[k], k
+
+
+def test_amr3_full_size_fp64_fixed_cycles_match_oracle(cmg, ctx):
+    """The configuration the benchmark times, in FP64 and in the benchmark's
+    launch configuration (the table colour-pass kernel, the grid tail, the
+    per-operation launches of the large MG levels): two V-cycles per level
+    from phi = 0, each level with the oracle's phi of its parent on both
+    sides, every cell against the oracle (run on all host cores; its results
+    do not depend on the thread count) to 1e-12, and the same residual
+    history."""
+    import os
+    cfg = inputs.mixed_amr()
+    threads = O.get_threads()
+    O.set_threads(len(os.sched_getaffinity(0)))
+    try:
+        G, R = _build(cmg, ctx, cfg)
+        for k in range(len(G)):
+            if k > 0:
+                cmg.cmg_level_set_phi(G[k - 1], R[k - 1].get_phi())
+            z = np.zeros((R[k].n, 8))
+            cmg.cmg_level_set_phi(G[k], z)
+            R[k].set_phi(z)
+            rc, st = cmg.cmg_level_solve(G[k], fixed_cycles=2)
+            ro, so = R[k].solve(fixed_cycles=2)
+            assert relerr(cmg.cmg_level_get_phi(G[k]), R[k].get_phi()) <= RTOL64, k
+            np.testing.assert_allclose(st["rel_history"], so["rel_history"], rtol=1e-9)
+        for L in reversed(G):
+            cmg.cmg_level_destroy(L)
+    finally:
+        O.set_threads(threads)
