@@ -211,3 +211,41 @@ def test_batch_autotune(cmg, setup):
     rc, st = cmg.cmg_batch_solve(B, tol=1e-10, precision=cmg.CMG_PREC_MIXED)
     assert rc == cmg.CMG_OK and st["n_converged"] == 12
     cmg.cmg_batch_set_schedule(B, threads=256, blocks_per_sm=2, n_pre=2, n_post=2, inner_cycles=1)
+
+
+def test_full_batch_sampled_patches_match_oracle(cmg, ctx):
+    """The benchmark's batch (512 patches, 14.7 M octs) in the launch shape
+    its FP64 autotuning picks (512 threads, one block per SM, V(2,3)): two
+    FP64 V-cycles of the whole batch, then 13 patches sampled across the size
+    range, each against the oracle solving that patch alone with the same
+    schedule and coarse_sweeps = n_pre + n_post = 5 (1e-12)."""
+    import os
+    b = inputs.batched_patches(n_patches=512, seed=4)
+    lev = b["level"]
+    P = cmg.cmg_level_build(ctx, lev - 1, cmg.cmg_morton_encode(ctx, b["parent_coords"]))
+    cmg.cmg_level_set_phi(P, b["parent_phi"])
+    F = cmg.cmg_level_build(ctx, lev, cmg.cmg_morton_encode(ctx, b["coords"]), parent=P)
+    cmg.cmg_level_set_density(F, b["rho"], 1.0)
+    B = cmg.cmg_batch_create(F, b["offsets"])
+    cmg.cmg_batch_set_schedule(B, threads=512, blocks_per_sm=1, n_pre=2, n_post=3, inner_cycles=1)
+    cmg.cmg_level_set_phi(F, np.zeros((len(b["coords"]), 8)))
+    rc, st = cmg.cmg_batch_solve(B, tol=1e-10, fixed_cycles=2)
+    assert rc == cmg.CMG_OK and st["cycles"] == 2
+    phi = cmg.cmg_level_get_phi(F)
+    cmg.cmg_batch_destroy(B)
+    cmg.cmg_level_destroy(F)
+    cmg.cmg_level_destroy(P)
+    sizes = np.diff(b["offsets"])
+    order = np.argsort(sizes)
+    sample = order[np.linspace(0, len(order) - 1, 13).round().astype(int)]
+    threads = O.get_threads()
+    O.set_threads(len(os.sched_getaffinity(0)))
+    try:
+        RP = O.Level(lev - 1, O.morton_encode(b["parent_coords"]))
+        RP.set_phi(b["parent_phi"])
+        for k in sample:
+            R, sl = _oracle_patch(b, RP, int(k))
+            R.solve(tol=1e-10, fixed_cycles=2, n_pre=2, n_post=3, coarse_sweeps=5)
+            assert _relerr(phi[sl], R.get_phi()) <= 1e-12, (int(k), int(sizes[k]))
+    finally:
+        O.set_threads(threads)
